@@ -1,0 +1,202 @@
+/*
+ * efe.h -- C ABI of the GB300 (sm_103a) enriched finite-element ChFSI library.
+ *
+ * The library discretises the Kohn-Sham eigenproblem in the enriched finite
+ * element basis of Kanungo & Gavini (arXiv:1610.02121): degree-4 spectral
+ * (GLL) hexahedral elements (Sec. III) augmented by compactly supported,
+ * atom-centred enrichment functions (Sec. IV.A-B), with an adaptive quadrature
+ * on enriched cells (Sec. IV.C), and solves it by Chebyshev-filtered subspace
+ * iteration (Sec. V) using the block-wise overlap inverse (Sec. IV.D).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Ownership: the caller owns every buffer passed in; the library owns only the
+ *   opaque handle, its operator storage and its workspace (device memory it
+ *   allocates with cudaMalloc in efe_create / efe_set_potential* / efe_reserve,
+ *   released by efe_destroy).
+ * Device: every call runs on the CUDA device that is current when efe_create is
+ *   called.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream); all device work of a call is ordered on that stream.  Calls that
+ *   return host values (eigenvalues, bounds) synchronise that stream.
+ * Block layout ("X layout"): a block of N vectors is a row-major FP64 device
+ *   array with n_nodes + n_enrich rows and leading dimension ld >= N
+ *   (elements).  Rows 0 .. n_nodes-1 are the classical coefficients at the
+ *   nodes of the tensor-product GLL node grid, node index
+ *   ix + NX*(iy + NY*iz) (x fastest), boundary nodes included: the box faces
+ *   carry homogeneous Dirichlet conditions (Sec. III.A), so boundary rows must
+ *   be zero on input and are zero on output.  Rows n_nodes .. n_nodes+n_enrich-1
+ *   are the enrichment coefficients psi^E_alpha (Eq. EFEMPsi), in the order of
+ *   efe_basis_desc.
+ * Errors: every function returns EFE_OK (0) or a positive EFE_ERR_* code and
+ *   never aborts, traps or throws; efe_last_error() gives a message for the
+ *   last failing call on a handle.  Bounded device waits return
+ *   EFE_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef EFE_H
+#define EFE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EFE_OK 0
+#define EFE_ERR_ARG 1      /* invalid argument or unsupported size */
+#define EFE_ERR_CUDA 2     /* a CUDA runtime call failed */
+#define EFE_ERR_CHOL 3     /* Cholesky breakdown (Gram matrix, S, or projected overlap) */
+#define EFE_ERR_NOCONV 4   /* an iteration did not converge */
+#define EFE_ERR_TIMEOUT 5  /* a bounded device wait ran out */
+#define EFE_ERR_NAN 6      /* non-finite value in an input or a result */
+#define EFE_ERR_ALLOC 7    /* device or host allocation failed */
+#define EFE_ERR_STATE 8    /* call out of order (e.g. no potential set) */
+
+/* precision modes of efe_chfsi_step (spec mixed-precision filter) */
+#define EFE_PREC_FP64 0    /* every product in FP64 */
+#define EFE_PREC_FP32 1    /* classical block in FP32, cell GEMMs FP32 (SIMT FFMA), FP32 accumulate */
+#define EFE_PREC_TF32 2    /* classical block in FP32, cell GEMMs on tcgen05 kind::tf32, FP32 accumulate */
+#define EFE_PREC_BF16 3    /* classical block in BF16, cell GEMMs on tcgen05 kind::f16 (bf16), FP32 accumulate */
+
+typedef struct efe_handle efe_handle;
+
+/* Tensor-product mesh of axis-aligned hexahedral cells (Sec. III.A, III.B). */
+typedef struct {
+  int32_t degree;            /* FE polynomial degree p; this build supports p = 4 only (HEX125SPEC) */
+  int32_t n_cells[3];        /* cells per axis, each >= 1 */
+  const double* breaks[3];   /* host; n_cells[d] + 1 strictly increasing break points (bohr) */
+  int32_t n_gauss;           /* Gauss points per axis in non-enriched cells (1..10) */
+} efe_mesh_desc;
+
+/* Nuclei (Eq. vext). */
+typedef struct {
+  int32_t n_atoms;
+  const double* xyz;         /* host, 3 * n_atoms, bohr */
+  const double* Z;           /* host, n_atoms nuclear charges */
+} efe_atoms_desc;
+
+/* Orbital enrichment functions N_alpha = R_nl(r) h(r~) Y_lm (Eqs. KSOrbitalSplit,
+ * EnrichedPsi, Moll1) and the adaptive rule of Sec. IV.C. */
+typedef struct {
+  int32_t n_funcs;           /* n_E (may be 0: classical basis only) */
+  const int32_t* atom;       /* host arrays of length n_funcs */
+  const int32_t* n;          /* principal quantum number (1 or 2) */
+  const int32_t* l;          /* 0 or 1 */
+  const int32_t* m;          /* -l..l; real Y_1m = sqrt(3/4pi) (y, z, x)/r for m = -1, 0, 1 */
+  const int32_t* kind;       /* 0: hydrogenic radial of the atom's Z; 1: Slater radial with zeta */
+  const double* zeta;        /* Slater exponent (kind 1) */
+  const double* r0;          /* cutoff start r0 (bohr) */
+  const double* t;           /* cutoff width parameter t; support radius r0 + r0/t */
+  double quad_tau;           /* absolute tolerance of the adaptive rule */
+  int32_t quad_max_depth;    /* cap on box bisections */
+  int32_t quad_n;            /* Gauss points per axis in each adaptive box */
+} efe_basis_desc;
+
+/* Analytic local potential V(x) = -sum_I Z_I/|x - R_I| (if nuclear)
+ *   + sum_g A_g exp(-|x - c_g|^2 / (2 s_g^2)) + omega^2 |x|^2 / 2. */
+typedef struct {
+  int32_t nuclear;
+  int32_t n_terms;
+  const double* A;           /* host, n_terms */
+  const double* s;           /* host, n_terms */
+  const double* c;           /* host, 3 * n_terms */
+  double omega;
+} efe_potential_desc;
+
+/* Build the mesh, quadrature (Gauss; adaptive on cells that meet an enrichment
+ * support, Sec. IV.C), the diagonal GLL overlap D (Sec. III.B), the overlap
+ * blocks M^ec, M^ee and the kinetic parts of H^ec, H^ee (Eqs. Hec, Hee, Mec,
+ * Mee), the Schur complement S = M^ee - M^ec D^-1 M^ec^T and S^-1 by Cholesky
+ * (Sec. IV.D), and upload them to the current device.  Descriptors are read
+ * during the call only.  Returns EFE_ERR_CHOL if S is not positive definite. */
+int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms,
+               const efe_basis_desc* basis, efe_handle** out);
+
+/* Release all device and host memory of the handle (NULL is accepted). */
+int efe_destroy(efe_handle* h);
+
+/* Message of the last failing call on h (static string if h is NULL). */
+const char* efe_last_error(const efe_handle* h);
+
+/* Sizes: grid nodes (incl. boundary), enrichment functions, quadrature points,
+ * cells, and nonzeros of the enrichment-classical coupling M^ec (function-node
+ * pairs).  Any output pointer may be NULL. */
+int efe_sizes(const efe_handle* h, int64_t* n_nodes, int64_t* n_enrich,
+              int64_t* n_qpoints, int64_t* n_cells, int64_t* n_coupling);
+
+/* Copy the quadrature points to xyzw_dev (device, 4 doubles per point: x, y, z,
+ * weight), ordered cell by cell (cell index i + nx*(j + ny*k)). */
+int efe_qpoints(efe_handle* h, double* xyzw_dev, void* stream);
+
+/* Set the effective potential from its values at the quadrature points
+ * (device, n_qpoints doubles, efe_qpoints order) and rebuild, on the device,
+ * every V-dependent block: per-cell H^cc_e (Eq. Hcc), H^ec (Eq. Hec) and
+ * H^ee (Eq. Hee), plus the FP32/BF16 copies of H^cc_e used by the mixed
+ * modes.  Returns EFE_ERR_NAN if V holds a non-finite value. */
+int efe_set_potential(efe_handle* h, const double* V_qpts_dev, void* stream);
+
+/* Evaluate the analytic potential of `pot` at the quadrature points on the
+ * device, then proceed as efe_set_potential. */
+int efe_set_potential_analytic(efe_handle* h, const efe_potential_desc* pot, void* stream);
+
+/* Allocate workspace for blocks of up to N vectors (optional; the block calls
+ * below reserve on first use). */
+int efe_reserve(efe_handle* h, int32_t N);
+
+/* Y = H^E X (Eq. H2x2): matrix-free cell products of H^cc plus the
+ * enrichment coupling, boundary rows zeroed.  X, Y in X layout (FP64 device). */
+int efe_apply_H(efe_handle* h, const double* X, int64_t ldx, int32_t N,
+                double* Y, int64_t ldy, void* stream);
+
+/* Y = M^E X (Eq. M2x2) with the GLL-diagonal M^cc. */
+int efe_apply_M(efe_handle* h, const double* X, int64_t ldx, int32_t N,
+                double* Y, int64_t ldy, void* stream);
+
+/* Y = (M^E)^-1 X by the block-wise (Banachiewicz) formula of Sec. IV.D,
+ * applied matrix-free: x_e = S^-1 (W_e - M^ec D^-1 W_c), x_c = D^-1 (W_c - M^ec^T x_e). */
+int efe_apply_Minv(efe_handle* h, const double* X, int64_t ldx, int32_t N,
+                   double* Y, int64_t ldy, void* stream);
+
+/* Upper bound b of the spectrum of H~ = (M^E)^-1 H^E (Sec. V, "a few Arnoldi
+ * iterations"): k Lanczos steps in the M-inner product from the device start
+ * vector v0 (X layout, one column), b = largest Ritz value + |beta_k|.
+ * Synchronises `stream`; writes *b_out on the host. */
+int efe_upper_bound(efe_handle* h, const double* v0, int32_t k, double* b_out, void* stream);
+
+/* Chebyshev filter of Sec. V in place: X <- T_m(t(H~)) X / T_m(t(a0)), with
+ * t(x) = (2x - a - b)/(b - a) and the three-term recurrence in its scaled
+ * form.  a: upper end of the wanted spectrum (largest Ritz value), b: upper
+ * bound of the spectrum, a0 < a: lower bound used for scaling.  precision is
+ * an EFE_PREC_* mode; the last `fp64_tail` degrees always run in FP64.
+ * X in X layout (FP64 device), N >= 1, m >= 1. */
+int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m,
+                   double a, double b, double a0, int32_t precision, int32_t fp64_tail,
+                   void* stream);
+
+/* Cholesky-QR (G = X^T X = R^T R, Q = X R^-1) and Rayleigh-Ritz
+ * (Q^T H Q Psi = eps Q^T M Q Psi, Sec. V) in FP64 on the device; X <- Q Psi
+ * (M-orthonormal Ritz vectors, ascending eps).  eig_host / resid_host (host,
+ * N doubles each; resid_host may be NULL) receive the Ritz values and
+ * ||H x_i - eps_i M x_i||_2.  Returns EFE_ERR_CHOL if G or Q^T M Q is not
+ * positive definite, EFE_ERR_NOCONV if the dense eigensolver does not
+ * converge.  Synchronises `stream`. */
+int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N,
+                      double* eig_host, double* resid_host, void* stream);
+
+/* Kernel timing: when enabled, the library brackets every launch of its
+ * classical cell-apply kernel (any precision) with CUDA events on the
+ * launching stream.  efe_kernel_stats synchronises the device, then returns
+ * the number of launches, their summed duration (ms) and the number of cell
+ * products they performed (cells x N-column blocks counted as cells * N), and
+ * optionally resets the counters. */
+int efe_enable_timing(efe_handle* h, int32_t enable);
+int efe_kernel_stats(efe_handle* h, int64_t* launches, double* total_ms, int64_t* cell_columns,
+                     int32_t reset);
+
+/* Number of CUDA kernels this library has launched since it was loaded (all
+ * handles, all threads); a diagnostic counter for benchmarks. */
+int efe_launch_count(int64_t* total);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EFE_H */

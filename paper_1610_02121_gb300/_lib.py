@@ -1,0 +1,275 @@
+"""ctypes binding of the C ABI in include/efe.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA library ``libefe.so``; this
+module only converts Python/NumPy descriptions into the C descriptors and
+passes device pointers of torch tensors plus the current CUDA stream.  There
+is no fallback: if the library is missing, importing this module raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libefe.so")
+
+EFE_OK = 0
+ERRORS = {1: "EFE_ERR_ARG", 2: "EFE_ERR_CUDA", 3: "EFE_ERR_CHOL", 4: "EFE_ERR_NOCONV",
+          5: "EFE_ERR_TIMEOUT", 6: "EFE_ERR_NAN", 7: "EFE_ERR_ALLOC", 8: "EFE_ERR_STATE"}
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+
+# the symbols declared in include/efe.h
+SYMBOLS = ["efe_create", "efe_destroy", "efe_last_error", "efe_sizes", "efe_qpoints", "efe_set_potential",
+           "efe_set_potential_analytic", "efe_reserve", "efe_apply_H", "efe_apply_M", "efe_apply_Minv",
+           "efe_upper_bound", "efe_chfsi_step", "efe_rayleigh_ritz", "efe_enable_timing", "efe_kernel_stats",
+           "efe_launch_count"]
+
+
+class EfeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("degree", C.c_int32), ("n_cells", C.c_int32 * 3), ("breaks", C.POINTER(C.c_double) * 3),
+                ("n_gauss", C.c_int32)]
+
+
+class AtomsDesc(C.Structure):
+    _fields_ = [("n_atoms", C.c_int32), ("xyz", C.POINTER(C.c_double)), ("Z", C.POINTER(C.c_double))]
+
+
+class BasisDesc(C.Structure):
+    _fields_ = [("n_funcs", C.c_int32), ("atom", C.POINTER(C.c_int32)), ("n", C.POINTER(C.c_int32)),
+                ("l", C.POINTER(C.c_int32)), ("m", C.POINTER(C.c_int32)), ("kind", C.POINTER(C.c_int32)),
+                ("zeta", C.POINTER(C.c_double)), ("r0", C.POINTER(C.c_double)), ("t", C.POINTER(C.c_double)),
+                ("quad_tau", C.c_double), ("quad_max_depth", C.c_int32), ("quad_n", C.c_int32)]
+
+
+class PotentialDesc(C.Structure):
+    _fields_ = [("nuclear", C.c_int32), ("n_terms", C.c_int32), ("A", C.POINTER(C.c_double)),
+                ("s", C.POINTER(C.c_double)), ("c", C.POINTER(C.c_double)), ("omega", C.c_double)]
+
+
+def load(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library {path} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    P64 = C.POINTER(C.c_int64)
+    PD = C.POINTER(C.c_double)
+    sig = {
+        "efe_create": [C.POINTER(MeshDesc), C.POINTER(AtomsDesc), C.POINTER(BasisDesc), C.POINTER(vp)],
+        "efe_destroy": [vp],
+        "efe_last_error": [vp],
+        "efe_sizes": [vp, P64, P64, P64, P64, P64],
+        "efe_qpoints": [vp, vp, vp],
+        "efe_set_potential": [vp, vp, vp],
+        "efe_set_potential_analytic": [vp, C.POINTER(PotentialDesc), vp],
+        "efe_reserve": [vp, i32],
+        "efe_apply_H": [vp, vp, i64, i32, vp, i64, vp],
+        "efe_apply_M": [vp, vp, i64, i32, vp, i64, vp],
+        "efe_apply_Minv": [vp, vp, i64, i32, vp, i64, vp],
+        "efe_upper_bound": [vp, vp, i32, PD, vp],
+        "efe_chfsi_step": [vp, vp, i64, i32, i32, dbl, dbl, dbl, i32, i32, vp],
+        "efe_rayleigh_ritz": [vp, vp, i64, i32, PD, PD, vp],
+        "efe_enable_timing": [vp, i32],
+        "efe_kernel_stats": [vp, P64, PD, P64, i32],
+        "efe_launch_count": [P64],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_char_p if name == "efe_last_error" else C.c_int
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load()
+    return _LIB
+
+
+def launch_count():
+    n = C.c_int64()
+    lib().efe_launch_count(C.byref(n))
+    return n.value
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+class System:
+    """One enriched-FE discretisation living on the current CUDA device."""
+
+    def __init__(self, system):
+        import torch  # device memory and streams only
+        self._torch = torch
+        self.L = lib()
+        self.system = system
+        self._keep = []
+        md = MeshDesc()
+        md.degree = system["p"]
+        for d in range(3):
+            b = np.ascontiguousarray(system["breaks"][d], dtype=np.float64)
+            self._keep.append(b)
+            md.n_cells[d] = len(b) - 1
+            md.breaks[d] = _dptr(b)
+        md.n_gauss = system["n_gauss"]
+        ad = AtomsDesc()
+        xyz = np.ascontiguousarray(system["atoms"], dtype=np.float64).reshape(-1)
+        Z = np.ascontiguousarray(system["Z"], dtype=np.float64)
+        self._keep += [xyz, Z]
+        ad.n_atoms = len(Z)
+        ad.xyz = _dptr(xyz)
+        ad.Z = _dptr(Z)
+        bd = BasisDesc()
+        f = system["funcs"]
+        cols = {
+            "atom": np.array([x["atom"] for x in f], dtype=np.int32),
+            "n": np.array([x["n"] for x in f], dtype=np.int32),
+            "l": np.array([x["l"] for x in f], dtype=np.int32),
+            "m": np.array([x["m"] for x in f], dtype=np.int32),
+            "kind": np.array([0 if x["kind"] == "hydrogenic" else 1 for x in f], dtype=np.int32),
+        }
+        dcols = {k: np.array([x[k] for x in f], dtype=np.float64) for k in ("zeta", "r0", "t")}
+        self._keep += list(cols.values()) + list(dcols.values())
+        bd.n_funcs = len(f)
+        for k, v in cols.items():
+            setattr(bd, k, _iptr(v))
+        for k, v in dcols.items():
+            setattr(bd, k, _dptr(v))
+        q = system["quad"]
+        bd.quad_tau = q["tau"]
+        bd.quad_max_depth = q["max_depth"]
+        bd.quad_n = q["n"]
+        h = C.c_void_p()
+        rc = self.L.efe_create(C.byref(md), C.byref(ad), C.byref(bd), C.byref(h))
+        self.h = h
+        if rc != EFE_OK:
+            msg = self.L.efe_last_error(h).decode() if h.value else "efe_create failed"
+            self.close()
+            raise EfeError(rc, msg)
+        n = [C.c_int64() for _ in range(5)]
+        self._check(self.L.efe_sizes(h, *[C.byref(x) for x in n]))
+        self.n_nodes, self.n_enrich, self.n_qpoints, self.n_cells, self.n_coupling = [x.value for x in n]
+        self.rows = self.n_nodes + self.n_enrich
+
+    # -- plumbing ------------------------------------------------------------
+    def _check(self, rc):
+        if rc != EFE_OK:
+            raise EfeError(rc, self.L.efe_last_error(self.h).decode())
+
+    def _stream(self):
+        return C.c_void_p(self._torch.cuda.current_stream().cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.efe_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _block(X):
+        assert X.is_cuda and X.dtype.is_floating_point and X.dim() == 2 and X.stride(1) == 1
+        return C.c_void_p(X.data_ptr()), X.stride(0), X.shape[1]
+
+    # -- API -------------------------------------------------------------------
+    def qpoints(self):
+        t = self._torch.empty((self.n_qpoints, 4), dtype=self._torch.float64, device="cuda")
+        self._check(self.L.efe_qpoints(self.h, C.c_void_p(t.data_ptr()), self._stream()))
+        return t
+
+    def set_potential(self, V):
+        assert V.is_cuda and V.dtype == self._torch.float64 and V.numel() == self.n_qpoints
+        self._check(self.L.efe_set_potential(self.h, C.c_void_p(V.data_ptr()), self._stream()))
+
+    def set_potential_analytic(self, pot=None):
+        pot = pot if pot is not None else self.system["potential"]
+        A = np.ascontiguousarray(pot["gauss_A"], dtype=np.float64)
+        s = np.ascontiguousarray(pot["gauss_s"], dtype=np.float64)
+        c = np.ascontiguousarray(pot["gauss_c"], dtype=np.float64).reshape(-1)
+        pd = PotentialDesc(int(bool(pot["nuclear"])), len(A), _dptr(A), _dptr(s), _dptr(c), float(pot["omega"]))
+        self._check(self.L.efe_set_potential_analytic(self.h, C.byref(pd), self._stream()))
+
+    def reserve(self, N):
+        self._check(self.L.efe_reserve(self.h, int(N)))
+
+    def _apply(self, fn, X, Y=None):
+        px, ldx, N = self._block(X)
+        if Y is None:
+            Y = self._torch.empty_like(X)
+        py, ldy, _ = self._block(Y)
+        self._check(fn(self.h, px, ldx, N, py, ldy, self._stream()))
+        return Y
+
+    def apply_H(self, X, Y=None):
+        return self._apply(self.L.efe_apply_H, X, Y)
+
+    def apply_M(self, X, Y=None):
+        return self._apply(self.L.efe_apply_M, X, Y)
+
+    def apply_Minv(self, X, Y=None):
+        return self._apply(self.L.efe_apply_Minv, X, Y)
+
+    def upper_bound(self, v0, k=10):
+        b = C.c_double()
+        self._check(self.L.efe_upper_bound(self.h, C.c_void_p(v0.data_ptr()), int(k), C.byref(b), self._stream()))
+        return b.value
+
+    def chfsi_step(self, X, m, a, b, a0, precision="fp64", fp64_tail=0):
+        px, ldx, N = self._block(X)
+        self._check(self.L.efe_chfsi_step(self.h, px, ldx, N, int(m), float(a), float(b), float(a0),
+                                          PREC[precision], int(fp64_tail), self._stream()))
+        return X
+
+    def rayleigh_ritz(self, X):
+        px, ldx, N = self._block(X)
+        eig = np.zeros(N)
+        res = np.zeros(N)
+        self._check(self.L.efe_rayleigh_ritz(self.h, px, ldx, N, _dptr(eig), _dptr(res), self._stream()))
+        return eig, res
+
+    def solve(self, X, m, tol=1e-8, max_iter=200, precision="fp64", fp64_tail=0, v0=None, n_conv=None,
+              k_lanczos=10):
+        """ChFSI for the current potential (Sec. V): Rayleigh-Ritz on X for a and
+        a0, a Lanczos bound b, then filter -> Cholesky-QR + Rayleigh-Ritz until the
+        residuals of the lowest ``n_conv`` Ritz pairs are below ``tol``.  Loop
+        control only; every step is a library call."""
+        eps, res = self.rayleigh_ritz(X)
+        if v0 is None:
+            v0 = X[:, -1].contiguous()
+        b = self.upper_bound(v0, k_lanczos)
+        it = 0
+        for it in range(1, max_iter + 1):
+            self.chfsi_step(X, m, eps.max(), b, eps.min(), precision=precision, fp64_tail=fp64_tail)
+            eps, res = self.rayleigh_ritz(X)
+            if res[:n_conv].max() < tol:
+                break
+        return eps, res, it, b
+
+    def enable_timing(self, on=True):
+        self._check(self.L.efe_enable_timing(self.h, int(bool(on))))
+
+    def kernel_stats(self, reset=True):
+        n = C.c_int64()
+        ms = C.c_double()
+        cc = C.c_int64()
+        self._check(self.L.efe_kernel_stats(self.h, C.byref(n), C.byref(ms), C.byref(cc), int(bool(reset))))
+        return n.value, ms.value, cc.value

@@ -1,0 +1,922 @@
+// C ABI of the enriched finite-element ChFSI library: handle, device storage,
+// and the orchestration of the filter (Sec. V), the block-wise overlap
+// inverse (Sec. IV.D), Cholesky-QR and Rayleigh-Ritz.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "efe_internal.h"
+#include "efe_kernels.h"
+
+using namespace efe;
+
+namespace {
+
+constexpr int64_t SEG = 2048;  // nnz per segment of a long enrichment row
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  int64_t n = 0;
+};
+
+}  // namespace
+
+struct efe_handle {
+  int dev = 0;
+  std::string err;
+  RefElem re;
+  MeshDev mesh;
+  int64_t n_nodes = 0, n_cell = 0, nE = 0, nq = 0, n_enr = 0, rows = 0;
+  int kmax = 0;
+  bool potential_set = false;
+  // device storage (all cudaMalloc'd, freed in efe_destroy)
+  std::vector<void*> allocs;
+  double* brk = nullptr;
+  int n_atoms = 0;
+  double *axyz = nullptr, *aZ = nullptr;
+  double* qpts = nullptr;
+  int64_t* qoff = nullptr;
+  double* V = nullptr;
+  int32_t* colour_cells = nullptr;
+  int64_t colour_off[9] = {0};
+  double *D = nullptr, *Dinv = nullptr, *mask = nullptr, *Dm = nullptr;
+  double* Hcc = nullptr;
+  float* Hcc32 = nullptr;
+  void* Hcc16 = nullptr;
+  DevFunc* funcs = nullptr;
+  int32_t *enr_cells = nullptr, *cf_ptr = nullptr, *cf_idx = nullptr;
+  int64_t *blkP_off = nullptr, *blkQ_off = nullptr;
+  int64_t nP = 0, nQ = 0;
+  double *Pblk = nullptr, *Qblk = nullptr;
+  int64_t nnz = 0;
+  int32_t* ec_col = nullptr;
+  double *mec = nullptr, *hec_kin = nullptr, *hec = nullptr;
+  int64_t *ec_cptr = nullptr, *ec_cidx = nullptr;
+  int64_t nseg = 0;
+  int64_t *seg_start = nullptr, *seg_end = nullptr, *row_seg_ptr = nullptr;
+  int64_t n_tn = 0;
+  int32_t* t_nodes = nullptr;
+  int64_t* t_ptr = nullptr;
+  int32_t* t_col = nullptr;
+  int64_t* t_perm = nullptr;
+  double *mecT = nullptr, *hecT = nullptr;
+  double *Mee = nullptr, *Hee_kin = nullptr, *Hee = nullptr, *Sinv = nullptr;
+  int64_t *ee_cptr = nullptr, *ee_cidx = nullptr;
+  int* info = nullptr;        // 8 ints
+  // workspace
+  int Nres = 0;
+  double *B1 = nullptr, *B2 = nullptr, *W = nullptr, *xe = nullptr, *rb = nullptr, *part = nullptr;
+  double* small = nullptr;    // 16 N x N blocks + vectors
+  double* tnwork = nullptr;
+  int64_t tnwork_elems = 0;
+  double* rpart = nullptr;
+  double* lz = nullptr;       // Lanczos vectors (6 * rows) + scalars
+  int Nres32 = 0;
+  float *Yf[3] = {nullptr, nullptr, nullptr}, *Wf = nullptr;
+  double* Ye[3] = {nullptr, nullptr, nullptr};
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_pairs;
+  int64_t t_launches = 0, t_cellcols = 0;
+  double t_ms = 0.0;
+  int64_t pend_cellcols = 0;
+};
+
+namespace {
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t _e = (call);                                                       \
+    if (_e != cudaSuccess) {                                                       \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(_e);                 \
+      return EFE_ERR_CUDA;                                                         \
+    }                                                                              \
+  } while (0)
+
+#define CKL()                                                                      \
+  do {                                                                             \
+    cudaError_t _e = cudaGetLastError();                                           \
+    if (_e != cudaSuccess) {                                                       \
+      h->err = std::string("kernel launch: ") + cudaGetErrorString(_e);            \
+      return EFE_ERR_CUDA;                                                         \
+    }                                                                              \
+  } while (0)
+
+#define TRY(x)                 \
+  do {                         \
+    int _r = (x);              \
+    if (_r != EFE_OK) return _r; \
+  } while (0)
+
+template <typename T>
+int dalloc(efe_handle* h, T** p, int64_t n) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(T) * (size_t)n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return EFE_ERR_ALLOC;
+  }
+  h->allocs.push_back(q);
+  *p = (T*)q;
+  return EFE_OK;
+}
+
+template <typename T>
+int upload(efe_handle* h, T** p, const std::vector<T>& v) {
+  TRY(dalloc(h, p, (int64_t)v.size()));
+  if (!v.empty()) CK(cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return EFE_OK;
+}
+
+void dfree(efe_handle* h, void* p) {
+  if (!p) return;
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it != h->allocs.end()) h->allocs.erase(it);
+  cudaFree(p);
+}
+
+int set_dev(efe_handle* h) {
+  CK(cudaSetDevice(h->dev));
+  return EFE_OK;
+}
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+int reserve(efe_handle* h, int N) {
+  if (N <= h->Nres) return EFE_OK;
+  for (void* p : {(void*)h->B1, (void*)h->B2, (void*)h->W, (void*)h->xe, (void*)h->rb, (void*)h->part,
+                  (void*)h->small, (void*)h->tnwork, (void*)h->rpart})
+    dfree(h, p);
+  const int64_t R = h->rows;
+  TRY(dalloc(h, &h->B1, R * N));
+  TRY(dalloc(h, &h->B2, R * N));
+  TRY(dalloc(h, &h->W, R * N));
+  TRY(dalloc(h, &h->xe, std::max<int64_t>(1, h->nE) * N));
+  TRY(dalloc(h, &h->rb, std::max<int64_t>(1, h->nE) * N));
+  TRY(dalloc(h, &h->part, std::max<int64_t>(1, h->nseg) * N));
+  TRY(dalloc(h, &h->small, 16 * (int64_t)N * N + 8 * (int64_t)N));
+  h->tnwork_elems = gemm_tn_work_elems(R, N, N);
+  TRY(dalloc(h, &h->tnwork, h->tnwork_elems));
+  TRY(dalloc(h, &h->rpart, ((R + 2047) / 2048 + 1) * (int64_t)N));
+  h->Nres = N;
+  return EFE_OK;
+}
+
+int reserve32(efe_handle* h, int N) {
+  if (N <= h->Nres32) return EFE_OK;
+  for (int i = 0; i < 3; ++i) { dfree(h, h->Yf[i]); dfree(h, h->Ye[i]); }
+  dfree(h, h->Wf);
+  for (int i = 0; i < 3; ++i) {
+    TRY(dalloc(h, &h->Yf[i], h->n_nodes * N));
+    TRY(dalloc(h, &h->Ye[i], std::max<int64_t>(1, h->nE) * N));
+  }
+  TRY(dalloc(h, &h->Wf, h->n_nodes * N));
+  h->Nres32 = N;
+  return EFE_OK;
+}
+
+// --- timing of the classical cell-apply launches ---
+int ev_get(efe_handle* h, int idx, cudaEvent_t* e) {
+  while ((int)h->ev_pool.size() <= idx) {
+    cudaEvent_t ev;
+    CK(cudaEventCreate(&ev));
+    h->ev_pool.push_back(ev);
+  }
+  *e = h->ev_pool[idx];
+  return EFE_OK;
+}
+
+int timed_begin(efe_handle* h, cudaStream_t st, int* slot) {
+  *slot = -1;
+  if (!h->timing) return EFE_OK;
+  const int i = 2 * (int)h->ev_pairs.size();
+  cudaEvent_t a, b;
+  TRY(ev_get(h, i, &a));
+  TRY(ev_get(h, i + 1, &b));
+  CK(cudaEventRecord(a, st));
+  *slot = i;
+  return EFE_OK;
+}
+
+int timed_end(efe_handle* h, cudaStream_t st, int slot, int64_t cellcols) {
+  if (slot < 0) return EFE_OK;
+  CK(cudaEventRecord(h->ev_pool[slot + 1], st));
+  h->ev_pairs.push_back({slot, slot + 1});
+  h->pend_cellcols += cellcols;
+  if (h->ev_pairs.size() >= 4096) {  // fold completed pairs to bound the pool
+    CK(cudaEventSynchronize(h->ev_pool[slot + 1]));
+    for (auto& pr : h->ev_pairs) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->ev_pool[pr.first], h->ev_pool[pr.second]));
+      h->t_ms += ms;
+      h->t_launches++;
+    }
+    h->ev_pairs.clear();
+    h->t_cellcols += h->pend_cellcols;
+    h->pend_cellcols = 0;
+  }
+  return EFE_OK;
+}
+
+// --- classical cell products, all 8 parity colours: W_c += H^cc Y_c ---
+template <typename T>
+int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, int64_t ldw, int N, cudaStream_t st) {
+  for (int c = 0; c < 8; ++c) {
+    const int64_t nc = h->colour_off[c + 1] - h->colour_off[c];
+    if (nc == 0) continue;
+    int slot;
+    TRY(timed_begin(h, st, &slot));
+    if constexpr (sizeof(T) == 8)
+      launch_cell_apply_f64((const double*)Hc, h->colour_cells + h->colour_off[c], nc, h->mesh, (const double*)Y,
+                            ldy, (double*)Wc, ldw, N, st);
+    else
+      launch_cell_apply_f32((const float*)Hc, h->colour_cells + h->colour_off[c], nc, h->mesh, (const float*)Y, ldy,
+                            (float*)Wc, ldw, N, st);
+    CKL();
+    TRY(timed_end(h, st, slot, nc * (int64_t)N));
+  }
+  return EFE_OK;
+}
+
+// --- H^E X: classical cell products + enrichment coupling (Eq. H2x2) ---
+//   Wc = H^cc Xc + (H^ec)^T Xe ;  We = H^ec Xc + H^ee Xe
+template <typename T>
+int apply_H_generic(efe_handle* h, const T* Xc, int64_t ldx, const double* Xe, int64_t ldxe, T* Wc, int64_t ldw,
+                    double* We, int64_t ldwe, int N, cudaStream_t st, const T* Hc) {
+  if (ldw == N) {
+    CK(cudaMemsetAsync(Wc, 0, sizeof(T) * h->n_nodes * N, st));
+  } else {
+    if constexpr (sizeof(T) == 8) launch_zero_rows(h->n_nodes, (double*)Wc, ldw, N, st);
+    else launch_zero_rows_f32(h->n_nodes, (float*)Wc, ldw, N, st);
+    CKL();
+  }
+  TRY(cell_apply_all<T>(h, Hc, Xc, ldx, Wc, ldw, N, st));
+  if (h->nE > 0) {
+    launch_spmm_nodes<T>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->hecT, 1.0, Xe, ldxe, Wc, ldw, N, st);
+    launch_spmm_segments<T>(h->nseg, h->seg_start, h->seg_end, h->ec_col, h->hec, nullptr, Xc, ldx, h->part, N, st);
+    launch_seg_reduce((int)h->nE, h->row_seg_ptr, h->part, 1.0, nullptr, 0, 0.0, We, ldwe, N, st);
+    launch_gemm_nn(h->nE, N, (int)h->nE, 1.0, h->Hee, h->nE, Xe, ldxe, 1.0, We, ldwe, st);
+    CKL();
+  }
+  return EFE_OK;
+}
+
+// --- block-wise inverse on W (Sec. IV.D), in place on Wc, result x_e in h->xe ---
+//   r = We - M^ec D^-1 Wc ; x_e = S^-1 r ; Wc <- Wc - (M^ec)^T x_e  (D^-1 applied later)
+template <typename T>
+int minv_core(efe_handle* h, T* Wc, int64_t ldw, const double* We, int64_t ldwe, int N, cudaStream_t st) {
+  if (h->nE == 0) return EFE_OK;
+  launch_spmm_segments<T>(h->nseg, h->seg_start, h->seg_end, h->ec_col, h->mec, h->Dinv, Wc, ldw, h->part, N, st);
+  launch_seg_reduce((int)h->nE, h->row_seg_ptr, h->part, -1.0, We, ldwe, 1.0, h->rb, N, N, st);
+  launch_gemm_nn(h->nE, N, (int)h->nE, 1.0, h->Sinv, h->nE, h->rb, N, 0.0, h->xe, N, st);
+  launch_spmm_nodes<T>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->mecT, -1.0, h->xe, N, Wc, ldw, N, st);
+  CKL();
+  return EFE_OK;
+}
+
+int apply_M_impl(efe_handle* h, const double* X, int64_t ldx, int N, double* Y, int64_t ldy, cudaStream_t st) {
+  const int64_t nn = h->n_nodes;
+  launch_row_scale<double>(nn, h->Dm, X, ldx, Y, ldy, N, st);
+  if (h->nE > 0) {
+    launch_spmm_nodes<double>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->mecT, 1.0, X + nn * ldx, ldx, Y, ldy, N, st);
+    launch_row_scale<double>(nn, h->mask, Y, ldy, Y, ldy, N, st);
+    launch_spmm_segments<double>(h->nseg, h->seg_start, h->seg_end, h->ec_col, h->mec, nullptr, X, ldx, h->part, N,
+                                 st);
+    launch_seg_reduce((int)h->nE, h->row_seg_ptr, h->part, 1.0, nullptr, 0, 0.0, Y + nn * ldy, ldy, N, st);
+    launch_gemm_nn(h->nE, N, (int)h->nE, 1.0, h->Mee, h->nE, X + nn * ldx, ldx, 1.0, Y + nn * ldy, ldy, st);
+  }
+  CKL();
+  return EFE_OK;
+}
+
+int apply_H_impl(efe_handle* h, const double* X, int64_t ldx, int N, double* Y, int64_t ldy, cudaStream_t st) {
+  const int64_t nn = h->n_nodes;
+  TRY(apply_H_generic<double>(h, X, ldx, X + nn * ldx, ldx, Y, ldy, Y + nn * ldy, ldy, N, st, h->Hcc));
+  launch_row_scale<double>(nn, h->mask, Y, ldy, Y, ldy, N, st);
+  CKL();
+  return EFE_OK;
+}
+
+int apply_Minv_impl(efe_handle* h, const double* X, int64_t ldx, int N, double* Y, int64_t ldy, cudaStream_t st) {
+  const int64_t nn = h->n_nodes;
+  // W = X copied into the workspace so the core can work in place
+  launch_copy_rows(h->rows, X, ldx, h->W, N, N, st);
+  TRY(minv_core<double>(h, h->W, N, h->W + nn * N, N, N, st));
+  launch_row_scale<double>(nn, h->Dinv, h->W, N, Y, ldy, N, st);
+  if (h->nE > 0) launch_copy_rows(h->nE, h->xe, N, Y + nn * ldy, ldy, N, st);
+  CKL();
+  return EFE_OK;
+}
+
+// --- one filter degree in FP64: Ynew = alpha (H~ Ycur - c Ycur) + beta Yprev ---
+int degree_f64(efe_handle* h, const double* Yc, int64_t ldc, const double* Yp, int64_t ldp, double* Yn, int64_t ldn,
+               double alpha, double cc, double beta, int N, cudaStream_t st) {
+  const int64_t nn = h->n_nodes;
+  double* Wc = h->W;
+  double* We = h->W + nn * N;
+  TRY(apply_H_generic<double>(h, Yc, ldc, Yc + nn * ldc, ldc, Wc, N, We, N, N, st, h->Hcc));
+  TRY(minv_core<double>(h, Wc, N, We, N, N, st));
+  launch_cheb_combine<double>(nn, h->Dinv, Wc, N, Yc, ldc, Yp, ldp, Yn, ldn, alpha, cc, beta, N, st);
+  if (h->nE > 0)
+    launch_cheb_combine<double>(h->nE, nullptr, h->xe, N, Yc + nn * ldc, ldc, Yp ? Yp + nn * ldp : nullptr, ldp,
+                                Yn + nn * ldn, ldn, alpha, cc, beta, N, st);
+  CKL();
+  return EFE_OK;
+}
+
+// --- one filter degree with the classical block in FP32 (enrichment rows FP64) ---
+int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Yp, const double* Ype, float* Yn,
+               double* Yne, double alpha, double cc, double beta, int N, cudaStream_t st) {
+  const int64_t nn = h->n_nodes;
+  double* We = h->W;  // nE x N FP64 scratch
+  TRY(apply_H_generic<float>(h, Yc, N, Yce, N, h->Wf, N, We, N, N, st, h->Hcc32));
+  TRY(minv_core<float>(h, h->Wf, N, We, N, N, st));
+  launch_cheb_combine<float>(nn, h->Dinv, h->Wf, N, Yc, N, Yp, N, Yn, N, alpha, cc, beta, N, st);
+  if (h->nE > 0) launch_cheb_combine<double>(h->nE, nullptr, h->xe, N, Yce, N, Ype, N, Yne, N, alpha, cc, beta, N, st);
+  CKL();
+  return EFE_OK;
+}
+
+bool is_finite_d(double x) { return std::isfinite(x); }
+
+// tiny host symmetric tridiagonal eigenvalues (Jacobi on a dense copy, k <= 64)
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int k = (int)a.size();
+  std::vector<double> A((size_t)k * k, 0.0);
+  for (int i = 0; i < k; ++i) {
+    A[(size_t)i * k + i] = a[i];
+    if (i + 1 < k) A[(size_t)i * k + i + 1] = A[(size_t)(i + 1) * k + i] = b[i];
+  }
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < k; ++p)
+      for (int q = p + 1; q < k; ++q) off += A[(size_t)p * k + q] * A[(size_t)p * k + q];
+    if (off < 1e-30) break;
+    for (int p = 0; p < k; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        const double apq = A[(size_t)p * k + q];
+        if (apq == 0.0) continue;
+        const double tau = (A[(size_t)q * k + q] - A[(size_t)p * k + p]) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int i = 0; i < k; ++i) {
+          const double aip = A[(size_t)i * k + p], aiq = A[(size_t)i * k + q];
+          A[(size_t)i * k + p] = c * aip - s * aiq;
+          A[(size_t)i * k + q] = s * aip + c * aiq;
+        }
+        for (int j = 0; j < k; ++j) {
+          const double apj = A[(size_t)p * k + j], aqj = A[(size_t)q * k + j];
+          A[(size_t)p * k + j] = c * apj - s * aqj;
+          A[(size_t)q * k + j] = s * apj + c * aqj;
+        }
+      }
+  }
+  double mx = -INFINITY;
+  for (int i = 0; i < k; ++i) mx = std::max(mx, A[(size_t)i * k + i]);
+  return mx;
+}
+
+}  // namespace
+
+extern "C" {
+
+int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe_basis_desc* basis,
+               efe_handle** out) {
+  if (!out) return EFE_ERR_ARG;
+  *out = nullptr;
+  efe_handle* h = new (std::nothrow) efe_handle();
+  if (!h) return EFE_ERR_ALLOC;
+  *out = h;
+  CK(cudaGetDevice(&h->dev));
+  Setup s;
+  int rc;
+  try {
+    rc = build_setup(mesh, atoms, basis, s);
+  } catch (...) {
+    h->err = "host allocation failed during set-up";
+    return EFE_ERR_ALLOC;
+  }
+  if (rc != EFE_OK) {
+    h->err = s.err;
+    return rc;
+  }
+  h->n_nodes = s.n_nodes;
+  h->n_cell = s.n_cell;
+  h->nE = s.nE;
+  h->nq = s.n_q;
+  h->rows = s.n_nodes + s.nE;
+  h->n_enr = (int64_t)s.enr_cells.size();
+  std::memcpy(h->re.z, s.gll_z, sizeof(h->re.z));
+  std::memcpy(h->re.w, s.gll_w, sizeof(h->re.w));
+  std::memcpy(h->re.M1, s.M1, sizeof(h->re.M1));
+  std::memcpy(h->re.K1, s.K1, sizeof(h->re.K1));
+  for (int d = 0; d < 3; ++d) {
+    h->mesh.nc[d] = s.nc[d];
+    h->mesh.nn[d] = s.nn[d];
+  }
+  std::vector<double> brk;
+  for (int d = 0; d < 3; ++d) brk.insert(brk.end(), s.brk[d].begin(), s.brk[d].end());
+  TRY(upload(h, &h->brk, brk));
+  h->mesh.brk = h->brk;
+  h->n_atoms = (int)s.atom_Z.size();
+  TRY(upload(h, &h->axyz, s.atom_xyz));
+  TRY(upload(h, &h->aZ, s.atom_Z));
+  TRY(upload(h, &h->qpts, s.qpts));
+  TRY(upload(h, &h->qoff, s.qoff));
+  TRY(dalloc(h, &h->V, h->nq));
+  // parity colours of the cells
+  {
+    std::vector<int32_t> cc;
+    h->colour_off[0] = 0;
+    for (int c = 0; c < 8; ++c) {
+      for (int64_t e = 0; e < s.n_cell; ++e) {
+        const int i = (int)(e % s.nc[0]), j = (int)((e / s.nc[0]) % s.nc[1]),
+                  k = (int)(e / ((int64_t)s.nc[0] * s.nc[1]));
+        if ((i & 1) + 2 * (j & 1) + 4 * (k & 1) == c) cc.push_back((int32_t)e);
+      }
+      h->colour_off[c + 1] = (int64_t)cc.size();
+    }
+    TRY(upload(h, &h->colour_cells, cc));
+  }
+  TRY(upload(h, &h->D, s.D));
+  TRY(upload(h, &h->Dinv, s.Dinv));
+  {
+    std::vector<double> mask(s.n_nodes), Dm(s.n_nodes);
+    for (int64_t g = 0; g < s.n_nodes; ++g) {
+      mask[g] = s.Dinv[g] != 0.0 ? 1.0 : 0.0;
+      Dm[g] = mask[g] * s.D[g];
+    }
+    TRY(upload(h, &h->mask, mask));
+    TRY(upload(h, &h->Dm, Dm));
+  }
+  TRY(dalloc(h, &h->Hcc, h->n_cell * NL * NL));
+  TRY(dalloc(h, &h->Hcc32, h->n_cell * NL * NL));
+  TRY(dalloc(h, (uint16_t**)&h->Hcc16, h->n_cell * NL * NL));
+  TRY(dalloc(h, &h->info, 8));
+  if (h->nE > 0) {
+    TRY(upload(h, &h->funcs, s.funcs));
+    TRY(upload(h, &h->enr_cells, s.enr_cells));
+    TRY(upload(h, &h->cf_ptr, s.cf_ptr));
+    TRY(upload(h, &h->cf_idx, s.cf_idx));
+    for (int64_t ei = 0; ei < h->n_enr; ++ei) h->kmax = std::max(h->kmax, s.cf_ptr[ei + 1] - s.cf_ptr[ei]);
+    if (h->kmax > 64) {
+      h->err = "more than 64 enrichment functions meet one cell";
+      return EFE_ERR_ARG;
+    }
+    TRY(upload(h, &h->blkP_off, s.blkP_off));
+    TRY(upload(h, &h->blkQ_off, s.blkQ_off));
+    h->nP = s.blkP_off.back();
+    h->nQ = s.blkQ_off.back();
+    TRY(dalloc(h, &h->Pblk, h->nP));
+    TRY(dalloc(h, &h->Qblk, h->nQ));
+    h->nnz = (int64_t)s.ec_col.size();
+    TRY(upload(h, &h->ec_col, s.ec_col));
+    TRY(upload(h, &h->mec, s.mec_val));
+    TRY(upload(h, &h->hec_kin, s.hec_kin));
+    TRY(dalloc(h, &h->hec, h->nnz));
+    TRY(upload(h, &h->ec_cptr, s.ec_contrib_ptr));
+    TRY(upload(h, &h->ec_cidx, s.ec_contrib_idx));
+    // segments of the long rows
+    std::vector<int64_t> ss, se, rsp(1, 0);
+    for (int a = 0; a < s.nE; ++a) {
+      for (int64_t q = s.ec_ptr[a]; q < s.ec_ptr[a + 1]; q += SEG) {
+        ss.push_back(q);
+        se.push_back(std::min(q + SEG, s.ec_ptr[a + 1]));
+      }
+      rsp.push_back((int64_t)ss.size());
+    }
+    h->nseg = (int64_t)ss.size();
+    TRY(upload(h, &h->seg_start, ss));
+    TRY(upload(h, &h->seg_end, se));
+    TRY(upload(h, &h->row_seg_ptr, rsp));
+    h->n_tn = (int64_t)s.t_nodes.size();
+    TRY(upload(h, &h->t_nodes, s.t_nodes));
+    TRY(upload(h, &h->t_ptr, s.t_ptr));
+    TRY(upload(h, &h->t_col, s.t_col));
+    TRY(upload(h, &h->t_perm, s.t_perm));
+    TRY(dalloc(h, &h->mecT, h->nnz));
+    TRY(dalloc(h, &h->hecT, h->nnz));
+    launch_permute(h->nnz, h->mec, h->t_perm, h->mecT, 0);
+    CKL();
+    TRY(upload(h, &h->Mee, s.Mee));
+    TRY(upload(h, &h->Hee_kin, s.Hee_kin));
+    TRY(dalloc(h, &h->Hee, h->nE * h->nE));
+    TRY(upload(h, &h->Sinv, s.Sinv));
+    TRY(upload(h, &h->ee_cptr, s.ee_contrib_ptr));
+    TRY(upload(h, &h->ee_cidx, s.ee_contrib_idx));
+  }
+  CK(cudaDeviceSynchronize());
+  return EFE_OK;
+}
+
+int efe_destroy(efe_handle* h) {
+  if (!h) return EFE_OK;
+  cudaSetDevice(h->dev);
+  for (void* p : h->allocs) cudaFree(p);
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+  return EFE_OK;
+}
+
+const char* efe_last_error(const efe_handle* h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+int efe_sizes(const efe_handle* h, int64_t* n_nodes, int64_t* n_enrich, int64_t* n_qpoints, int64_t* n_cells,
+              int64_t* n_coupling) {
+  if (!h) return EFE_ERR_ARG;
+  if (n_coupling) *n_coupling = h->nnz;
+  if (n_nodes) *n_nodes = h->n_nodes;
+  if (n_enrich) *n_enrich = h->nE;
+  if (n_qpoints) *n_qpoints = h->nq;
+  if (n_cells) *n_cells = h->n_cell;
+  return EFE_OK;
+}
+
+int efe_qpoints(efe_handle* h, double* xyzw, void* stream) {
+  if (!h || !xyzw) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  CK(cudaMemcpyAsync(xyzw, h->qpts, sizeof(double) * 4 * h->nq, cudaMemcpyDeviceToDevice, S(stream)));
+  return EFE_OK;
+}
+
+int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
+  if (!h || !Vq) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  cudaStream_t st = S(stream);
+  if (Vq != h->V) CK(cudaMemcpyAsync(h->V, Vq, sizeof(double) * h->nq, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(h->info, 0, sizeof(int), st));
+  launch_check_finite(h->V, h->nq, h->info, st);
+  CKL();
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, h->info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flag) {
+    h->err = "non-finite potential value";
+    return EFE_ERR_NAN;
+  }
+  launch_hcc_build(h->re, h->mesh, h->qoff, h->qpts, h->V, h->n_cell, h->Hcc, st);
+  CKL();
+  if (h->nE > 0) {
+    launch_enr_blocks(h->re, h->mesh, h->enr_cells, h->n_enr, h->cf_ptr, h->cf_idx, h->funcs, h->qoff, h->qpts, h->V,
+                      h->blkP_off, h->blkQ_off, h->kmax, h->Pblk, h->Qblk, st);
+    CKL();
+    launch_gather_sum(h->nnz, h->hec_kin, h->ec_cptr, h->ec_cidx, h->Pblk, h->hec, st);
+    launch_permute(h->nnz, h->hec, h->t_perm, h->hecT, st);
+    launch_gather_sum(h->nE * h->nE, h->Hee_kin, h->ee_cptr, h->ee_cidx, h->Qblk, h->Hee, st);
+    launch_symmetrize(h->Hee, (int)h->nE, (int)h->nE, st);
+    CKL();
+  }
+  launch_to_f32(h->Hcc, h->Hcc32, h->n_cell * NL * NL, st);
+  launch_to_bf16(h->Hcc, h->Hcc16, h->n_cell * NL * NL, st);
+  CKL();
+  h->potential_set = true;
+  return EFE_OK;
+}
+
+int efe_set_potential_analytic(efe_handle* h, const efe_potential_desc* pot, void* stream) {
+  if (!h || !pot || pot->n_terms < 0) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  cudaStream_t st = S(stream);
+  double *dA = nullptr, *ds = nullptr, *dc = nullptr;
+  const int nt = pot->n_terms;
+  if (nt > 0) {
+    TRY(dalloc(h, &dA, nt));
+    TRY(dalloc(h, &ds, nt));
+    TRY(dalloc(h, &dc, 3 * nt));
+    CK(cudaMemcpy(dA, pot->A, sizeof(double) * nt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ds, pot->s, sizeof(double) * nt, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dc, pot->c, sizeof(double) * 3 * nt, cudaMemcpyHostToDevice));
+  }
+  launch_potential_analytic(h->qpts, h->nq, h->axyz, h->aZ, h->n_atoms, pot->nuclear, dA, ds, dc,
+                            nt, pot->omega, h->V, st);
+  CKL();
+  int rc = efe_set_potential(h, h->V, stream);
+  CK(cudaStreamSynchronize(st));
+  dfree(h, dA);
+  dfree(h, ds);
+  dfree(h, dc);
+  return rc;
+}
+
+int efe_reserve(efe_handle* h, int32_t N) {
+  if (!h || N < 1) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  return reserve(h, N);
+}
+
+static int check_block(efe_handle* h, const void* X, int64_t ldx, int N) {
+  if (!X || N < 1 || ldx < N) {
+    h->err = "bad block argument (null pointer, N < 1 or ld < N)";
+    return EFE_ERR_ARG;
+  }
+  if (!h->potential_set) {
+    h->err = "no potential set (call efe_set_potential first)";
+    return EFE_ERR_STATE;
+  }
+  return EFE_OK;
+}
+
+int efe_apply_H(efe_handle* h, const double* X, int64_t ldx, int32_t N, double* Y, int64_t ldy, void* stream) {
+  if (!h) return EFE_ERR_ARG;
+  TRY(check_block(h, X, ldx, N));
+  TRY(check_block(h, Y, ldy, N));
+  TRY(set_dev(h));
+  TRY(reserve(h, N));
+  return apply_H_impl(h, X, ldx, N, Y, ldy, S(stream));
+}
+
+int efe_apply_M(efe_handle* h, const double* X, int64_t ldx, int32_t N, double* Y, int64_t ldy, void* stream) {
+  if (!h) return EFE_ERR_ARG;
+  TRY(check_block(h, X, ldx, N));
+  TRY(check_block(h, Y, ldy, N));
+  TRY(set_dev(h));
+  TRY(reserve(h, N));
+  return apply_M_impl(h, X, ldx, N, Y, ldy, S(stream));
+}
+
+int efe_apply_Minv(efe_handle* h, const double* X, int64_t ldx, int32_t N, double* Y, int64_t ldy, void* stream) {
+  if (!h) return EFE_ERR_ARG;
+  TRY(check_block(h, X, ldx, N));
+  TRY(check_block(h, Y, ldy, N));
+  TRY(set_dev(h));
+  TRY(reserve(h, N));
+  return apply_Minv_impl(h, X, ldx, N, Y, ldy, S(stream));
+}
+
+int efe_upper_bound(efe_handle* h, const double* v0, int32_t k, double* b_out, void* stream) {
+  if (!h || !b_out || k < 1 || k > 64) return EFE_ERR_ARG;
+  TRY(check_block(h, v0, 1, 1));
+  TRY(set_dev(h));
+  TRY(reserve(h, 1));
+  cudaStream_t st = S(stream);
+  const int64_t R = h->rows;
+  if (!h->lz) TRY(dalloc(h, &h->lz, 6 * R + 512));
+  double *v = h->lz, *vp = v + R, *w = vp + R, *Mv = w + R, *tmp = Mv + R, *scal = tmp + R, *part = scal + 8;
+  auto dot = [&](const double* x, const double* y, double* out) -> int {
+    launch_dot(R, x, y, part, scal, st);
+    CKL();
+    CK(cudaMemcpyAsync(out, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return EFE_OK;
+  };
+  TRY(apply_M_impl(h, v0, 1, 1, Mv, 1, st));
+  double nrm2;
+  TRY(dot(v0, Mv, &nrm2));
+  if (!(nrm2 > 0.0) || !is_finite_d(nrm2)) {
+    h->err = "start vector has zero or non-finite M-norm";
+    return EFE_ERR_ARG;
+  }
+  launch_scale(R, v0, 1.0 / sqrt(nrm2), v, st);
+  CK(cudaMemsetAsync(vp, 0, sizeof(double) * R, st));
+  std::vector<double> al, be;
+  double beta = 0.0;
+  for (int j = 0; j < k; ++j) {
+    TRY(apply_H_impl(h, v, 1, 1, tmp, 1, st));
+    TRY(apply_Minv_impl(h, tmp, 1, 1, w, 1, st));
+    TRY(apply_M_impl(h, v, 1, 1, Mv, 1, st));
+    double alpha;
+    TRY(dot(w, Mv, &alpha));
+    launch_axpby3(R, w, v, vp, alpha, beta, st);
+    CKL();
+    TRY(apply_M_impl(h, w, 1, 1, Mv, 1, st));
+    double b2;
+    TRY(dot(w, Mv, &b2));
+    if (!is_finite_d(alpha) || !is_finite_d(b2)) {
+      h->err = "non-finite value in the Lanczos bound";
+      return EFE_ERR_NAN;
+    }
+    beta = sqrt(std::max(b2, 0.0));
+    al.push_back(alpha);
+    be.push_back(beta);
+    if (beta == 0.0) break;
+    CK(cudaMemcpyAsync(vp, v, sizeof(double) * R, cudaMemcpyDeviceToDevice, st));
+    launch_scale(R, w, 1.0 / beta, v, st);
+    CKL();
+  }
+  *b_out = tridiag_max_eig(al, be) + fabs(be.back());
+  return EFE_OK;
+}
+
+int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, double a, double b, double a0,
+                   int32_t precision, int32_t fp64_tail, void* stream) {
+  if (!h) return EFE_ERR_ARG;
+  TRY(check_block(h, X, ldx, N));
+  if (m < 1 || !(b > a) || !(a > a0) || !is_finite_d(a) || !is_finite_d(b) || !is_finite_d(a0) || fp64_tail < 0) {
+    h->err = "bad filter parameters (need m >= 1, a0 < a < b, finite)";
+    return EFE_ERR_ARG;
+  }
+  if (precision != EFE_PREC_FP64 && precision != EFE_PREC_FP32) {
+    h->err = "precision mode not available in this build";
+    return EFE_ERR_ARG;
+  }
+  TRY(set_dev(h));
+  TRY(reserve(h, N));
+  cudaStream_t st = S(stream);
+  const int64_t nn = h->n_nodes;
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double s1 = e / (a0 - c);
+  double sig = s1;
+  // coefficients of degree k (1-based): Ynew = alpha (H~ Ycur - c Ycur) + beta Yprev
+  auto coef = [&](int k, double* alpha, double* beta) {
+    if (k == 1) {
+      *alpha = s1 / e;
+      *beta = 0.0;
+      return;
+    }
+    const double sn = 1.0 / (2.0 / s1 - sig);
+    *alpha = 2.0 * sn / e;
+    *beta = -sig * sn;
+    sig = sn;
+  };
+  const int n_low = (precision == EFE_PREC_FP64) ? 0 : std::max(0, m - fp64_tail);
+  // FP64 buffers: slot 0 = X (user, ldx), 1 = B1, 2 = B2 (ld = N)
+  double* buf[3] = {X, h->B1, h->B2};
+  int64_t ld[3] = {ldx, N, N};
+  int prev = -1, cur = 0;
+  int k = 1;
+  if (n_low > 0) {
+    TRY(reserve32(h, N));
+    // load Y_0 into the low-precision buffers
+    launch_f64_to_f32_rows(nn, X, ldx, h->Yf[0], N, N, st);
+    if (h->nE > 0) launch_copy_rows(h->nE, X + nn * ldx, ldx, h->Ye[0], N, N, st);
+    CKL();
+    int p32 = -1, c32 = 0;
+    for (; k <= n_low; ++k) {
+      double al, be;
+      coef(k, &al, &be);
+      const int nx = (c32 + 1) % 3 == p32 ? (c32 + 2) % 3 : (c32 + 1) % 3;
+      TRY(degree_f32(h, h->Yf[c32], h->Ye[c32], p32 >= 0 ? h->Yf[p32] : nullptr, p32 >= 0 ? h->Ye[p32] : nullptr,
+                     h->Yf[nx], h->Ye[nx], al, c, be, N, st));
+      p32 = c32;
+      c32 = nx;
+    }
+    // hand the last two degrees to FP64 storage: prev -> B1, cur -> B2
+    launch_f32_to_f64_rows(nn, h->Yf[c32], N, h->B2, N, N, st);
+    if (h->nE > 0) launch_copy_rows(h->nE, h->Ye[c32], N, h->B2 + nn * N, N, N, st);
+    cur = 2;
+    if (p32 >= 0) {
+      launch_f32_to_f64_rows(nn, h->Yf[p32], N, h->B1, N, N, st);
+      if (h->nE > 0) launch_copy_rows(h->nE, h->Ye[p32], N, h->B1 + nn * N, N, N, st);
+      prev = 1;
+    }
+    CKL();
+  }
+  for (; k <= m; ++k) {
+    double al, be;
+    coef(k, &al, &be);
+    int nx = 0;
+    while (nx == cur || nx == prev) ++nx;
+    TRY(degree_f64(h, buf[cur], ld[cur], prev >= 0 ? buf[prev] : nullptr, prev >= 0 ? ld[prev] : 0, buf[nx], ld[nx],
+                   al, c, be, N, st));
+    prev = cur;
+    cur = nx;
+  }
+  if (cur != 0) {
+    launch_copy_rows(h->rows, buf[cur], ld[cur], X, ldx, N, st);
+    CKL();
+  }
+  return EFE_OK;
+}
+
+int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* eig_host, double* resid_host,
+                      void* stream) {
+  if (!h || !eig_host) return EFE_ERR_ARG;
+  TRY(check_block(h, X, ldx, N));
+  if (N > 2048) {
+    h->err = "N > 2048 not supported by the one-CTA dense eigensolver";
+    return EFE_ERR_ARG;
+  }
+  TRY(set_dev(h));
+  TRY(reserve(h, N));
+  cudaStream_t st = S(stream);
+  const int64_t R = h->rows;
+  const int64_t NN = (int64_t)N * N;
+  double* G = h->small;
+  double* Linv = G + NN;
+  double* Rinv = Linv + NN;
+  double* Hp = Rinv + NN;
+  double* Mp = Hp + NN;
+  double* Lm = Mp + NN;
+  double* Lminv = Lm + NN;
+  double* LminvT = Lminv + NN;
+  double* T1 = LminvT + NN;
+  double* C = T1 + NN;
+  double* Vj = C + NN;
+  double* Z = Vj + NN;
+  double* Psi = Z + NN;
+  double* wv = Psi + NN;
+  double* eps = wv + N;
+  double* res = eps + N;
+  double *Q = h->B1, *HQ = h->B2, *MQ = h->W;
+  int inf[2] = {0, 0};
+  // Cholesky-QR: G = X^T X = L L^T, Q = X L^-T
+  launch_gemm_tn(R, N, N, X, ldx, X, ldx, G, N, h->tnwork, h->tnwork_elems, st);
+  launch_symmetrize(G, N, N, st);
+  launch_chol(G, N, N, h->info, st);
+  CKL();
+  CK(cudaMemcpyAsync(inf, h->info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (inf[0]) {
+    h->err = "Cholesky-QR breakdown: Gram matrix X^T X is not positive definite (rank-deficient block)";
+    return EFE_ERR_CHOL;
+  }
+  launch_trinv_lower(G, N, N, Linv, N, st);
+  launch_transpose(Linv, N, N, Rinv, N, st);
+  launch_gemm_nn(R, N, N, 1.0, X, ldx, Rinv, N, 0.0, Q, N, st);
+  CKL();
+  // projections
+  TRY(apply_H_impl(h, Q, N, N, HQ, N, st));
+  TRY(apply_M_impl(h, Q, N, N, MQ, N, st));
+  launch_gemm_tn(R, N, N, Q, N, HQ, N, Hp, N, h->tnwork, h->tnwork_elems, st);
+  launch_gemm_tn(R, N, N, Q, N, MQ, N, Mp, N, h->tnwork, h->tnwork_elems, st);
+  launch_symmetrize(Hp, N, N, st);
+  launch_symmetrize(Mp, N, N, st);
+  CK(cudaMemcpyAsync(Lm, Mp, sizeof(double) * NN, cudaMemcpyDeviceToDevice, st));
+  launch_chol(Lm, N, N, h->info, st);
+  CKL();
+  CK(cudaMemcpyAsync(inf, h->info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (inf[0]) {
+    h->err = "projected overlap Q^T M Q is not positive definite";
+    return EFE_ERR_CHOL;
+  }
+  // C = Lm^-1 Hp Lm^-T, eig(C) = (eps, Z), Psi = Lm^-T Z
+  launch_trinv_lower(Lm, N, N, Lminv, N, st);
+  launch_transpose(Lminv, N, N, LminvT, N, st);
+  launch_gemm_nn(N, N, N, 1.0, Lminv, N, Hp, N, 0.0, T1, N, st);
+  launch_gemm_nn(N, N, N, 1.0, T1, N, LminvT, N, 0.0, C, N, st);
+  launch_symmetrize(C, N, N, st);
+  launch_jacobi(C, N, N, Vj, N, wv, 40, h->info + 1, st);
+  launch_sort_eig(wv, Vj, N, N, eps, Z, N, st);
+  launch_gemm_nn(N, N, N, 1.0, LminvT, N, Z, N, 0.0, Psi, N, st);
+  // rotation and residuals
+  launch_gemm_nn(R, N, N, 1.0, Q, N, Psi, N, 0.0, X, ldx, st);
+  launch_gemm_nn(R, N, N, 1.0, HQ, N, Psi, N, 0.0, Q, N, st);    // HX
+  launch_gemm_nn(R, N, N, 1.0, MQ, N, Psi, N, 0.0, HQ, N, st);   // MX
+  launch_resid_norms(R, Q, N, HQ, N, eps, N, h->rpart, res, st);
+  CKL();
+  CK(cudaMemcpyAsync(inf + 1, h->info + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(eig_host, eps, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+  if (resid_host) CK(cudaMemcpyAsync(resid_host, res, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (inf[1]) {
+    h->err = "Jacobi eigensolver did not converge";
+    return EFE_ERR_NOCONV;
+  }
+  for (int i = 0; i < N; ++i)
+    if (!is_finite_d(eig_host[i])) {
+      h->err = "non-finite Ritz value";
+      return EFE_ERR_NAN;
+    }
+  return EFE_OK;
+}
+
+int efe_launch_count(int64_t* total) {
+  if (!total) return EFE_ERR_ARG;
+  *total = g_launches.load();
+  return EFE_OK;
+}
+
+int efe_enable_timing(efe_handle* h, int32_t enable) {
+  if (!h) return EFE_ERR_ARG;
+  h->timing = enable != 0;
+  return EFE_OK;
+}
+
+int efe_kernel_stats(efe_handle* h, int64_t* launches, double* total_ms, int64_t* cell_columns, int32_t reset) {
+  if (!h) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  CK(cudaDeviceSynchronize());
+  for (auto& pr : h->ev_pairs) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev_pool[pr.first], h->ev_pool[pr.second]));
+    h->t_ms += ms;
+    h->t_launches++;
+  }
+  h->ev_pairs.clear();
+  h->t_cellcols += h->pend_cellcols;
+  h->pend_cellcols = 0;
+  if (launches) *launches = h->t_launches;
+  if (total_ms) *total_ms = h->t_ms;
+  if (cell_columns) *cell_columns = h->t_cellcols;
+  if (reset) {
+    h->t_launches = 0;
+    h->t_ms = 0.0;
+    h->t_cellcols = 0;
+  }
+  return EFE_OK;
+}
+
+}  // extern "C"

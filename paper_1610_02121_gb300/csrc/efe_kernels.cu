@@ -1,0 +1,1013 @@
+// CUDA kernels of the enriched finite-element ChFSI library (sm_103a).
+//
+// Set-up kernels (efe_set_potential), FP64 / FP32-storage hot-path kernels of
+// the Chebyshev filter (Sec. V) -- cell products of H^cc (Eq. Hcc) with a
+// deterministic parity-coloured scatter, enrichment coupling H^ec / M^ec
+// (Eqs. Hec, Mec) as sparse row products, the block-wise overlap inverse
+// (Sec. IV.D) and the scaled three-term recurrence -- and the FP64 dense kernels
+// of Cholesky-QR and Rayleigh-Ritz.  No FP atomics anywhere: every reduction
+// has a fixed order, so results are bitwise reproducible run to run.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <atomic>
+
+#include "efe_func.h"
+#include "efe_kernels.h"
+
+namespace efe {
+
+std::atomic<int64_t> g_launches{0};
+
+namespace {
+
+inline unsigned grid1(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+__device__ __forceinline__ void lagrange_dev(const double* z, double xi, double* l) {
+#pragma unroll
+  for (int a = 0; a < NP1; ++a) {
+    double v = 1.0;
+#pragma unroll
+    for (int b = 0; b < NP1; ++b)
+      if (b != a) v *= (xi - z[b]) / (z[a] - z[b]);
+    l[a] = v;
+  }
+}
+
+__device__ __forceinline__ void cell_geom(const MeshDev& m, int64_t e, int* ijk, double* lo, double* h) {
+  ijk[0] = (int)(e % m.nc[0]);
+  ijk[1] = (int)((e / m.nc[0]) % m.nc[1]);
+  ijk[2] = (int)(e / ((int64_t)m.nc[0] * m.nc[1]));
+  const double* bx = m.brk;
+  const double* by = bx + m.nc[0] + 1;
+  const double* bz = by + m.nc[1] + 1;
+  lo[0] = bx[ijk[0]]; h[0] = bx[ijk[0] + 1] - lo[0];
+  lo[1] = by[ijk[1]]; h[1] = by[ijk[1] + 1] - lo[1];
+  lo[2] = bz[ijk[2]]; h[2] = bz[ijk[2] + 1] - lo[2];
+}
+
+// ---------------------------------------------------------------------------
+// set_potential
+// ---------------------------------------------------------------------------
+__global__ void k_potential(const double* __restrict__ qpts, int64_t nq, const double* __restrict__ axyz,
+                            const double* __restrict__ aZ, int na, int nuclear, const double* __restrict__ gA,
+                            const double* __restrict__ gs, const double* __restrict__ gc, int nt, double omega,
+                            double* __restrict__ V) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const double x = qpts[4 * q], y = qpts[4 * q + 1], z = qpts[4 * q + 2];
+  double v = 0.0;
+  if (nuclear)
+    for (int a = 0; a < na; ++a) {
+      const double dx = x - axyz[3 * a], dy = y - axyz[3 * a + 1], dz = z - axyz[3 * a + 2];
+      v -= aZ[a] / sqrt(dx * dx + dy * dy + dz * dz);
+    }
+  for (int g = 0; g < nt; ++g) {
+    const double dx = x - gc[3 * g], dy = y - gc[3 * g + 1], dz = z - gc[3 * g + 2];
+    v += gA[g] * exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * gs[g] * gs[g]));
+  }
+  if (omega != 0.0) v += 0.5 * omega * omega * (x * x + y * y + z * z);
+  V[q] = v;
+}
+
+__global__ void k_check_finite(const double* __restrict__ x, int64_t n, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) *flag = 1;
+}
+
+// H^cc_e = 1/2 int grad N_j . grad N_k (closed form on the axis-aligned cell)
+//        + sum_q w_q V_q N_j(x_q) N_k(x_q)           (Eq. Hcc)
+// One CTA per cell; the potential part is a 125 x nq x 125 product tiled in
+// 8 x 8 register blocks over a 128 x 128 padded output.
+__global__ void __launch_bounds__(256) k_hcc_build(RefElem re, MeshDev m, const int64_t* __restrict__ qoff,
+                                                   const double* __restrict__ qpts, const double* __restrict__ V,
+                                                   double* __restrict__ Hcc) {
+  const int64_t e = blockIdx.x;
+  int ijk[3];
+  double lo[3], h[3];
+  cell_geom(m, e, ijk, lo, h);
+  __shared__ double Bs[16][128];
+  __shared__ double Bw[16][128];
+  __shared__ double L[16][3][NP1];
+  const int tid = threadIdx.x;
+  const int ty = tid / 16, tx = tid % 16;
+  double acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+  const int64_t qb = qoff[e], qe = qoff[e + 1];
+  for (int64_t q0 = qb; q0 < qe; q0 += 16) {
+    const int np = (int)min((int64_t)16, qe - q0);
+    if (tid < 48) {
+      const int p = tid / 3, d = tid % 3;
+      if (p < np) {
+        const double xi = 2.0 * (qpts[4 * (q0 + p) + d] - lo[d]) / h[d] - 1.0;
+        lagrange_dev(re.z, xi, L[p][d]);
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 16 * 128; idx += 256) {
+      const int p = idx / 128, jl = idx % 128;
+      double b = 0.0, bw = 0.0;
+      if (p < np && jl < NL) {
+        b = L[p][0][jl % NP1] * L[p][1][(jl / NP1) % NP1] * L[p][2][jl / (NP1 * NP1)];
+        bw = b * qpts[4 * (q0 + p) + 3] * V[q0 + p];
+      }
+      Bs[p][jl] = b;
+      Bw[p][jl] = bw;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int p = 0; p < 16; ++p) {
+      double ar[8], bc[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) ar[i] = Bw[p][ty * 8 + i];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) bc[j] = Bs[p][tx * 8 + j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fma(ar[i], bc[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const double cx = h[1] * h[2] / (2.0 * h[0]), cy = h[0] * h[2] / (2.0 * h[1]), cz = h[0] * h[1] / (2.0 * h[2]);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = ty * 8 + i;
+    if (r >= NL) continue;
+    const int ra = r % NP1, rb = (r / NP1) % NP1, rc = r / (NP1 * NP1);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = tx * 8 + j;
+      if (c >= NL) continue;
+      const int ca = c % NP1, cb = (c / NP1) % NP1, cc = c / (NP1 * NP1);
+      const double kin =
+          0.5 * (cx * re.K1[ra * NP1 + ca] * re.M1[rb * NP1 + cb] * re.M1[rc * NP1 + cc] +
+                 cy * re.M1[ra * NP1 + ca] * re.K1[rb * NP1 + cb] * re.M1[rc * NP1 + cc] +
+                 cz * re.M1[ra * NP1 + ca] * re.M1[rb * NP1 + cb] * re.K1[rc * NP1 + cc]);
+      Hcc[e * (int64_t)(NL * NL) + r * NL + c] = kin + acc[i][j];
+    }
+  }
+}
+
+// Potential parts of the enrichment blocks on one enriched cell:
+//   P[a][j] = sum_q w V N_a N_j  (Eq. Hec),   Q[a][b] = sum_q w V N_a N_b  (Eq. Hee)
+__global__ void __launch_bounds__(128) k_enr_blocks(RefElem re, MeshDev m, const int32_t* __restrict__ enr_cells,
+                                                    const int32_t* __restrict__ cf_ptr,
+                                                    const int32_t* __restrict__ cf_idx,
+                                                    const DevFunc* __restrict__ funcs,
+                                                    const int64_t* __restrict__ qoff,
+                                                    const double* __restrict__ qpts, const double* __restrict__ V,
+                                                    const int64_t* __restrict__ blkP_off,
+                                                    const int64_t* __restrict__ blkQ_off, int kmax,
+                                                    double* __restrict__ Pblk, double* __restrict__ Qblk) {
+  extern __shared__ double sm[];
+  const int ei = blockIdx.x;
+  const int64_t e = enr_cells[ei];
+  const int k = cf_ptr[ei + 1] - cf_ptr[ei];
+  const int32_t* fl = cf_idx + cf_ptr[ei];
+  int ijk[3];
+  double lo[3], h[3];
+  cell_geom(m, e, ijk, lo, h);
+  constexpr int CH = 32;
+  double* Bsm = sm;                       // CH * NL
+  double* Esm = Bsm + CH * NL;            // CH * kmax
+  double* wV = Esm + CH * kmax;           // CH
+  double* Lsm = wV + CH;                  // CH * 3 * NP1
+  double* Pacc = Lsm + CH * 3 * NP1;      // kmax * NL
+  double* Qacc = Pacc + kmax * NL;        // kmax * kmax
+  const int tid = threadIdx.x;
+  for (int i = tid; i < k * NL; i += blockDim.x) Pacc[i] = 0.0;
+  for (int i = tid; i < k * k; i += blockDim.x) Qacc[i] = 0.0;
+  const int64_t qb = qoff[e], qe = qoff[e + 1];
+  for (int64_t q0 = qb; q0 < qe; q0 += CH) {
+    const int np = (int)min((int64_t)CH, qe - q0);
+    __syncthreads();
+    if (tid < CH * 3) {
+      const int p = tid / 3, d = tid % 3;
+      if (p < np) lagrange_dev(re.z, 2.0 * (qpts[4 * (q0 + p) + d] - lo[d]) / h[d] - 1.0, Lsm + (p * 3 + d) * NP1);
+    }
+    if (tid < CH) wV[tid] = (tid < np) ? qpts[4 * (q0 + tid) + 3] * V[q0 + tid] : 0.0;
+    for (int idx = tid; idx < CH * k; idx += blockDim.x) {
+      const int p = idx / k, a = idx % k;
+      double v = 0.0;
+      if (p < np) {
+        const double* x = qpts + 4 * (q0 + p);
+        v = eval_func_value(funcs[fl[a]], x[0], x[1], x[2]);
+      }
+      Esm[p * kmax + a] = v;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < CH * NL; idx += blockDim.x) {
+      const int p = idx / NL, jl = idx % NL;
+      const double* Lp = Lsm + p * 3 * NP1;
+      Bsm[idx] = (p < np) ? Lp[jl % NP1] * Lp[NP1 + (jl / NP1) % NP1] * Lp[2 * NP1 + jl / (NP1 * NP1)] : 0.0;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < k * NL; idx += blockDim.x) {
+      const int a = idx / NL, jl = idx % NL;
+      double s = 0.0;
+      for (int p = 0; p < np; ++p) s = fma(wV[p] * Esm[p * kmax + a], Bsm[p * NL + jl], s);
+      Pacc[idx] += s;
+    }
+    for (int idx = tid; idx < k * k; idx += blockDim.x) {
+      const int a = idx / k, b = idx % k;
+      double s = 0.0;
+      for (int p = 0; p < np; ++p) s = fma(wV[p] * Esm[p * kmax + a], Esm[p * kmax + b], s);
+      Qacc[idx] += s;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < k * NL; i += blockDim.x) Pblk[blkP_off[ei] + i] = Pacc[i];
+  for (int i = tid; i < k * k; i += blockDim.x) Qblk[blkQ_off[ei] + i] = Qacc[i];
+}
+
+__global__ void k_gather_sum(int64_t n, const double* __restrict__ base, const int64_t* __restrict__ cptr,
+                             const int64_t* __restrict__ cidx, const double* __restrict__ blk,
+                             double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = base ? base[i] : 0.0;
+  for (int64_t q = cptr[i]; q < cptr[i + 1]; ++q) v += blk[cidx[q]];
+  out[i] = v;
+}
+
+__global__ void k_permute(int64_t n, const double* __restrict__ src, const int64_t* __restrict__ perm,
+                          double* __restrict__ dst) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[perm[i]];
+}
+
+__global__ void k_to_f32(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) d[i] = (float)s[i];
+}
+
+__global__ void k_to_bf16(const double* __restrict__ s, __nv_bfloat16* __restrict__ d, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) d[i] = __double2bfloat16(s[i]);
+}
+
+// ---------------------------------------------------------------------------
+// hot path
+// ---------------------------------------------------------------------------
+// W_c(nodes of e) += H_e Y_e for every cell e of one parity colour.  Cells of
+// one colour share no node, so the read-modify-write scatter needs no atomics.
+// CTA = (cell, 32-column tile); 256 threads in 4 x 4 register blocks.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cell_apply(const T* __restrict__ Hcc, const int32_t* __restrict__ cells,
+                                                    MeshDev m, const T* __restrict__ Y, int64_t ldy,
+                                                    T* __restrict__ W, int64_t ldw, int N) {
+  const int64_t e = cells[blockIdx.x];
+  const int c0 = blockIdx.y * 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int64_t* gnode = reinterpret_cast<int64_t*>(smraw);                          // NL
+  T(*Ys)[33] = reinterpret_cast<T(*)[33]>(smraw + sizeof(int64_t) * 128);       // NL x 33
+  T(*Hs)[26] = reinterpret_cast<T(*)[26]>(smraw + sizeof(int64_t) * 128 + sizeof(T) * NL * 33);  // 128 x 26
+  const int tid = threadIdx.x;
+  const int i = (int)(e % m.nc[0]), j = (int)((e / m.nc[0]) % m.nc[1]), k = (int)(e / ((int64_t)m.nc[0] * m.nc[1]));
+  const int64_t NX = m.nn[0], NY = m.nn[1];
+  if (tid < NL) {
+    const int a = tid % NP1, b = (tid / NP1) % NP1, c = tid / (NP1 * NP1);
+    gnode[tid] = (int64_t)(P * i + a) + NX * ((int64_t)(P * j + b) + NY * (int64_t)(P * k + c));
+  }
+  if (tid < 3 * 26) Hs[125 + tid / 26][tid % 26] = T(0);
+  __syncthreads();
+  for (int idx = tid; idx < NL * 32; idx += 256) {
+    const int r = idx / 32, cc = idx % 32;
+    const int col = c0 + cc;
+    Ys[r][cc] = (col < N) ? Y[gnode[r] * ldy + col] : T(0);
+  }
+  const int ty = tid / 8, tx = tid % 8;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  const T* He = Hcc + e * (int64_t)(NL * NL);
+  for (int kc = 0; kc < NL; kc += 25) {
+    __syncthreads();
+    for (int idx = tid; idx < NL * 25; idx += 256) {
+      const int r = idx / 25, kk = idx % 25;
+      Hs[r][kk] = He[r * NL + kc + kk];
+    }
+    __syncthreads();
+#pragma unroll 5
+    for (int kk = 0; kk < 25; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = Hs[ty * 4 + a][kk];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Ys[kc + kk][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = ty * 4 + a;
+    if (r >= NL) continue;
+    T* wr = W + gnode[r] * ldw;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int col = c0 + tx * 4 + b;
+      if (col < N) wr[col] += acc[a][b];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_spmm_nodes(int64_t nrows, const int32_t* __restrict__ rnode, const int64_t* __restrict__ ptr,
+                             const int32_t* __restrict__ col, const double* __restrict__ val, double sgn,
+                             const double* __restrict__ Xe, int64_t ldxe, T* __restrict__ out, int64_t ldo, int N) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  const int64_t g = rnode[w];
+  const int64_t q0 = ptr[w], q1 = ptr[w + 1];
+  for (int c = lane; c < N; c += 32) {
+    double s = 0.0;
+    for (int64_t q = q0; q < q1; ++q) s = fma(val[q], Xe[(int64_t)col[q] * ldxe + c], s);
+    T* o = out + g * ldo + c;
+    *o = (T)((double)(*o) + sgn * s);
+  }
+}
+
+template <typename T>
+__global__ void k_spmm_segments(const int64_t* __restrict__ seg_start, const int64_t* __restrict__ seg_end,
+                                const int32_t* __restrict__ col, const double* __restrict__ val,
+                                const double* __restrict__ scale, const T* __restrict__ Xc, int64_t ldx,
+                                double* __restrict__ part, int N) {
+  const int64_t seg = blockIdx.x;
+  const int64_t q0 = seg_start[seg], q1 = seg_end[seg];
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    double s = 0.0;
+    for (int64_t q = q0; q < q1; ++q) {
+      const int64_t g = col[q];
+      const double v = scale ? val[q] * scale[g] : val[q];
+      s = fma(v, (double)Xc[g * ldx + c], s);
+    }
+    part[seg * N + c] = s;
+  }
+}
+
+__global__ void k_seg_reduce(int nrows, const int64_t* __restrict__ row_seg_ptr, const double* __restrict__ part,
+                             double sgn, const double* __restrict__ base, int64_t ldb, double alpha_base,
+                             double* __restrict__ out, int64_t ldo, int N) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nrows * N) return;
+  const int r = (int)(idx / N), c = (int)(idx % N);
+  double s = 0.0;
+  for (int64_t sg = row_seg_ptr[r]; sg < row_seg_ptr[r + 1]; ++sg) s += part[sg * N + c];
+  double v = sgn * s;
+  if (base) v += alpha_base * base[(int64_t)r * ldb + c];
+  out[(int64_t)r * ldo + c] = v;
+}
+
+template <typename T>
+__global__ void k_cheb_combine(int64_t nrows, const double* __restrict__ rowscale, const T* __restrict__ X,
+                               int64_t ldx, const T* __restrict__ Yc, int64_t ldc, const T* __restrict__ Yp,
+                               int64_t ldp, T* __restrict__ Yn, int64_t ldn, double alpha, double cc, double beta,
+                               int N) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nrows * N) return;
+  const int64_t r = idx / N;
+  const int c = (int)(idx % N);
+  double x = (double)X[r * ldx + c];
+  if (rowscale) x *= rowscale[r];
+  double y = alpha * (x - cc * (double)Yc[r * ldc + c]);
+  if (Yp) y += beta * (double)Yp[r * ldp + c];
+  Yn[r * ldn + c] = (T)y;
+}
+
+template <typename T>
+__global__ void k_row_scale(int64_t nrows, const double* __restrict__ s, const T* __restrict__ X, int64_t ldx,
+                            T* __restrict__ Y, int64_t ldy, int N) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nrows * N) return;
+  const int64_t r = idx / N;
+  const int c = (int)(idx % N);
+  Y[r * ldy + c] = (T)(s[r] * (double)X[r * ldx + c]);
+}
+
+template <typename S, typename D>
+__global__ void k_convert_rows(int64_t nrows, const S* __restrict__ X, int64_t ldx, D* __restrict__ Y, int64_t ldy,
+                               int N) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nrows * N) return;
+  const int64_t r = idx / N;
+  const int c = (int)(idx % N);
+  Y[r * ldy + c] = (D)X[r * ldx + c];
+}
+
+template <typename T>
+__global__ void k_zero_rows(int64_t nrows, T* __restrict__ X, int64_t ldx, int N) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nrows * N) return;
+  X[(idx / N) * ldx + idx % N] = T(0);
+}
+
+// ---------------------------------------------------------------------------
+// dense FP64
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gemm_nn(int64_t M, int Nc, int K, double alpha,
+                                                 const double* __restrict__ A, int64_t lda,
+                                                 const double* __restrict__ B, int64_t ldb, double beta,
+                                                 double* __restrict__ C, int64_t ldc) {
+  __shared__ double As[16][65];
+  __shared__ double Bs[16][65];
+  const int64_t row0 = (int64_t)blockIdx.x * 64;
+  const int col0 = blockIdx.y * 64;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int idx = tid; idx < 1024; idx += 256) {
+      const int r = idx / 16, kk = idx % 16;
+      As[kk][r] = (row0 + r < M && k0 + kk < K) ? A[(row0 + r) * lda + k0 + kk] : 0.0;
+      const int kb = idx / 64, cc = idx % 64;
+      Bs[kb][cc] = (k0 + kb < K && col0 + cc < Nc) ? B[(int64_t)(k0 + kb) * ldb + col0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t r = row0 + ty * 4 + a;
+    if (r >= M) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = col0 + tx * 4 + b;
+      if (c >= Nc) continue;
+      double v = alpha * acc[a][b];
+      if (beta != 0.0) v += beta * C[r * ldc + c];
+      C[r * ldc + c] = v;
+    }
+  }
+}
+
+constexpr int64_t TN_KC = 8192;
+
+__global__ void __launch_bounds__(256) k_gemm_tn_part(int64_t K, int Na, int Nb, const double* __restrict__ A,
+                                                      int64_t lda, const double* __restrict__ B, int64_t ldb,
+                                                      double* __restrict__ part) {
+  __shared__ double As[16][65];
+  __shared__ double Bs[16][65];
+  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+  const int64_t kb = (int64_t)blockIdx.z * TN_KC;
+  const int64_t ke = min(K, kb + TN_KC);
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  double acc[4][4] = {};
+  for (int64_t k0 = kb; k0 < ke; k0 += 16) {
+    for (int idx = tid; idx < 1024; idx += 256) {
+      const int kk = idx / 64, c = idx % 64;
+      const bool okk = k0 + kk < ke;
+      As[kk][c] = (okk && i0 + c < Na) ? A[(k0 + kk) * lda + i0 + c] : 0.0;
+      Bs[kk][c] = (okk && j0 + c < Nb) ? B[(k0 + kk) * ldb + j0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  double* P = part + (int64_t)blockIdx.z * Na * Nb;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int r = i0 + ty * 4 + a;
+    if (r >= Na) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = j0 + tx * 4 + b;
+      if (c < Nb) P[(int64_t)r * Nb + c] = acc[a][b];
+    }
+  }
+}
+
+__global__ void k_gemm_tn_reduce(int nsplit, int Na, int Nb, const double* __restrict__ part, double* __restrict__ C,
+                                 int64_t ldc) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)Na * Nb) return;
+  double s = 0.0;
+  for (int sp = 0; sp < nsplit; ++sp) s += part[(int64_t)sp * Na * Nb + idx];
+  C[(idx / Nb) * ldc + idx % Nb] = s;
+}
+
+// Right-looking Cholesky A = L L^T in one CTA (lower triangle; upper zeroed).
+__global__ void __launch_bounds__(1024) k_chol(double* A, int n, int lda, int* info) {
+  __shared__ double piv;
+  __shared__ int bad;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  if (tid == 0) bad = 0;
+  for (int j = 0; j < n; ++j) {
+    __syncthreads();
+    if (tid == 0) {
+      const double d = A[(int64_t)j * lda + j];
+      if (!(d > 0.0) || !isfinite(d)) bad = j + 1;
+      else { piv = sqrt(d); A[(int64_t)j * lda + j] = piv; }
+    }
+    __syncthreads();
+    if (bad) break;
+    for (int i = j + 1 + tid; i < n; i += bd) A[(int64_t)i * lda + j] /= piv;
+    __syncthreads();
+    const int64_t mm = n - j - 1;
+    const int64_t tot = mm * (mm + 1) / 2;
+    for (int64_t t = tid; t < tot; t += bd) {
+      int64_t ii = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+      while (ii * (ii + 1) / 2 > t) --ii;
+      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+      const int64_t cc = t - ii * (ii + 1) / 2;
+      const int i = j + 1 + (int)ii, c = j + 1 + (int)cc;
+      A[(int64_t)i * lda + c] -= A[(int64_t)i * lda + j] * A[(int64_t)c * lda + j];
+    }
+  }
+  __syncthreads();
+  for (int64_t t = tid; t < (int64_t)n * n; t += bd) {
+    const int i = (int)(t / n), c = (int)(t % n);
+    if (c > i) A[(int64_t)i * lda + c] = 0.0;
+  }
+  if (tid == 0) *info = bad;
+}
+
+// Li = L^-1 (lower), one column per thread by forward substitution.
+__global__ void k_trinv_lower(const double* __restrict__ L, int n, int lda, double* __restrict__ Li, int ldi) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    for (int i = 0; i < j; ++i) Li[(int64_t)i * ldi + j] = 0.0;
+    for (int i = j; i < n; ++i) {
+      double v = (i == j) ? 1.0 : 0.0;
+      for (int k = j; k < i; ++k) v -= L[(int64_t)i * lda + k] * Li[(int64_t)k * ldi + j];
+      Li[(int64_t)i * ldi + j] = v / L[(int64_t)i * lda + i];
+    }
+  }
+}
+
+__global__ void k_transpose(const double* __restrict__ A, int n, int lda, double* __restrict__ B, int ldb) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  B[(int64_t)j * ldb + i] = A[(int64_t)i * lda + j];
+}
+
+__global__ void k_symmetrize(double* A, int n, int lda) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  if (j <= i) return;
+  const double v = 0.5 * (A[(int64_t)i * lda + j] + A[(int64_t)j * lda + i]);
+  A[(int64_t)i * lda + j] = v;
+  A[(int64_t)j * lda + i] = v;
+}
+
+// Parallel cyclic Jacobi (round-robin pairing) for a symmetric n x n matrix in
+// one CTA: A <- J^T A J with disjoint rotations per round, V <- V J.
+__global__ void __launch_bounds__(1024) k_jacobi(double* A, int n, int lda, double* V, int ldv, double* w,
+                                                 int max_sweeps, int* info) {
+  __shared__ double cs[1024], sn[1024];
+  __shared__ int pp[1024], qq[1024];
+  __shared__ double red[2][32];
+  __shared__ int done;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int n2 = n + (n & 1);
+  const int np = n2 / 2;
+  for (int64_t t = tid; t < (int64_t)n * n; t += bd) V[(t / n) * ldv + t % n] = (t / n == t % n) ? 1.0 : 0.0;
+  if (tid == 0) done = 0;
+  int sweep = 0;
+  for (; sweep <= max_sweeps; ++sweep) {
+    __syncthreads();
+    double off = 0.0, tot = 0.0;
+    for (int64_t t = tid; t < (int64_t)n * n; t += bd) {
+      const double a = A[(t / n) * lda + t % n];
+      tot += a * a;
+      if (t / n != t % n) off += a * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_down_sync(0xffffffffu, off, o);
+      tot += __shfl_down_sync(0xffffffffu, tot, o);
+    }
+    if ((tid & 31) == 0) { red[0][tid >> 5] = off; red[1][tid >> 5] = tot; }
+    __syncthreads();
+    if (tid == 0) {
+      double so = 0.0, st = 0.0;
+      for (int i = 0; i < (bd + 31) / 32; ++i) { so += red[0][i]; st += red[1][i]; }
+      done = (so <= 1e-30 * st) ? 1 : 0;
+    }
+    __syncthreads();
+    if (done || sweep == max_sweeps) break;
+    for (int r = 0; r < n2 - 1; ++r) {
+      for (int k = tid; k < np; k += bd) {
+        const int s1 = k, s2 = n2 - 1 - k;
+        const int pl1 = (s1 == 0) ? 0 : ((s1 - 1 + r) % (n2 - 1)) + 1;
+        const int pl2 = (s2 == 0) ? 0 : ((s2 - 1 + r) % (n2 - 1)) + 1;
+        const int p = min(pl1, pl2), q = max(pl1, pl2);
+        if (q >= n) { pp[k] = -1; continue; }
+        const double apq = A[(int64_t)p * lda + q];
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0) {
+          const double app = A[(int64_t)p * lda + p], aqq = A[(int64_t)q * lda + q];
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s;
+      }
+      __syncthreads();
+      for (int64_t t = tid; t < (int64_t)n * np; t += bd) {
+        const int i = (int)(t / np), k = (int)(t % np);
+        const int p = pp[k];
+        if (p < 0) continue;
+        const int q = qq[k];
+        const double c = cs[k], s = sn[k];
+        double* Ai = A + (int64_t)i * lda;
+        const double aip = Ai[p], aiq = Ai[q];
+        Ai[p] = c * aip - s * aiq;
+        Ai[q] = s * aip + c * aiq;
+        double* Vi = V + (int64_t)i * ldv;
+        const double vip = Vi[p], viq = Vi[q];
+        Vi[p] = c * vip - s * viq;
+        Vi[q] = s * vip + c * viq;
+      }
+      __syncthreads();
+      for (int64_t t = tid; t < (int64_t)n * np; t += bd) {
+        const int j = (int)(t / np), k = (int)(t % np);
+        const int p = pp[k];
+        if (p < 0) continue;
+        const int q = qq[k];
+        const double c = cs[k], s = sn[k];
+        const double apj = A[(int64_t)p * lda + j], aqj = A[(int64_t)q * lda + j];
+        A[(int64_t)p * lda + j] = c * apj - s * aqj;
+        A[(int64_t)q * lda + j] = s * apj + c * aqj;
+      }
+      __syncthreads();
+      for (int k = tid; k < np; k += bd) {
+        const int p = pp[k];
+        if (p < 0) continue;
+        A[(int64_t)p * lda + qq[k]] = 0.0;
+        A[(int64_t)qq[k] * lda + p] = 0.0;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += bd) w[i] = A[(int64_t)i * lda + i];
+  if (tid == 0) *info = done ? 0 : 1;
+}
+
+__global__ void k_sort_eig(const double* __restrict__ w, const double* __restrict__ V, int n, int ldv,
+                           double* __restrict__ ws, double* __restrict__ Vs, int ldvs) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int rank = 0;
+    const double wi = w[i];
+    for (int j = 0; j < n; ++j) rank += (w[j] < wi || (w[j] == wi && j < i)) ? 1 : 0;
+    ws[rank] = wi;
+    for (int r = 0; r < n; ++r) Vs[(int64_t)r * ldvs + rank] = V[(int64_t)r * ldv + i];
+  }
+}
+
+constexpr int RN_ROWS = 2048;
+
+__global__ void k_resid_part(int64_t nrows, const double* __restrict__ HX, int64_t ldh, const double* __restrict__ MX,
+                             int64_t ldm, const double* __restrict__ eps, int N, double* __restrict__ part) {
+  const int64_t r0 = (int64_t)blockIdx.x * RN_ROWS;
+  const int64_t r1 = min(nrows, r0 + RN_ROWS);
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    const double ec = eps[c];
+    double s = 0.0;
+    for (int64_t r = r0; r < r1; ++r) {
+      const double d = HX[r * ldh + c] - ec * MX[r * ldm + c];
+      s = fma(d, d, s);
+    }
+    part[(int64_t)blockIdx.x * N + c] = s;
+  }
+}
+
+__global__ void k_resid_final(int nb, int N, const double* __restrict__ part, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(int64_t)b * N + c];
+  out[c] = sqrt(s);
+}
+
+__global__ void k_dot_part(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                           double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(x[i], y[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) t += red[i];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_dot_final(int nb, const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    *out = s;
+  }
+}
+
+__global__ void k_axpby3(int64_t n, double* __restrict__ w, const double* __restrict__ v,
+                         const double* __restrict__ vp, double a, double b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) w[i] = w[i] - a * v[i] - b * vp[i];
+}
+
+__global__ void k_scale(int64_t n, const double* __restrict__ x, double s, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = s * x[i];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_potential_analytic(const double* qpts, int64_t nq, const double* axyz, const double* aZ, int na,
+                               int nuclear, const double* gA, const double* gs, const double* gc, int nt,
+                               double omega, double* V, cudaStream_t st) {
+  if (nq <= 0) return;
+  k_potential<<<grid1(nq, 256), 256, 0, st>>>(qpts, nq, axyz, aZ, na, nuclear, gA, gs, gc, nt, omega, V);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st) {
+  if (n <= 0) return;
+  k_check_finite<<<(grid1(n, 256) < 4096u ? grid1(n, 256) : 4096u), 256, 0, st>>>(x, n, flag);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_hcc_build(const RefElem& re, const MeshDev& m, const int64_t* qoff, const double* qpts,
+                      const double* V, int64_t n_cell, double* Hcc, cudaStream_t st) {
+  if (n_cell <= 0) return;
+  k_hcc_build<<<(unsigned)n_cell, 256, 0, st>>>(re, m, qoff, qpts, V, Hcc);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_enr_blocks(const RefElem& re, const MeshDev& m, const int32_t* enr_cells, int64_t n_enr,
+                       const int32_t* cf_ptr, const int32_t* cf_idx, const DevFunc* funcs, const int64_t* qoff,
+                       const double* qpts, const double* V, const int64_t* blkP_off, const int64_t* blkQ_off,
+                       int kmax, double* Pblk, double* Qblk, cudaStream_t st) {
+  if (n_enr <= 0) return;
+  const size_t smem = sizeof(double) * (32 * NL + 32 * kmax + 32 + 32 * 3 * NP1 + kmax * NL + kmax * kmax);
+  cudaFuncSetAttribute(k_enr_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_enr_blocks<<<(unsigned)n_enr, 128, smem, st>>>(re, m, enr_cells, cf_ptr, cf_idx, funcs, qoff, qpts, V, blkP_off,
+                                                   blkQ_off, kmax, Pblk, Qblk);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_gather_sum(int64_t n_out, const double* base, const int64_t* cptr, const int64_t* cidx,
+                       const double* blk, double* out, cudaStream_t st) {
+  if (n_out <= 0) return;
+  k_gather_sum<<<grid1(n_out, 256), 256, 0, st>>>(n_out, base, cptr, cidx, blk, out);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_permute(int64_t n, const double* src, const int64_t* perm, double* dst, cudaStream_t st) {
+  if (n <= 0) return;
+  k_permute<<<grid1(n, 256), 256, 0, st>>>(n, src, perm, dst);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_to_f32<<<grid1(n, 256), 256, 0, st>>>(src, dst, n);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_to_bf16(const double* src, void* dst, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_to_bf16<<<grid1(n, 256), 256, 0, st>>>(src, (__nv_bfloat16*)dst, n);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_cell_apply_f64(const double* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                           const double* Y, int64_t ldy, double* W, int64_t ldw, int N, cudaStream_t st) {
+  if (ncells <= 0 || N <= 0) return;
+  dim3 g((unsigned)ncells, (unsigned)((N + 31) / 32));
+  const size_t smem = sizeof(int64_t) * 128 + sizeof(double) * (NL * 33 + 128 * 26);
+  cudaFuncSetAttribute(k_cell_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_cell_apply<double><<<g, 256, smem, st>>>(Hcc, cells, m, Y, ldy, W, ldw, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_cell_apply_f32(const float* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                           const float* Y, int64_t ldy, float* W, int64_t ldw, int N, cudaStream_t st) {
+  if (ncells <= 0 || N <= 0) return;
+  dim3 g((unsigned)ncells, (unsigned)((N + 31) / 32));
+  const size_t smem = sizeof(int64_t) * 128 + sizeof(float) * (NL * 33 + 128 * 26);
+  cudaFuncSetAttribute(k_cell_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_cell_apply<float><<<g, 256, smem, st>>>(Hcc, cells, m, Y, ldy, W, ldw, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+template <typename T>
+void launch_spmm_nodes(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
+                       const double* val, double sgn, const double* Xe, int64_t ldxe, T* out, int64_t ldo, int N,
+                       cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_spmm_nodes<T><<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out, ldo, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+template void launch_spmm_nodes<double>(int64_t, const int32_t*, const int64_t*, const int32_t*, const double*,
+                                        double, const double*, int64_t, double*, int64_t, int, cudaStream_t);
+template void launch_spmm_nodes<float>(int64_t, const int32_t*, const int64_t*, const int32_t*, const double*,
+                                       double, const double*, int64_t, float*, int64_t, int, cudaStream_t);
+
+template <typename T>
+void launch_spmm_segments(int64_t nseg, const int64_t* seg_start, const int64_t* seg_end, const int32_t* col,
+                          const double* val, const double* scale, const T* Xc, int64_t ldx, double* part, int N,
+                          cudaStream_t st) {
+  if (nseg <= 0 || N <= 0) return;
+  const int t = N >= 128 ? 128 : ((N + 31) / 32) * 32;
+  k_spmm_segments<T><<<(unsigned)nseg, t, 0, st>>>(seg_start, seg_end, col, val, scale, Xc, ldx, part, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+template void launch_spmm_segments<double>(int64_t, const int64_t*, const int64_t*, const int32_t*, const double*,
+                                           const double*, const double*, int64_t, double*, int, cudaStream_t);
+template void launch_spmm_segments<float>(int64_t, const int64_t*, const int64_t*, const int32_t*, const double*,
+                                          const double*, const float*, int64_t, double*, int, cudaStream_t);
+
+void launch_seg_reduce(int nrows, const int64_t* row_seg_ptr, const double* part, double sgn, const double* base,
+                       int64_t ldb, double alpha_base, double* out, int64_t ldo, int N, cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_seg_reduce<<<grid1((int64_t)nrows * N, 256), 256, 0, st>>>(nrows, row_seg_ptr, part, sgn, base, ldb, alpha_base,
+                                                                out, ldo, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+template <typename T>
+void launch_cheb_combine(int64_t nrows, const double* rowscale, const T* Xsrc, int64_t ldx, const T* Ycur,
+                         int64_t ldc, const T* Yprev, int64_t ldp, T* Ynew, int64_t ldn, double alpha, double c,
+                         double beta, int N, cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_cheb_combine<T><<<grid1(nrows * N, 256), 256, 0, st>>>(nrows, rowscale, Xsrc, ldx, Ycur, ldc, Yprev, ldp, Ynew,
+                                                           ldn, alpha, c, beta, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+template void launch_cheb_combine<double>(int64_t, const double*, const double*, int64_t, const double*, int64_t,
+                                          const double*, int64_t, double*, int64_t, double, double, double, int,
+                                          cudaStream_t);
+template void launch_cheb_combine<float>(int64_t, const double*, const float*, int64_t, const float*, int64_t,
+                                         const float*, int64_t, float*, int64_t, double, double, double, int,
+                                         cudaStream_t);
+
+template <typename T>
+void launch_row_scale(int64_t nrows, const double* rowscale, const T* X, int64_t ldx, T* Y, int64_t ldy, int N,
+                      cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_row_scale<T><<<grid1(nrows * N, 256), 256, 0, st>>>(nrows, rowscale, X, ldx, Y, ldy, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+template void launch_row_scale<double>(int64_t, const double*, const double*, int64_t, double*, int64_t, int,
+                                       cudaStream_t);
+template void launch_row_scale<float>(int64_t, const double*, const float*, int64_t, float*, int64_t, int,
+                                      cudaStream_t);
+
+void launch_f64_to_f32_rows(int64_t nrows, const double* X, int64_t ldx, float* Y, int64_t ldy, int N,
+                            cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_convert_rows<double, float><<<grid1(nrows * N, 256), 256, 0, st>>>(nrows, X, ldx, Y, ldy, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_f32_to_f64_rows(int64_t nrows, const float* X, int64_t ldx, double* Y, int64_t ldy, int N,
+                            cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_convert_rows<float, double><<<grid1(nrows * N, 256), 256, 0, st>>>(nrows, X, ldx, Y, ldy, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_copy_rows(int64_t nrows, const double* X, int64_t ldx, double* Y, int64_t ldy, int N, cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_convert_rows<double, double><<<grid1(nrows * N, 256), 256, 0, st>>>(nrows, X, ldx, Y, ldy, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_zero_rows(int64_t nrows, double* X, int64_t ldx, int N, cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_zero_rows<double><<<grid1(nrows * N, 256), 256, 0, st>>>(nrows, X, ldx, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_zero_rows_f32(int64_t nrows, float* X, int64_t ldx, int N, cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_zero_rows<float><<<grid1(nrows * N, 256), 256, 0, st>>>(nrows, X, ldx, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_gemm_nn(int64_t M, int Nc, int K, double alpha, const double* A, int64_t lda, const double* B,
+                    int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st) {
+  if (M <= 0 || Nc <= 0) return;
+  dim3 g((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
+  k_gemm_nn<<<g, 256, 0, st>>>(M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+int64_t gemm_tn_work_elems(int64_t K, int Na, int Nb) {
+  const int64_t nsplit = (K + TN_KC - 1) / TN_KC;
+  return (nsplit < 1 ? 1 : nsplit) * (int64_t)Na * Nb;
+}
+
+void launch_gemm_tn(int64_t K, int Na, int Nb, const double* A, int64_t lda, const double* B, int64_t ldb,
+                    double* C, int64_t ldc, double* work, int64_t work_elems, cudaStream_t st) {
+  if (Na <= 0 || Nb <= 0) return;
+  int64_t nsplit = (K + TN_KC - 1) / TN_KC;
+  if (nsplit < 1) nsplit = 1;
+  (void)work_elems;
+  dim3 g((unsigned)((Na + 63) / 64), (unsigned)((Nb + 63) / 64), (unsigned)nsplit);
+  k_gemm_tn_part<<<g, 256, 0, st>>>(K, Na, Nb, A, lda, B, ldb, work);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_gemm_tn_reduce<<<grid1((int64_t)Na * Nb, 256), 256, 0, st>>>((int)nsplit, Na, Nb, work, C, ldc);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_chol(double* A, int n, int lda, int* info, cudaStream_t st) {
+  k_chol<<<1, 1024, 0, st>>>(A, n, lda, info);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_trinv_lower(const double* L, int n, int lda, double* Li, int ldi, cudaStream_t st) {
+  k_trinv_lower<<<grid1(n, 128), 128, 0, st>>>(L, n, lda, Li, ldi);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_transpose(const double* A, int n, int lda, double* B, int ldb, cudaStream_t st) {
+  k_transpose<<<grid1((int64_t)n * n, 256), 256, 0, st>>>(A, n, lda, B, ldb);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_symmetrize(double* A, int n, int lda, cudaStream_t st) {
+  k_symmetrize<<<grid1((int64_t)n * n, 256), 256, 0, st>>>(A, n, lda);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_jacobi(double* A, int n, int lda, double* V, int ldv, double* w, int max_sweeps, int* info,
+                   cudaStream_t st) {
+  k_jacobi<<<1, 1024, 0, st>>>(A, n, lda, V, ldv, w, max_sweeps, info);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_sort_eig(const double* w, const double* V, int n, int ldv, double* ws, double* Vs, int ldvs,
+                     cudaStream_t st) {
+  k_sort_eig<<<grid1(n, 128), 128, 0, st>>>(w, V, n, ldv, ws, Vs, ldvs);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_resid_norms(int64_t nrows, const double* HX, int64_t ldh, const double* MX, int64_t ldm,
+                        const double* eps, int N, double* part, double* out, cudaStream_t st) {
+  const int nb = (int)((nrows + RN_ROWS - 1) / RN_ROWS);
+  k_resid_part<<<nb, 128, 0, st>>>(nrows, HX, ldh, MX, ldm, eps, N, part);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_resid_final<<<grid1(N, 128), 128, 0, st>>>(nb, N, part, out);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_dot(int64_t n, const double* x, const double* y, double* part, double* out, cudaStream_t st) {
+  k_dot_part<<<256, 256, 0, st>>>(n, x, y, part);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  k_dot_final<<<1, 32, 0, st>>>(256, part, out);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_axpby3(int64_t n, double* w, const double* v, const double* vp, double a, double b, cudaStream_t st) {
+  k_axpby3<<<grid1(n, 256), 256, 0, st>>>(n, w, v, vp, a, b);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_scale(int64_t n, const double* x, double s, double* y, cudaStream_t st) {
+  k_scale<<<grid1(n, 256), 256, 0, st>>>(n, x, s, y);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+}  // namespace efe

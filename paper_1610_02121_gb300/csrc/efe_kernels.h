@@ -1,0 +1,105 @@
+// Launchers of the library's CUDA kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "efe_internal.h"
+
+#include <atomic>
+
+namespace efe {
+
+// number of kernels launched by this library since it was loaded
+extern std::atomic<int64_t> g_launches;
+
+// Reference element and mesh geometry passed by value to the set-up kernels.
+struct RefElem {
+  double z[NP1], w[NP1];
+  double M1[NP1 * NP1], K1[NP1 * NP1];
+};
+
+struct MeshDev {
+  int nc[3];
+  int nn[3];
+  const double* brk;  // concatenated break points: x (nc0+1), y (nc1+1), z (nc2+1)
+};
+
+// ---- set-up / set_potential ----
+void launch_potential_analytic(const double* qpts, int64_t nq, const double* axyz, const double* aZ, int na,
+                               int nuclear, const double* gA, const double* gs, const double* gc, int nt,
+                               double omega, double* V, cudaStream_t st);
+void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st);
+void launch_hcc_build(const RefElem& re, const MeshDev& m, const int64_t* qoff, const double* qpts,
+                      const double* V, int64_t n_cell, double* Hcc, cudaStream_t st);
+void launch_enr_blocks(const RefElem& re, const MeshDev& m, const int32_t* enr_cells, int64_t n_enr,
+                       const int32_t* cf_ptr, const int32_t* cf_idx, const DevFunc* funcs, const int64_t* qoff,
+                       const double* qpts, const double* V, const int64_t* blkP_off, const int64_t* blkQ_off,
+                       int kmax, double* Pblk, double* Qblk, cudaStream_t st);
+void launch_gather_sum(int64_t n_out, const double* base, const int64_t* cptr, const int64_t* cidx,
+                       const double* blk, double* out, cudaStream_t st);
+void launch_permute(int64_t n, const double* src, const int64_t* perm, double* dst, cudaStream_t st);
+void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
+void launch_to_bf16(const double* src, void* dst, int64_t n, cudaStream_t st);
+
+// ---- hot path (FP64 and FP32 storage) ----
+// W_c(cell nodes) += H_e Y_e for the cells of one parity colour
+void launch_cell_apply_f64(const double* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                           const double* Y, int64_t ldy, double* W, int64_t ldw, int N, cudaStream_t st);
+void launch_cell_apply_f32(const float* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                           const float* Y, int64_t ldy, float* W, int64_t ldw, int N, cudaStream_t st);
+// out[node_r] += sgn * sum_q val[q] * Xe[col[q]]   (rows = nodes that meet a support)
+template <typename T>
+void launch_spmm_nodes(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
+                       const double* val, double sgn, const double* Xe, int64_t ldxe, T* out, int64_t ldo,
+                       int N, cudaStream_t st);
+// part[seg] = sum_{q in seg} val[q] * scale[col[q]] * Xc[col[q]]  (scale may be NULL)
+template <typename T>
+void launch_spmm_segments(int64_t nseg, const int64_t* seg_start, const int64_t* seg_end, const int32_t* col,
+                          const double* val, const double* scale, const T* Xc, int64_t ldx, double* part,
+                          int N, cudaStream_t st);
+// out[r] = alpha_base * base[r] + sgn * sum_{segs of r} part[seg]
+void launch_seg_reduce(int nrows, const int64_t* row_seg_ptr, const double* part, double sgn,
+                       const double* base, int64_t ldb, double alpha_base, double* out, int64_t ldo, int N,
+                       cudaStream_t st);
+// Chebyshev combine: Ynew = alpha (x - c Ycur) + beta Yprev, x = scale_row * Xsrc
+template <typename T>
+void launch_cheb_combine(int64_t nrows, const double* rowscale, const T* Xsrc, int64_t ldx, const T* Ycur,
+                         int64_t ldc, const T* Yprev, int64_t ldp, T* Ynew, int64_t ldn, double alpha, double c,
+                         double beta, int N, cudaStream_t st);
+template <typename T>
+void launch_row_scale(int64_t nrows, const double* rowscale, const T* X, int64_t ldx, T* Y, int64_t ldy, int N,
+                      cudaStream_t st);
+void launch_f64_to_f32_rows(int64_t nrows, const double* X, int64_t ldx, float* Y, int64_t ldy, int N,
+                            cudaStream_t st);
+void launch_f32_to_f64_rows(int64_t nrows, const float* X, int64_t ldx, double* Y, int64_t ldy, int N,
+                            cudaStream_t st);
+void launch_copy_rows(int64_t nrows, const double* X, int64_t ldx, double* Y, int64_t ldy, int N,
+                      cudaStream_t st);
+void launch_zero_rows(int64_t nrows, double* X, int64_t ldx, int N, cudaStream_t st);
+void launch_zero_rows_f32(int64_t nrows, float* X, int64_t ldx, int N, cudaStream_t st);
+
+// ---- dense FP64 ----
+// C[M x Nc] = alpha * A[M x K] B[K x Nc] + beta * C   (row-major, lda/ldb/ldc)
+void launch_gemm_nn(int64_t M, int Nc, int K, double alpha, const double* A, int64_t lda, const double* B,
+                    int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st);
+// C[Na x Nb] = A^T B with A[K x Na], B[K x Nb], K large (split-K, deterministic reduce)
+void launch_gemm_tn(int64_t K, int Na, int Nb, const double* A, int64_t lda, const double* B, int64_t ldb,
+                    double* C, int64_t ldc, double* work, int64_t work_elems, cudaStream_t st);
+int64_t gemm_tn_work_elems(int64_t K, int Na, int Nb);
+void launch_chol(double* A, int n, int lda, int* info, cudaStream_t st);
+void launch_trinv_lower(const double* L, int n, int lda, double* Li, int ldi, cudaStream_t st);
+void launch_transpose(const double* A, int n, int lda, double* B, int ldb, cudaStream_t st);
+void launch_symmetrize(double* A, int n, int lda, cudaStream_t st);
+void launch_jacobi(double* A, int n, int lda, double* V, int ldv, double* w, int max_sweeps, int* info,
+                   cudaStream_t st);
+void launch_sort_eig(const double* w, const double* V, int n, int ldv, double* ws, double* Vs, int ldvs,
+                     cudaStream_t st);
+// per-column ||HX - eps MX||^2 partial sums, then sqrt
+void launch_resid_norms(int64_t nrows, const double* HX, int64_t ldh, const double* MX, int64_t ldm,
+                        const double* eps, int N, double* part, double* out, cudaStream_t st);
+void launch_dot(int64_t n, const double* x, const double* y, double* part, double* out, cudaStream_t st);
+void launch_axpby3(int64_t n, double* w, const double* v, const double* vp, double a, double b, cudaStream_t st);
+void launch_scale(int64_t n, const double* x, double s, double* y, cudaStream_t st);
+
+}  // namespace efe

@@ -1,0 +1,177 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Every comparison is element by element on the same seeded inputs.  FP64 mode
+must agree to rounding (relative 1e-11 for single products, 1e-9 after a
+degree-7 filter whose scaled polynomial amplifies rounding by its condition);
+the FP32-storage mode to 1e-5 relative (FP32 unit round-off 6e-8 times the
+filter's growth).  Eigenvalues in FP64 mode: 1e-6 Ha (spec tolerance).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_util import cuda_available, gpu_system, rel_err, to_dev, torch
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module")
+def tiny_pair():
+    from oracle.operators import Discretisation
+    s = W.tiny(seed=11)
+    return Discretisation(s), gpu_system(s)
+
+
+@pytest.fixture(scope="module")
+def ho_pair():
+    from oracle.operators import Discretisation
+    s = W.harmonic(cells=3, half=6.0)
+    return Discretisation(s), gpu_system(s)
+
+
+@pytest.mark.parametrize("N", [1, 7, 33, 70])
+def test_apply_H_M_Minv(tiny_pair, N):
+    d, G = tiny_pair
+    X = W.random_block(d.system, N, seed=100 + N)
+    Xd = to_dev(X)
+    assert rel_err(G.apply_H(Xd), d.apply_H_assembled(X)) < 1e-11
+    assert rel_err(G.apply_M(Xd), d.apply_M_assembled(X)) < 1e-12
+    assert rel_err(G.apply_Minv(Xd), d.apply_Minv_block(X)) < 1e-10
+
+
+def test_padded_leading_dimension(tiny_pair):
+    d, G = tiny_pair
+    X = W.random_block(d.system, 9, seed=7)
+    big = torch.zeros((X.shape[0], 16), dtype=torch.float64, device="cuda")
+    big[:, :9] = to_dev(X)
+    out = torch.full_like(big, 7.0)
+    G.apply_H(big[:, :9], out[:, :9])
+    assert rel_err(out[:, :9], d.apply_H_assembled(X)) < 1e-11
+    assert torch.all(out[:, 9:] == 7.0)       # columns beyond N untouched
+
+
+def test_classical_only_system(ho_pair):
+    d, G = ho_pair
+    X = W.random_block(d.system, 5, seed=3)
+    Xd = to_dev(X)
+    assert rel_err(G.apply_H(Xd), d.apply_H_assembled(X)) < 1e-11
+    assert rel_err(G.apply_Minv(Xd), d.apply_Minv_block(X)) < 1e-12
+
+
+def _bounds(d, N):
+    from oracle.chfsi import dense_eigs
+    H, M, act = d.dense_active()
+    import scipy.linalg as sla
+    ev = sla.eigh(H, M, eigvals_only=True)
+    return ev[N - 1], ev.max() * 1.05, ev[0]
+
+
+@pytest.mark.parametrize("N,m", [(10, 7), (33, 4)])
+def test_chfsi_step_fp64(tiny_pair, N, m):
+    from oracle.chfsi import chebyshev_filter_scaled
+    d, G = tiny_pair
+    X = W.initial_block(d.system, N, seed=1)
+    a, b, a0 = _bounds(d, N)
+    ref = chebyshev_filter_scaled(d.apply_Htilde, X, m, a, b, a0)
+    Xd = to_dev(X)
+    G.chfsi_step(Xd, m, a, b, a0, precision="fp64")
+    assert rel_err(Xd, ref) < 1e-9
+    # bitwise reproducible
+    Xd2 = to_dev(X)
+    G.chfsi_step(Xd2, m, a, b, a0, precision="fp64")
+    assert torch.equal(Xd, Xd2)
+
+
+@pytest.mark.parametrize("tail", [0, 2])
+def test_chfsi_step_fp32(tiny_pair, tail):
+    from oracle.chfsi import chebyshev_filter_scaled
+    d, G = tiny_pair
+    N, m = 12, 7
+    X = W.initial_block(d.system, N, seed=2)
+    a, b, a0 = _bounds(d, N)
+    ref = chebyshev_filter_scaled(d.apply_Htilde, X, m, a, b, a0)
+    Xd = to_dev(X)
+    G.chfsi_step(Xd, m, a, b, a0, precision="fp32", fp64_tail=tail)
+    err = rel_err(Xd, ref)
+    assert err < 2e-5, err
+
+
+def test_rayleigh_ritz_fp64(tiny_pair):
+    from oracle.chfsi import cholqr, rayleigh_ritz
+    d, G = tiny_pair
+    N = 10
+    X = W.initial_block(d.system, N, seed=4)
+    Q, _ = cholqr(X)
+    eps_ref, Xr, res_ref = rayleigh_ritz(d.apply_H_assembled, d.apply_M_assembled, Q)
+    Xd = to_dev(X)
+    eps, res = G.rayleigh_ritz(Xd)
+    np.testing.assert_allclose(eps, eps_ref, atol=1e-9, rtol=1e-10)
+    np.testing.assert_allclose(res, res_ref, atol=1e-8, rtol=1e-6)
+    # Ritz vectors are M-orthonormal: X^T M X = I
+    MX = G.apply_M(Xd)
+    gram = (Xd.T @ MX).cpu().numpy()
+    np.testing.assert_allclose(gram, np.eye(N), atol=1e-10)
+
+
+def test_upper_bound_matches_oracle(tiny_pair):
+    from oracle.chfsi import lanczos_upper_bound
+    d, G = tiny_pair
+    v0 = W.lanczos_start(d.system)
+    ref = lanczos_upper_bound(d.apply_Htilde, d.apply_M_assembled, v0, 10)
+    b = G.upper_bound(to_dev(v0), 10)
+    assert abs(b - ref) < 1e-8 * abs(ref)
+    H, M, act = d.dense_active()
+    import scipy.linalg as sla
+    assert b >= sla.eigh(H, M, eigvals_only=True).max() * (1 - 1e-12)
+
+
+def test_chfsi_converges_to_dense_tiny(tiny_pair):
+    from oracle.chfsi import dense_eigs
+    d, G = tiny_pair
+    N, m, nconv = 10, 12, 7
+    X = to_dev(W.initial_block(d.system, N, seed=1))
+    eps, res, it, b = G.solve(X, m, tol=1e-9, v0=to_dev(W.lanczos_start(d.system)), n_conv=nconv)
+    ref = dense_eigs(d, N)
+    assert res[:nconv].max() < 1e-9
+    np.testing.assert_allclose(eps[:nconv], ref[:nconv], atol=1e-9)
+
+
+def test_error_paths(tiny_pair):
+    from paper_1610_02121_gb300 import EfeError
+    d, G = tiny_pair
+    X = to_dev(W.initial_block(d.system, 4, seed=1))
+    with pytest.raises(EfeError) as e:
+        G.chfsi_step(X, 3, 1.0, 0.5, 0.0)            # a > b
+    assert e.value.code == 1
+    Xr = to_dev(W.initial_block(d.system, 4, seed=1))
+    Xr[:, 3] = Xr[:, 2]                               # rank-deficient block
+    with pytest.raises(EfeError) as e:
+        G.rayleigh_ritz(Xr)
+    assert e.value.code == 3
+    V = torch.full((G.n_qpoints,), float("nan"), dtype=torch.float64, device="cuda")
+    with pytest.raises(EfeError) as e:
+        G.set_potential(V)
+    assert e.value.code == 6
+    G.set_potential_analytic()                         # restore
+
+
+def test_hydrogen_config1_converged():
+    """6x6x6 cells, degree 4, 20-bohr box, hydrogenic enrichment, N = 8, m = 20, FP64,
+    residual < 1e-8: eigenvalues against the oracle's assembled problem (sparse
+    shift-invert, the plain definition) and the closed form -1/2 for 1s."""
+    import scipy.sparse.linalg as ssl
+    from oracle.operators import Discretisation
+    s = W.hydrogen()
+    G = gpu_system(s)
+    N, m, nconv = 8, 20, 5
+    X = to_dev(W.initial_block(s, N, seed=1))
+    eps, res, it, b = G.solve(X, m, tol=1e-8, v0=to_dev(W.lanczos_start(s)), n_conv=nconv)
+    assert res[:nconv].max() < 1e-8
+    d = Discretisation(s)
+    act = np.nonzero(d.active)[0]
+    H = d.H[act][:, act].tocsc()
+    M = d.M[act][:, act].tocsc()
+    ref = np.sort(ssl.eigsh(H, k=nconv, M=M, sigma=-0.6, which="LM")[0])
+    np.testing.assert_allclose(eps[:nconv], ref, atol=1e-6)
+    assert abs(eps[0] + 0.5) < 1e-3
+    assert np.ptp(eps[1:4]) < 1e-7          # 2p triplet (cubic symmetry about the nucleus)

@@ -190,7 +190,7 @@ def tiny(seed=11, cells=(2, 3, 2), n_gauss=6, with_enrichment=True, n_gaussians=
                    max_depth=max_depth, name=f"tiny_s{seed}")
 
 
-def si_cluster(n_cells_x=2, h_min=0.80, h_max=3.0, pad=10.0, r_c=4.0, seed=2,
+def si_cluster(n_cells_x=2, h_min=0.90, h_max=3.0, pad=10.0, r_c=4.0, seed=2,
                pot_seed=3, n_gaussians=32, tau=1e-9, max_depth=9):
     """16-atom silicon-like cluster (two conventional diamond cells along x,
     Z=14), graded degree-4 mesh, Slater 1s/2s/2p enrichment (5 per atom) with
