@@ -47,13 +47,15 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", default="si16", choices=["si16", "hydrogen"])
+    p.add_argument("--workload", default="si16", choices=["si16", "si16s", "hydrogen"])
     return p.parse_args()
 
 
 def workload(name):
     if name == "si16":
         return W.si_cluster(), N_VEC, M_DEG
+    if name == "si16s":  # coarser mesh of the same cluster (profiling captures)
+        return W.si_cluster(h_min=1.6, h_max=4.0), N_VEC, M_DEG
     return W.hydrogen(), 8, 20
 
 

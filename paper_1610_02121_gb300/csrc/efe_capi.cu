@@ -49,6 +49,9 @@ struct efe_handle {
   double* Hcc = nullptr;
   float* Hcc32 = nullptr;
   void* Hcc16 = nullptr;
+  float* Aimg32 = nullptr;  // tcgen05 A images (TF32 in FP32 words)
+  void* Aimg16 = nullptr;   // tcgen05 A images (BF16)
+  int tc_mode = 0;          // 1: cell products of the FP32 filter on tcgen05 (TF32)
   DevFunc* funcs = nullptr;
   int32_t *enr_cells = nullptr, *cf_ptr = nullptr, *cf_idx = nullptr;
   int64_t *blkP_off = nullptr, *blkQ_off = nullptr;
@@ -77,8 +80,9 @@ struct efe_handle {
   int64_t tnwork_elems = 0;
   double* rpart = nullptr;
   double* lz = nullptr;       // Lanczos vectors (6 * rows) + scalars
-  int Nres32 = 0;
-  float *Yf[3] = {nullptr, nullptr, nullptr}, *Wf = nullptr;
+  int Nres32 = 0, ld32 = 0, npc = 0, ncb = 0;
+  float *Yf[3] = {nullptr, nullptr, nullptr}, *Wf = nullptr, *cpart = nullptr;
+  float *mecT32 = nullptr, *hecT32 = nullptr;
   double* Ye[3] = {nullptr, nullptr, nullptr};
   // timing
   bool timing = false;
@@ -176,11 +180,21 @@ int reserve32(efe_handle* h, int N) {
   if (N <= h->Nres32) return EFE_OK;
   for (int i = 0; i < 3; ++i) { dfree(h, h->Yf[i]); dfree(h, h->Ye[i]); }
   dfree(h, h->Wf);
+  dfree(h, h->cpart);
+  // classical rows padded to a multiple of 8 elements: 16-byte aligned rows for
+  // vector loads and TMA boxes; the padding columns are zero and stay zero
+  const int ld = (N + 7) / 8 * 8;
   for (int i = 0; i < 3; ++i) {
-    TRY(dalloc(h, &h->Yf[i], h->n_nodes * N));
+    TRY(dalloc(h, &h->Yf[i], h->n_nodes * ld));
+    CK(cudaMemset(h->Yf[i], 0, sizeof(float) * h->n_nodes * ld));
     TRY(dalloc(h, &h->Ye[i], std::max<int64_t>(1, h->nE) * N));
   }
-  TRY(dalloc(h, &h->Wf, h->n_nodes * N));
+  TRY(dalloc(h, &h->Wf, h->n_nodes * ld));
+  CK(cudaMemset(h->Wf, 0, sizeof(float) * h->n_nodes * ld));
+  h->npc = (int)std::max<int64_t>(64, (h->n_tn + 303) / 304);
+  h->ncb = coup_nblocks(std::max<int64_t>(1, h->n_tn), h->npc);
+  TRY(dalloc(h, &h->cpart, (int64_t)h->ncb * std::max<int64_t>(1, h->nE) * N));
+  h->ld32 = ld;
   h->Nres32 = N;
   return EFE_OK;
 }
@@ -230,18 +244,27 @@ int timed_end(efe_handle* h, cudaStream_t st, int slot, int64_t cellcols) {
 
 // --- classical cell products, all 8 parity colours: W_c += H^cc Y_c ---
 template <typename T>
-int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, int64_t ldw, int N, cudaStream_t st) {
+int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, int64_t ldw, int N, cudaStream_t st,
+                   bool tc = false) {
   for (int c = 0; c < 8; ++c) {
     const int64_t nc = h->colour_off[c + 1] - h->colour_off[c];
     if (nc == 0) continue;
     int slot;
     TRY(timed_begin(h, st, &slot));
-    if constexpr (sizeof(T) == 8)
-      launch_cell_apply_f64((const double*)Hc, h->colour_cells + h->colour_off[c], nc, h->mesh, (const double*)Y,
-                            ldy, (double*)Wc, ldw, N, st);
-    else
-      launch_cell_apply_f32((const float*)Hc, h->colour_cells + h->colour_off[c], nc, h->mesh, (const float*)Y, ldy,
-                            (float*)Wc, ldw, N, st);
+    const int32_t* cl = h->colour_cells + h->colour_off[c];
+    if constexpr (sizeof(T) == 8) {
+      if (N <= 8)
+        launch_cell_apply_narrow_f64((const double*)Hc, cl, nc, h->mesh, (const double*)Y, ldy, (double*)Wc, ldw, N, st);
+      else
+        launch_cell_apply_f64((const double*)Hc, cl, nc, h->mesh, (const double*)Y, ldy, (double*)Wc, ldw, N, st);
+    } else {
+      if (tc)
+        launch_cell_tc_tf32(h->Aimg32, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N, h->info + 4, st);
+      else if (N <= 8)
+        launch_cell_apply_narrow_f32((const float*)Hc, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N, st);
+      else
+        launch_cell_apply_f32((const float*)Hc, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N, st);
+    }
     CKL();
     TRY(timed_end(h, st, slot, nc * (int64_t)N));
   }
@@ -335,13 +358,41 @@ int degree_f64(efe_handle* h, const double* Yc, int64_t ldc, const double* Yp, i
 }
 
 // --- one filter degree with the classical block in FP32 (enrichment rows FP64) ---
+// Classical rows use the padded leading dimension ld32; the enrichment
+// coupling runs node-major with FP32 products and FP64 cross-block sums.
 int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Yp, const double* Ype, float* Yn,
                double* Yne, double alpha, double cc, double beta, int N, cudaStream_t st) {
   const int64_t nn = h->n_nodes;
+  const int ld = h->ld32;
   double* We = h->W;  // nE x N FP64 scratch
-  TRY(apply_H_generic<float>(h, Yc, N, Yce, N, h->Wf, N, We, N, N, st, h->Hcc32));
-  TRY(minv_core<float>(h, h->Wf, N, We, N, N, st));
-  launch_cheb_combine<float>(nn, h->Dinv, h->Wf, N, Yc, N, Yp, N, Yn, N, alpha, cc, beta, N, st);
+  CK(cudaMemsetAsync(h->Wf, 0, sizeof(float) * nn * ld, st));
+  TRY(cell_apply_all<float>(h, h->Hcc32, Yc, ld, h->Wf, ld, N, st, h->tc_mode == 1));
+  if (h->nE > 0) {
+    const int nE = (int)h->nE;
+    if ((int64_t)nE * N * 4 <= 200 * 1024) {
+      launch_coup_cols<float>(h->n_tn, h->npc, h->t_nodes, h->t_ptr, h->t_col, h->hecT32, 1.f, Yce, N, nE, N, h->Wf,
+                              ld, st);
+      launch_coup_rows<float>(h->n_tn, h->npc, h->t_nodes, h->t_ptr, h->t_col, h->hecT32, nullptr, Yc, ld, nE, N,
+                              h->cpart, st);
+      launch_coup_reduce(h->ncb, nE, N, h->cpart, 1.0, nullptr, 0, 0.0, We, N, st);
+      launch_gemm_nn(nE, N, nE, 1.0, h->Hee, nE, Yce, N, 1.0, We, N, st);
+      // block-wise inverse: r = We - M^ec D^-1 Wc, x_e = S^-1 r, Wc -= M^ec^T x_e
+      launch_coup_rows<float>(h->n_tn, h->npc, h->t_nodes, h->t_ptr, h->t_col, h->mecT32, h->Dinv, h->Wf, ld, nE, N,
+                              h->cpart, st);
+      launch_coup_reduce(h->ncb, nE, N, h->cpart, -1.0, We, N, 1.0, h->rb, N, st);
+      launch_gemm_nn(nE, N, nE, 1.0, h->Sinv, nE, h->rb, N, 0.0, h->xe, N, st);
+      launch_coup_cols<float>(h->n_tn, h->npc, h->t_nodes, h->t_ptr, h->t_col, h->mecT32, -1.f, h->xe, N, nE, N,
+                              h->Wf, ld, st);
+    } else {
+      launch_spmm_nodes<float>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->hecT, 1.0, Yce, N, h->Wf, ld, N, st);
+      launch_spmm_segments<float>(h->nseg, h->seg_start, h->seg_end, h->ec_col, h->hec, nullptr, Yc, ld, h->part, N,
+                                  st);
+      launch_seg_reduce(nE, h->row_seg_ptr, h->part, 1.0, nullptr, 0, 0.0, We, N, N, st);
+      launch_gemm_nn(nE, N, nE, 1.0, h->Hee, nE, Yce, N, 1.0, We, N, st);
+      TRY(minv_core<float>(h, h->Wf, ld, We, N, N, st));
+    }
+  }
+  launch_cheb_combine_f4(nn, ld, h->Dinv, h->Wf, Yc, Yp, Yn, alpha, cc, beta, st);
   if (h->nE > 0) launch_cheb_combine<double>(h->nE, nullptr, h->xe, N, Yce, N, Ype, N, Yne, N, alpha, cc, beta, N, st);
   CKL();
   return EFE_OK;
@@ -462,6 +513,8 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
   TRY(dalloc(h, &h->Hcc, h->n_cell * NL * NL));
   TRY(dalloc(h, &h->Hcc32, h->n_cell * NL * NL));
   TRY(dalloc(h, (uint16_t**)&h->Hcc16, h->n_cell * NL * NL));
+  TRY(dalloc(h, &h->Aimg32, tc_image_elems(h->n_cell)));
+  TRY(dalloc(h, (uint16_t**)&h->Aimg16, tc_image_elems(h->n_cell)));
   TRY(dalloc(h, &h->info, 8));
   if (h->nE > 0) {
     TRY(upload(h, &h->funcs, s.funcs));
@@ -506,7 +559,10 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
     TRY(upload(h, &h->t_perm, s.t_perm));
     TRY(dalloc(h, &h->mecT, h->nnz));
     TRY(dalloc(h, &h->hecT, h->nnz));
+    TRY(dalloc(h, &h->mecT32, h->nnz));
+    TRY(dalloc(h, &h->hecT32, h->nnz));
     launch_permute(h->nnz, h->mec, h->t_perm, h->mecT, 0);
+    launch_to_f32(h->mecT, h->mecT32, h->nnz, 0);
     CKL();
     TRY(upload(h, &h->Mee, s.Mee));
     TRY(upload(h, &h->Hee_kin, s.Hee_kin));
@@ -574,12 +630,15 @@ int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
     CKL();
     launch_gather_sum(h->nnz, h->hec_kin, h->ec_cptr, h->ec_cidx, h->Pblk, h->hec, st);
     launch_permute(h->nnz, h->hec, h->t_perm, h->hecT, st);
+    launch_to_f32(h->hecT, h->hecT32, h->nnz, st);
     launch_gather_sum(h->nE * h->nE, h->Hee_kin, h->ee_cptr, h->ee_cidx, h->Qblk, h->Hee, st);
     launch_symmetrize(h->Hee, (int)h->nE, (int)h->nE, st);
     CKL();
   }
   launch_to_f32(h->Hcc, h->Hcc32, h->n_cell * NL * NL, st);
   launch_to_bf16(h->Hcc, h->Hcc16, h->n_cell * NL * NL, st);
+  launch_build_aimg_tf32(h->Hcc, h->n_cell, h->Aimg32, st);
+  launch_build_aimg_bf16(h->Hcc, h->n_cell, h->Aimg16, st);
   CKL();
   h->potential_set = true;
   return EFE_OK;
@@ -717,7 +776,7 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
     h->err = "bad filter parameters (need m >= 1, a0 < a < b, finite)";
     return EFE_ERR_ARG;
   }
-  if (precision != EFE_PREC_FP64 && precision != EFE_PREC_FP32) {
+  if (precision != EFE_PREC_FP64 && precision != EFE_PREC_FP32 && precision != EFE_PREC_TF32) {
     h->err = "precision mode not available in this build";
     return EFE_ERR_ARG;
   }
@@ -741,6 +800,8 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
     sig = sn;
   };
   const int n_low = (precision == EFE_PREC_FP64) ? 0 : std::max(0, m - fp64_tail);
+  h->tc_mode = (precision == EFE_PREC_TF32) ? 1 : 0;
+  CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
   // FP64 buffers: slot 0 = X (user, ldx), 1 = B1, 2 = B2 (ld = N)
   double* buf[3] = {X, h->B1, h->B2};
   int64_t ld[3] = {ldx, N, N};
@@ -749,7 +810,7 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
   if (n_low > 0) {
     TRY(reserve32(h, N));
     // load Y_0 into the low-precision buffers
-    launch_f64_to_f32_rows(nn, X, ldx, h->Yf[0], N, N, st);
+    launch_f64_to_f32_rows(nn, X, ldx, h->Yf[0], h->ld32, N, st);
     if (h->nE > 0) launch_copy_rows(h->nE, X + nn * ldx, ldx, h->Ye[0], N, N, st);
     CKL();
     int p32 = -1, c32 = 0;
@@ -763,11 +824,11 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
       c32 = nx;
     }
     // hand the last two degrees to FP64 storage: prev -> B1, cur -> B2
-    launch_f32_to_f64_rows(nn, h->Yf[c32], N, h->B2, N, N, st);
+    launch_f32_to_f64_rows(nn, h->Yf[c32], h->ld32, h->B2, N, N, st);
     if (h->nE > 0) launch_copy_rows(h->nE, h->Ye[c32], N, h->B2 + nn * N, N, N, st);
     cur = 2;
     if (p32 >= 0) {
-      launch_f32_to_f64_rows(nn, h->Yf[p32], N, h->B1, N, N, st);
+      launch_f32_to_f64_rows(nn, h->Yf[p32], h->ld32, h->B1, N, N, st);
       if (h->nE > 0) launch_copy_rows(h->nE, h->Ye[p32], N, h->B1 + nn * N, N, N, st);
       prev = 1;
     }
@@ -786,6 +847,15 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
   if (cur != 0) {
     launch_copy_rows(h->rows, buf[cur], ld[cur], X, ldx, N, st);
     CKL();
+  }
+  if (n_low > 0 && h->tc_mode) {
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->info + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (flag) {
+      h->err = "tensor-core cell kernel: bounded mbarrier wait ran out";
+      return EFE_ERR_TIMEOUT;
+    }
   }
   return EFE_OK;
 }

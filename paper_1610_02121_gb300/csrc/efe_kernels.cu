@@ -411,48 +411,189 @@ __global__ void k_zero_rows(int64_t nrows, T* __restrict__ X, int64_t ldx, int N
   X[(idx / N) * ldx + idx % N] = T(0);
 }
 
+// Cell products for a narrow block (N <= 8 columns, e.g. the single-vector
+// Lanczos bound): one CTA per cell, each warp takes rows of H_e, lanes split
+// the 125 columns and reduce with shuffles, so the cell matrix is read once
+// with coalesced row loads and no work is spent on empty column tiles.
+template <typename T, int NMAX>
+__global__ void __launch_bounds__(256) k_cell_apply_narrow(const T* __restrict__ Hcc, const int32_t* __restrict__ cells,
+                                                           MeshDev m, const T* __restrict__ Y, int64_t ldy,
+                                                           T* __restrict__ W, int64_t ldw, int N) {
+  const int64_t e = cells[blockIdx.x];
+  __shared__ T ys[NL][NMAX];
+  __shared__ int64_t gnode[NL];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i = (int)(e % m.nc[0]), j = (int)((e / m.nc[0]) % m.nc[1]), k = (int)(e / ((int64_t)m.nc[0] * m.nc[1]));
+  const int64_t NX = m.nn[0], NY = m.nn[1];
+  if (tid < NL) {
+    const int a = tid % NP1, b = (tid / NP1) % NP1, c = tid / (NP1 * NP1);
+    const int64_t g = (int64_t)(P * i + a) + NX * ((int64_t)(P * j + b) + NY * (int64_t)(P * k + c));
+    gnode[tid] = g;
+#pragma unroll
+    for (int cc = 0; cc < NMAX; ++cc) ys[tid][cc] = (cc < N) ? Y[g * ldy + cc] : T(0);
+  }
+  __syncthreads();
+  const T* He = Hcc + e * (int64_t)(NL * NL);
+  for (int r = warp; r < NL; r += 8) {
+    T acc[NMAX];
+#pragma unroll
+    for (int cc = 0; cc < NMAX; ++cc) acc[cc] = T(0);
+    for (int kk = lane; kk < NL; kk += 32) {
+      const T h = He[r * NL + kk];
+#pragma unroll
+      for (int cc = 0; cc < NMAX; ++cc) acc[cc] = fma(h, ys[kk][cc], acc[cc]);
+    }
+#pragma unroll
+    for (int cc = 0; cc < NMAX; ++cc)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[cc] += __shfl_down_sync(0xffffffffu, acc[cc], o);
+    if (lane == 0) {
+      T* wr = W + gnode[r] * ldw;
+#pragma unroll
+      for (int cc = 0; cc < NMAX; ++cc)
+        if (cc < N) wr[cc] += acc[cc];
+    }
+  }
+}
+
+// Node-major enrichment products (FP32 arithmetic, mixed-precision filter).
+// Rows product: part[b][a][c] = sum over the nodes g of chunk b of
+//   sum_{a in pattern(g)} val[g, a] * scale[g] * X[g][c]
+// with the (n_E x N) accumulator in shared memory, so each vector row is read
+// once however many enrichment supports contain its node.
+template <typename T>
+__global__ void k_coup_rows(int64_t n_tn, int npc, const int32_t* __restrict__ t_nodes,
+                            const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_col,
+                            const float* __restrict__ tval, const double* __restrict__ scale,
+                            const T* __restrict__ X, int64_t ldx, int nE, int N, float* __restrict__ part) {
+  extern __shared__ float acc[];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int i = tid; i < nE * N; i += bd) acc[i] = 0.f;
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * npc;
+  const int64_t r1 = min(n_tn, r0 + npc);
+  for (int64_t r = r0; r < r1; ++r) {
+    const int64_t g = t_nodes[r];
+    const float s = scale ? (float)scale[g] : 1.f;
+    const int64_t q0 = t_ptr[r], q1 = t_ptr[r + 1];
+    for (int c = tid; c < N; c += bd) {
+      const float x = s * (float)X[g * ldx + c];
+      for (int64_t q = q0; q < q1; ++q) acc[t_col[q] * N + c] = fmaf(tval[q], x, acc[t_col[q] * N + c]);
+    }
+  }
+  __syncthreads();
+  float* P = part + (int64_t)blockIdx.x * nE * N;
+  for (int i = tid; i < nE * N; i += bd) P[i] = acc[i];
+}
+
+// out[a][c] = alpha_base * base[a][c] + sgn * sum_b part[b][a][c]  (fixed order, FP64)
+__global__ void k_coup_reduce(int nb, int nE, int N, const float* __restrict__ part, double sgn,
+                              const double* __restrict__ base, int64_t ldb, double alpha_base,
+                              double* __restrict__ out, int64_t ldo) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nE * N) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += (double)part[(int64_t)b * nE * N + idx];
+  const int a = (int)(idx / N), c = (int)(idx % N);
+  double v = sgn * s;
+  if (base) v += alpha_base * base[(int64_t)a * ldb + c];
+  out[(int64_t)a * ldo + c] = v;
+}
+
+// Columns product: W[g][c] += sgn * sum_{a in pattern(g)} val[g, a] * Xe[a][c], Xe staged in
+// shared memory as FP32.
+template <typename T>
+__global__ void k_coup_cols(int64_t n_tn, int npc, const int32_t* __restrict__ t_nodes,
+                            const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_col,
+                            const float* __restrict__ tval, float sgn, const double* __restrict__ Xe, int64_t ldxe,
+                            int nE, int N, T* __restrict__ W, int64_t ldw) {
+  extern __shared__ float xs[];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int i = tid; i < nE * N; i += bd) xs[i] = (float)Xe[(int64_t)(i / N) * ldxe + i % N];
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * npc;
+  const int64_t r1 = min(n_tn, r0 + npc);
+  for (int64_t r = r0; r < r1; ++r) {
+    const int64_t g = t_nodes[r];
+    const int64_t q0 = t_ptr[r], q1 = t_ptr[r + 1];
+    for (int c = tid; c < N; c += bd) {
+      float s = 0.f;
+      for (int64_t q = q0; q < q1; ++q) s = fmaf(tval[q], xs[t_col[q] * N + c], s);
+      T* w = W + g * ldw + c;
+      *w = (T)((float)(*w) + sgn * s);
+    }
+  }
+}
+
+// Chebyshev combine on 16-byte aligned FP32 rows (ld multiple of 4): four columns per thread.
+__global__ void k_cheb_combine_f4(int64_t nrows, int ld4, const double* __restrict__ rowscale,
+                                  const float4* __restrict__ X, const float4* __restrict__ Yc,
+                                  const float4* __restrict__ Yp, float4* __restrict__ Yn, float alpha, float cc,
+                                  float beta) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nrows * ld4) return;
+  const int64_t r = idx / ld4;
+  const float sc = rowscale ? (float)rowscale[r] : 1.f;
+  const float4 x = X[idx], y = Yc[idx];
+  float4 o;
+  o.x = alpha * (sc * x.x - cc * y.x);
+  o.y = alpha * (sc * x.y - cc * y.y);
+  o.z = alpha * (sc * x.z - cc * y.z);
+  o.w = alpha * (sc * x.w - cc * y.w);
+  if (Yp) {
+    const float4 p = Yp[idx];
+    o.x += beta * p.x;
+    o.y += beta * p.y;
+    o.z += beta * p.z;
+    o.w += beta * p.w;
+  }
+  Yn[idx] = o;
+}
+
 // ---------------------------------------------------------------------------
 // dense FP64
 // ---------------------------------------------------------------------------
+constexpr int GT = 48;  // output tile (16 x 16 threads, 3 x 3 each)
+
 __global__ void __launch_bounds__(256) k_gemm_nn(int64_t M, int Nc, int K, double alpha,
                                                  const double* __restrict__ A, int64_t lda,
                                                  const double* __restrict__ B, int64_t ldb, double beta,
                                                  double* __restrict__ C, int64_t ldc) {
-  __shared__ double As[16][65];
-  __shared__ double Bs[16][65];
-  const int64_t row0 = (int64_t)blockIdx.x * 64;
-  const int col0 = blockIdx.y * 64;
+  __shared__ double As[16][GT + 1];
+  __shared__ double Bs[16][GT + 1];
+  const int64_t row0 = (int64_t)blockIdx.x * GT;
+  const int col0 = blockIdx.y * GT;
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-  double acc[4][4] = {};
+  double acc[3][3] = {};
   for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int idx = tid; idx < 1024; idx += 256) {
+    for (int idx = tid; idx < 16 * GT; idx += 256) {
       const int r = idx / 16, kk = idx % 16;
       As[kk][r] = (row0 + r < M && k0 + kk < K) ? A[(row0 + r) * lda + k0 + kk] : 0.0;
-      const int kb = idx / 64, cc = idx % 64;
+      const int kb = idx / GT, cc = idx % GT;
       Bs[kb][cc] = (k0 + kb < K && col0 + cc < Nc) ? B[(int64_t)(k0 + kb) * ldb + col0 + cc] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      double av[4], bv[4];
+      double av[3], bv[3];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+      for (int a = 0; a < 3; ++a) av[a] = As[kk][ty * 3 + a];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+      for (int b = 0; b < 3; ++b) bv[b] = Bs[kk][tx * 3 + b];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        for (int b = 0; b < 3; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int64_t r = row0 + ty * 4 + a;
+  for (int a = 0; a < 3; ++a) {
+    const int64_t r = row0 + ty * 3 + a;
     if (r >= M) continue;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int c = col0 + tx * 4 + b;
+    for (int b = 0; b < 3; ++b) {
+      const int c = col0 + tx * 3 + b;
       if (c >= Nc) continue;
       double v = alpha * acc[a][b];
       if (beta != 0.0) v += beta * C[r * ldc + c];
@@ -466,16 +607,16 @@ constexpr int64_t TN_KC = 8192;
 __global__ void __launch_bounds__(256) k_gemm_tn_part(int64_t K, int Na, int Nb, const double* __restrict__ A,
                                                       int64_t lda, const double* __restrict__ B, int64_t ldb,
                                                       double* __restrict__ part) {
-  __shared__ double As[16][65];
-  __shared__ double Bs[16][65];
-  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+  __shared__ double As[16][GT + 1];
+  __shared__ double Bs[16][GT + 1];
+  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
   const int64_t kb = (int64_t)blockIdx.z * TN_KC;
   const int64_t ke = min(K, kb + TN_KC);
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-  double acc[4][4] = {};
+  double acc[3][3] = {};
   for (int64_t k0 = kb; k0 < ke; k0 += 16) {
-    for (int idx = tid; idx < 1024; idx += 256) {
-      const int kk = idx / 64, c = idx % 64;
+    for (int idx = tid; idx < 16 * GT; idx += 256) {
+      const int kk = idx / GT, c = idx % GT;
       const bool okk = k0 + kk < ke;
       As[kk][c] = (okk && i0 + c < Na) ? A[(k0 + kk) * lda + i0 + c] : 0.0;
       Bs[kk][c] = (okk && j0 + c < Nb) ? B[(k0 + kk) * ldb + j0 + c] : 0.0;
@@ -483,27 +624,27 @@ __global__ void __launch_bounds__(256) k_gemm_tn_part(int64_t K, int Na, int Nb,
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      double av[4], bv[4];
+      double av[3], bv[3];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+      for (int a = 0; a < 3; ++a) av[a] = As[kk][ty * 3 + a];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+      for (int b = 0; b < 3; ++b) bv[b] = Bs[kk][tx * 3 + b];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        for (int b = 0; b < 3; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
     __syncthreads();
   }
-  double* P = part + (int64_t)blockIdx.z * Na * Nb;
+  double* Pp = part + (int64_t)blockIdx.z * Na * Nb;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int r = i0 + ty * 4 + a;
+  for (int a = 0; a < 3; ++a) {
+    const int r = i0 + ty * 3 + a;
     if (r >= Na) continue;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int c = j0 + tx * 4 + b;
-      if (c < Nb) P[(int64_t)r * Nb + c] = acc[a][b];
+    for (int b = 0; b < 3; ++b) {
+      const int c = j0 + tx * 3 + b;
+      if (c < Nb) Pp[(int64_t)r * Nb + c] = acc[a][b];
     }
   }
 }
@@ -929,7 +1070,7 @@ void launch_zero_rows_f32(int64_t nrows, float* X, int64_t ldx, int N, cudaStrea
 void launch_gemm_nn(int64_t M, int Nc, int K, double alpha, const double* A, int64_t lda, const double* B,
                     int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st) {
   if (M <= 0 || Nc <= 0) return;
-  dim3 g((unsigned)((M + 63) / 64), (unsigned)((Nc + 63) / 64));
+  dim3 g((unsigned)((M + GT - 1) / GT), (unsigned)((Nc + GT - 1) / GT));
   k_gemm_nn<<<g, 256, 0, st>>>(M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
@@ -945,7 +1086,7 @@ void launch_gemm_tn(int64_t K, int Na, int Nb, const double* A, int64_t lda, con
   int64_t nsplit = (K + TN_KC - 1) / TN_KC;
   if (nsplit < 1) nsplit = 1;
   (void)work_elems;
-  dim3 g((unsigned)((Na + 63) / 64), (unsigned)((Nb + 63) / 64), (unsigned)nsplit);
+  dim3 g((unsigned)((Na + GT - 1) / GT), (unsigned)((Nb + GT - 1) / GT), (unsigned)nsplit);
   k_gemm_tn_part<<<g, 256, 0, st>>>(K, Na, Nb, A, lda, B, ldb, work);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_gemm_tn_reduce<<<grid1((int64_t)Na * Nb, 256), 256, 0, st>>>((int)nsplit, Na, Nb, work, C, ldc);
@@ -1007,6 +1148,71 @@ void launch_axpby3(int64_t n, double* w, const double* v, const double* vp, doub
 
 void launch_scale(int64_t n, const double* x, double s, double* y, cudaStream_t st) {
   k_scale<<<grid1(n, 256), 256, 0, st>>>(n, x, s, y);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_cell_apply_narrow_f64(const double* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                                  const double* Y, int64_t ldy, double* W, int64_t ldw, int N, cudaStream_t st) {
+  if (ncells <= 0 || N <= 0) return;
+  if (N == 1) k_cell_apply_narrow<double, 1><<<(unsigned)ncells, 256, 0, st>>>(Hcc, cells, m, Y, ldy, W, ldw, N);
+  else k_cell_apply_narrow<double, 8><<<(unsigned)ncells, 256, 0, st>>>(Hcc, cells, m, Y, ldy, W, ldw, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_cell_apply_narrow_f32(const float* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                                  const float* Y, int64_t ldy, float* W, int64_t ldw, int N, cudaStream_t st) {
+  if (ncells <= 0 || N <= 0) return;
+  if (N == 1) k_cell_apply_narrow<float, 1><<<(unsigned)ncells, 256, 0, st>>>(Hcc, cells, m, Y, ldy, W, ldw, N);
+  else k_cell_apply_narrow<float, 8><<<(unsigned)ncells, 256, 0, st>>>(Hcc, cells, m, Y, ldy, W, ldw, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+int coup_nblocks(int64_t n_tn, int npc) { return (int)((n_tn + npc - 1) / npc); }
+
+template <typename T>
+void launch_coup_rows(int64_t n_tn, int npc, const int32_t* t_nodes, const int64_t* t_ptr, const int32_t* t_col,
+                      const float* tval, const double* scale, const T* X, int64_t ldx, int nE, int N, float* part,
+                      cudaStream_t st) {
+  if (n_tn <= 0 || N <= 0 || nE <= 0) return;
+  const int nb = coup_nblocks(n_tn, npc);
+  const int t = N >= 256 ? 256 : ((N + 31) / 32) * 32;
+  const size_t smem = sizeof(float) * (size_t)nE * N;
+  cudaFuncSetAttribute(k_coup_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_coup_rows<T><<<nb, t, smem, st>>>(n_tn, npc, t_nodes, t_ptr, t_col, tval, scale, X, ldx, nE, N, part);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+template void launch_coup_rows<float>(int64_t, int, const int32_t*, const int64_t*, const int32_t*, const float*,
+                                      const double*, const float*, int64_t, int, int, float*, cudaStream_t);
+
+void launch_coup_reduce(int nb, int nE, int N, const float* part, double sgn, const double* base, int64_t ldb,
+                        double alpha_base, double* out, int64_t ldo, cudaStream_t st) {
+  if (nE <= 0 || N <= 0) return;
+  k_coup_reduce<<<grid1((int64_t)nE * N, 256), 256, 0, st>>>(nb, nE, N, part, sgn, base, ldb, alpha_base, out, ldo);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+template <typename T>
+void launch_coup_cols(int64_t n_tn, int npc, const int32_t* t_nodes, const int64_t* t_ptr, const int32_t* t_col,
+                      const float* tval, float sgn, const double* Xe, int64_t ldxe, int nE, int N, T* W, int64_t ldw,
+                      cudaStream_t st) {
+  if (n_tn <= 0 || N <= 0 || nE <= 0) return;
+  const int nb = coup_nblocks(n_tn, npc);
+  const int t = N >= 256 ? 256 : ((N + 31) / 32) * 32;
+  const size_t smem = sizeof(float) * (size_t)nE * N;
+  cudaFuncSetAttribute(k_coup_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_coup_cols<T><<<nb, t, smem, st>>>(n_tn, npc, t_nodes, t_ptr, t_col, tval, sgn, Xe, ldxe, nE, N, W, ldw);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+template void launch_coup_cols<float>(int64_t, int, const int32_t*, const int64_t*, const int32_t*, const float*,
+                                      float, const double*, int64_t, int, int, float*, int64_t, cudaStream_t);
+
+void launch_cheb_combine_f4(int64_t nrows, int ld, const double* rowscale, const float* X, const float* Yc,
+                            const float* Yp, float* Yn, double alpha, double c, double beta, cudaStream_t st) {
+  if (nrows <= 0) return;
+  const int ld4 = ld / 4;
+  k_cheb_combine_f4<<<grid1(nrows * ld4, 256), 256, 0, st>>>(nrows, ld4, rowscale, (const float4*)X,
+                                                            (const float4*)Yc, (const float4*)Yp, (float4*)Yn,
+                                                            (float)alpha, (float)c, (float)beta);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 

@@ -48,6 +48,25 @@ void launch_cell_apply_f64(const double* Hcc, const int32_t* cells, int64_t ncel
                            const double* Y, int64_t ldy, double* W, int64_t ldw, int N, cudaStream_t st);
 void launch_cell_apply_f32(const float* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
                            const float* Y, int64_t ldy, float* W, int64_t ldw, int N, cudaStream_t st);
+// narrow blocks (N <= 8): one warp per row of H_e
+void launch_cell_apply_narrow_f64(const double* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                                  const double* Y, int64_t ldy, double* W, int64_t ldw, int N, cudaStream_t st);
+void launch_cell_apply_narrow_f32(const float* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                                  const float* Y, int64_t ldy, float* W, int64_t ldw, int N, cudaStream_t st);
+// node-major enrichment products with FP32 arithmetic (mixed-precision filter)
+int coup_nblocks(int64_t n_tn, int npc);
+template <typename T>
+void launch_coup_rows(int64_t n_tn, int npc, const int32_t* t_nodes, const int64_t* t_ptr, const int32_t* t_col,
+                      const float* tval, const double* scale, const T* X, int64_t ldx, int nE, int N, float* part,
+                      cudaStream_t st);
+void launch_coup_reduce(int nb, int nE, int N, const float* part, double sgn, const double* base, int64_t ldb,
+                        double alpha_base, double* out, int64_t ldo, cudaStream_t st);
+template <typename T>
+void launch_coup_cols(int64_t n_tn, int npc, const int32_t* t_nodes, const int64_t* t_ptr, const int32_t* t_col,
+                      const float* tval, float sgn, const double* Xe, int64_t ldxe, int nE, int N, T* W, int64_t ldw,
+                      cudaStream_t st);
+void launch_cheb_combine_f4(int64_t nrows, int ld, const double* rowscale, const float* X, const float* Yc,
+                            const float* Yp, float* Yn, double alpha, double c, double beta, cudaStream_t st);
 // out[node_r] += sgn * sum_q val[q] * Xe[col[q]]   (rows = nodes that meet a support)
 template <typename T>
 void launch_spmm_nodes(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
@@ -78,6 +97,15 @@ void launch_copy_rows(int64_t nrows, const double* X, int64_t ldx, double* Y, in
                       cudaStream_t st);
 void launch_zero_rows(int64_t nrows, double* X, int64_t ldx, int N, cudaStream_t st);
 void launch_zero_rows_f32(int64_t nrows, float* X, int64_t ldx, int N, cudaStream_t st);
+
+// ---- tcgen05 cell products (efe_cell_tc.cu) ----
+int64_t tc_image_elems(int64_t n_cell);
+void launch_build_aimg_tf32(const double* Hcc, int64_t n_cell, float* img, cudaStream_t st);
+void launch_build_aimg_bf16(const double* Hcc, int64_t n_cell, void* img, cudaStream_t st);
+int launch_cell_tc_tf32(const float* Aimg, const int32_t* cells, int64_t ncells, const MeshDev& m, const float* Y,
+                        int64_t ldy, float* W, int64_t ldw, int N, int* err, cudaStream_t st);
+int launch_cell_tc_bf16(const void* Aimg, const int32_t* cells, int64_t ncells, const MeshDev& m, const void* Y,
+                        int64_t ldy, void* W, int64_t ldw, int N, int* err, cudaStream_t st);
 
 // ---- dense FP64 ----
 // C[M x Nc] = alpha * A[M x K] B[K x Nc] + beta * C   (row-major, lda/ldb/ldc)

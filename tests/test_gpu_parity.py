@@ -175,3 +175,34 @@ def test_hydrogen_config1_converged():
     np.testing.assert_allclose(eps[:nconv], ref, atol=1e-6)
     assert abs(eps[0] + 0.5) < 1e-3
     assert np.ptp(eps[1:4]) < 1e-7          # 2p triplet (cubic symmetry about the nucleus)
+
+
+@pytest.mark.parametrize("N", [17, 135, 300])
+def test_chfsi_step_tf32_tensor_cores(tiny_pair, N):
+    """tcgen05 TF32 cell products (FP32 accumulation, FP32 vector storage): one
+    degree agrees with the FP64 oracle to TF32 accuracy (unit round-off 2^-11,
+    bound 3e-3 relative), a degree-7 filter to 2e-2; N = 300 spans two 256-column
+    tensor-core tiles with a ragged tail."""
+    from oracle.chfsi import chebyshev_filter_scaled
+    d, G = tiny_pair
+    X = W.random_block(d.system, N, seed=30 + N)
+    a, b, a0 = _bounds(d, 10)
+    for m, tol in [(1, 3e-3), (7, 2e-2)]:
+        ref = chebyshev_filter_scaled(d.apply_Htilde, X, m, a, b, a0)
+        Xd = to_dev(X)
+        G.chfsi_step(Xd, m, a, b, a0, precision="tf32", fp64_tail=0)
+        err = rel_err(Xd, ref)
+        assert err < tol, (m, err)
+
+
+def test_chfsi_converges_tf32_tiny(tiny_pair):
+    """Mixed precision (TF32 tensor-core filter, FP64 tail degrees, FP64 CholQR and
+    Rayleigh-Ritz) reaches the dense eigenvalues within 1e-5 Ha."""
+    from oracle.chfsi import dense_eigs
+    d, G = tiny_pair
+    N, m, nconv = 10, 12, 7
+    X = to_dev(W.initial_block(d.system, N, seed=1))
+    eps, res, it, b = G.solve(X, m, tol=1e-7, precision="tf32", fp64_tail=2,
+                              v0=to_dev(W.lanczos_start(d.system)), n_conv=nconv, max_iter=300)
+    ref = dense_eigs(d, N)
+    np.testing.assert_allclose(eps[:nconv], ref[:nconv], atol=1e-5)
