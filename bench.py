@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "fp64"])
+    p.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32", "tf32", "fp64"])
     p.add_argument("--fp64-tail", type=int, default=2)
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--no-fp64", action="store_true")
@@ -252,7 +252,7 @@ def main():
     value = world * flops_step / (ms * 1e-3) / 1e12
     # dominant kernel: classical cell products
     n_launch, k_ms, cellcols = stats
-    s_el = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16": 2}[prec]
+    s_el = {"fp64": 8, "fp32": 4, "tf32": 4, "tf32x3": 4, "bf16": 2}[prec]
     h_bytes = G.n_cells * NL * NL * s_el
     v_bytes = 2.0 * G.n_nodes * N * s_el
     frac_cells = cellcols / float(G.n_cells * N)
@@ -271,7 +271,8 @@ def main():
     else:
         achieved = alg_bytes / (k_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "kernel": "k_cell_tc", "launches": n_launch,
+                "traffic": None, "kernel": "k_cell_tc2<%s>" % ("true" if prec == "tf32x3" else "false"),
+                "launches": n_launch, "algorithmic_tflops": alg_flops / (k_ms * 1e-3) / 1e12,
                 "avg_launch_ms": k_ms / max(n_launch, 1), "peak_source": peak_src}
     line = {"metric": "chfsi_filter_tflops", "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,

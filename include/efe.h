@@ -54,8 +54,10 @@ extern "C" {
 /* precision modes of efe_chfsi_step (spec mixed-precision filter) */
 #define EFE_PREC_FP64 0    /* every product in FP64 */
 #define EFE_PREC_FP32 1    /* classical block in FP32, cell GEMMs FP32 (SIMT FFMA), FP32 accumulate */
-#define EFE_PREC_TF32 2    /* classical block in FP32, cell GEMMs on tcgen05 kind::tf32, FP32 accumulate */
-#define EFE_PREC_BF16 3    /* classical block in BF16, cell GEMMs on tcgen05 kind::f16 (bf16), FP32 accumulate */
+#define EFE_PREC_TF32 2    /* classical block in FP32, cell GEMMs on tcgen05 kind::tf32 (one pass), FP32 accumulate */
+#define EFE_PREC_BF16 3    /* reserved: classical block in BF16, tcgen05 kind::f16 (not available in this build) */
+#define EFE_PREC_TF32X3 4  /* classical block in FP32, cell GEMMs on tcgen05 kind::tf32 with the 3-term operand
+                              split (a1 b1 + a1 b2 + a2 b1): FP32-grade products, FP32 accumulate */
 
 typedef struct efe_handle efe_handle;
 

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libefe.so")
 EFE_OK = 0
 ERRORS = {1: "EFE_ERR_ARG", 2: "EFE_ERR_CUDA", 3: "EFE_ERR_CHOL", 4: "EFE_ERR_NOCONV",
           5: "EFE_ERR_TIMEOUT", 6: "EFE_ERR_NAN", 7: "EFE_ERR_ALLOC", 8: "EFE_ERR_STATE"}
-PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
 
 # the symbols declared in include/efe.h
 SYMBOLS = ["efe_create", "efe_destroy", "efe_last_error", "efe_sizes", "efe_qpoints", "efe_set_potential",

@@ -49,9 +49,11 @@ struct efe_handle {
   double* Hcc = nullptr;
   float* Hcc32 = nullptr;
   void* Hcc16 = nullptr;
-  float* Aimg32 = nullptr;  // tcgen05 A images (TF32 in FP32 words)
+  float* Araw = nullptr;    // tcgen05 A images (FP32 values, core-matrix layout)
   void* Aimg16 = nullptr;   // tcgen05 A images (BF16)
-  int tc_mode = 0;          // 1: cell products of the FP32 filter on tcgen05 (TF32)
+  int tc_mode = 0;          // 1: TF32 tcgen05 cell products, 2: 3-term split TF32 (FP32-grade)
+  int n_sm = 148;
+  bool time_this = false;   // the cell-apply timer records only the filter's mixed-precision launches
   DevFunc* funcs = nullptr;
   int32_t *enr_cells = nullptr, *cf_ptr = nullptr, *cf_idx = nullptr;
   int64_t *blkP_off = nullptr, *blkQ_off = nullptr;
@@ -212,7 +214,7 @@ int ev_get(efe_handle* h, int idx, cudaEvent_t* e) {
 
 int timed_begin(efe_handle* h, cudaStream_t st, int* slot) {
   *slot = -1;
-  if (!h->timing) return EFE_OK;
+  if (!h->timing || !h->time_this) return EFE_OK;
   const int i = 2 * (int)h->ev_pairs.size();
   cudaEvent_t a, b;
   TRY(ev_get(h, i, &a));
@@ -259,7 +261,8 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
         launch_cell_apply_f64((const double*)Hc, cl, nc, h->mesh, (const double*)Y, ldy, (double*)Wc, ldw, N, st);
     } else {
       if (tc)
-        launch_cell_tc_tf32(h->Aimg32, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N, h->info + 4, st);
+        launch_cell_tc2(h->Araw, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N, h->tc_mode == 2, h->n_sm,
+                        h->info + 4, st);
       else if (N <= 8)
         launch_cell_apply_narrow_f32((const float*)Hc, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N, st);
       else
@@ -366,7 +369,9 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
   const int ld = h->ld32;
   double* We = h->W;  // nE x N FP64 scratch
   CK(cudaMemsetAsync(h->Wf, 0, sizeof(float) * nn * ld, st));
-  TRY(cell_apply_all<float>(h, h->Hcc32, Yc, ld, h->Wf, ld, N, st, h->tc_mode == 1));
+  h->time_this = true;
+  TRY(cell_apply_all<float>(h, h->Hcc32, Yc, ld, h->Wf, ld, N, st, h->tc_mode != 0));
+  h->time_this = false;
   if (h->nE > 0) {
     const int nE = (int)h->nE;
     if ((int64_t)nE * N * 4 <= 200 * 1024) {
@@ -449,6 +454,11 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
   if (!h) return EFE_ERR_ALLOC;
   *out = h;
   CK(cudaGetDevice(&h->dev));
+  {
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
+    h->n_sm = nsm > 0 ? nsm : 148;
+  }
   Setup s;
   int rc;
   try {
@@ -513,7 +523,7 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
   TRY(dalloc(h, &h->Hcc, h->n_cell * NL * NL));
   TRY(dalloc(h, &h->Hcc32, h->n_cell * NL * NL));
   TRY(dalloc(h, (uint16_t**)&h->Hcc16, h->n_cell * NL * NL));
-  TRY(dalloc(h, &h->Aimg32, tc_image_elems(h->n_cell)));
+  TRY(dalloc(h, &h->Araw, tc_image_elems(h->n_cell)));
   TRY(dalloc(h, (uint16_t**)&h->Aimg16, tc_image_elems(h->n_cell)));
   TRY(dalloc(h, &h->info, 8));
   if (h->nE > 0) {
@@ -637,7 +647,7 @@ int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
   }
   launch_to_f32(h->Hcc, h->Hcc32, h->n_cell * NL * NL, st);
   launch_to_bf16(h->Hcc, h->Hcc16, h->n_cell * NL * NL, st);
-  launch_build_aimg_tf32(h->Hcc, h->n_cell, h->Aimg32, st);
+  launch_build_araw(h->Hcc, h->n_cell, h->Araw, st);
   launch_build_aimg_bf16(h->Hcc, h->n_cell, h->Aimg16, st);
   CKL();
   h->potential_set = true;
@@ -776,7 +786,8 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
     h->err = "bad filter parameters (need m >= 1, a0 < a < b, finite)";
     return EFE_ERR_ARG;
   }
-  if (precision != EFE_PREC_FP64 && precision != EFE_PREC_FP32 && precision != EFE_PREC_TF32) {
+  if (precision != EFE_PREC_FP64 && precision != EFE_PREC_FP32 && precision != EFE_PREC_TF32 &&
+      precision != EFE_PREC_TF32X3) {
     h->err = "precision mode not available in this build";
     return EFE_ERR_ARG;
   }
@@ -800,7 +811,7 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
     sig = sn;
   };
   const int n_low = (precision == EFE_PREC_FP64) ? 0 : std::max(0, m - fp64_tail);
-  h->tc_mode = (precision == EFE_PREC_TF32) ? 1 : 0;
+  h->tc_mode = (precision == EFE_PREC_TF32) ? 1 : (precision == EFE_PREC_TF32X3 ? 2 : 0);
   CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
   // FP64 buffers: slot 0 = X (user, ldx), 1 = B1, 2 = B2 (ld = N)
   double* buf[3] = {X, h->B1, h->B2};

@@ -107,6 +107,10 @@ int launch_cell_tc_tf32(const float* Aimg, const int32_t* cells, int64_t ncells,
 int launch_cell_tc_bf16(const void* Aimg, const int32_t* cells, int64_t ncells, const MeshDev& m, const void* Y,
                         int64_t ldy, void* W, int64_t ldw, int N, int* err, cudaStream_t st);
 
+void launch_build_araw(const double* Hcc, int64_t n_cell, float* img, cudaStream_t st);
+int launch_cell_tc2(const float* Araw, const int32_t* cells, int64_t ncells, const MeshDev& m, const float* Y,
+                    int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err, cudaStream_t st);
+
 // ---- dense FP64 ----
 // C[M x Nc] = alpha * A[M x K] B[K x Nc] + beta * C   (row-major, lda/ldb/ldc)
 void launch_gemm_nn(int64_t M, int Nc, int K, double alpha, const double* A, int64_t lda, const double* B,

@@ -178,31 +178,35 @@ def test_hydrogen_config1_converged():
 
 
 @pytest.mark.parametrize("N", [17, 135, 300])
-def test_chfsi_step_tf32_tensor_cores(tiny_pair, N):
-    """tcgen05 TF32 cell products (FP32 accumulation, FP32 vector storage): one
-    degree agrees with the FP64 oracle to TF32 accuracy (unit round-off 2^-11,
-    bound 3e-3 relative), a degree-7 filter to 2e-2; N = 300 spans two 256-column
-    tensor-core tiles with a ragged tail."""
+@pytest.mark.parametrize("prec,tols", [("tf32", [(1, 3e-3), (7, 2e-2)]), ("tf32x3", [(1, 2e-6), (7, 2e-5)])])
+def test_chfsi_step_tf32_tensor_cores(tiny_pair, N, prec, tols):
+    """tcgen05 cell products (FP32 accumulation, FP32 vector storage).  One TF32
+    pass: one degree agrees with the FP64 oracle to TF32 accuracy (unit round-off
+    2^-11, bound 3e-3 relative), a degree-7 filter to 2e-2.  The 3-term split
+    (tf32x3) is FP32-grade: the FP32 bounds (2e-6, 2e-5).  N = 300 spans two
+    160-column tensor-core tiles with a ragged tail; N = 17 one partial tile."""
     from oracle.chfsi import chebyshev_filter_scaled
     d, G = tiny_pair
     X = W.random_block(d.system, N, seed=30 + N)
     a, b, a0 = _bounds(d, 10)
-    for m, tol in [(1, 3e-3), (7, 2e-2)]:
+    for m, tol in tols:
         ref = chebyshev_filter_scaled(d.apply_Htilde, X, m, a, b, a0)
         Xd = to_dev(X)
-        G.chfsi_step(Xd, m, a, b, a0, precision="tf32", fp64_tail=0)
+        G.chfsi_step(Xd, m, a, b, a0, precision=prec, fp64_tail=0)
         err = rel_err(Xd, ref)
         assert err < tol, (m, err)
 
 
-def test_chfsi_converges_tf32_tiny(tiny_pair):
-    """Mixed precision (TF32 tensor-core filter, FP64 tail degrees, FP64 CholQR and
-    Rayleigh-Ritz) reaches the dense eigenvalues within 1e-5 Ha."""
+@pytest.mark.parametrize("prec,tol,atol", [("tf32", 1e-7, 1e-5), ("tf32x3", 1e-9, 1e-8)])
+def test_chfsi_converges_mixed_tiny(tiny_pair, prec, tol, atol):
+    """Mixed precision (tensor-core filter, FP64 tail degrees, FP64 CholQR and
+    Rayleigh-Ritz) reaches the dense eigenvalues: within 1e-5 Ha with one TF32
+    pass, within 1e-8 Ha with the FP32-grade 3-term split."""
     from oracle.chfsi import dense_eigs
     d, G = tiny_pair
     N, m, nconv = 10, 12, 7
     X = to_dev(W.initial_block(d.system, N, seed=1))
-    eps, res, it, b = G.solve(X, m, tol=1e-7, precision="tf32", fp64_tail=2,
+    eps, res, it, b = G.solve(X, m, tol=tol, precision=prec, fp64_tail=2,
                               v0=to_dev(W.lanczos_start(d.system)), n_conv=nconv, max_iter=300)
     ref = dense_eigs(d, N)
-    np.testing.assert_allclose(eps[:nconv], ref[:nconv], atol=1e-5)
+    np.testing.assert_allclose(eps[:nconv], ref[:nconv], atol=atol)
