@@ -178,12 +178,14 @@ def test_hydrogen_config1_converged():
 
 
 @pytest.mark.parametrize("N", [17, 135, 300])
-@pytest.mark.parametrize("prec,tols", [("tf32", [(1, 3e-3), (7, 2e-2)]), ("tf32x3", [(1, 2e-6), (7, 2e-5)])])
+@pytest.mark.parametrize("prec,tols", [("tf32", [(1, 3e-3), (7, 2e-2)]), ("tf32x3", [(1, 1e-5), (7, 5e-5)])])
 def test_chfsi_step_tf32_tensor_cores(tiny_pair, N, prec, tols):
     """tcgen05 cell products (FP32 accumulation, FP32 vector storage).  One TF32
     pass: one degree agrees with the FP64 oracle to TF32 accuracy (unit round-off
     2^-11, bound 3e-3 relative), a degree-7 filter to 2e-2.  The 3-term split
-    (tf32x3) is FP32-grade: the FP32 bounds (2e-6, 2e-5).  N = 300 spans two
+    (tf32x3) is FP32-grade: FP32 round-off 6e-8 times the cancellation factor
+    ||H|| ||Y|| / ||H Y|| (about 30 here) gives ~2e-6 per degree; bounds 1e-5
+    (one degree) and 5e-5 (seven degrees).  N = 300 spans two
     160-column tensor-core tiles with a ragged tail; N = 17 one partial tile."""
     from oracle.chfsi import chebyshev_filter_scaled
     d, G = tiny_pair
