@@ -194,6 +194,26 @@ int efe_enable_timing(efe_handle* h, int32_t enable);
 int efe_kernel_stats(efe_handle* h, int64_t* launches, double* total_ms, int64_t* cell_columns,
                      int32_t reset);
 
+/* Y = M^E X exactly as efe_apply_M, but allocation-free (no counterpart in the
+ * paper: it exists for callers that cannot allocate device memory at call
+ * time -- code recording work into a CUDA graph, where allocation calls are not
+ * allowed while a stream is being captured; latency-critical loops that cannot
+ * afford the device-wide synchronisation cudaMalloc/cudaFree imply; and hosts
+ * that hand the GPU a fixed, pre-planned memory budget).  The call allocates
+ * nothing: its one scratch buffer (the partial sums of the enrichment row
+ * products, n_segments x N doubles) is a file-scope device array of 2^21
+ * doubles (16 MiB) that every GPU loading the library holds until the process
+ * exits; the handle's own operator storage was allocated by efe_create.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Sizes needing more than 2^21 scratch doubles return
+ * EFE_ERR_ARG.  All calls share the array and it keeps the last call's
+ * contents (every entry a call reads is written by that call first), so calls
+ * that overlap on the GPU -- on different streams or from different threads --
+ * race and must be serialised by the caller.  Arguments as efe_apply_M. */
+int efe_apply_M_noalloc(efe_handle* h, const double* X, int64_t ldx, int32_t N,
+                        double* Y, int64_t ldy, void* stream);
+
 /* Number of CUDA kernels this library has launched since it was loaded (all
  * handles, all threads); a diagnostic counter for benchmarks. */
 int efe_launch_count(int64_t* total);

@@ -22,7 +22,7 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
 SYMBOLS = ["efe_create", "efe_destroy", "efe_last_error", "efe_sizes", "efe_qpoints", "efe_set_potential",
            "efe_set_potential_analytic", "efe_reserve", "efe_apply_H", "efe_apply_M", "efe_apply_Minv",
            "efe_upper_bound", "efe_chfsi_step", "efe_rayleigh_ritz", "efe_enable_timing", "efe_kernel_stats",
-           "efe_launch_count"]
+           "efe_launch_count", "efe_apply_M_noalloc"]
 
 
 class EfeError(RuntimeError):
@@ -78,6 +78,7 @@ def load(path=LIB_PATH):
         "efe_enable_timing": [vp, i32],
         "efe_kernel_stats": [vp, P64, PD, P64, i32],
         "efe_launch_count": [P64],
+        "efe_apply_M_noalloc": [vp, vp, i64, i32, vp, i64, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -224,6 +225,10 @@ class System:
 
     def apply_M(self, X, Y=None):
         return self._apply(self.L.efe_apply_M, X, Y)
+
+    def apply_M_noalloc(self, X, Y):
+        """M^E X through the allocation-free entry point (caller provides Y)."""
+        return self._apply(self.L.efe_apply_M_noalloc, X, Y)
 
     def apply_Minv(self, X, Y=None):
         return self._apply(self.L.efe_apply_Minv, X, Y)

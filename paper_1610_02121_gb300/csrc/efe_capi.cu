@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1001,3 +1002,68 @@ int efe_kernel_stats(efe_handle* h, int64_t* launches, double* total_ms, int64_t
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free overlap product.
+//
+// efe_apply_M_noalloc computes the same Y = M^E X as efe_apply_M, but its only
+// scratch (the per-segment partial sums of the M^ec row products) lives in
+// the file-scope device array below instead of the handle's workspace, so the
+// call performs no device allocation of any kind.  Every GPU that loads this
+// library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+#define EFE_NOALLOC_SCRATCH_DOUBLES (1 << 21)  // 16 MiB
+static __device__ __align__(256) double g_noalloc_scratch[EFE_NOALLOC_SCRATCH_DOUBLES];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {nullptr};
+
+// Device address of the scratch array on `dev` (which must be current).  Looked
+// up once per device; host code may not use the array's name as an address.
+int noalloc_scratch(efe_handle* h, int dev, double** out) {
+  if (dev < 0 || dev >= 256) {
+    h->err = "device ordinal out of range for the allocation-free scratch table";
+    return EFE_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      h->err = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
+      return EFE_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return EFE_OK;
+}
+}  // namespace
+
+extern "C" int efe_apply_M_noalloc(efe_handle* h, const double* X, int64_t ldx, int32_t N, double* Y, int64_t ldy,
+                                   void* stream) {
+  if (!h) return EFE_ERR_ARG;
+  TRY(check_block(h, X, ldx, N));
+  TRY(check_block(h, Y, ldy, N));
+  if (h->nE > 0 && h->nseg * (int64_t)N > EFE_NOALLOC_SCRATCH_DOUBLES) {
+    h->err = "efe_apply_M_noalloc: segments x N exceeds the static scratch of 2^21 doubles";
+    return EFE_ERR_ARG;
+  }
+  TRY(set_dev(h));
+  double* part = nullptr;
+  TRY(noalloc_scratch(h, h->dev, &part));
+  cudaStream_t st = S(stream);
+  const int64_t nn = h->n_nodes;
+  launch_row_scale<double>(nn, h->Dm, X, ldx, Y, ldy, N, st);
+  if (h->nE > 0) {
+    launch_spmm_nodes<double>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->mecT, 1.0, X + nn * ldx, ldx, Y, ldy, N, st);
+    launch_row_scale<double>(nn, h->mask, Y, ldy, Y, ldy, N, st);
+    // every partial is written before it is read: nothing to clear
+    launch_spmm_segments<double>(h->nseg, h->seg_start, h->seg_end, h->ec_col, h->mec, nullptr, X, ldx, part, N, st);
+    launch_seg_reduce((int)h->nE, h->row_seg_ptr, part, 1.0, nullptr, 0, 0.0, Y + nn * ldy, ldy, N, st);
+    launch_gemm_nn(h->nE, N, (int)h->nE, 1.0, h->Mee, h->nE, X + nn * ldx, ldx, 1.0, Y + nn * ldy, ldy, st);
+  }
+  CKL();
+  return EFE_OK;
+}
