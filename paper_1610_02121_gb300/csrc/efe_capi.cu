@@ -49,9 +49,7 @@ struct efe_handle {
   double *D = nullptr, *Dinv = nullptr, *mask = nullptr, *Dm = nullptr;
   double* Hcc = nullptr;
   float* Hcc32 = nullptr;
-  void* Hcc16 = nullptr;
-  float* Araw = nullptr;    // tcgen05 A images (FP32 values, core-matrix layout)
-  void* Aimg16 = nullptr;   // tcgen05 A images (BF16)
+  float *As1 = nullptr, *As2 = nullptr;  // TF32 split images of H^cc_e (chunk-major)
   int tc_mode = 0;          // 1: TF32 tcgen05 cell products, 2: 3-term split TF32 (FP32-grade)
   int n_sm = 148;
   bool time_this = false;   // the cell-apply timer records only the filter's mixed-precision launches
@@ -194,7 +192,7 @@ int reserve32(efe_handle* h, int N) {
   }
   TRY(dalloc(h, &h->Wf, h->n_nodes * ld));
   CK(cudaMemset(h->Wf, 0, sizeof(float) * h->n_nodes * ld));
-  h->npc = (int)std::max<int64_t>(64, (h->n_tn + 303) / 304);
+  h->npc = (int)std::max<int64_t>(32, (h->n_tn + 4 * h->n_sm - 1) / (4 * h->n_sm));
   h->ncb = coup_nblocks(std::max<int64_t>(1, h->n_tn), h->npc);
   TRY(dalloc(h, &h->cpart, (int64_t)h->ncb * std::max<int64_t>(1, h->nE) * N));
   h->ld32 = ld;
@@ -261,9 +259,13 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
       else
         launch_cell_apply_f64((const double*)Hc, cl, nc, h->mesh, (const double*)Y, ldy, (double*)Wc, ldw, N, st);
     } else {
-      if (tc)
-        launch_cell_tc2(h->Araw, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N, h->tc_mode == 2, h->n_sm,
-                        h->info + 4, st);
+      if (tc) {
+        if (launch_cell_tc3(h->As1, h->As2, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N,
+                            h->tc_mode == 2, h->n_sm, h->info + 4, st)) {
+          h->err = "tensor-core cell kernel needs 16-byte aligned rows";
+          return EFE_ERR_ARG;
+        }
+      }
       else if (N <= 8)
         launch_cell_apply_narrow_f32((const float*)Hc, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N, st);
       else
@@ -375,7 +377,7 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
   h->time_this = false;
   if (h->nE > 0) {
     const int nE = (int)h->nE;
-    if ((int64_t)nE * N * 4 <= 200 * 1024) {
+    if ((int64_t)nE * N * 4 <= 160 * 1024 && h->kmax <= 64) {
       launch_coup_cols<float>(h->n_tn, h->npc, h->t_nodes, h->t_ptr, h->t_col, h->hecT32, 1.f, Yce, N, nE, N, h->Wf,
                               ld, st);
       launch_coup_rows<float>(h->n_tn, h->npc, h->t_nodes, h->t_ptr, h->t_col, h->hecT32, nullptr, Yc, ld, nE, N,
@@ -523,9 +525,8 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
   }
   TRY(dalloc(h, &h->Hcc, h->n_cell * NL * NL));
   TRY(dalloc(h, &h->Hcc32, h->n_cell * NL * NL));
-  TRY(dalloc(h, (uint16_t**)&h->Hcc16, h->n_cell * NL * NL));
-  TRY(dalloc(h, &h->Araw, tc_image_elems(h->n_cell)));
-  TRY(dalloc(h, (uint16_t**)&h->Aimg16, tc_image_elems(h->n_cell)));
+  TRY(dalloc(h, &h->As1, tc3_image_elems(h->n_cell)));
+  TRY(dalloc(h, &h->As2, tc3_image_elems(h->n_cell)));
   TRY(dalloc(h, &h->info, 8));
   if (h->nE > 0) {
     TRY(upload(h, &h->funcs, s.funcs));
@@ -647,9 +648,7 @@ int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
     CKL();
   }
   launch_to_f32(h->Hcc, h->Hcc32, h->n_cell * NL * NL, st);
-  launch_to_bf16(h->Hcc, h->Hcc16, h->n_cell * NL * NL, st);
-  launch_build_araw(h->Hcc, h->n_cell, h->Araw, st);
-  launch_build_aimg_bf16(h->Hcc, h->n_cell, h->Aimg16, st);
+  launch_build_asplit(h->Hcc, h->n_cell, h->As1, h->As2, st);
   CKL();
   h->potential_set = true;
   return EFE_OK;

@@ -245,11 +245,6 @@ __global__ void k_to_f32(const double* __restrict__ s, float* __restrict__ d, in
   if (i < n) d[i] = (float)s[i];
 }
 
-__global__ void k_to_bf16(const double* __restrict__ s, __nv_bfloat16* __restrict__ d, int64_t n) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) d[i] = __double2bfloat16(s[i]);
-}
-
 // ---------------------------------------------------------------------------
 // hot path
 // ---------------------------------------------------------------------------
@@ -457,33 +452,64 @@ __global__ void __launch_bounds__(256) k_cell_apply_narrow(const T* __restrict__
 }
 
 // Node-major enrichment products (FP32 arithmetic, mixed-precision filter).
-// Rows product: part[b][a][c] = sum over the nodes g of chunk b of
+// Nodes are processed in chunks of CH: the chunk's slice of the pattern
+// (function ids and values) is staged in shared memory, then every thread
+// (one vector column) issues the chunk's CH independent row loads before it
+// uses them, so many loads are in flight per thread.
+constexpr int CPL_CH = 32;           // nodes per chunk
+constexpr int CPL_QMAX = CPL_CH * 64; // pattern entries per chunk (<= 64 functions per node)
+
+// Rows product: part[b][a][c] = sum over the nodes g of CTA b of
 //   sum_{a in pattern(g)} val[g, a] * scale[g] * X[g][c]
 // with the (n_E x N) accumulator in shared memory, so each vector row is read
 // once however many enrichment supports contain its node.
 template <typename T>
-__global__ void k_coup_rows(int64_t n_tn, int npc, const int32_t* __restrict__ t_nodes,
-                            const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_col,
-                            const float* __restrict__ tval, const double* __restrict__ scale,
-                            const T* __restrict__ X, int64_t ldx, int nE, int N, float* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, int npc, const int32_t* __restrict__ t_nodes,
+                                                   const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_col,
+                                                   const float* __restrict__ tval, const double* __restrict__ scale,
+                                                   const T* __restrict__ X, int64_t ldx, int nE, int N,
+                                                   float* __restrict__ part) {
   extern __shared__ float acc[];
+  __shared__ int64_t sg[CPL_CH];
+  __shared__ float ss[CPL_CH];
+  __shared__ int sp[CPL_CH + 1];
+  __shared__ int scol[CPL_QMAX];
+  __shared__ float sval[CPL_QMAX];
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int i = tid; i < nE * N; i += bd) acc[i] = 0.f;
-  __syncthreads();
   const int64_t r0 = (int64_t)blockIdx.x * npc;
   const int64_t r1 = min(n_tn, r0 + npc);
-  for (int64_t r = r0; r < r1; ++r) {
-    const int64_t g = t_nodes[r];
-    const float s = scale ? (float)scale[g] : 1.f;
-    const int64_t q0 = t_ptr[r], q1 = t_ptr[r + 1];
+  for (int64_t rc = r0; rc < r1; rc += CPL_CH) {
+    const int nn = (int)min((int64_t)CPL_CH, r1 - rc);
+    const int64_t qa = t_ptr[rc];
+    __syncthreads();
+    if (tid < nn) {
+      const int64_t g = t_nodes[rc + tid];
+      sg[tid] = g;
+      ss[tid] = scale ? (float)scale[g] : 1.f;
+    }
+    if (tid <= nn) sp[tid] = (int)(t_ptr[rc + tid] - qa);
+    const int nq = (int)(t_ptr[rc + nn] - qa);
+    for (int q = tid; q < nq; q += bd) {
+      scol[q] = t_col[qa + q];
+      sval[q] = tval[qa + q];
+    }
+    __syncthreads();
     for (int c = tid; c < N; c += bd) {
-      const float x = s * (float)X[g * ldx + c];
-      for (int64_t q = q0; q < q1; ++q) acc[t_col[q] * N + c] = fmaf(tval[q], x, acc[t_col[q] * N + c]);
+      float xv[CPL_CH];
+#pragma unroll
+      for (int u = 0; u < CPL_CH; ++u) xv[u] = (u < nn) ? (float)X[sg[u] * ldx + c] : 0.f;
+#pragma unroll
+      for (int u = 0; u < CPL_CH; ++u) {
+        if (u >= nn) break;
+        const float x = ss[u] * xv[u];
+        for (int q = sp[u]; q < sp[u + 1]; ++q) acc[scol[q] * N + c] = fmaf(sval[q], x, acc[scol[q] * N + c]);
+      }
     }
   }
   __syncthreads();
-  float* P = part + (int64_t)blockIdx.x * nE * N;
-  for (int i = tid; i < nE * N; i += bd) P[i] = acc[i];
+  float* Pp = part + (int64_t)blockIdx.x * nE * N;
+  for (int i = tid; i < nE * N; i += bd) Pp[i] = acc[i];
 }
 
 // out[a][c] = alpha_base * base[a][c] + sgn * sum_b part[b][a][c]  (fixed order, FP64)
@@ -503,24 +529,43 @@ __global__ void k_coup_reduce(int nb, int nE, int N, const float* __restrict__ p
 // Columns product: W[g][c] += sgn * sum_{a in pattern(g)} val[g, a] * Xe[a][c], Xe staged in
 // shared memory as FP32.
 template <typename T>
-__global__ void k_coup_cols(int64_t n_tn, int npc, const int32_t* __restrict__ t_nodes,
-                            const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_col,
-                            const float* __restrict__ tval, float sgn, const double* __restrict__ Xe, int64_t ldxe,
-                            int nE, int N, T* __restrict__ W, int64_t ldw) {
+__global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, int npc, const int32_t* __restrict__ t_nodes,
+                                                   const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_col,
+                                                   const float* __restrict__ tval, float sgn,
+                                                   const double* __restrict__ Xe, int64_t ldxe, int nE, int N,
+                                                   T* __restrict__ W, int64_t ldw) {
   extern __shared__ float xs[];
+  __shared__ int64_t sg[CPL_CH];
+  __shared__ int sp[CPL_CH + 1];
+  __shared__ int scol[CPL_QMAX];
+  __shared__ float sval[CPL_QMAX];
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int i = tid; i < nE * N; i += bd) xs[i] = (float)Xe[(int64_t)(i / N) * ldxe + i % N];
-  __syncthreads();
   const int64_t r0 = (int64_t)blockIdx.x * npc;
   const int64_t r1 = min(n_tn, r0 + npc);
-  for (int64_t r = r0; r < r1; ++r) {
-    const int64_t g = t_nodes[r];
-    const int64_t q0 = t_ptr[r], q1 = t_ptr[r + 1];
+  for (int64_t rc = r0; rc < r1; rc += CPL_CH) {
+    const int nn = (int)min((int64_t)CPL_CH, r1 - rc);
+    const int64_t qa = t_ptr[rc];
+    __syncthreads();
+    if (tid < nn) sg[tid] = t_nodes[rc + tid];
+    if (tid <= nn) sp[tid] = (int)(t_ptr[rc + tid] - qa);
+    const int nq = (int)(t_ptr[rc + nn] - qa);
+    for (int q = tid; q < nq; q += bd) {
+      scol[q] = t_col[qa + q];
+      sval[q] = tval[qa + q];
+    }
+    __syncthreads();
     for (int c = tid; c < N; c += bd) {
-      float s = 0.f;
-      for (int64_t q = q0; q < q1; ++q) s = fmaf(tval[q], xs[t_col[q] * N + c], s);
-      T* w = W + g * ldw + c;
-      *w = (T)((float)(*w) + sgn * s);
+      float wv[CPL_CH];
+#pragma unroll
+      for (int u = 0; u < CPL_CH; ++u) wv[u] = (u < nn) ? (float)W[sg[u] * ldw + c] : 0.f;
+#pragma unroll
+      for (int u = 0; u < CPL_CH; ++u) {
+        if (u >= nn) break;
+        float s = 0.f;
+        for (int q = sp[u]; q < sp[u + 1]; ++q) s = fmaf(sval[q], xs[scol[q] * N + c], s);
+        W[sg[u] * ldw + c] = (T)(wv[u] + sgn * s);
+      }
     }
   }
 }
@@ -946,12 +991,6 @@ void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-void launch_to_bf16(const double* src, void* dst, int64_t n, cudaStream_t st) {
-  if (n <= 0) return;
-  k_to_bf16<<<grid1(n, 256), 256, 0, st>>>(src, (__nv_bfloat16*)dst, n);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-}
-
 void launch_cell_apply_f64(const double* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
                            const double* Y, int64_t ldy, double* W, int64_t ldw, int N, cudaStream_t st) {
   if (ncells <= 0 || N <= 0) return;
@@ -1175,7 +1214,7 @@ void launch_coup_rows(int64_t n_tn, int npc, const int32_t* t_nodes, const int64
                       cudaStream_t st) {
   if (n_tn <= 0 || N <= 0 || nE <= 0) return;
   const int nb = coup_nblocks(n_tn, npc);
-  const int t = N >= 256 ? 256 : ((N + 31) / 32) * 32;
+  const int t = N >= 256 ? 256 : (N < 64 ? 64 : ((N + 31) / 32) * 32);
   const size_t smem = sizeof(float) * (size_t)nE * N;
   cudaFuncSetAttribute(k_coup_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_coup_rows<T><<<nb, t, smem, st>>>(n_tn, npc, t_nodes, t_ptr, t_col, tval, scale, X, ldx, nE, N, part);
@@ -1197,7 +1236,7 @@ void launch_coup_cols(int64_t n_tn, int npc, const int32_t* t_nodes, const int64
                       cudaStream_t st) {
   if (n_tn <= 0 || N <= 0 || nE <= 0) return;
   const int nb = coup_nblocks(n_tn, npc);
-  const int t = N >= 256 ? 256 : ((N + 31) / 32) * 32;
+  const int t = N >= 256 ? 256 : (N < 64 ? 64 : ((N + 31) / 32) * 32);
   const size_t smem = sizeof(float) * (size_t)nE * N;
   cudaFuncSetAttribute(k_coup_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_coup_cols<T><<<nb, t, smem, st>>>(n_tn, npc, t_nodes, t_ptr, t_col, tval, sgn, Xe, ldxe, nE, N, W, ldw);

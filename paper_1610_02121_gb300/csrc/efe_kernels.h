@@ -40,7 +40,6 @@ void launch_gather_sum(int64_t n_out, const double* base, const int64_t* cptr, c
                        const double* blk, double* out, cudaStream_t st);
 void launch_permute(int64_t n, const double* src, const int64_t* perm, double* dst, cudaStream_t st);
 void launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t st);
-void launch_to_bf16(const double* src, void* dst, int64_t n, cudaStream_t st);
 
 // ---- hot path (FP64 and FP32 storage) ----
 // W_c(cell nodes) += H_e Y_e for the cells of one parity colour
@@ -98,18 +97,12 @@ void launch_copy_rows(int64_t nrows, const double* X, int64_t ldx, double* Y, in
 void launch_zero_rows(int64_t nrows, double* X, int64_t ldx, int N, cudaStream_t st);
 void launch_zero_rows_f32(int64_t nrows, float* X, int64_t ldx, int N, cudaStream_t st);
 
-// ---- tcgen05 cell products (efe_cell_tc.cu) ----
-int64_t tc_image_elems(int64_t n_cell);
-void launch_build_aimg_tf32(const double* Hcc, int64_t n_cell, float* img, cudaStream_t st);
-void launch_build_aimg_bf16(const double* Hcc, int64_t n_cell, void* img, cudaStream_t st);
-int launch_cell_tc_tf32(const float* Aimg, const int32_t* cells, int64_t ncells, const MeshDev& m, const float* Y,
-                        int64_t ldy, float* W, int64_t ldw, int N, int* err, cudaStream_t st);
-int launch_cell_tc_bf16(const void* Aimg, const int32_t* cells, int64_t ncells, const MeshDev& m, const void* Y,
-                        int64_t ldy, void* W, int64_t ldw, int N, int* err, cudaStream_t st);
-
-void launch_build_araw(const double* Hcc, int64_t n_cell, float* img, cudaStream_t st);
-int launch_cell_tc2(const float* Araw, const int32_t* cells, int64_t ncells, const MeshDev& m, const float* Y,
-                    int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err, cudaStream_t st);
+// ---- tcgen05 cell products (efe_cell_tc3.cu) ----
+int64_t tc3_image_elems(int64_t n_cell);
+void launch_build_asplit(const double* Hcc, int64_t n_cell, float* A1, float* A2, cudaStream_t st);
+int launch_cell_tc3(const float* A1, const float* A2, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                    const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
+                    cudaStream_t st);
 
 // ---- dense FP64 ----
 // C[M x Nc] = alpha * A[M x K] B[K x Nc] + beta * C   (row-major, lda/ldb/ldc)
