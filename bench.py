@@ -271,7 +271,7 @@ def main():
     else:
         achieved = alg_bytes / (k_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "kernel": "k_cell_tc2<%s>" % ("true" if prec == "tf32x3" else "false"),
+                "traffic": None, "kernel": "k_cell_tc3<%s>" % ("true" if prec == "tf32x3" else "false"),
                 "launches": n_launch, "algorithmic_tflops": alg_flops / (k_ms * 1e-3) / 1e12,
                 "avg_launch_ms": k_ms / max(n_launch, 1), "peak_source": peak_src}
     line = {"metric": "chfsi_filter_tflops", "value": value, "unit": "TFLOP/s", "n_gpus": world,
