@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32", "tf32", "fp64"])
     p.add_argument("--fp64-tail", type=int, default=2)
+    p.add_argument("--fp64-engine", default="tensor", choices=["tensor", "dfma"],
+                   help="engine of the FP64 parts of the mixed step (the FP64 comparison always uses dfma)")
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -215,7 +217,8 @@ def main():
         e, r = G.rayleigh_ritz(Xb)
         return e, r, b
 
-    def timed(prec, warm, steps, timing=False):
+    def timed(prec, warm, steps, timing=False, engine=None):
+        G.set_fp64_engine(engine or (args.fp64_engine if prec != "fp64" else "dfma"))
         Xb = X_start.clone()
         e = eps_start.copy()
         for _ in range(warm):
@@ -283,6 +286,7 @@ def main():
                                                            else "hydrogen Z=1, 6x6x6 cells"),
                        "nodes": G.n_nodes, "cells": G.n_cells, "n_enrich": G.n_enrich, "N": N, "m": m,
                        "fp64_tail": args.fp64_tail if prec != "fp64" else 0,
+                       "fp64_engine": args.fp64_engine if prec != "fp64" else "dfma",
                        "l2": "vector blocks (>= 0.8 GB) and cell matrices exceed the 129 MB L2",
                        "step": "Lanczos bound (10) + degree-m filter + CholQR + Rayleigh-Ritz",
                        "filter_flops_per_step": flops_step, "setup_s": t_setup},
@@ -291,12 +295,16 @@ def main():
         line["clocks"] = clocks
     # FP64 mode of the same step
     if not args.no_fp64 and prec != "fp64":
-        ms64, eps64, res64, _, _, _, _ = timed("fp64", 1, args.fp64_steps)
+        ms64, eps64, res64, _, _, _, _ = timed("fp64", 1, args.fp64_steps, engine="dfma")
         _, eps_chk, _, _, _, _, _ = timed(prec, 1, args.fp64_steps)
+        ms64t, eps64t, _, _, _, _, _ = timed("fp64", 1, args.fp64_steps, engine="tensor")
         line["fp64"] = {"ms_per_step": ms64, "tflops": flops_step / (ms64 * 1e-3) / 1e12,
+                        "engine": "dfma (plain FP64)",
                         "speedup_mixed_vs_fp64": ms64 / ms,
                         "max_abs_eig_diff_vs_fp64_Ha": float(np.abs(eps_chk - eps64).max()),
                         "steps_compared": 1 + args.fp64_steps}
+        line["fp64_tensor_engine"] = {"ms_per_step": ms64t, "tflops": flops_step / (ms64t * 1e-3) / 1e12,
+                                      "max_abs_eig_diff_vs_dfma_Ha": float(np.abs(eps64t - eps64).max())}
     # end to end through the public API with host buffers
     if not args.no_e2e:
         Xh = X_start.cpu().pin_memory()

@@ -184,6 +184,15 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m,
 int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N,
                       double* eig_host, double* resid_host, void* stream);
 
+/* Engine for the FP64 products (the FP64 filter degrees, the H apply and the
+ * tall N x N products of Rayleigh-Ritz): 0 = FP64 DFMA (default, the plain
+ * FP64 path); 1 = FP64-grade products on the BF16 tensor cores by error-free
+ * operand slicing (Ozaki scheme: seven 7-bit digits per operand, exact FP32
+ * accumulation of the leading digit products; error within a few units of
+ * 2^-48 of sum |a||b|).  Applies to N > 8 cell products and to N <= 144 tall
+ * products; other cases keep DFMA.  Host setting, no device work. */
+int efe_set_fp64_engine(efe_handle* h, int32_t engine);
+
 /* Kernel timing: when enabled, the library brackets every launch of its
  * classical cell-apply kernel (any precision) with CUDA events on the
  * launching stream.  efe_kernel_stats synchronises the device, then returns

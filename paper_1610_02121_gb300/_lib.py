@@ -22,7 +22,7 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
 SYMBOLS = ["efe_create", "efe_destroy", "efe_last_error", "efe_sizes", "efe_qpoints", "efe_set_potential",
            "efe_set_potential_analytic", "efe_reserve", "efe_apply_H", "efe_apply_M", "efe_apply_Minv",
            "efe_upper_bound", "efe_chfsi_step", "efe_rayleigh_ritz", "efe_enable_timing", "efe_kernel_stats",
-           "efe_launch_count", "efe_apply_M_noalloc"]
+           "efe_launch_count", "efe_apply_M_noalloc", "efe_set_fp64_engine"]
 
 
 class EfeError(RuntimeError):
@@ -79,6 +79,7 @@ def load(path=LIB_PATH):
         "efe_kernel_stats": [vp, P64, PD, P64, i32],
         "efe_launch_count": [P64],
         "efe_apply_M_noalloc": [vp, vp, i64, i32, vp, i64, vp],
+        "efe_set_fp64_engine": [vp, i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -268,6 +269,11 @@ class System:
             if res[:n_conv].max() < tol:
                 break
         return eps, res, it, b
+
+    def set_fp64_engine(self, engine):
+        """0: FP64 DFMA products; 1 (or "tensor"): FP64-grade products on the BF16 tensor cores."""
+        e = {"dfma": 0, "tensor": 1}.get(engine, engine)
+        self._check(self.L.efe_set_fp64_engine(self.h, int(e)))
 
     def enable_timing(self, on=True):
         self._check(self.L.efe_enable_timing(self.h, int(bool(on))))

@@ -52,6 +52,11 @@ struct efe_handle {
   float *As1 = nullptr, *As2 = nullptr;  // TF32 split images of H^cc_e (chunk-major)
   int tc_mode = 0;          // 1: TF32 tcgen05 cell products, 2: 3-term split TF32 (FP32-grade)
   int n_sm = 148;
+  int fp64_engine = 0;      // 0: FP64 DFMA products; 1: FP64-grade products on the BF16 tensor cores
+  int* hexp = nullptr;      // per-cell row exponents of H^cc_e (tensor-core FP64 products)
+  int* oz_fexp = nullptr;   // per-column exponents (N)
+  int* oz_bexp = nullptr;   // per-column exponents of small right-hand matrices (N)
+  int* oz_aexp = nullptr;   // per-row exponents of tall left-hand matrices (rows)
   bool time_this = false;   // the cell-apply timer records only the filter's mixed-precision launches
   DevFunc* funcs = nullptr;
   int32_t *enr_cells = nullptr, *cf_ptr = nullptr, *cf_idx = nullptr;
@@ -173,6 +178,10 @@ int reserve(efe_handle* h, int N) {
   h->tnwork_elems = gemm_tn_work_elems(R, N, N);
   TRY(dalloc(h, &h->tnwork, h->tnwork_elems));
   TRY(dalloc(h, &h->rpart, ((R + 2047) / 2048 + 1) * (int64_t)N));
+  dfree(h, h->oz_fexp);
+  dfree(h, h->oz_bexp);
+  TRY(dalloc(h, &h->oz_fexp, N));
+  TRY(dalloc(h, &h->oz_bexp, N));
   h->Nres = N;
   return EFE_OK;
 }
@@ -247,6 +256,19 @@ int timed_end(efe_handle* h, cudaStream_t st, int slot, int64_t cellcols) {
 template <typename T>
 int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, int64_t ldw, int N, cudaStream_t st,
                    bool tc = false) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->fp64_engine == 1 && N > 8) {
+      launch_oz_colexp((const double*)Y, ldy, h->n_nodes, N, h->oz_fexp, st);
+      for (int c = 0; c < 8; ++c) {
+        const int64_t nc = h->colour_off[c + 1] - h->colour_off[c];
+        if (nc == 0) continue;
+        launch_oz_cell(h->Hcc, h->hexp, h->colour_cells + h->colour_off[c], nc, h->mesh, (const double*)Y, ldy,
+                       h->oz_fexp, (double*)Wc, ldw, N, h->n_sm, h->info + 4, st);
+      }
+      CKL();
+      return EFE_OK;
+    }
+  }
   for (int c = 0; c < 8; ++c) {
     const int64_t nc = h->colour_off[c + 1] - h->colour_off[c];
     if (nc == 0) continue;
@@ -525,6 +547,8 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
   }
   TRY(dalloc(h, &h->Hcc, h->n_cell * NL * NL));
   TRY(dalloc(h, &h->Hcc32, h->n_cell * NL * NL));
+  TRY(dalloc(h, &h->hexp, oz_hexp_elems(h->n_cell)));
+  TRY(dalloc(h, &h->oz_aexp, h->rows));
   TRY(dalloc(h, &h->As1, tc3_image_elems(h->n_cell)));
   TRY(dalloc(h, &h->As2, tc3_image_elems(h->n_cell)));
   TRY(dalloc(h, &h->info, 8));
@@ -649,6 +673,7 @@ int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
   }
   launch_to_f32(h->Hcc, h->Hcc32, h->n_cell * NL * NL, st);
   launch_build_asplit(h->Hcc, h->n_cell, h->As1, h->As2, st);
+  launch_oz_hexp(h->Hcc, h->n_cell, h->hexp, st);
   CKL();
   h->potential_set = true;
   return EFE_OK;
@@ -859,7 +884,7 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
     launch_copy_rows(h->rows, buf[cur], ld[cur], X, ldx, N, st);
     CKL();
   }
-  if (n_low > 0 && h->tc_mode) {
+  if ((n_low > 0 && h->tc_mode) || h->fp64_engine == 1) {
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, h->info + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -868,6 +893,21 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
       return EFE_ERR_TIMEOUT;
     }
   }
+  return EFE_OK;
+}
+
+// C = A B for a tall A (rows x N) and a small B (N x N): tensor-core FP64-grade
+// products when enabled (N <= 144), FP64 DFMA otherwise.
+int gemm_tall(efe_handle* h, int64_t rows, int N, const double* A, int64_t lda, const double* B, double* C,
+              int64_t ldc, cudaStream_t st) {
+  if (h->fp64_engine == 1 && N <= 144) {
+    launch_oz_rowexp(A, lda, rows, N, h->oz_aexp, st);
+    launch_oz_colexp(B, N, N, N, h->oz_bexp, st);
+    launch_oz_rows(A, lda, rows, N, h->oz_aexp, B, N, h->oz_bexp, C, ldc, N, h->n_sm, h->info + 4, st);
+  } else {
+    launch_gemm_nn(rows, N, N, 1.0, A, lda, B, N, 0.0, C, ldc, st);
+  }
+  CKL();
   return EFE_OK;
 }
 
@@ -915,8 +955,8 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   }
   launch_trinv_lower(G, N, N, Linv, N, st);
   launch_transpose(Linv, N, N, Rinv, N, st);
-  launch_gemm_nn(R, N, N, 1.0, X, ldx, Rinv, N, 0.0, Q, N, st);
-  CKL();
+  CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
+  TRY(gemm_tall(h, R, N, X, ldx, Rinv, Q, N, st));
   // projections
   TRY(apply_H_impl(h, Q, N, N, HQ, N, st));
   TRY(apply_M_impl(h, Q, N, N, MQ, N, st));
@@ -943,15 +983,20 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   launch_sort_eig(wv, Vj, N, N, eps, Z, N, st);
   launch_gemm_nn(N, N, N, 1.0, LminvT, N, Z, N, 0.0, Psi, N, st);
   // rotation and residuals
-  launch_gemm_nn(R, N, N, 1.0, Q, N, Psi, N, 0.0, X, ldx, st);
-  launch_gemm_nn(R, N, N, 1.0, HQ, N, Psi, N, 0.0, Q, N, st);    // HX
-  launch_gemm_nn(R, N, N, 1.0, MQ, N, Psi, N, 0.0, HQ, N, st);   // MX
+  TRY(gemm_tall(h, R, N, Q, N, Psi, X, ldx, st));
+  TRY(gemm_tall(h, R, N, HQ, N, Psi, Q, N, st));     // HX
+  TRY(gemm_tall(h, R, N, MQ, N, Psi, HQ, N, st));    // MX
   launch_resid_norms(R, Q, N, HQ, N, eps, N, h->rpart, res, st);
   CKL();
   CK(cudaMemcpyAsync(inf + 1, h->info + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(eig_host, eps, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
   if (resid_host) CK(cudaMemcpyAsync(resid_host, res, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(inf, h->info + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (inf[0]) {
+    h->err = "tensor-core FP64 product: bounded wait ran out";
+    return EFE_ERR_TIMEOUT;
+  }
   if (inf[1]) {
     h->err = "Jacobi eigensolver did not converge";
     return EFE_ERR_NOCONV;
@@ -961,6 +1006,12 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
       h->err = "non-finite Ritz value";
       return EFE_ERR_NAN;
     }
+  return EFE_OK;
+}
+
+int efe_set_fp64_engine(efe_handle* h, int32_t engine) {
+  if (!h || (engine != 0 && engine != 1)) return EFE_ERR_ARG;
+  h->fp64_engine = engine;
   return EFE_OK;
 }
 

@@ -104,6 +104,17 @@ int launch_cell_tc3(const float* A1, const float* A2, const int32_t* cells, int6
                     const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
                     cudaStream_t st);
 
+// ---- FP64-grade products on the BF16 tensor cores (efe_oz.cu) ----
+int64_t oz_hexp_elems(int64_t n_cell);
+void launch_oz_hexp(const double* Hcc, int64_t n_cell, int* hexp, cudaStream_t st);
+void launch_oz_colexp(const double* Y, int64_t ldy, int64_t rows, int N, int* fexp, cudaStream_t st);
+void launch_oz_rowexp(const double* A, int64_t lda, int64_t rows, int K, int* aexp, cudaStream_t st);
+int launch_oz_cell(const double* Hcc, const int* hexp, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                   const double* Y, int64_t ldy, const int* fexp, double* W, int64_t ldw, int N, int n_sm, int* err,
+                   cudaStream_t st);
+int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, const double* B, int64_t ldb,
+                   const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st);
+
 // ---- dense FP64 ----
 // C[M x Nc] = alpha * A[M x K] B[K x Nc] + beta * C   (row-major, lda/ldb/ldc)
 void launch_gemm_nn(int64_t M, int Nc, int K, double alpha, const double* A, int64_t lda, const double* B,

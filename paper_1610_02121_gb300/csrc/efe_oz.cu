@@ -1,0 +1,505 @@
+// FP64-grade products on the BF16 tensor cores by error-free slicing (Ozaki scheme;
+// Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012), sm_103a tcgen05.
+//
+// Each FP64 operand row (of A) / column (of B) is scaled by a power of two so
+// that its largest entry is below 1 in magnitude, truncated to 49 bits, and cut
+// into seven signed 7-bit digits d_1..d_7 (x ~ 2^E sum_i d_i 2^-7i).  Digit i
+// is stored in BF16 as d_i 2^-7(i-1) (exact: 7 significant bits).  The product
+// sum_k a_i b_j of digit slices has weight 2^-7(i+j-2); for a fixed t = i + j
+// every partial sum is an integer multiple of 2^-7(t-2) below 2^24 of that
+// unit (K <= 144, at most four pairs), so the FP32 tensor-core accumulators
+// for t = 2, 3, 4, 5 are exact.  The pairs with t = 6..8 share a fifth
+// accumulator (their FP32 rounding is below 2^-52 of the result); pairs with
+// t > 8 fall below the 49-bit truncation and are dropped.  The epilogue adds
+// the five accumulators with error-free FP32 sums into a (hi, lo) pair and
+// forms the FP64 result 2^(E_A + E_B - 14) (hi + lo).  The error is within a
+// few units of 2^-48 of sum_k |a_k||b_k|, comparable to FP64 GEMM rounding.
+//
+// Modes:
+//   CELL  W(cell nodes) += H^cc_e Y_e for the cells of one parity colour
+//         (Sec. V, last paragraph; cells of a colour share no node);
+//   ROWS  C = A B for a tall A (rows x K, K <= 144) and a small B (K x N).
+//
+// Warp roles (512 threads): warp 0 issues the MMAs (one elected lane),
+// warps 1-11 slice operands into the shared-memory stage ring (3 stages),
+// warps 12-15 combine the accumulators and write the result.  All waits are
+// bounded (about one second); on timeout the CTA records an error and leaves.
+#include <stdint.h>
+
+#include "efe_kernels.h"
+
+namespace efe {
+
+namespace {
+
+constexpr int OZ_S = 7;            // digits per operand
+constexpr int OZ_M = 128;          // MMA rows
+constexpr int OZ_KC = 16;          // K per chunk (one BF16 MMA)
+constexpr int OZ_TW = 96;          // column tile
+constexpr int OZ_NACC = 5;         // accumulators: t = 2, 3, 4, 5 exact; t = 6..8 shared
+constexpr int OZ_STAGES = 3;
+constexpr int OZ_THREADS = 512;
+constexpr int OZ_CONV_W0 = 1, OZ_CONV_WN = 11, OZ_EPI_W0 = 12;
+constexpr int OZ_CONV_T = OZ_CONV_WN * 32;
+constexpr uint32_t OZ_TMEM_COLS = 512;
+constexpr long long OZ_WAIT = 2000000000LL;
+
+struct OzL {
+  static constexpr uint32_t ASL = OZ_M * OZ_KC * 2;        // one A slice, 4 KB
+  static constexpr uint32_t BSL = OZ_TW * OZ_KC * 2;       // one B slice, 3 KB
+  static constexpr uint32_t STAGE = OZ_S * (ASL + BSL);    // 49 KB
+  static constexpr uint32_t BARS = OZ_STAGES * STAGE;
+  static constexpr size_t TOTAL = (size_t)BARS + 256;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major, no swizzle, BF16: core matrix 8 rows x 16 B; LBO = 128 B (next 8 K), SBO = 256 B (next 8 rows)
+__device__ __forceinline__ uint32_t bo(int row, int k) {
+  return (uint32_t)(row >> 3) * 256u + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(256u >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(OZ_M >> 4) << 24);
+}
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
+  uint32_t done = 0;
+  const long long t0 = clock64();
+  do {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  } while (clock64() - t0 < OZ_WAIT);
+  return false;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+               : "memory");
+}
+
+// scale exponent of one value: |x| < 2^E (zero -> very small)
+__device__ __forceinline__ int exp_of(double x) {
+  const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+  return ex == 0 ? -2000 : ex - 1022;
+}
+
+// seven BF16 digit slices of x with row/column exponent E, written to slice
+// buffers base + i * stride at byte offset off
+__device__ __forceinline__ void slice_store(double x, int E, unsigned char* base, uint32_t stride, uint32_t off) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  const uint16_t sgn = (uint16_t)((bits >> 48) & 0x8000);
+  unsigned long long q = 0;
+  const int rs = 1026 + E - ex;
+  if (ex != 0 && rs >= 0 && rs < 64) q = ((unsigned long long)(bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> rs;
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i) {
+    const uint32_t d = (uint32_t)(q >> (42 - 7 * i)) & 127u;
+    uint16_t v = 0;
+    if (d) {
+      const int p = 31 - __clz(d);
+      v = (uint16_t)(sgn | (uint16_t)((p + 127 - 7 * i) << 7) | (uint16_t)((d << (7 - p)) & 0x7Fu));
+    }
+    *reinterpret_cast<uint16_t*>(base + i * stride + off) = v;
+  }
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+struct OzArgs {
+  int mode;                 // 0: CELL, 1: ROWS
+  // CELL
+  const double* H;          // n_cell x 125 x 125
+  const int* hexp;          // n_cell x 128 row exponents
+  const int32_t* cells;
+  int64_t ncells;
+  MeshDev m;
+  // ROWS
+  const double* A;          // rows x K
+  int64_t lda, arows;
+  const int* aexp;          // per row of A
+  const double* B;          // K x N
+  int64_t ldb;
+  // common
+  int K;                    // reduction length (<= 144)
+  const double* Y;          // CELL: vector block (nodes x N)
+  int64_t ldy;
+  const int* fexp;          // per column of Y (CELL) or of B (ROWS)
+  double* out;              // CELL: W (accumulated); ROWS: C (stored)
+  int64_t ldo;
+  int N, ntiles;
+  int* err;
+};
+
+__device__ __forceinline__ int64_t oz_cell_node(const MeshDev& m, int64_t e, int k) {
+  const int i = (int)(e % m.nc[0]), j = (int)((e / m.nc[0]) % m.nc[1]), kk = (int)(e / ((int64_t)m.nc[0] * m.nc[1]));
+  const int a = k % NP1, b = (k / NP1) % NP1, c = k / (NP1 * NP1);
+  return (int64_t)(P * i + a) + (int64_t)m.nn[0] * ((int64_t)(P * j + b) + (int64_t)m.nn[1] * (int64_t)(P * kk + c));
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ int s_skip;
+  if (tid == 0) s_skip = *(volatile int*)g.err;
+  __syncthreads();
+  if (s_skip) return;
+  uint64_t* conv = reinterpret_cast<uint64_t*>(sm + OzL::BARS);  // [3]
+  uint64_t* empty = conv + 3;                                   // [3]
+  uint64_t* accf = conv + 6;
+  uint64_t* acce = conv + 7;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(conv + 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(conv + 9);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      bar_init(conv + s, OZ_CONV_T);
+      bar_init(empty + s, 1);
+    }
+    bar_init(accf, 1);
+    bar_init(acce, 128);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const int64_t nA = (g.mode == 0) ? g.ncells : (g.arows + OZ_M - 1) / OZ_M;
+  const int64_t nitems = nA * g.ntiles;
+  const int64_t my = nitems > blockIdx.x ? (nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int nch = (g.K + OZ_KC - 1) / OZ_KC;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- MMA issuer
+    for (int64_t t = 0; t < my && !*abort_flag; ++t) {
+      const int64_t item = blockIdx.x + t * gridDim.x;
+      const int c0 = (int)(item % g.ntiles) * OZ_TW;
+      const int ncol = min(OZ_TW, g.N - c0);
+      const int nmma = ((ncol + 15) / 16) * 16;
+      bool ok = true;
+      if (t >= 1) ok = bar_wait(acce, (uint32_t)((t - 1) & 1));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int kc = 0; kc < nch && ok; ++kc) {
+        const int64_t ch = t * nch + kc;
+        const int s = (int)(ch % OZ_STAGES);
+        ok = bar_wait(conv + s, (uint32_t)((ch / OZ_STAGES) & 1));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) break;
+        if (lane == 0) {
+          const uint32_t sA = su32(sm + s * OzL::STAGE);
+          const uint32_t sB = sA + OZ_S * OzL::ASL;
+          const uint32_t id = idesc_bf16(nmma);
+          bool first[OZ_NACC] = {true, true, true, true, true};
+#pragma unroll
+          for (int tt = 2; tt <= 8; ++tt) {
+            const int a = tt <= 5 ? tt - 2 : 4;
+#pragma unroll
+            for (int i = 1; i < tt; ++i) {
+              const int j = tt - i;
+              if (i > OZ_S || j > OZ_S) continue;
+              const uint32_t acc = (kc > 0 || !first[a]) ? 1u : 0u;
+              first[a] = false;
+              mma_bf16(tmem + (uint32_t)(a * OZ_TW), sdesc(sA + (uint32_t)(i - 1) * OzL::ASL),
+                       sdesc(sB + (uint32_t)(j - 1) * OzL::BSL), id, acc);
+            }
+          }
+          mma_commit(empty + s);
+          if (kc == nch - 1) mma_commit(accf);
+        }
+        __syncwarp();
+      }
+      if (!ok) {
+        if (lane == 0) { *abort_flag = 1; atomicExch(g.err, 1); }
+        break;
+      }
+    }
+  } else if (warp < OZ_CONV_W0 + OZ_CONV_WN) {
+    // ---------------------------------------------------------------- slicers
+    const int ct = tid - OZ_CONV_W0 * 32;
+    for (int64_t t = 0; t < my && !*abort_flag; ++t) {
+      const int64_t item = blockIdx.x + t * gridDim.x;
+      const int64_t ia = item / g.ntiles;
+      const int c0 = (int)(item % g.ntiles) * OZ_TW;
+      const int ncol = min(OZ_TW, g.N - c0);
+      const int nmma = ((ncol + 15) / 16) * 16;
+      const int64_t e = (g.mode == 0) ? g.cells[ia] : 0;
+      bool ok = true;
+      for (int kc = 0; kc < nch; ++kc) {
+        const int64_t ch = t * nch + kc;
+        const int s = (int)(ch % OZ_STAGES);
+        if (ch >= OZ_STAGES) {
+          ok = bar_wait(empty + s, (uint32_t)((ch / OZ_STAGES - 1) & 1));
+          if (!ok) break;
+        }
+        unsigned char* SA = sm + s * OzL::STAGE;
+        unsigned char* SB = SA + OZ_S * OzL::ASL;
+        // A chunk: 128 rows x 16 k
+        for (int v = ct; v < OZ_M * OZ_KC; v += OZ_CONV_T) {
+          const int r = v / OZ_KC, kl = v % OZ_KC, k = kc * OZ_KC + kl;
+          double x = 0.0;
+          int E = -2000;
+          if (g.mode == 0) {
+            if (r < NL && k < NL) x = g.H[e * (int64_t)(NL * NL) + r * NL + k];
+            E = g.hexp[e * OZ_M + r];
+          } else {
+            const int64_t row = ia * OZ_M + r;
+            if (row < g.arows) {
+              if (k < g.K) x = g.A[row * g.lda + k];
+              E = g.aexp[row];
+            }
+          }
+          slice_store(x, E, SA, OzL::ASL, bo(r, kl));
+        }
+        // B chunk: nmma rows (columns of the product) x 16 k
+        for (int v = ct; v < nmma * OZ_KC; v += OZ_CONV_T) {
+          const int kl = v / nmma, n = v % nmma, k = kc * OZ_KC + kl;
+          double x = 0.0;
+          const int E = (n < ncol) ? g.fexp[c0 + n] : -2000;
+          if (n < ncol) {
+            if (g.mode == 0) {
+              if (k < NL) x = g.Y[oz_cell_node(g.m, e, k) * g.ldy + c0 + n];
+            } else {
+              if (k < g.K) x = g.B[(int64_t)k * g.ldb + c0 + n];
+            }
+          }
+          slice_store(x, E, SB, OzL::BSL, bo(n, kl));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bar_arrive(conv + s);
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(g.err, 1);
+        break;
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;
+    for (int64_t t = 0; t < my && !*abort_flag; ++t) {
+      const int64_t item = blockIdx.x + t * gridDim.x;
+      const int64_t ia = item / g.ntiles;
+      const int c0 = (int)(item % g.ntiles) * OZ_TW;
+      const int ncol = min(OZ_TW, g.N - c0);
+      if (!bar_wait(accf, (uint32_t)(t & 1))) {
+        *abort_flag = 1;
+        atomicExch(g.err, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      bool live;
+      int Er;
+      double* orow;
+      if (g.mode == 0) {
+        const int64_t e = g.cells[ia];
+        live = r < NL;
+        Er = g.hexp[e * OZ_M + r];
+        orow = live ? g.out + oz_cell_node(g.m, e, r) * g.ldo + c0 : nullptr;
+      } else {
+        const int64_t row = ia * OZ_M + r;
+        live = row < g.arows;
+        Er = live ? g.aexp[row] : 0;
+        orow = live ? g.out + row * g.ldo + c0 : nullptr;
+      }
+      for (int cb = 0; cb < ncol; cb += 16) {
+        uint32_t v[OZ_NACC][16];
+#pragma unroll
+        for (int a = 0; a < OZ_NACC; ++a)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
+                "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]), "=r"(v[a][10]), "=r"(v[a][11]),
+                "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]), "=r"(v[a][15])
+              : "r"(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * OZ_TW + cb))
+              : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (live) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int n = cb + q;
+            if (n >= ncol) break;
+            float s1, e1, s2, e2, s3, e3;
+            two_sum(__uint_as_float(v[0][q]), __uint_as_float(v[1][q]), s1, e1);
+            two_sum(s1, __uint_as_float(v[2][q]), s2, e2);
+            two_sum(s2, __uint_as_float(v[3][q]), s3, e3);
+            const float lo = ((__uint_as_float(v[4][q]) + e3) + e2) + e1;
+            const double val = ldexp((double)s3 + (double)lo, Er + g.fexp[c0 + n] - 14);
+            if (g.mode == 0) orow[n] += val;
+            else orow[n] = val;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      bar_arrive(acce);
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && my > 0 && *abort_flag) bar_wait(accf, (uint32_t)((my - 1) & 1));
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
+  }
+}
+
+// per-row scale exponents of an FP64 matrix (one warp per row)
+__global__ void k_oz_rowexp(const double* __restrict__ A, int64_t lda, int64_t rows, int K, int* __restrict__ eout) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  int E = -2000;
+  for (int k = lane; k < K; k += 32) E = max(E, exp_of(A[w * lda + k]));
+  for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_down_sync(0xffffffffu, E, o));
+  if (lane == 0) eout[w] = E;
+}
+
+// per-column scale exponents (max over rows), combined with integer atomicMax
+__global__ void k_oz_colexp(const double* __restrict__ Y, int64_t ldy, int64_t rows, int N, int rows_per_block,
+                            int* __restrict__ fout) {
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t r1 = min(rows, r0 + rows_per_block);
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    int E = -2000;
+    for (int64_t r = r0; r < r1; ++r) E = max(E, exp_of(Y[r * ldy + c]));
+    atomicMax(fout + c, E);
+  }
+}
+
+__global__ void k_oz_fill(int* p, int n, int v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// row exponents of every cell block (rows 125..127 of the padded block get -2000)
+__global__ void k_oz_hexp(const double* __restrict__ H, int64_t n_cell, int* __restrict__ hexp) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_cell * OZ_M) return;
+  const int64_t e = w / OZ_M;
+  const int r = (int)(w % OZ_M);
+  int E = -2000;
+  if (r < NL)
+    for (int k = lane; k < NL; k += 32) E = max(E, exp_of(H[e * (int64_t)(NL * NL) + r * NL + k]));
+  for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_down_sync(0xffffffffu, E, o));
+  if (lane == 0) hexp[w] = E;
+}
+
+int oz_launch(const OzArgs& a, int n_sm, cudaStream_t st) {
+  const int64_t nA = (a.mode == 0) ? a.ncells : (a.arows + OZ_M - 1) / OZ_M;
+  const int64_t items = nA * a.ntiles;
+  if (items <= 0) return 0;
+  const unsigned grid = (unsigned)(items < n_sm ? items : n_sm);
+  cudaFuncSetAttribute(k_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OzL::TOTAL);
+  k_oz<<<grid, OZ_THREADS, OzL::TOTAL, st>>>(a);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return 0;
+}
+
+}  // namespace
+
+int64_t oz_hexp_elems(int64_t n_cell) { return n_cell * OZ_M; }
+
+void launch_oz_hexp(const double* Hcc, int64_t n_cell, int* hexp, cudaStream_t st) {
+  const int64_t w = n_cell * OZ_M;
+  if (w <= 0) return;
+  k_oz_hexp<<<(unsigned)((w * 32 + 255) / 256), 256, 0, st>>>(Hcc, n_cell, hexp);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_oz_colexp(const double* Y, int64_t ldy, int64_t rows, int N, int* fexp, cudaStream_t st) {
+  if (N <= 0) return;
+  k_oz_fill<<<(N + 255) / 256, 256, 0, st>>>(fexp, N, -2000);
+  const int rpb = 2048;
+  const int64_t nb = (rows + rpb - 1) / rpb;
+  if (nb > 0) k_oz_colexp<<<(unsigned)nb, N >= 128 ? 128 : 64, 0, st>>>(Y, ldy, rows, N, rpb, fexp);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+}
+
+void launch_oz_rowexp(const double* A, int64_t lda, int64_t rows, int K, int* aexp, cudaStream_t st) {
+  if (rows <= 0) return;
+  k_oz_rowexp<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(A, lda, rows, K, aexp);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+// W(nodes of the colour's cells) += H^cc_e Y_e, FP64-grade through the BF16 tensor cores.
+// fexp: per-column exponents of Y (launch_oz_colexp).
+int launch_oz_cell(const double* Hcc, const int* hexp, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                   const double* Y, int64_t ldy, const int* fexp, double* W, int64_t ldw, int N, int n_sm, int* err,
+                   cudaStream_t st) {
+  if (ncells <= 0 || N <= 0) return 0;
+  OzArgs a{};
+  a.mode = 0;
+  a.H = Hcc;
+  a.hexp = hexp;
+  a.cells = cells;
+  a.ncells = ncells;
+  a.m = m;
+  a.K = NL;
+  a.Y = Y;
+  a.ldy = ldy;
+  a.fexp = fexp;
+  a.out = W;
+  a.ldo = ldw;
+  a.N = N;
+  a.ntiles = (N + OZ_TW - 1) / OZ_TW;
+  a.err = err;
+  return oz_launch(a, n_sm, st);
+}
+
+// C = A B (A: rows x K, K <= 144; B: K x N), FP64-grade; aexp / bexp from
+// launch_oz_rowexp(A) and launch_oz_colexp(B).
+int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, const double* B, int64_t ldb,
+                   const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st) {
+  if (rows <= 0 || N <= 0) return 0;
+  if (K > 144) return 1;
+  OzArgs a{};
+  a.mode = 1;
+  a.A = A;
+  a.lda = lda;
+  a.arows = rows;
+  a.aexp = aexp;
+  a.B = B;
+  a.ldb = ldb;
+  a.K = K;
+  a.fexp = bexp;
+  a.out = C;
+  a.ldo = ldc;
+  a.N = N;
+  a.ntiles = (N + OZ_TW - 1) / OZ_TW;
+  a.err = err;
+  return oz_launch(a, n_sm, st);
+}
+
+}  // namespace efe

@@ -212,3 +212,46 @@ def test_chfsi_converges_mixed_tiny(tiny_pair, prec, tol, atol):
                               v0=to_dev(W.lanczos_start(d.system)), n_conv=nconv, max_iter=300)
     ref = dense_eigs(d, N)
     np.testing.assert_allclose(eps[:nconv], ref[:nconv], atol=atol)
+
+
+def test_fp64_tensor_engine_products(tiny_pair):
+    """FP64-grade products on the BF16 tensor cores (error-free 7-digit slicing):
+    the H apply (N > 8 uses the engine) and the filter agree with the FP64
+    oracle to FP64-level tolerances, and Rayleigh-Ritz (tall products through
+    the engine) reproduces the oracle's Ritz values."""
+    from oracle.chfsi import chebyshev_filter_scaled, cholqr, rayleigh_ritz
+    d, G = tiny_pair
+    G.set_fp64_engine("tensor")
+    try:
+        for N in (9, 33, 135, 200):
+            X = W.random_block(d.system, N, seed=60 + N)
+            assert rel_err(G.apply_H(to_dev(X)), d.apply_H_assembled(X)) < 1e-10
+        N, m = 33, 7
+        X = W.initial_block(d.system, N, seed=3)
+        a, b, a0 = _bounds(d, N)
+        ref = chebyshev_filter_scaled(d.apply_Htilde, X, m, a, b, a0)
+        Xd = to_dev(X)
+        G.chfsi_step(Xd, m, a, b, a0, precision="fp64")
+        assert rel_err(Xd, ref) < 1e-8
+        X = W.initial_block(d.system, 20, seed=4)
+        Q, _ = cholqr(X)
+        eps_ref, _, res_ref = rayleigh_ritz(d.apply_H_assembled, d.apply_M_assembled, Q)
+        eps, res = G.rayleigh_ritz(to_dev(X))
+        np.testing.assert_allclose(eps, eps_ref, atol=1e-9, rtol=1e-10)
+    finally:
+        G.set_fp64_engine("dfma")
+
+
+def test_fp64_tensor_engine_converges(tiny_pair):
+    from oracle.chfsi import dense_eigs
+    d, G = tiny_pair
+    G.set_fp64_engine("tensor")
+    try:
+        N, m, nconv = 12, 12, 7
+        X = to_dev(W.initial_block(d.system, N, seed=1))
+        eps, res, it, b = G.solve(X, m, tol=1e-9, precision="tf32x3", fp64_tail=2,
+                                  v0=to_dev(W.lanczos_start(d.system)), n_conv=nconv, max_iter=300)
+        ref = dense_eigs(d, N)
+        np.testing.assert_allclose(eps[:nconv], ref[:nconv], atol=1e-8)
+    finally:
+        G.set_fp64_engine("dfma")
