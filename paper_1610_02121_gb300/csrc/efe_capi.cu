@@ -943,7 +943,7 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   double *Q = h->B1, *HQ = h->B2, *MQ = h->W;
   int inf[2] = {0, 0};
   // Cholesky-QR: G = X^T X = L L^T, Q = X L^-T
-  launch_gemm_tn(R, N, N, X, ldx, X, ldx, G, N, h->tnwork, h->tnwork_elems, st);
+  launch_gemm_tn(R, N, N, X, ldx, X, ldx, G, N, h->tnwork, h->tnwork_elems, st, true);
   launch_symmetrize(G, N, N, st);
   launch_chol(G, N, N, h->info, st);
   CKL();
@@ -960,8 +960,8 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   // projections
   TRY(apply_H_impl(h, Q, N, N, HQ, N, st));
   TRY(apply_M_impl(h, Q, N, N, MQ, N, st));
-  launch_gemm_tn(R, N, N, Q, N, HQ, N, Hp, N, h->tnwork, h->tnwork_elems, st);
-  launch_gemm_tn(R, N, N, Q, N, MQ, N, Mp, N, h->tnwork, h->tnwork_elems, st);
+  launch_gemm_tn(R, N, N, Q, N, HQ, N, Hp, N, h->tnwork, h->tnwork_elems, st, true);
+  launch_gemm_tn(R, N, N, Q, N, MQ, N, Mp, N, h->tnwork, h->tnwork_elems, st, true);
   launch_symmetrize(Hp, N, N, st);
   launch_symmetrize(Mp, N, N, st);
   CK(cudaMemcpyAsync(Lm, Mp, sizeof(double) * NN, cudaMemcpyDeviceToDevice, st));

@@ -651,7 +651,9 @@ constexpr int64_t TN_KC = 8192;
 
 __global__ void __launch_bounds__(256) k_gemm_tn_part(int64_t K, int Na, int Nb, const double* __restrict__ A,
                                                       int64_t lda, const double* __restrict__ B, int64_t ldb,
-                                                      double* __restrict__ part) {
+                                                      double* __restrict__ part, int sym) {
+  // symmetric products: only tiles on or above the diagonal are formed
+  if (sym && blockIdx.x > blockIdx.y) return;
   __shared__ double As[16][GT + 1];
   __shared__ double Bs[16][GT + 1];
   const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
@@ -695,11 +697,17 @@ __global__ void __launch_bounds__(256) k_gemm_tn_part(int64_t K, int Na, int Nb,
 }
 
 __global__ void k_gemm_tn_reduce(int nsplit, int Na, int Nb, const double* __restrict__ part, double* __restrict__ C,
-                                 int64_t ldc) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)Na * Nb) return;
+                                 int64_t ldc, int sym) {
+  const int64_t idx0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx0 >= (int64_t)Na * Nb) return;
+  const int64_t idx = idx0;
+  int64_t src = idx;
+  if (sym) {
+    const int i = (int)(idx / Nb), j = (int)(idx % Nb);
+    if (i / GT > j / GT) src = (int64_t)j * Nb + i;  // mirrored from the tile above the diagonal
+  }
   double s = 0.0;
-  for (int sp = 0; sp < nsplit; ++sp) s += part[(int64_t)sp * Na * Nb + idx];
+  for (int sp = 0; sp < nsplit; ++sp) s += part[(int64_t)sp * Na * Nb + src];
   C[(idx / Nb) * ldc + idx % Nb] = s;
 }
 
@@ -1120,15 +1128,16 @@ int64_t gemm_tn_work_elems(int64_t K, int Na, int Nb) {
 }
 
 void launch_gemm_tn(int64_t K, int Na, int Nb, const double* A, int64_t lda, const double* B, int64_t ldb,
-                    double* C, int64_t ldc, double* work, int64_t work_elems, cudaStream_t st) {
+                    double* C, int64_t ldc, double* work, int64_t work_elems, cudaStream_t st, bool sym) {
   if (Na <= 0 || Nb <= 0) return;
   int64_t nsplit = (K + TN_KC - 1) / TN_KC;
   if (nsplit < 1) nsplit = 1;
   (void)work_elems;
   dim3 g((unsigned)((Na + GT - 1) / GT), (unsigned)((Nb + GT - 1) / GT), (unsigned)nsplit);
-  k_gemm_tn_part<<<g, 256, 0, st>>>(K, Na, Nb, A, lda, B, ldb, work);
+  const int sy = (sym && Na == Nb) ? 1 : 0;
+  k_gemm_tn_part<<<g, 256, 0, st>>>(K, Na, Nb, A, lda, B, ldb, work, sy);
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  k_gemm_tn_reduce<<<grid1((int64_t)Na * Nb, 256), 256, 0, st>>>((int)nsplit, Na, Nb, work, C, ldc);
+  k_gemm_tn_reduce<<<grid1((int64_t)Na * Nb, 256), 256, 0, st>>>((int)nsplit, Na, Nb, work, C, ldc, sy);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 

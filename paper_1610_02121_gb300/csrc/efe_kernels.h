@@ -120,8 +120,10 @@ int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int*
 void launch_gemm_nn(int64_t M, int Nc, int K, double alpha, const double* A, int64_t lda, const double* B,
                     int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st);
 // C[Na x Nb] = A^T B with A[K x Na], B[K x Nb], K large (split-K, deterministic reduce)
+// sym: the product is symmetric in exact arithmetic (A^T A, Q^T H Q, Q^T M Q): only
+// tiles on or above the diagonal are formed and the rest mirrored
 void launch_gemm_tn(int64_t K, int Na, int Nb, const double* A, int64_t lda, const double* B, int64_t ldb,
-                    double* C, int64_t ldc, double* work, int64_t work_elems, cudaStream_t st);
+                    double* C, int64_t ldc, double* work, int64_t work_elems, cudaStream_t st, bool sym = false);
 int64_t gemm_tn_work_elems(int64_t K, int Na, int Nb);
 void launch_chol(double* A, int n, int lda, int* info, cudaStream_t st);
 void launch_trinv_lower(const double* L, int n, int lda, double* Li, int ldi, cudaStream_t st);

@@ -263,36 +263,58 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         }
         unsigned char* SA = sm + s * OzL::STAGE;
         unsigned char* SB = SA + OZ_S * OzL::ASL;
-        // A chunk: 128 rows x 16 k
-        for (int v = ct; v < OZ_M * OZ_KC; v += OZ_CONV_T) {
+        // gather first (all loads of the chunk in flight), then slice
+        constexpr int NA = (OZ_M * OZ_KC + OZ_CONV_T - 1) / OZ_CONV_T;   // 6
+        constexpr int NB = (OZ_TW * OZ_KC + OZ_CONV_T - 1) / OZ_CONV_T;  // 5
+        double xa[NA], xb[NB];
+        int ea[NA], eb[NB];
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          const int v = ct + u * OZ_CONV_T;
           const int r = v / OZ_KC, kl = v % OZ_KC, k = kc * OZ_KC + kl;
           double x = 0.0;
           int E = -2000;
-          if (g.mode == 0) {
-            if (r < NL && k < NL) x = g.H[e * (int64_t)(NL * NL) + r * NL + k];
-            E = g.hexp[e * OZ_M + r];
-          } else {
-            const int64_t row = ia * OZ_M + r;
-            if (row < g.arows) {
-              if (k < g.K) x = g.A[row * g.lda + k];
-              E = g.aexp[row];
+          if (v < OZ_M * OZ_KC) {
+            if (g.mode == 0) {
+              if (r < NL && k < NL) x = g.H[e * (int64_t)(NL * NL) + r * NL + k];
+              E = g.hexp[e * OZ_M + r];
+            } else {
+              const int64_t row = ia * OZ_M + r;
+              if (row < g.arows) {
+                if (k < g.K) x = g.A[row * g.lda + k];
+                E = g.aexp[row];
+              }
             }
           }
-          slice_store(x, E, SA, OzL::ASL, bo(r, kl));
+          xa[u] = x;
+          ea[u] = E;
         }
-        // B chunk: nmma rows (columns of the product) x 16 k
-        for (int v = ct; v < nmma * OZ_KC; v += OZ_CONV_T) {
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int v = ct + u * OZ_CONV_T;
           const int kl = v / nmma, n = v % nmma, k = kc * OZ_KC + kl;
           double x = 0.0;
-          const int E = (n < ncol) ? g.fexp[c0 + n] : -2000;
-          if (n < ncol) {
+          int E = -2000;
+          if (v < nmma * OZ_KC && n < ncol) {
+            E = g.fexp[c0 + n];
             if (g.mode == 0) {
               if (k < NL) x = g.Y[oz_cell_node(g.m, e, k) * g.ldy + c0 + n];
             } else {
               if (k < g.K) x = g.B[(int64_t)k * g.ldb + c0 + n];
             }
           }
-          slice_store(x, E, SB, OzL::BSL, bo(n, kl));
+          xb[u] = x;
+          eb[u] = E;
+        }
+#pragma unroll
+        for (int u = 0; u < NA; ++u) {
+          const int v = ct + u * OZ_CONV_T;
+          if (v < OZ_M * OZ_KC) slice_store(xa[u], ea[u], SA, OzL::ASL, bo(v / OZ_KC, v % OZ_KC));
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+          const int v = ct + u * OZ_CONV_T;
+          if (v < nmma * OZ_KC) slice_store(xb[u], eb[u], SB, OzL::BSL, bo(v % nmma, v / nmma));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         bar_arrive(conv + s);
@@ -332,21 +354,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         Er = live ? g.aexp[row] : 0;
         orow = live ? g.out + row * g.ldo + c0 : nullptr;
       }
-      for (int cb = 0; cb < ncol; cb += 16) {
-        uint32_t v[OZ_NACC][16];
+      for (int cb = 0; cb < ncol; cb += 8) {
+        uint32_t v[OZ_NACC][8];
 #pragma unroll
         for (int a = 0; a < OZ_NACC; ++a)
           asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
               : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
-                "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]), "=r"(v[a][10]), "=r"(v[a][11]),
-                "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]), "=r"(v[a][15])
+                "=r"(v[a][6]), "=r"(v[a][7])
               : "r"(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * OZ_TW + cb))
               : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (live) {
+          double cur[8];
+          if (g.mode == 0) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
+            for (int q = 0; q < 8; ++q) cur[q] = (cb + q < ncol) ? orow[cb + q] : 0.0;
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
             const int n = cb + q;
             if (n >= ncol) break;
             float s1, e1, s2, e2, s3, e3;
@@ -354,8 +380,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
             two_sum(s1, __uint_as_float(v[2][q]), s2, e2);
             two_sum(s2, __uint_as_float(v[3][q]), s3, e3);
             const float lo = ((__uint_as_float(v[4][q]) + e3) + e2) + e1;
-            const double val = ldexp((double)s3 + (double)lo, Er + g.fexp[c0 + n] - 14);
-            if (g.mode == 0) orow[n] += val;
+            // exact power-of-two scale built from its bit pattern (normal range), ldexp otherwise
+            const int k2 = Er + g.fexp[c0 + n] - 14;
+            const double sc = (k2 > -1022 && k2 < 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52)
+                                                        : ldexp(1.0, k2);
+            const double val = ((double)s3 + (double)lo) * sc;
+            if (g.mode == 0) orow[n] = cur[q] + val;
             else orow[n] = val;
           }
         }
