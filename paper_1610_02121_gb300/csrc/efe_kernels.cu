@@ -503,7 +503,9 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, int npc, const 
       for (int u = 0; u < CPL_CH; ++u) {
         if (u >= nn) break;
         const float x = ss[u] * xv[u];
-        for (int q = sp[u]; q < sp[u + 1]; ++q) acc[scol[q] * N + c] = fmaf(sval[q], x, acc[scol[q] * N + c]);
+        // each accumulator address (a, c) belongs to thread c alone: the reductions
+        // land in program order (deterministic) without stalling the thread
+        for (int q = sp[u]; q < sp[u + 1]; ++q) atomicAdd(&acc[scol[q] * N + c], sval[q] * x);
       }
     }
   }
@@ -529,7 +531,7 @@ __global__ void k_coup_reduce(int nb, int nE, int N, const float* __restrict__ p
 // Columns product: W[g][c] += sgn * sum_{a in pattern(g)} val[g, a] * Xe[a][c], Xe staged in
 // shared memory as FP32.
 template <typename T>
-__global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, int npc, const int32_t* __restrict__ t_nodes,
+__global__ void __launch_bounds__(1024) k_coup_cols(int64_t n_tn, int npc, const int32_t* __restrict__ t_nodes,
                                                    const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_col,
                                                    const float* __restrict__ tval, float sgn,
                                                    const double* __restrict__ Xe, int64_t ldxe, int nE, int N,
@@ -555,16 +557,24 @@ __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, int npc, const 
       sval[q] = tval[qa + q];
     }
     __syncthreads();
-    for (int c = tid; c < N; c += bd) {
-      float wv[CPL_CH];
+    // NL_LANES node lanes x column threads: every (node, column) is written by one thread
+    constexpr int NLN = 4;
+    const int cthreads = bd / NLN;
+    const int lane_n = tid / cthreads, ct = tid % cthreads;
+    for (int c = ct; c < N; c += cthreads) {
+      float wv[CPL_CH / NLN];
 #pragma unroll
-      for (int u = 0; u < CPL_CH; ++u) wv[u] = (u < nn) ? (float)W[sg[u] * ldw + c] : 0.f;
+      for (int v = 0; v < CPL_CH / NLN; ++v) {
+        const int u = v * NLN + lane_n;
+        wv[v] = (u < nn) ? (float)W[sg[u] * ldw + c] : 0.f;
+      }
 #pragma unroll
-      for (int u = 0; u < CPL_CH; ++u) {
+      for (int v = 0; v < CPL_CH / NLN; ++v) {
+        const int u = v * NLN + lane_n;
         if (u >= nn) break;
         float s = 0.f;
         for (int q = sp[u]; q < sp[u + 1]; ++q) s = fmaf(sval[q], xs[scol[q] * N + c], s);
-        W[sg[u] * ldw + c] = (T)(wv[u] + sgn * s);
+        W[sg[u] * ldw + c] = (T)(wv[v] + sgn * s);
       }
     }
   }
@@ -778,13 +788,22 @@ __global__ void k_symmetrize(double* A, int n, int lda) {
 
 // Parallel cyclic Jacobi (round-robin pairing) for a symmetric n x n matrix in
 // one CTA: A <- J^T A J with disjoint rotations per round, V <- V J.
-__global__ void __launch_bounds__(1024) k_jacobi(double* A, int n, int lda, double* V, int ldv, double* w,
+template <bool SMEM>
+__global__ void __launch_bounds__(1024) k_jacobi(double* Ag, int n, int ldag, double* V, int ldv, double* w,
                                                  int max_sweeps, int* info) {
   __shared__ double cs[1024], sn[1024];
   __shared__ int pp[1024], qq[1024];
   __shared__ double red[2][32];
   __shared__ int done;
+  extern __shared__ double As_dyn[];
   const int tid = threadIdx.x, bd = blockDim.x;
+  // the working matrix lives in shared memory when it fits (n <= 150), else in global memory
+  double* A = SMEM ? As_dyn : Ag;
+  const int lda = SMEM ? n : ldag;
+  if (SMEM) {
+    for (int64_t t = tid; t < (int64_t)n * n; t += bd) As_dyn[t] = Ag[(t / n) * (int64_t)ldag + t % n];
+    __syncthreads();
+  }
   const int n2 = n + (n & 1);
   const int np = n2 / 2;
   for (int64_t t = tid; t < (int64_t)n * n; t += bd) V[(t / n) * ldv + t % n] = (t / n == t % n) ? 1.0 : 0.0;
@@ -1163,7 +1182,13 @@ void launch_symmetrize(double* A, int n, int lda, cudaStream_t st) {
 
 void launch_jacobi(double* A, int n, int lda, double* V, int ldv, double* w, int max_sweeps, int* info,
                    cudaStream_t st) {
-  k_jacobi<<<1, 1024, 0, st>>>(A, n, lda, V, ldv, w, max_sweeps, info);
+  const size_t smem = sizeof(double) * (size_t)n * n;
+  if (smem <= 180 * 1024) {
+    cudaFuncSetAttribute(k_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobi<true><<<1, 1024, smem, st>>>(A, n, lda, V, ldv, w, max_sweeps, info);
+  } else {
+    k_jacobi<false><<<1, 1024, 0, st>>>(A, n, lda, V, ldv, w, max_sweeps, info);
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
@@ -1245,7 +1270,8 @@ void launch_coup_cols(int64_t n_tn, int npc, const int32_t* t_nodes, const int64
                       cudaStream_t st) {
   if (n_tn <= 0 || N <= 0 || nE <= 0) return;
   const int nb = coup_nblocks(n_tn, npc);
-  const int t = N >= 256 ? 256 : (N < 64 ? 64 : ((N + 31) / 32) * 32);
+  const int tc = N >= 256 ? 256 : (N < 64 ? 64 : ((N + 31) / 32) * 32);
+  const int t = 4 * tc;  // four node lanes
   const size_t smem = sizeof(float) * (size_t)nE * N;
   cudaFuncSetAttribute(k_coup_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_coup_cols<T><<<nb, t, smem, st>>>(n_tn, npc, t_nodes, t_ptr, t_col, tval, sgn, Xe, ldxe, nE, N, W, ldw);

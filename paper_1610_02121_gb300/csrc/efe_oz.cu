@@ -263,58 +263,79 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         }
         unsigned char* SA = sm + s * OzL::STAGE;
         unsigned char* SB = SA + OZ_S * OzL::ASL;
-        // gather first (all loads of the chunk in flight), then slice
-        constexpr int NA = (OZ_M * OZ_KC + OZ_CONV_T - 1) / OZ_CONV_T;   // 6
-        constexpr int NB = (OZ_TW * OZ_KC + OZ_CONV_T - 1) / OZ_CONV_T;  // 5
-        double xa[NA], xb[NB];
-        int ea[NA], eb[NB];
-#pragma unroll
-        for (int u = 0; u < NA; ++u) {
-          const int v = ct + u * OZ_CONV_T;
-          const int r = v / OZ_KC, kl = v % OZ_KC, k = kc * OZ_KC + kl;
-          double x = 0.0;
+        // one thread per (row, 8-wide K octet): eight loads in flight, then seven
+        // 16-byte slice stores (one core-matrix row each)
+        for (int v = ct; v < (OZ_M + nmma) * 2; v += OZ_CONV_T) {
+          const bool isA = v < OZ_M * 2;
+          const int w = isA ? v : v - OZ_M * 2;
+          const int row = w >> 1, oct = w & 1;        // row of A, or column n of the product
+          double x[8];
           int E = -2000;
-          if (v < OZ_M * OZ_KC) {
+          if (isA) {
             if (g.mode == 0) {
-              if (r < NL && k < NL) x = g.H[e * (int64_t)(NL * NL) + r * NL + k];
-              E = g.hexp[e * OZ_M + r];
+              E = g.hexp[e * OZ_M + row];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int k = kc * OZ_KC + oct * 8 + q;
+                x[q] = (row < NL && k < NL) ? g.H[e * (int64_t)(NL * NL) + row * NL + k] : 0.0;
+              }
             } else {
-              const int64_t row = ia * OZ_M + r;
-              if (row < g.arows) {
-                if (k < g.K) x = g.A[row * g.lda + k];
-                E = g.aexp[row];
+              const int64_t ar = ia * OZ_M + row;
+              if (ar < g.arows) E = g.aexp[ar];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const int k = kc * OZ_KC + oct * 8 + q;
+                x[q] = (ar < g.arows && k < g.K) ? g.A[ar * g.lda + k] : 0.0;
               }
             }
-          }
-          xa[u] = x;
-          ea[u] = E;
-        }
+          } else {
+            const int n = row;
+            if (n < ncol) E = g.fexp[c0 + n];
 #pragma unroll
-        for (int u = 0; u < NB; ++u) {
-          const int v = ct + u * OZ_CONV_T;
-          const int kl = v / nmma, n = v % nmma, k = kc * OZ_KC + kl;
-          double x = 0.0;
-          int E = -2000;
-          if (v < nmma * OZ_KC && n < ncol) {
-            E = g.fexp[c0 + n];
-            if (g.mode == 0) {
-              if (k < NL) x = g.Y[oz_cell_node(g.m, e, k) * g.ldy + c0 + n];
-            } else {
-              if (k < g.K) x = g.B[(int64_t)k * g.ldb + c0 + n];
+            for (int q = 0; q < 8; ++q) {
+              const int k = kc * OZ_KC + oct * 8 + q;
+              double xv = 0.0;
+              if (n < ncol) {
+                if (g.mode == 0) {
+                  if (k < NL) xv = g.Y[oz_cell_node(g.m, e, k) * g.ldy + c0 + n];
+                } else {
+                  if (k < g.K) xv = g.B[(int64_t)k * g.ldb + c0 + n];
+                }
+              }
+              x[q] = xv;
             }
           }
-          xb[u] = x;
-          eb[u] = E;
-        }
+          // digits of the eight values, packed slice by slice
+          uint32_t pk[OZ_S][4];
 #pragma unroll
-        for (int u = 0; u < NA; ++u) {
-          const int v = ct + u * OZ_CONV_T;
-          if (v < OZ_M * OZ_KC) slice_store(xa[u], ea[u], SA, OzL::ASL, bo(v / OZ_KC, v % OZ_KC));
-        }
+          for (int i2 = 0; i2 < OZ_S; ++i2)
 #pragma unroll
-        for (int u = 0; u < NB; ++u) {
-          const int v = ct + u * OZ_CONV_T;
-          if (v < nmma * OZ_KC) slice_store(xb[u], eb[u], SB, OzL::BSL, bo(v % nmma, v / nmma));
+            for (int q = 0; q < 4; ++q) pk[i2][q] = 0u;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const long long bits = __double_as_longlong(x[q]);
+            const int ex = (int)((bits >> 52) & 0x7FF);
+            const uint32_t sgn = (uint32_t)((bits >> 48) & 0x8000);
+            unsigned long long qq = 0;
+            const int rs = 1026 + E - ex;
+            if (ex != 0 && rs >= 0 && rs < 64) qq = ((unsigned long long)(bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> rs;
+#pragma unroll
+            for (int i2 = 0; i2 < OZ_S; ++i2) {
+              const uint32_t d = (uint32_t)(qq >> (42 - 7 * i2)) & 127u;
+              uint32_t h16 = 0;
+              if (d) {
+                const int p = 31 - __clz(d);
+                h16 = sgn | ((uint32_t)(p + 127 - 7 * i2) << 7) | ((d << (7 - p)) & 0x7Fu);
+              }
+              pk[i2][q >> 1] |= h16 << (16 * (q & 1));
+            }
+          }
+          unsigned char* dst = isA ? SA : SB;
+          const uint32_t stride = isA ? OzL::ASL : OzL::BSL;
+          const uint32_t off = bo(row, oct * 8);
+#pragma unroll
+          for (int i2 = 0; i2 < OZ_S; ++i2)
+            *reinterpret_cast<uint4*>(dst + i2 * stride + off) = make_uint4(pk[i2][0], pk[i2][1], pk[i2][2], pk[i2][3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         bar_arrive(conv + s);
