@@ -112,12 +112,17 @@ class Discretisation:
         self.Dinv = np.where(self.interior, 1.0 / D, 0.0)
 
     def cell_quadrature(self, e):
-        """Gauss tensor rule, or the adaptive rule in enriched cells (Sec. IV.C)."""
-        if self.enriched[e]:
-            q = self.system["quad"]
-            return adaptive_rule(self.system, self.lo[e], self.hi[e], self.funcs_of_cell[e],
-                                 q["tau"], q["max_depth"], q["n"])
-        return gauss_box(self.lo[e], self.hi[e], self.system["n_gauss"])
+        """Gauss tensor rule, or the adaptive rule in enriched cells (Sec. IV.C).
+        Rules depend on the mesh and basis only and are cached."""
+        cache = self.__dict__.setdefault("_quad", {})
+        if e not in cache:
+            if self.enriched[e]:
+                q = self.system["quad"]
+                cache[e] = adaptive_rule(self.system, self.lo[e], self.hi[e], self.funcs_of_cell[e],
+                                         q["tau"], q["max_depth"], q["n"])
+            else:
+                cache[e] = gauss_box(self.lo[e], self.hi[e], self.system["n_gauss"])
+        return cache[e]
 
     def basis_at(self, e, pts):
         """Classical basis values B (npt, 125) and physical gradients dB (npt, 125, 3)."""
@@ -143,11 +148,14 @@ class Discretisation:
         return 0.5 * T
 
     # -- operator blocks ---------------------------------------------------------
-    def build(self, V=None):
+    def build(self, V=None, Vq=None):
         """Per-cell H^cc_e, per-enriched-cell H^ec_e and M^ec_e, global H^ee and M^ee.
 
-        ``V`` is an optional callable V(points); default is the workload's
-        analytic potential."""
+        ``V`` is an optional callable V(points); ``Vq`` optional values at every
+        quadrature point in cell order; default is the workload's analytic potential."""
+        if Vq is not None:
+            offs = np.cumsum([0] + [len(self.cell_quadrature(e)[1]) for e in range(self.n_cell)])
+            Vq = np.asarray(Vq, dtype=np.float64)
         Vf = V if V is not None else (lambda pts: potential(self.system, pts))
         self.Hcc = np.zeros((self.n_cell, self.nl, self.nl))
         self.Hec = {}
@@ -159,7 +167,7 @@ class Discretisation:
             pts, w = self.cell_quadrature(e)
             self.nq[e] = len(w)
             B, dB = self.basis_at(e, pts)
-            wV = w * Vf(pts)
+            wV = w * (Vq[offs[e]:offs[e + 1]] if Vq is not None else Vf(pts))
             self.Hcc[e] = self.kinetic_cell(e) + B.T @ (wV[:, None] * B)
             fl = self.funcs_of_cell[e]
             if fl:
