@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-scf", action="store_true")
+    p.add_argument("--scf-steps", type=int, default=3)
     p.add_argument("--workload", default="si16", choices=["si16", "si16s", "hydrogen"])
     return p.parse_args()
 
@@ -284,7 +286,7 @@ def main():
             "config": {"workload": f"{args.workload}: " + ("16-atom Si-like cluster (Z=14, diamond a=10.26), "
                                                            "graded degree-4 mesh" if args.workload == "si16"
                                                            else "hydrogen Z=1, 6x6x6 cells"),
-                       "nodes": G.n_nodes, "cells": G.n_cells, "n_enrich": G.n_enrich, "N": N, "m": m,
+                       "nodes": G.n_nodes, "cells": G.n_cells, "n_enrich": G.n_enrich, "n_coupling": G.n_coupling, "N": N, "m": m,
                        "fp64_tail": args.fp64_tail if prec != "fp64" else 0,
                        "fp64_engine": args.fp64_engine if prec != "fp64" else "dfma",
                        "l2": "vector blocks (>= 0.8 GB) and cell matrices exceed the 129 MB L2",
@@ -321,6 +323,38 @@ def main():
         nb = X_start.numel() * 8
         line["e2e"] = {"value": world * flops_step / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": nb,
                        "d2h_bytes_per_step": nb + 2 * 8 * N, "ms_per_step": te * 1e3}
+    # full SCF iterations (Sec. V) on the same system: V_eff from rho_in (Hartree
+    # solve + LDA), bound, filter pass, Rayleigh-Ritz, occupations, density,
+    # Hartree of rho_out, energies, Anderson mixing
+    if not args.no_scf:
+        G.set_fp64_engine(args.fp64_engine)
+        ne = float(np.sum(system["Z"]))
+        occ0, _ = P._lib.fermi(eps_start, ne, 500 * P._lib.KB_HA_PER_K)
+        rho_in = G.density(X_start, occ0)
+        w = G.qpoints()[:, 3]
+        rho_in *= ne / float((w * rho_in).sum())
+        rho_out = torch.empty_like(rho_in)
+        Xs = X_start.clone()
+        G.scf_init(ne)
+        tail = args.fp64_tail if prec != "fp64" else 0
+        r0 = G.scf_step(Xs, rho_in, rho_out, m, precision=prec, fp64_tail=tail)   # warm-up
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        hist = []
+        for _ in range(args.scf_steps):
+            hist.append(G.scf_step(Xs, rho_in, rho_out, m, precision=prec, fp64_tail=tail))
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms_scf = s0.elapsed_time(s1) / max(args.scf_steps, 1)
+        line["scf"] = {"s_per_iteration": ms_scf * 1e-3, "iterations_timed": args.scf_steps,
+                       "n_electrons": ne, "kT_K": 500.0, "anderson_stages": 5, "mixing": 0.5,
+                       "filter": f"one degree-{m} pass, {prec}", "n_qpoints": G.n_qpoints,
+                       "poisson_cg_iterations": [h["poisson_iters"] for h in hist],
+                       "total_energy_Ha": [h["total"] for h in [r0] + hist],
+                       "drho": [h["drho"] for h in [r0] + hist],
+                       "start": "density of the Rayleigh-Ritz-rotated atomic-orbital block, renormalised to N_e"}
     if not args.no_cpu and rank == 0 and world == 1:
         v, dt, desc = cpu_sample(system, N)
         line["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)),

@@ -227,6 +227,98 @@ int efe_apply_M_noalloc(efe_handle* h, const double* X, int64_t ldx, int32_t N,
  * handles, all threads); a diagnostic counter for benchmarks. */
 int efe_launch_count(int64_t* total);
 
+/* ------------------------------------------------------------------------
+ * Self-consistent field (Sec. V): rho_in -> V_eff (Eq. veff) -> ChFSI ->
+ * Fermi-Dirac occupations (Eqs. FermiDirac, Mu) -> rho_out (Eq. Rho) ->
+ * energy (Sec. II) -> n-stage Anderson mixing (Sec. VI).
+ *
+ * Quadrature-point layout ("Q layout"): FP64 device arrays of n_qpoints values
+ * in the order of efe_qpoints (cell by cell; within a cell the rule's tensor
+ * Gauss boxes in order, x fastest).  Densities are electrons per bohr^3,
+ * potentials and energies Hartree.
+ * Readings of what the paper leaves open: LDA = Slater exchange + Ceperley-
+ * Alder correlation in the Perdew-Zunger (1981) parametrisation, spin-
+ * unpolarised; the Hartree problem (Eq. Poisson) is solved in the classical
+ * basis with Dirichlet data from the monopole and dipole of rho about its
+ * centre of charge; the energy of a pair (rho_in, rho_out) is the Kohn-Sham
+ * functional at rho_out with the potential of rho_in (equal to the paper's
+ * expression at self-consistency); Anderson mixing acts on rho at the points
+ * with the quadrature-weighted L2 inner product.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double n_electrons;        /* N_e of Eq. Mu */
+  double kT;                 /* k_B T (Hartree); 500 K = 1.5834e-3 */
+  double mix_beta;           /* Anderson mixing parameter (0, 1] */
+  int32_t n_hist;            /* Anderson stages, 1 .. 8 (1 = linear mixing) */
+  double poisson_tol;        /* relative residual |b - A phi| / |b| of each Hartree solve */
+  int32_t poisson_max_iter;  /* cap on inner CG iterations per defect-correction step */
+  int32_t lanczos_k;         /* Lanczos steps of the upper bound b per SCF step */
+} efe_scf_params;
+
+typedef struct {
+  double band;               /* 2 sum_i f_i eps_i */
+  double xc;                 /* int rho_out eps_xc(rho_out) */
+  double hartree;            /* 1/2 int rho_out V_H[rho_out] */
+  double zz;                 /* nuclear repulsion 1/2 sum_{I!=J} Z_I Z_J / |R_I - R_J| */
+  double double_counting;    /* int rho_out (V_H[rho_in] + V_xc[rho_in]) */
+  double total;              /* band - double_counting + hartree + xc + zz */
+  double fermi_level;        /* mu of Eq. Mu */
+  double drho;               /* |rho_out - rho_in|_L2 */
+  double n_out;              /* int rho_out */
+  double upper_bound;        /* b used by the filter */
+  int32_t poisson_iters;     /* inner CG iterations of the step's two Hartree solves */
+  int32_t filter_passes;
+} efe_scf_result;
+
+/* rho(x_q) = 2 sum_i occ_i psi_i(x_q)^2 (Eq. Rho) at every quadrature point,
+ * psi_i the FE function with coefficients X[:, i] (X layout, N columns).
+ * occ: N FP64 device values.  rho: Q layout, written. */
+int efe_density(efe_handle* h, const double* X, int64_t ldx, int32_t N, const double* occ, double* rho,
+                void* stream);
+
+/* LDA energy per electron eps_xc(rho) and potential v_xc = d(rho eps_xc)/d rho
+ * at every point (Q layout); exc or vxc may be NULL.  rho is clamped below at
+ * 1e-30. */
+int efe_xc_lda(efe_handle* h, const double* rho, double* exc, double* vxc, void* stream);
+
+/* Hartree potential of rho (Q layout): -lap V_H / (4 pi) = rho (Eq. Poisson),
+ * classical basis, Dirichlet data Q/r + d.r/r^3 on the box faces.  phi: nodal
+ * potential (n_nodes FP64, device) -- on entry the interior values are the
+ * starting guess, on exit the solution; NULL uses an internal zero start.
+ * vh: V_H at the points (Q layout), written.  iters: inner CG iterations
+ * (host, may be NULL).  Returns EFE_ERR_NOCONV if the relative residual stays
+ * above 1e3 * tol. */
+int efe_hartree(efe_handle* h, const double* rho, double* vh, double* phi, double tol, int32_t max_iter,
+                int32_t* iters, void* stream);
+
+/* Fermi-Dirac occupations (Eq. FermiDirac) with mu from 2 sum_i f_i = N_e
+ * (Eq. Mu) by bisection.  Host arrays; EFE_ERR_ARG if the N states cannot hold
+ * N_e electrons. */
+int efe_fermi(const double* eps, int32_t N, double n_electrons, double kT, double* occ, double* mu);
+
+/* One n-stage Anderson update from n (rho_in, rho_out) pairs (n x n_qpoints,
+ * device, oldest first; n = 1 .. 8): writes the next rho_in to rho_next. */
+int efe_anderson(efe_handle* h, const double* rho_in_hist, const double* rho_out_hist, int32_t n, double beta,
+                 double* rho_next, void* stream);
+
+/* Start an SCF run: checks the parameters, allocates the SCF buffers, forms
+ * V_ext = -sum_I Z_I / |x - R_I| at the points and clears the mixing history
+ * and the Ritz values. */
+int efe_scf_init(efe_handle* h, const efe_scf_params* params, void* stream);
+
+/* One SCF iteration on the subspace X (X layout, N columns, filtered in place):
+ * V_eff(rho_in) -> efe_set_potential -> Lanczos bound b -> `passes` x
+ * (degree-m filter + Rayleigh-Ritz; multiple passes re-orthonormalise between
+ * them, Sec. VI.B.2) -> occupations -> rho_out -> V_H[rho_out] -> energies ->
+ * Anderson.  rho_in (Q layout) is read and then overwritten with the next
+ * mixed input density; rho_out (Q layout) is written.  eig, occ: N host
+ * values written (may be NULL); res: the energies.  The first step after
+ * efe_scf_init runs a Rayleigh-Ritz step on X first to obtain the filter
+ * interval. */
+int efe_scf_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, int32_t passes, int32_t precision,
+                 int32_t fp64_tail, double* rho_in, double* rho_out, double* eig, double* occ, efe_scf_result* res,
+                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,8 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
 SYMBOLS = ["efe_create", "efe_destroy", "efe_last_error", "efe_sizes", "efe_qpoints", "efe_set_potential",
            "efe_set_potential_analytic", "efe_reserve", "efe_apply_H", "efe_apply_M", "efe_apply_Minv",
            "efe_upper_bound", "efe_chfsi_step", "efe_rayleigh_ritz", "efe_enable_timing", "efe_kernel_stats",
-           "efe_launch_count", "efe_apply_M_noalloc", "efe_set_fp64_engine"]
+           "efe_launch_count", "efe_apply_M_noalloc", "efe_set_fp64_engine", "efe_density", "efe_xc_lda",
+           "efe_hartree", "efe_fermi", "efe_anderson", "efe_scf_init", "efe_scf_step"]
 
 
 class EfeError(RuntimeError):
@@ -50,6 +51,24 @@ class BasisDesc(C.Structure):
 class PotentialDesc(C.Structure):
     _fields_ = [("nuclear", C.c_int32), ("n_terms", C.c_int32), ("A", C.POINTER(C.c_double)),
                 ("s", C.POINTER(C.c_double)), ("c", C.POINTER(C.c_double)), ("omega", C.c_double)]
+
+
+class ScfParams(C.Structure):
+    _fields_ = [("n_electrons", C.c_double), ("kT", C.c_double), ("mix_beta", C.c_double), ("n_hist", C.c_int32),
+                ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32), ("lanczos_k", C.c_int32)]
+
+
+class ScfResult(C.Structure):
+    _fields_ = [("band", C.c_double), ("xc", C.c_double), ("hartree", C.c_double), ("zz", C.c_double),
+                ("double_counting", C.c_double), ("total", C.c_double), ("fermi_level", C.c_double),
+                ("drho", C.c_double), ("n_out", C.c_double), ("upper_bound", C.c_double),
+                ("poisson_iters", C.c_int32), ("filter_passes", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+KB_HA_PER_K = 3.166811563e-6   # Boltzmann constant (Ha/K)
 
 
 def load(path=LIB_PATH):
@@ -80,6 +99,13 @@ def load(path=LIB_PATH):
         "efe_launch_count": [P64],
         "efe_apply_M_noalloc": [vp, vp, i64, i32, vp, i64, vp],
         "efe_set_fp64_engine": [vp, i32],
+        "efe_density": [vp, vp, i64, i32, vp, vp, vp],
+        "efe_xc_lda": [vp, vp, vp, vp, vp],
+        "efe_hartree": [vp, vp, vp, vp, dbl, i32, C.POINTER(C.c_int32), vp],
+        "efe_fermi": [PD, i32, dbl, dbl, PD, PD],
+        "efe_anderson": [vp, vp, vp, i32, dbl, vp, vp],
+        "efe_scf_init": [vp, C.POINTER(ScfParams), vp],
+        "efe_scf_step": [vp, vp, i64, i32, i32, i32, i32, i32, vp, vp, PD, PD, C.POINTER(ScfResult), vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -102,6 +128,17 @@ def launch_count():
     n = C.c_int64()
     lib().efe_launch_count(C.byref(n))
     return n.value
+
+
+def fermi(eps, n_electrons, kT):
+    """Fermi-Dirac occupations and Fermi level (host routine of the library)."""
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    occ = np.zeros_like(eps)
+    mu = C.c_double()
+    rc = lib().efe_fermi(_dptr(eps), len(eps), float(n_electrons), float(kT), _dptr(occ), C.byref(mu))
+    if rc != EFE_OK:
+        raise EfeError(rc, "efe_fermi: not enough states for the electron count")
+    return occ, mu.value
 
 
 def _dptr(a):
@@ -269,6 +306,67 @@ class System:
             if res[:n_conv].max() < tol:
                 break
         return eps, res, it, b
+
+    # -- self-consistent field ---------------------------------------------------
+    def _qvec(self, t):
+        assert t.is_cuda and t.dtype == self._torch.float64 and t.is_contiguous() and t.numel() == self.n_qpoints
+        return C.c_void_p(t.data_ptr())
+
+    def density(self, X, occ, rho=None):
+        """rho = 2 sum_i occ_i psi_i^2 at the quadrature points (Eq. Rho)."""
+        px, ldx, N = self._block(X)
+        occ = self._torch.as_tensor(occ, dtype=self._torch.float64, device=X.device).contiguous()
+        if rho is None:
+            rho = self._torch.empty(self.n_qpoints, dtype=self._torch.float64, device=X.device)
+        self._check(self.L.efe_density(self.h, px, ldx, N, C.c_void_p(occ.data_ptr()), self._qvec(rho),
+                                       self._stream()))
+        return rho
+
+    def xc_lda(self, rho):
+        exc = self._torch.empty_like(rho)
+        vxc = self._torch.empty_like(rho)
+        self._check(self.L.efe_xc_lda(self.h, self._qvec(rho), self._qvec(exc), self._qvec(vxc), self._stream()))
+        return exc, vxc
+
+    def hartree(self, rho, phi=None, tol=1e-11, max_iter=5000):
+        """V_H at the quadrature points, the nodal potential and the CG iteration count."""
+        vh = self._torch.empty_like(rho)
+        if phi is None:
+            phi = self._torch.zeros(self.n_nodes, dtype=self._torch.float64, device=rho.device)
+        it = C.c_int32()
+        self._check(self.L.efe_hartree(self.h, self._qvec(rho), self._qvec(vh), C.c_void_p(phi.data_ptr()),
+                                       float(tol), int(max_iter), C.byref(it), self._stream()))
+        return vh, phi, it.value
+
+    def anderson(self, rho_in_hist, rho_out_hist, beta):
+        """Next input density from n (rho_in, rho_out) pairs (n x n_qpoints tensors, oldest first)."""
+        n = rho_in_hist.shape[0]
+        assert rho_in_hist.is_contiguous() and rho_out_hist.is_contiguous() and rho_out_hist.shape[0] == n
+        out = self._torch.empty(self.n_qpoints, dtype=self._torch.float64, device=rho_in_hist.device)
+        self._check(self.L.efe_anderson(self.h, C.c_void_p(rho_in_hist.data_ptr()),
+                                        C.c_void_p(rho_out_hist.data_ptr()), int(n), float(beta),
+                                        C.c_void_p(out.data_ptr()), self._stream()))
+        return out
+
+    def scf_init(self, n_electrons, kT=500 * KB_HA_PER_K, beta=0.5, n_hist=5, poisson_tol=1e-11,
+                 poisson_max_iter=5000, lanczos_k=10):
+        p = ScfParams(float(n_electrons), float(kT), float(beta), int(n_hist), float(poisson_tol),
+                      int(poisson_max_iter), int(lanczos_k))
+        self._check(self.L.efe_scf_init(self.h, C.byref(p), self._stream()))
+
+    def scf_step(self, X, rho_in, rho_out, m, passes=1, precision="fp64", fp64_tail=0):
+        """One SCF iteration (Sec. V); rho_in is overwritten with the next mixed density."""
+        px, ldx, N = self._block(X)
+        eig = np.zeros(N)
+        occ = np.zeros(N)
+        r = ScfResult()
+        self._check(self.L.efe_scf_step(self.h, px, ldx, N, int(m), int(passes), PREC[precision], int(fp64_tail),
+                                        self._qvec(rho_in), self._qvec(rho_out), _dptr(eig), _dptr(occ),
+                                        C.byref(r), self._stream()))
+        out = r.as_dict()
+        out["eig"] = eig
+        out["occ"] = occ
+        return out
 
     def set_fp64_engine(self, engine):
         """0: FP64 DFMA products; 1 (or "tensor"): FP64-grade products on the BF16 tensor cores."""

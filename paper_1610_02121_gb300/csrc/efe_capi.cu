@@ -90,6 +90,32 @@ struct efe_handle {
   float *Yf[3] = {nullptr, nullptr, nullptr}, *Wf = nullptr, *cpart = nullptr;
   float *mecT32 = nullptr, *hecT32 = nullptr;
   double* Ye[3] = {nullptr, nullptr, nullptr};
+  // self-consistent field (Sec. V): quadrature leaves, Hartree operator, SCF state
+  int64_t n_leaf = 0;
+  int leaf_nmax = 1;
+  int64_t *leaf_off = nullptr, *leaf_ptr = nullptr;
+  int32_t *leaf_n = nullptr, *leaf_cell = nullptr, *cell_enr = nullptr;
+  int64_t* eq_off = nullptr;
+  int64_t eq_elems = 0;
+  double* Eq = nullptr;                      // enrichment values at enriched-cell points (lazy)
+  double* band[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // Kx Ky Kz Mx My Mz
+  double* node_xyz = nullptr;                // node coordinates per axis
+  float* dinvA = nullptr;                    // inverse diagonal of the Hartree stiffness
+  double e_zz = 0.0;
+  bool scf_ready = false;
+  efe_scf_params scfp{};
+  double *hb = nullptr, *hr64 = nullptr, *hlb = nullptr, *hphi = nullptr;
+  float *hr32 = nullptr, *hz32 = nullptr, *hp0 = nullptr, *hp1 = nullptr, *hq = nullptr, *hd = nullptr;
+  double *hpart_rz0 = nullptr, *hpart_rr = nullptr, *hpart_pq = nullptr, *hpart_rz = nullptr, *hrz = nullptr;
+  int* hdone = nullptr;
+  int hmax_it = 0;
+  double *red_part = nullptr, *red_out = nullptr;
+  double *vext = nullptr, *vh_in = nullptr, *vxc_in = nullptr, *vh_out = nullptr, *phi_in = nullptr,
+         *phi_out = nullptr, *occ_dev = nullptr, *v0 = nullptr;
+  double* hist[2 * ANDERSON_MAX] = {nullptr};  // rho_in ring, then rho_out ring
+  int hist_count = 0, hist_head = 0, occ_cap = 0;
+  std::vector<double> ritz;                  // Ritz values of the last Rayleigh-Ritz step
+  int scf_iter = 0;
   // timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -467,6 +493,312 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
   return mx;
 }
 
+
+// Quadrature leaves, enrichment-value offsets, the assembled 1-D operators of
+// the Hartree stiffness and the node coordinates (self-consistent field).
+int scf_setup_upload(efe_handle* h, const Setup& s) {
+  h->n_leaf = (int64_t)s.leaf_n.size();
+  for (int32_t n : s.leaf_n) h->leaf_nmax = std::max(h->leaf_nmax, (int)n);
+  TRY(upload(h, &h->leaf_off, s.leaf_off));
+  TRY(upload(h, &h->leaf_ptr, s.leaf_ptr));
+  TRY(upload(h, &h->leaf_n, s.leaf_n));
+  TRY(upload(h, &h->leaf_cell, s.leaf_cell));
+  TRY(upload(h, &h->cell_enr, s.cell_enr));
+  {
+    std::vector<int64_t> eo(s.enr_cells.size() + 1, 0);
+    for (size_t ei = 0; ei < s.enr_cells.size(); ++ei) {
+      const int64_t e = s.enr_cells[ei];
+      eo[ei + 1] = eo[ei] + (s.qoff[e + 1] - s.qoff[e]) * (int64_t)(s.cf_ptr[ei + 1] - s.cf_ptr[ei]);
+    }
+    h->eq_elems = eo.back();
+    TRY(upload(h, &h->eq_off, eo));
+  }
+  // K_d = sum_cells (2/h) K1, M_d = sum_cells (h/2) M1 on the nodes of axis d,
+  // stored as 9-entry bands (column offsets -4 .. 4)
+  std::vector<double> xyz;
+  for (int d = 0; d < 3; ++d) {
+    const int nn = s.nn[d];
+    std::vector<double> K((size_t)nn * 9, 0.0), M((size_t)nn * 9, 0.0);
+    for (int c = 0; c < s.nc[d]; ++c) {
+      const double hc = s.brk[d][c + 1] - s.brk[d][c];
+      for (int a = 0; a < NP1; ++a)
+        for (int b = 0; b < NP1; ++b) {
+          const size_t idx = (size_t)(P * c + a) * 9 + (b - a + 4);
+          K[idx] += (2.0 / hc) * s.K1[a * NP1 + b];
+          M[idx] += (hc / 2.0) * s.M1[a * NP1 + b];
+        }
+    }
+    TRY(upload(h, &h->band[d], K));
+    TRY(upload(h, &h->band[3 + d], M));
+    xyz.push_back(s.brk[d][0]);
+    for (int c = 0; c < s.nc[d]; ++c) {
+      const double lo = s.brk[d][c], hc = s.brk[d][c + 1] - s.brk[d][c];
+      for (int a = 1; a < NP1; ++a) xyz.push_back(lo + 0.5 * (s.gll_z[a] + 1.0) * hc);
+    }
+    // diagonal entries for the Jacobi preconditioner
+  }
+  TRY(upload(h, &h->node_xyz, xyz));
+  {
+    // diag A = (Kx_ii My_jj Mz_kk + Mx_ii Ky_jj Mz_kk + Mx_ii My_jj Kz_kk) / (4 pi)
+    std::vector<double> kd[3], md[3];
+    for (int d = 0; d < 3; ++d) {
+      kd[d].assign(s.nn[d], 0.0);
+      md[d].assign(s.nn[d], 0.0);
+      for (int c = 0; c < s.nc[d]; ++c) {
+        const double hc = s.brk[d][c + 1] - s.brk[d][c];
+        for (int a = 0; a < NP1; ++a) {
+          kd[d][P * c + a] += (2.0 / hc) * s.K1[a * NP1 + a];
+          md[d][P * c + a] += (hc / 2.0) * s.M1[a * NP1 + a];
+        }
+      }
+    }
+    std::vector<float> dv(s.n_nodes);
+    const double inv4pi = 1.0 / (4.0 * M_PI);
+    for (int64_t g = 0; g < s.n_nodes; ++g) {
+      const int i = (int)(g % s.nn[0]), j = (int)((g / s.nn[0]) % s.nn[1]), k = (int)(g / ((int64_t)s.nn[0] * s.nn[1]));
+      const double dg = inv4pi * (kd[0][i] * md[1][j] * md[2][k] + md[0][i] * kd[1][j] * md[2][k] +
+                                  md[0][i] * md[1][j] * kd[2][k]);
+      dv[g] = (s.Dinv[g] != 0.0) ? (float)(1.0 / dg) : 0.0f;
+    }
+    TRY(upload(h, &h->dinvA, dv));
+  }
+  // nuclear repulsion E_ZZ
+  h->e_zz = 0.0;
+  const int na = (int)s.atom_Z.size();
+  for (int a = 0; a < na; ++a)
+    for (int b = a + 1; b < na; ++b) {
+      double d2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double t = s.atom_xyz[3 * a + d] - s.atom_xyz[3 * b + d];
+        d2 += t * t;
+      }
+      h->e_zz += s.atom_Z[a] * s.atom_Z[b] / sqrt(d2);
+    }
+  return EFE_OK;
+}
+
+LeafDev leaf_dev(const efe_handle* h) {
+  return LeafDev{h->leaf_off, h->leaf_n, h->leaf_cell, h->qpts, h->leaf_nmax};
+}
+
+BandsDev bands_dev(const efe_handle* h) {
+  BandsDev b;
+  for (int d = 0; d < 3; ++d) {
+    b.K[d] = h->band[d];
+    b.M[d] = h->band[3 + d];
+    b.nn[d] = h->mesh.nn[d];
+  }
+  return b;
+}
+
+// enrichment values at the enriched cells' points, computed on first use
+int ensure_eq(efe_handle* h, cudaStream_t st) {
+  if (h->Eq || h->nE == 0) return EFE_OK;
+  TRY(dalloc(h, &h->Eq, h->eq_elems));
+  EnrDev en{h->cell_enr, h->cf_ptr, h->cf_idx, h->qoff, h->eq_off, h->Eq, h->n_nodes};
+  launch_enr_values(en, h->enr_cells, h->qoff, h->qpts, h->funcs, h->n_enr, st);
+  CKL();
+  return EFE_OK;
+}
+
+EnrDev enr_dev(const efe_handle* h) {
+  if (h->nE == 0) return EnrDev{nullptr, nullptr, nullptr, h->qoff, nullptr, nullptr, h->n_nodes};
+  return EnrDev{h->cell_enr, h->cf_ptr, h->cf_idx, h->qoff, h->eq_off, h->Eq, h->n_nodes};
+}
+
+// Hartree work buffers (allocated once)
+int hartree_alloc(efe_handle* h, int max_it) {
+  const int64_t nn = h->n_nodes;
+  if (!h->hb) {
+    const int64_t nt = stiff_tiles(bands_dev(h));
+    TRY(dalloc(h, &h->hb, nn));
+    TRY(dalloc(h, &h->hr64, nn));
+    TRY(dalloc(h, &h->hphi, nn));
+    TRY(dalloc(h, &h->hlb, std::max<int64_t>(1, h->n_leaf) * NL));
+    TRY(dalloc(h, &h->hr32, nn));
+    TRY(dalloc(h, &h->hz32, nn));
+    TRY(dalloc(h, &h->hp0, nn));
+    TRY(dalloc(h, &h->hp1, nn));
+    TRY(dalloc(h, &h->hq, nn));
+    TRY(dalloc(h, &h->hd, nn));
+    TRY(dalloc(h, &h->hpart_rz0, nt));
+    TRY(dalloc(h, &h->hpart_rr, nt));
+    TRY(dalloc(h, &h->hpart_pq, nt));
+    TRY(dalloc(h, &h->hpart_rz, cg_reduce_blocks()));
+    TRY(dalloc(h, &h->hdone, 1));
+    TRY(dalloc(h, &h->red_part, 64 * (int64_t)cg_reduce_blocks()));
+    TRY(dalloc(h, &h->red_out, 64));
+    CK(cudaMemset(h->hphi, 0, sizeof(double) * nn));
+  }
+  if (max_it + 2 > h->hmax_it) {
+    if (h->hrz) dfree(h, h->hrz);
+    h->hmax_it = max_it + 2;
+    TRY(dalloc(h, &h->hrz, h->hmax_it));
+  }
+  return EFE_OK;
+}
+
+// -lap phi / (4 pi) = rho with multipole Dirichlet data: FP64 defect
+// correction around a Jacobi-preconditioned FP32 CG (inner relative
+// reduction 1e-5 of the preconditioned residual norm).
+int hartree_solve(efe_handle* h, const double* rho, double* vh, double* phi, double tol, int max_it, int* iters,
+                  double* relres, cudaStream_t st) {
+  TRY(hartree_alloc(h, max_it));
+  const int64_t nn = h->n_nodes;
+  const LeafDev lf = leaf_dev(h);
+  const BandsDev bd = bands_dev(h);
+  const int64_t nt = stiff_tiles(bd);
+  launch_hartree_load(lf, h->n_leaf, h->mesh, h->re, h->leaf_ptr, rho, h->mask, nn, h->hlb, h->hb, st);
+  launch_moments(h->qpts, rho, h->nq, h->red_part, h->red_out, st);
+  launch_hartree_bc(h->mesh, h->node_xyz, h->mask, h->red_out, nn, phi, st);
+  launch_dot(nn, h->hb, h->hb, h->red_part, h->red_out + 8, st);
+  CKL();
+  double bb = 0.0;
+  CK(cudaMemcpyAsync(&bb, h->red_out + 8, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  CgDev cg;
+  cg.done = h->hdone;
+  cg.part_rz0 = h->hpart_rz0;
+  cg.part_rz = h->hpart_rz;
+  cg.part_pq = h->hpart_pq;
+  cg.rz_hist = h->hrz;
+  cg.tol2 = 1e-10;
+  cg.max_it = max_it;
+  cg.p[0] = h->hp0;
+  cg.p[1] = h->hp1;
+  cg.z = h->hz32;
+  cg.q = h->hq;
+  cg.r = h->hr32;
+  cg.d = h->hd;
+  cg.dinv = h->dinvA;
+  cg.mask = h->mask;
+  int total = 0;
+  double rr = 0.0, rr_prev = -1.0;
+  for (int outer = 0; outer < 40; ++outer) {
+    if (launch_stiff_resid(bd, phi, h->hb, h->mask, h->dinvA, h->hr64, h->hr32, h->hz32, h->hpart_rz0,
+                           h->hpart_rr, st)) {
+      h->err = "Hartree residual kernel: shared-memory configuration failed";
+      return EFE_ERR_CUDA;
+    }
+    launch_finish(h->hpart_rr, (int)nt, 1, h->red_out + 9, st);
+    CKL();
+    CK(cudaMemcpyAsync(&rr, h->red_out + 9, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (!std::isfinite(rr)) {
+      h->err = "non-finite Hartree residual";
+      return EFE_ERR_NAN;
+    }
+    if (rr <= tol * tol * bb) break;
+    if (rr_prev >= 0.0 && rr > 0.25 * rr_prev) break;  // stagnation at the FP64 rounding floor
+    rr_prev = rr;
+    CK(cudaMemsetAsync(h->hd, 0, sizeof(float) * nn, st));
+    CK(cudaMemsetAsync(h->hdone, 0, sizeof(int), st));
+    int it = 0, done = 0;
+    while (!done && it <= max_it) {
+      for (int j = 0; j < 32 && it <= max_it; ++j, ++it)
+        if (launch_cg_iteration(bd, cg, it, nn, st)) {
+          h->err = "Hartree CG kernel: shared-memory configuration failed";
+          return EFE_ERR_CUDA;
+        }
+      CKL();
+      CK(cudaMemcpyAsync(&done, h->hdone, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    total += done > 0 ? done - 1 : it;
+    launch_add_f32(nn, h->hd, phi, st);
+    CKL();
+  }
+  if (relres) *relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  if (iters) *iters = total;
+  launch_leaf_interp(lf, h->n_leaf, h->mesh, h->re, phi, vh, st);
+  CKL();
+  if (bb > 0.0 && rr > 1e6 * tol * tol * bb) {
+    h->err = "Hartree solve did not reach the requested residual";
+    return EFE_ERR_NOCONV;
+  }
+  return EFE_OK;
+}
+
+// host: occupations by bisection on mu (same steps as the electron-count condition)
+int fermi_host(const double* eps, int N, double ne, double kT, double* occ, double* mu_out) {
+  if (N < 1 || !(kT > 0.0) || !(ne >= 0.0)) return EFE_ERR_ARG;
+  double emin = eps[0], emax = eps[0];
+  for (int i = 1; i < N; ++i) {
+    emin = std::min(emin, eps[i]);
+    emax = std::max(emax, eps[i]);
+  }
+  auto count = [&](double mu) {
+    double c = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double x = std::min(700.0, std::max(-700.0, (eps[i] - mu) / kT));
+      c += 1.0 / (1.0 + exp(x));
+    }
+    return 2.0 * c;
+  };
+  double lo = emin - 50.0 * kT - 1.0, hi = emax + 50.0 * kT + 1.0;
+  if (count(hi) < ne) return EFE_ERR_ARG;
+  for (int k = 0; k < 400; ++k) {
+    const double mid = 0.5 * (lo + hi);
+    if (count(mid) < ne) lo = mid; else hi = mid;
+    if (hi - lo < 1e-14) break;
+  }
+  const double mu = 0.5 * (lo + hi);
+  for (int i = 0; i < N; ++i) {
+    const double x = std::min(700.0, std::max(-700.0, (eps[i] - mu) / kT));
+    occ[i] = 1.0 / (1.0 + exp(x));
+  }
+  if (mu_out) *mu_out = mu;
+  return EFE_OK;
+}
+
+// Anderson: weighted Gram of the residual differences on the device, the
+// (n-1) x (n-1) system on the host (Gaussian elimination with partial pivoting;
+// a pivot below 1e-14 of the largest diagonal drops that stage), then the mix.
+int anderson_apply(efe_handle* h, const HistDev& hs, double beta, double* out, cudaStream_t st) {
+  const int n = hs.n, m = n - 1;
+  AndersonCoef th;
+  for (int k = 0; k < ANDERSON_MAX; ++k) th.t[k] = 0.0;
+  if (m > 0) {
+    const int nv = anderson_values(n);
+    launch_anderson_gram(h->qpts, h->nq, hs, h->red_part, h->red_out, st);
+    CKL();
+    double v[64];
+    CK(cudaMemcpyAsync(v, h->red_out, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double A[ANDERSON_MAX][ANDERSON_MAX + 1];
+    int c = 0;
+    for (int k = 0; k < m; ++k)
+      for (int l = k; l < m; ++l) A[k][l] = A[l][k] = v[c++];
+    for (int k = 0; k < m; ++k) A[k][m] = v[c++];
+    double dmax = 0.0;
+    for (int k = 0; k < m; ++k) dmax = std::max(dmax, fabs(A[k][k]));
+    bool use[ANDERSON_MAX];
+    for (int k = 0; k < m; ++k) use[k] = true;
+    for (int col = 0; col < m; ++col) {
+      int piv = -1;
+      double best = 0.0;
+      for (int r = col; r < m; ++r)
+        if (fabs(A[r][col]) > best) { best = fabs(A[r][col]); piv = r; }
+      if (piv < 0 || best <= 1e-14 * dmax) { use[col] = false; continue; }
+      if (piv != col)
+        for (int j = 0; j <= m; ++j) std::swap(A[piv][j], A[col][j]);
+      for (int r = col + 1; r < m; ++r) {
+        const double f = A[r][col] / A[col][col];
+        for (int j = col; j <= m; ++j) A[r][j] -= f * A[col][j];
+      }
+    }
+    for (int col = m - 1; col >= 0; --col) {
+      if (!use[col]) { th.t[col] = 0.0; continue; }
+      double sv = A[col][m];
+      for (int j = col + 1; j < m; ++j) sv -= A[col][j] * th.t[j];
+      th.t[col] = sv / A[col][col];
+    }
+  }
+  launch_anderson_mix(h->nq, hs, th, beta, out, st);
+  CKL();
+  return EFE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -519,6 +851,7 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
   TRY(upload(h, &h->aZ, s.atom_Z));
   TRY(upload(h, &h->qpts, s.qpts));
   TRY(upload(h, &h->qoff, s.qoff));
+  TRY(scf_setup_upload(h, s));
   TRY(dalloc(h, &h->V, h->nq));
   // parity colours of the cells
   {
@@ -1048,6 +1381,189 @@ int efe_kernel_stats(efe_handle* h, int64_t* launches, double* total_ms, int64_t
     h->t_ms = 0.0;
     h->t_cellcols = 0;
   }
+  return EFE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// self-consistent field
+int efe_density(efe_handle* h, const double* X, int64_t ldx, int32_t N, const double* occ, double* rho,
+                void* stream) {
+  if (!h || !X || !occ || !rho || N < 1 || ldx < N) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  cudaStream_t st = S(stream);
+  TRY(ensure_eq(h, st));
+  if (launch_leaf_density(leaf_dev(h), h->n_leaf, h->mesh, h->re, enr_dev(h), h->kmax, X, ldx, N, occ, rho, st)) {
+    h->err = "density kernel: shared-memory request too large (enrichment functions per cell)";
+    return EFE_ERR_ARG;
+  }
+  CKL();
+  return EFE_OK;
+}
+
+int efe_xc_lda(efe_handle* h, const double* rho, double* exc, double* vxc, void* stream) {
+  if (!h || !rho || (!exc && !vxc)) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  launch_lda(h->nq, rho, exc, vxc, S(stream));
+  CKL();
+  return EFE_OK;
+}
+
+int efe_hartree(efe_handle* h, const double* rho, double* vh, double* phi, double tol, int32_t max_iter,
+                int32_t* iters, void* stream) {
+  if (!h || !rho || !vh || !(tol > 0.0) || max_iter < 1) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  cudaStream_t st = S(stream);
+  TRY(hartree_alloc(h, max_iter));
+  if (!phi) {
+    phi = h->hphi;
+    CK(cudaMemsetAsync(phi, 0, sizeof(double) * h->n_nodes, st));
+  }
+  int it = 0;
+  const int rc = hartree_solve(h, rho, vh, phi, tol, max_iter, &it, nullptr, st);
+  if (iters) *iters = it;
+  return rc;
+}
+
+int efe_fermi(const double* eps, int32_t N, double n_electrons, double kT, double* occ, double* mu) {
+  if (!eps || !occ) return EFE_ERR_ARG;
+  return fermi_host(eps, N, n_electrons, kT, occ, mu);
+}
+
+int efe_anderson(efe_handle* h, const double* rho_in_hist, const double* rho_out_hist, int32_t n, double beta,
+                 double* rho_next, void* stream) {
+  if (!h || !rho_in_hist || !rho_out_hist || !rho_next || n < 1 || n > ANDERSON_MAX) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  TRY(hartree_alloc(h, 1));
+  HistDev hs;
+  hs.n = n;
+  for (int k = 0; k < n; ++k) {
+    hs.rin[k] = rho_in_hist + (int64_t)k * h->nq;
+    hs.rout[k] = rho_out_hist + (int64_t)k * h->nq;
+  }
+  return anderson_apply(h, hs, beta, rho_next, S(stream));
+}
+
+int efe_scf_init(efe_handle* h, const efe_scf_params* p, void* stream) {
+  if (!h || !p) return EFE_ERR_ARG;
+  if (!(p->n_electrons > 0.0) || !(p->kT > 0.0) || !(p->mix_beta > 0.0) || p->mix_beta > 1.0 || p->n_hist < 1 ||
+      p->n_hist > ANDERSON_MAX || !(p->poisson_tol > 0.0) || p->poisson_max_iter < 1 || p->lanczos_k < 2) {
+    h->err = "SCF parameters out of range";
+    return EFE_ERR_ARG;
+  }
+  TRY(set_dev(h));
+  cudaStream_t st = S(stream);
+  if (!h->vext) {
+    TRY(dalloc(h, &h->vext, h->nq));
+    TRY(dalloc(h, &h->vh_in, h->nq));
+    TRY(dalloc(h, &h->vxc_in, h->nq));
+    TRY(dalloc(h, &h->vh_out, h->nq));
+    TRY(dalloc(h, &h->phi_in, h->n_nodes));
+    TRY(dalloc(h, &h->phi_out, h->n_nodes));
+    TRY(dalloc(h, &h->v0, h->rows));
+    for (int k = 0; k < 2 * ANDERSON_MAX; ++k) TRY(dalloc(h, &h->hist[k], h->nq));
+  }
+  CK(cudaMemsetAsync(h->phi_in, 0, sizeof(double) * h->n_nodes, st));
+  CK(cudaMemsetAsync(h->phi_out, 0, sizeof(double) * h->n_nodes, st));
+  launch_potential_analytic(h->qpts, h->nq, h->axyz, h->aZ, h->n_atoms, 1, nullptr, nullptr, nullptr, 0, 0.0,
+                            h->vext, st);
+  CKL();
+  TRY(ensure_eq(h, st));
+  TRY(hartree_alloc(h, p->poisson_max_iter));
+  h->scfp = *p;
+  h->hist_count = 0;
+  h->hist_head = 0;
+  h->ritz.clear();
+  h->scf_iter = 0;
+  h->scf_ready = true;
+  CK(cudaStreamSynchronize(st));
+  return EFE_OK;
+}
+
+int efe_scf_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, int32_t passes, int32_t precision,
+                 int32_t fp64_tail, double* rho_in, double* rho_out, double* eig, double* occ, efe_scf_result* res,
+                 void* stream) {
+  if (!h || !X || !rho_in || !rho_out || !res || N < 1 || ldx < N || m < 1 || passes < 1) return EFE_ERR_ARG;
+  if (!h->scf_ready) {
+    h->err = "call efe_scf_init first";
+    return EFE_ERR_STATE;
+  }
+  TRY(set_dev(h));
+  cudaStream_t st = S(stream);
+  const efe_scf_params& p = h->scfp;
+  std::memset(res, 0, sizeof(*res));
+  // V_eff = V_ext + V_H[rho_in] + v_xc(rho_in)   (Eq. veff)
+  int it1 = 0, it2 = 0;
+  TRY(hartree_solve(h, rho_in, h->vh_in, h->phi_in, p.poisson_tol, p.poisson_max_iter, &it1, nullptr, st));
+  launch_veff(h->nq, rho_in, h->vext, h->vh_in, h->vxc_in, h->V, st);
+  CKL();
+  TRY(efe_set_potential(h, h->V, stream));
+  std::vector<double> ev(N), rv(N), fv(N);
+  if ((int)h->ritz.size() != N) {
+    TRY(efe_rayleigh_ritz(h, X, ldx, N, ev.data(), rv.data(), stream));
+    h->ritz = ev;
+  }
+  // Lanczos start: the last column of X
+  CK(cudaMemcpy2DAsync(h->v0, sizeof(double), X + (N - 1), sizeof(double) * ldx, sizeof(double), h->rows,
+                       cudaMemcpyDeviceToDevice, st));
+  double b = 0.0;
+  TRY(efe_upper_bound(h, h->v0, p.lanczos_k, &b, stream));
+  for (int pass = 0; pass < passes; ++pass) {
+    const double a = *std::max_element(h->ritz.begin(), h->ritz.end());
+    const double a0 = *std::min_element(h->ritz.begin(), h->ritz.end());
+    TRY(efe_chfsi_step(h, X, ldx, N, m, a, b, a0, precision, fp64_tail, stream));
+    TRY(efe_rayleigh_ritz(h, X, ldx, N, ev.data(), rv.data(), stream));
+    h->ritz = ev;
+  }
+  double mu = 0.0;
+  if (fermi_host(h->ritz.data(), N, p.n_electrons, p.kT, fv.data(), &mu) != EFE_OK) {
+    h->err = "the subspace holds fewer than N_e / 2 states";
+    return EFE_ERR_ARG;
+  }
+  if (h->occ_cap < N) {
+    if (h->occ_dev) dfree(h, h->occ_dev);
+    TRY(dalloc(h, &h->occ_dev, N));
+    h->occ_cap = N;
+  }
+  CK(cudaMemcpyAsync(h->occ_dev, fv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
+  TRY(efe_density(h, X, ldx, N, h->occ_dev, rho_out, stream));
+  TRY(hartree_solve(h, rho_out, h->vh_out, h->phi_out, p.poisson_tol, p.poisson_max_iter, &it2, nullptr, st));
+  launch_scf_sums(h->qpts, h->nq, rho_in, rho_out, h->vh_in, h->vxc_in, h->vh_out, h->red_part, h->red_out + 16, st);
+  CKL();
+  double sums[5];
+  CK(cudaMemcpyAsync(sums, h->red_out + 16, sizeof(sums), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  double band = 0.0;
+  for (int i = 0; i < N; ++i) band += 2.0 * fv[i] * h->ritz[i];
+  res->band = band;
+  res->xc = sums[0];
+  res->hartree = 0.5 * sums[1];
+  res->double_counting = sums[2];
+  res->drho = sqrt(sums[3]);
+  res->n_out = sums[4];
+  res->zz = h->e_zz;
+  res->total = res->band - res->double_counting + res->hartree + res->xc + res->zz;
+  res->fermi_level = mu;
+  res->upper_bound = b;
+  res->poisson_iters = it1 + it2;
+  res->filter_passes = passes;
+  if (eig) std::memcpy(eig, h->ritz.data(), sizeof(double) * N);
+  if (occ) std::memcpy(occ, fv.data(), sizeof(double) * N);
+  // n-stage Anderson mixing: push (rho_in, rho_out), then overwrite rho_in
+  const int nh = p.n_hist;
+  const int slot = h->hist_head;
+  CK(cudaMemcpyAsync(h->hist[slot], rho_in, sizeof(double) * h->nq, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->hist[ANDERSON_MAX + slot], rho_out, sizeof(double) * h->nq, cudaMemcpyDeviceToDevice, st));
+  h->hist_head = (slot + 1) % nh;
+  h->hist_count = std::min(h->hist_count + 1, nh);
+  HistDev hs;
+  hs.n = h->hist_count;
+  for (int k = 0; k < hs.n; ++k) {
+    const int sk = ((h->hist_head - hs.n + k) % nh + nh) % nh;
+    hs.rin[k] = h->hist[sk];
+    hs.rout[k] = h->hist[ANDERSON_MAX + sk];
+  }
+  TRY(anderson_apply(h, hs, p.mix_beta, rho_in, st));
+  h->scf_iter++;
   return EFE_OK;
 }
 

@@ -43,6 +43,12 @@ struct Setup {
   // quadrature: all cells, 4 doubles per point (x, y, z, w)
   std::vector<int64_t> qoff;            // n_cell + 1
   std::vector<double> qpts;
+  // quadrature leaves (tensor Gauss boxes, points contiguous, x fastest)
+  std::vector<int64_t> leaf_ptr;        // n_cell + 1: leaves of each cell
+  std::vector<int64_t> leaf_off;        // n_leaf + 1: first point of each leaf
+  std::vector<int32_t> leaf_n;          // points per axis
+  std::vector<int32_t> leaf_cell;       // owning cell
+  std::vector<double> leaf_box;         // lo[3], hi[3]
   // GLL-diagonal overlap
   std::vector<double> D, Dinv;
   // M^ec / H^ec sparsity (rows = functions), kinetic part of H^ec

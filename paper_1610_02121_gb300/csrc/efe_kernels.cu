@@ -503,9 +503,9 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, int npc, const 
       for (int u = 0; u < CPL_CH; ++u) {
         if (u >= nn) break;
         const float x = ss[u] * xv[u];
-        // each accumulator address (a, c) belongs to thread c alone: the reductions
-        // land in program order (deterministic) without stalling the thread
-        for (int q = sp[u]; q < sp[u + 1]; ++q) atomicAdd(&acc[scol[q] * N + c], sval[q] * x);
+        // each accumulator address (a, c) belongs to thread c alone: plain
+        // read-modify-write, in program order (deterministic)
+        for (int q = sp[u]; q < sp[u + 1]; ++q) acc[scol[q] * N + c] += sval[q] * x;
       }
     }
   }

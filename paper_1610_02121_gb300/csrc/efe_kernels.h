@@ -140,4 +140,88 @@ void launch_dot(int64_t n, const double* x, const double* y, double* part, doubl
 void launch_axpby3(int64_t n, double* w, const double* v, const double* vp, double a, double b, cudaStream_t st);
 void launch_scale(int64_t n, const double* x, double s, double* y, cudaStream_t st);
 
+// ---- self-consistent field (efe_scf.cu) ----
+constexpr int ANDERSON_MAX = 8;   // stages of Anderson mixing
+
+struct LeafDev {          // tensor Gauss boxes of the quadrature
+  const int64_t* off;     // first point of each leaf
+  const int32_t* n;       // points per axis
+  const int32_t* cell;    // owning cell
+  const double* qpts;     // (x, y, z, w) per point
+  int nmax;               // largest n
+};
+
+struct EnrDev {           // enrichment values at the points of the enriched cells
+  const int32_t* cell_enr;  // cell -> enriched-cell index or -1 (NULL: no enrichment)
+  const int32_t* cf_ptr;
+  const int32_t* cf_idx;
+  const int64_t* qoff;      // first point of each cell
+  const int64_t* eq_off;    // per enriched cell: offset of its [point][function] block
+  double* Eq;
+  int64_t n_nodes;          // row of the first enrichment coefficient
+};
+
+struct BandsDev {         // assembled 1-D stiffness / exact mass, 9 entries per row (offsets -4..4)
+  const double* K[3];
+  const double* M[3];
+  int nn[3];
+};
+
+struct CgDev {            // device state of the inner FP32 conjugate-gradient solve
+  int* done;              // 0 while running, else (last iteration + 1)
+  const double* part_rz0; // r.z partials of the residual kernel (one per tile)
+  double* part_rz;        // r.z partials of the update kernel
+  double* part_pq;        // p.q partials (one per tile)
+  double* rz_hist;        // r.z per iteration
+  double tol2;            // stop when r.z <= tol2 * (r.z)_0
+  int max_it;
+  float* p[2];
+  float *z, *q, *r, *d;
+  const float* dinv;      // inverse diagonal of A (0 on Dirichlet nodes)
+  const double* mask;     // 1 interior, 0 Dirichlet
+};
+
+struct HistDev {          // Anderson history, oldest first
+  const double* rin[ANDERSON_MAX];
+  const double* rout[ANDERSON_MAX];
+  int n;
+};
+
+struct AndersonCoef {
+  double t[ANDERSON_MAX];
+};
+
+int launch_leaf_density(const LeafDev& lf, int64_t n_leaf, const MeshDev& m, const RefElem& re, const EnrDev& en,
+                        int kmax, const double* X, int64_t ldx, int N, const double* occ, double* rho,
+                        cudaStream_t st);
+size_t leaf_density_smem(int nm, int kmax);
+void launch_leaf_interp(const LeafDev& lf, int64_t n_leaf, const MeshDev& m, const RefElem& re, const double* phi,
+                        double* out, cudaStream_t st);
+void launch_hartree_load(const LeafDev& lf, int64_t n_leaf, const MeshDev& m, const RefElem& re,
+                         const int64_t* leaf_ptr, const double* rho, const double* mask, int64_t n_nodes,
+                         double* lb, double* b, cudaStream_t st);
+void launch_enr_values(const EnrDev& en, const int32_t* enr_cells, const int64_t* qoff, const double* qpts,
+                       const DevFunc* funcs, int64_t n_enr, cudaStream_t st);
+int64_t stiff_tiles(const BandsDev& bd);
+int cg_reduce_blocks();
+int launch_stiff_resid(const BandsDev& bd, const double* phi, const double* b, const double* mask, const float* dinv,
+                       double* r64, float* r32, float* z32, double* part_rz, double* part_rr, cudaStream_t st);
+int launch_cg_iteration(const BandsDev& bd, const CgDev& cg, int it, int64_t n, cudaStream_t st);
+void launch_add_f32(int64_t n, const float* d, double* phi, cudaStream_t st);
+void launch_moments(const double* qpts, const double* rho, int64_t nq, double* part, double* mom, cudaStream_t st);
+void launch_finish(const double* part, int nb, int nv, double* out, cudaStream_t st);
+void launch_hartree_bc(const MeshDev& m, const double* node_xyz, const double* mask, const double* mom,
+                       int64_t n_nodes, double* phi, cudaStream_t st);
+void launch_lda(int64_t nq, const double* rho, double* exc, double* vxc, cudaStream_t st);
+void launch_veff(int64_t nq, const double* rho, const double* vext, const double* vh, double* vxc, double* veff,
+                 cudaStream_t st);
+void launch_scf_sums(const double* qpts, int64_t nq, const double* rho_in, const double* rho_out, const double* vh_in,
+                     const double* vxc_in, const double* vh_out, double* part, double* out, cudaStream_t st);
+int anderson_values(int n);
+void launch_anderson_gram(const double* qpts, int64_t nq, const HistDev& hs, double* part, double* out,
+                          cudaStream_t st);
+void launch_anderson_mix(int64_t nq, const HistDev& hs, const AndersonCoef& th, double beta, double* out,
+                         cudaStream_t st);
+void launch_scale_to(int64_t n, double* x, const double* num, double target, cudaStream_t st);
+
 }  // namespace efe

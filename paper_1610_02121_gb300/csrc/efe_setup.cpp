@@ -151,12 +151,18 @@ void trial_integrals(const TrialCtx& c, const double* pts, size_t np, double I[3
 // Sec. IV.C: append the parent's Gauss points if |I^p - sum I^c| < tau for every
 // trial function (or at the depth cap), otherwise recurse into the 8 children
 // (child c = cx + 2 cy + 4 cz).
+void push_box(const Box& b, std::vector<double>& boxes) {
+  for (int d = 0; d < 3; ++d) boxes.push_back(b.lo[d]);
+  for (int d = 0; d < 3; ++d) boxes.push_back(b.hi[d]);
+}
+
 void adaptive(const TrialCtx& c, const Box& b, int depth, int max_depth, double tau,
-              std::vector<double>& out) {
+              std::vector<double>& out, std::vector<double>& boxes) {
   std::vector<double> parent;
   gauss_box(b, c.n, c.gx, c.gw, parent);
   if (depth >= max_depth) {
     out.insert(out.end(), parent.begin(), parent.end());
+    push_box(b, boxes);
     return;
   }
   double Ip[3];
@@ -181,9 +187,10 @@ void adaptive(const TrialCtx& c, const Box& b, int depth, int max_depth, double 
   for (int d = 0; d < 3; ++d) ok = ok && (fabs(Ip[d] - Ic[d]) < tau);
   if (ok) {
     out.insert(out.end(), parent.begin(), parent.end());
+    push_box(b, boxes);
     return;
   }
-  for (int k = 0; k < 8; ++k) adaptive(c, kids[k], depth + 1, max_depth, tau, out);
+  for (int k = 0; k < 8; ++k) adaptive(c, kids[k], depth + 1, max_depth, tau, out, boxes);
 }
 
 }  // namespace
@@ -343,7 +350,7 @@ int build_setup(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const ef
   const int64_t n_enr = (int64_t)s.enr_cells.size();
 
   // per-enriched-cell adaptive rule and overlap / kinetic blocks (parallel)
-  std::vector<std::vector<double>> epts(n_enr);
+  std::vector<std::vector<double>> epts(n_enr), eboxes(n_enr);
   std::vector<std::vector<double>> bMec(n_enr), bHkin(n_enr), bMee(n_enr), bHkee(n_enr);
   int bad_alloc = 0;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -358,7 +365,7 @@ int build_setup(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const ef
     const int kf = s.cf_ptr[ei + 1] - s.cf_ptr[ei];
     TrialCtx c{&s, fl, kf, qn, gxa, gwa};
     try {
-      adaptive(c, b, 0, basis->quad_max_depth, basis->quad_tau, epts[ei]);
+      adaptive(c, b, 0, basis->quad_max_depth, basis->quad_tau, epts[ei], eboxes[ei]);
       bMec[ei].assign((size_t)kf * NL, 0.0);
       bHkin[ei].assign((size_t)kf * NL, 0.0);
       bMee[ei].assign((size_t)kf * kf, 0.0);
@@ -438,6 +445,40 @@ int build_setup(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const ef
   }
   epts.clear();
   epts.shrink_to_fit();
+
+  // quadrature leaves: every rule above is a union of tensor Gauss boxes whose
+  // points are stored contiguously, x fastest (an ordinary cell is one box)
+  s.leaf_ptr.assign(s.n_cell + 1, 0);
+  for (int64_t e = 0; e < s.n_cell; ++e)
+    s.leaf_ptr[e + 1] = s.leaf_ptr[e] + (s.cell_enr[e] >= 0 ? (int64_t)(eboxes[s.cell_enr[e]].size() / 6) : 1);
+  const int64_t n_leaf = s.leaf_ptr[s.n_cell];
+  s.leaf_box.assign((size_t)n_leaf * 6, 0.0);
+  s.leaf_off.assign(n_leaf + 1, 0);
+  s.leaf_n.assign(n_leaf, 0);
+  s.leaf_cell.assign(n_leaf, 0);
+  for (int64_t e = 0; e < s.n_cell; ++e) {
+    const int64_t l0 = s.leaf_ptr[e];
+    if (s.cell_enr[e] >= 0) {
+      const auto& bx = eboxes[s.cell_enr[e]];
+      const int64_t nl = (int64_t)(bx.size() / 6);
+      std::copy(bx.begin(), bx.end(), &s.leaf_box[(size_t)l0 * 6]);
+      for (int64_t l = 0; l < nl; ++l) {
+        s.leaf_n[l0 + l] = qn;
+        s.leaf_cell[l0 + l] = (int32_t)e;
+        s.leaf_off[l0 + l] = s.qoff[e] + l * (int64_t)qn * qn * qn;
+      }
+    } else {
+      const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((int64_t)nx * ny));
+      double* bx = &s.leaf_box[(size_t)l0 * 6];
+      bx[0] = s.brk[0][i]; bx[1] = s.brk[1][j]; bx[2] = s.brk[2][k];
+      bx[3] = s.brk[0][i + 1]; bx[4] = s.brk[1][j + 1]; bx[5] = s.brk[2][k + 1];
+      s.leaf_n[l0] = s.ng;
+      s.leaf_cell[l0] = (int32_t)e;
+      s.leaf_off[l0] = s.qoff[e];
+    }
+  }
+  s.leaf_off[n_leaf] = s.n_q;
+  eboxes.clear();
 
   // GLL-diagonal overlap D (Sec. III.B); D^-1 zero on the Dirichlet faces
   const int NX = s.nn[0], NY = s.nn[1], NZ = s.nn[2];

@@ -1,0 +1,188 @@
+"""GPU parity of the self-consistent-field kernels (Sec. V) against the FP64 oracle.
+
+Densities, LDA values, Hartree potentials, Fermi occupations and Anderson
+updates are compared element by element on the same seeded inputs; the SCF
+loop is compared at its fixed point with the oracle's converged run stored in
+tests/golden/scf_hydrogen_4c.json (written by tests/golden/make_scf_golden.py,
+which calls only the oracle).  Tolerances: FP64 rounding (1e-12 relative) for
+pointwise values; the Hartree solve stops at a relative residual of 1e-12, so
+its values agree to 1e-9 of their scale; energies at the fixed point to 1e-6 Ha.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_util import cuda_available, gpu_system, to_dev, torch
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_available(), reason="needs a CUDA GPU")]
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "scf_hydrogen_4c.json")
+
+
+def point_perm(gpu_pts, ora_pts):
+    """Index map oracle point -> GPU point (both lists hold the same points)."""
+    kg = np.lexsort(np.round(gpu_pts[:, 2::-1].T, 9))
+    ko = np.lexsort(np.round(ora_pts[:, 2::-1].T, 9))
+    assert np.abs(gpu_pts[kg] - ora_pts[ko]).max() < 1e-12
+    perm = np.empty(len(ko), dtype=np.int64)
+    perm[ko] = kg
+    return perm
+
+
+class Pair:
+    def __init__(self, system):
+        from oracle import scf as S
+        from oracle.operators import Discretisation
+        self.s = system
+        self.d = Discretisation(system)
+        self.qc = S.QuadCache(self.d)
+        self.G = gpu_system(system)
+        q = self.G.qpoints().cpu().numpy()
+        self.gpts = q
+        self.perm = point_perm(q, np.column_stack([self.qc.all_pts, self.qc.all_w]))
+
+    def to_gpu_order(self, v_oracle):
+        out = np.empty_like(v_oracle)
+        out[self.perm] = v_oracle
+        return out
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return Pair(W.tiny(seed=11))
+
+
+@pytest.fixture(scope="module")
+def ho():
+    return Pair(W.harmonic(cells=3, half=6.0))
+
+
+def test_qpoints_are_the_oracle_rule(tiny):
+    w = tiny.gpts[:, 3]
+    np.testing.assert_allclose(w, tiny.to_gpu_order(tiny.qc.all_w), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("N", [1, 16, 37])
+def test_density_parity(tiny, N):
+    from oracle import scf as S
+    X = W.random_block(tiny.s, N, seed=21 + N)
+    occ = np.random.default_rng(N).uniform(0.0, 1.0, N)
+    rho = tiny.G.density(to_dev(X), occ).cpu().numpy()
+    ref = tiny.to_gpu_order(S.density(tiny.qc, X, occ))
+    assert np.abs(rho - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_density_classical_only(ho):
+    from oracle import scf as S
+    X = W.random_block(ho.s, 5, seed=3)
+    occ = np.array([1.0, 0.5, 0.25, 0.0, 1.0])
+    rho = ho.G.density(to_dev(X), occ).cpu().numpy()
+    ref = ho.to_gpu_order(S.density(ho.qc, X, occ))
+    assert np.abs(rho - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_lda_parity(tiny):
+    from oracle import scf as S
+    n = tiny.G.n_qpoints
+    rho = np.logspace(-12, 4, n)
+    rho[::7] = 3.0 / (4.0 * math.pi)          # r_s = 1 exactly, the branch point
+    rho[1::11] = 0.0
+    exc, vxc = tiny.G.xc_lda(to_dev(rho))
+    e_ref, v_ref = S.lda_pz81(rho)
+    np.testing.assert_allclose(exc.cpu().numpy(), e_ref, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(vxc.cpu().numpy(), v_ref, rtol=1e-13, atol=0)
+
+
+def _cloud(pts, centre, width):
+    r2 = np.sum((pts - np.asarray(centre)[None, :]) ** 2, axis=1)
+    return np.exp(-r2 / (2 * width * width))
+
+
+@pytest.mark.parametrize("which", ["tiny", "ho"])
+def test_hartree_parity(which, tiny, ho):
+    from oracle import scf as S
+    P = {"tiny": tiny, "ho": ho}[which]
+    rho_o = 2.0 * _cloud(P.qc.all_pts, [0.3, -0.2, 0.1], 1.1) + 0.5 * _cloud(P.qc.all_pts, [-1.0, 0.8, 0.0], 0.6)
+    VH_o, phi_o = S.hartree(P.qc, rho_o)
+    vh, phi, it = P.G.hartree(to_dev(P.to_gpu_order(rho_o)), tol=1e-12)
+    vh = vh.cpu().numpy()
+    scale = np.abs(VH_o).max()
+    assert np.abs(vh - P.to_gpu_order(VH_o)).max() <= 1e-9 * scale
+    assert np.abs(phi.cpu().numpy() - phi_o).max() <= 1e-9 * scale
+    assert it > 0
+
+
+def test_hartree_warm_start_and_zero_density(tiny):
+    rho = np.zeros(tiny.G.n_qpoints)
+    vh, phi, it = tiny.G.hartree(to_dev(rho))
+    assert np.abs(vh.cpu().numpy()).max() == 0.0 and it == 0
+    rho = _cloud(tiny.gpts[:, :3], [0.0, 0.0, 0.0], 1.0)
+    vh1, phi1, it1 = tiny.G.hartree(to_dev(rho), tol=1e-12)
+    vh2, phi2, it2 = tiny.G.hartree(to_dev(rho), phi=phi1.clone(), tol=1e-12)
+    assert it2 < max(it1, 1)
+    assert np.abs((vh2 - vh1).cpu().numpy()).max() <= 1e-9 * np.abs(vh1.cpu().numpy()).max()
+
+
+@pytest.mark.parametrize("ne", [1.0, 2.0, 7.0, 20.0])
+def test_fermi_parity(ne):
+    from oracle import scf as S
+    from paper_1610_02121_gb300 import _lib
+    eps = np.sort(np.random.default_rng(int(ne)).normal(0.0, 0.3, 12))
+    eps[4] = eps[5]                               # a degenerate pair
+    kT = 500 * S.KB_HA_PER_K
+    f, mu = _lib.fermi(eps, ne, kT)
+    f_o, mu_o = S.fermi_occupations(eps, ne, kT)
+    np.testing.assert_allclose(f, f_o, rtol=0, atol=1e-12)
+    assert abs(mu - mu_o) < 1e-12
+    with pytest.raises(Exception):
+        _lib.fermi(eps, 30.0, kT)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_anderson_parity(tiny, n):
+    from oracle import scf as S
+    rng = np.random.default_rng(100 + n)
+    nq = tiny.G.n_qpoints
+    base = _cloud(tiny.gpts[:, :3], [0.0, 0.0, 0.0], 1.5)
+    rin = np.stack([base * (1 + 0.1 * rng.standard_normal(nq)) for _ in range(n)])
+    rout = np.stack([base * (1 + 0.1 * rng.standard_normal(nq)) for _ in range(n)])
+    out = tiny.G.anderson(to_dev(rin), to_dev(rout), 0.37).cpu().numpy()
+    ref = S.anderson(list(rin), list(rout), tiny.gpts[:, 3], beta=0.37)
+    assert np.abs(out - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_scf_hydrogen_fixed_point():
+    """GPU SCF (one degree-12 filter pass per iteration, FP64) reaches the oracle's
+    converged LDA hydrogen atom: energies and 1s eigenvalue within 1e-6 Ha."""
+    g = json.load(open(GOLDEN))
+    c = g["settings"]
+    s = W.hydrogen(cells=c["cells"], half=c["half"], tau=c["tau"], max_depth=c["max_depth"])
+    G = gpu_system(s)
+    q = G.qpoints()
+    assert q.shape[0] == g["n_qpoints"]
+    pts = q[:, :3].cpu().numpy()
+    w = q[:, 3].cpu().numpy()
+    r = np.sqrt(np.sum(pts * pts, axis=1))
+    rho0 = np.exp(-r * r / (2.0 * c["start_width"] ** 2))
+    rho0 /= np.sum(w * rho0)
+    rho_in = to_dev(rho0)
+    rho_out = torch.empty_like(rho_in)
+    X = to_dev(W.initial_block(s, c["N"], seed=c["block_seed"]))
+    from oracle.scf import KB_HA_PER_K
+    G.scf_init(1.0, kT=c["kT_K"] * KB_HA_PER_K, beta=c["beta"], n_hist=c["n_hist"], poisson_tol=1e-12)
+    e_prev, res = None, None
+    for it in range(150):
+        res = G.scf_step(X, rho_in, rho_out, c["m"])
+        if e_prev is not None and abs(res["total"] - e_prev) < 1e-10 and res["drho"] < 1e-7:
+            break
+        e_prev = res["total"]
+    ge = g["energies"]
+    for k in ("total", "band", "xc", "hartree", "double_counting"):
+        assert abs(res[k] - ge[k]) < 1e-6, (k, res[k], ge[k])
+    assert abs(res["eig"][0] - g["eps"][0]) < 1e-6
+    assert abs(2 * res["occ"].sum() - 1.0) < 1e-12
+    assert abs(res["n_out"] - g["int_rho"]) < 1e-8
