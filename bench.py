@@ -351,7 +351,7 @@ def main():
         line["scf"] = {"s_per_iteration": ms_scf * 1e-3, "iterations_timed": args.scf_steps,
                        "n_electrons": ne, "kT_K": 500.0, "anderson_stages": 5, "mixing": 0.5,
                        "filter": f"one degree-{m} pass, {prec}", "n_qpoints": G.n_qpoints,
-                       "poisson_cg_iterations": [h["poisson_iters"] for h in hist],
+                       "poisson_correction_steps": [h["poisson_steps"] for h in hist],
                        "total_energy_Ha": [h["total"] for h in [r0] + hist],
                        "drho": [h["drho"] for h in [r0] + hist],
                        "start": "density of the Rayleigh-Ritz-rotated atomic-orbital block, renormalised to N_e"}

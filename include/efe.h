@@ -251,7 +251,7 @@ typedef struct {
   double mix_beta;           /* Anderson mixing parameter (0, 1] */
   int32_t n_hist;            /* Anderson stages, 1 .. 8 (1 = linear mixing) */
   double poisson_tol;        /* relative residual |b - A phi| / |b| of each Hartree solve */
-  int32_t poisson_max_iter;  /* cap on inner CG iterations per defect-correction step */
+  int32_t poisson_max_steps; /* cap on exact-solve correction steps per Hartree solve (2 is ample) */
   int32_t lanczos_k;         /* Lanczos steps of the upper bound b per SCF step */
 } efe_scf_params;
 
@@ -266,7 +266,7 @@ typedef struct {
   double drho;               /* |rho_out - rho_in|_L2 */
   double n_out;              /* int rho_out */
   double upper_bound;        /* b used by the filter */
-  int32_t poisson_iters;     /* inner CG iterations of the step's two Hartree solves */
+  int32_t poisson_steps;     /* correction steps of the step's two Hartree solves */
   int32_t filter_passes;
 } efe_scf_result;
 
@@ -282,14 +282,17 @@ int efe_density(efe_handle* h, const double* X, int64_t ldx, int32_t N, const do
 int efe_xc_lda(efe_handle* h, const double* rho, double* exc, double* vxc, void* stream);
 
 /* Hartree potential of rho (Q layout): -lap V_H / (4 pi) = rho (Eq. Poisson),
- * classical basis, Dirichlet data Q/r + d.r/r^3 on the box faces.  phi: nodal
- * potential (n_nodes FP64, device) -- on entry the interior values are the
- * starting guess, on exit the solution; NULL uses an internal zero start.
- * vh: V_H at the points (Q layout), written.  iters: inner CG iterations
- * (host, may be NULL).  Returns EFE_ERR_NOCONV if the relative residual stays
- * above 1e3 * tol. */
-int efe_hartree(efe_handle* h, const double* rho, double* vh, double* phi, double tol, int32_t max_iter,
-                int32_t* iters, void* stream);
+ * classical basis, Dirichlet data Q/r + d.r/r^3 on the box faces.  The
+ * interior block of the stiffness of the tensor-product mesh is a Kronecker
+ * sum of 1-D operators and is solved exactly by fast diagonalisation; the
+ * call repeats phi += A_ii^-1 (b - A phi)_i until |b - A phi| <= tol |b| or
+ * max_steps corrections.  phi: nodal potential (n_nodes FP64, device) -- on
+ * entry the interior values are the starting guess, on exit the solution;
+ * NULL uses an internal zero start.  vh: V_H at the points (Q layout),
+ * written.  steps: corrections taken (host, may be NULL).  Returns
+ * EFE_ERR_NOCONV if the relative residual stays above 1e3 * tol. */
+int efe_hartree(efe_handle* h, const double* rho, double* vh, double* phi, double tol, int32_t max_steps,
+                int32_t* steps, void* stream);
 
 /* Fermi-Dirac occupations (Eq. FermiDirac) with mu from 2 sum_i f_i = N_e
  * (Eq. Mu) by bisection.  Host arrays; EFE_ERR_ARG if the N states cannot hold

@@ -55,14 +55,14 @@ class PotentialDesc(C.Structure):
 
 class ScfParams(C.Structure):
     _fields_ = [("n_electrons", C.c_double), ("kT", C.c_double), ("mix_beta", C.c_double), ("n_hist", C.c_int32),
-                ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int32), ("lanczos_k", C.c_int32)]
+                ("poisson_tol", C.c_double), ("poisson_max_steps", C.c_int32), ("lanczos_k", C.c_int32)]
 
 
 class ScfResult(C.Structure):
     _fields_ = [("band", C.c_double), ("xc", C.c_double), ("hartree", C.c_double), ("zz", C.c_double),
                 ("double_counting", C.c_double), ("total", C.c_double), ("fermi_level", C.c_double),
                 ("drho", C.c_double), ("n_out", C.c_double), ("upper_bound", C.c_double),
-                ("poisson_iters", C.c_int32), ("filter_passes", C.c_int32)]
+                ("poisson_steps", C.c_int32), ("filter_passes", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -328,14 +328,14 @@ class System:
         self._check(self.L.efe_xc_lda(self.h, self._qvec(rho), self._qvec(exc), self._qvec(vxc), self._stream()))
         return exc, vxc
 
-    def hartree(self, rho, phi=None, tol=1e-11, max_iter=5000):
-        """V_H at the quadrature points, the nodal potential and the CG iteration count."""
+    def hartree(self, rho, phi=None, tol=1e-12, max_steps=3):
+        """V_H at the quadrature points, the nodal potential and the number of exact-solve corrections."""
         vh = self._torch.empty_like(rho)
         if phi is None:
             phi = self._torch.zeros(self.n_nodes, dtype=self._torch.float64, device=rho.device)
         it = C.c_int32()
         self._check(self.L.efe_hartree(self.h, self._qvec(rho), self._qvec(vh), C.c_void_p(phi.data_ptr()),
-                                       float(tol), int(max_iter), C.byref(it), self._stream()))
+                                       float(tol), int(max_steps), C.byref(it), self._stream()))
         return vh, phi, it.value
 
     def anderson(self, rho_in_hist, rho_out_hist, beta):
@@ -348,10 +348,10 @@ class System:
                                         C.c_void_p(out.data_ptr()), self._stream()))
         return out
 
-    def scf_init(self, n_electrons, kT=500 * KB_HA_PER_K, beta=0.5, n_hist=5, poisson_tol=1e-11,
-                 poisson_max_iter=5000, lanczos_k=10):
+    def scf_init(self, n_electrons, kT=500 * KB_HA_PER_K, beta=0.5, n_hist=5, poisson_tol=1e-12,
+                 poisson_max_steps=3, lanczos_k=10):
         p = ScfParams(float(n_electrons), float(kT), float(beta), int(n_hist), float(poisson_tol),
-                      int(poisson_max_iter), int(lanczos_k))
+                      int(poisson_max_steps), int(lanczos_k))
         self._check(self.L.efe_scf_init(self.h, C.byref(p), self._stream()))
 
     def scf_step(self, X, rho_in, rho_out, m, passes=1, precision="fp64", fp64_tail=0):

@@ -100,15 +100,13 @@ struct efe_handle {
   double* Eq = nullptr;                      // enrichment values at enriched-cell points (lazy)
   double* band[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // Kx Ky Kz Mx My Mz
   double* node_xyz = nullptr;                // node coordinates per axis
-  float* dinvA = nullptr;                    // inverse diagonal of the Hartree stiffness
   double e_zz = 0.0;
   bool scf_ready = false;
   efe_scf_params scfp{};
-  double *hb = nullptr, *hr64 = nullptr, *hlb = nullptr, *hphi = nullptr;
-  float *hr32 = nullptr, *hz32 = nullptr, *hp0 = nullptr, *hp1 = nullptr, *hq = nullptr, *hd = nullptr;
-  double *hpart_rz0 = nullptr, *hpart_rr = nullptr, *hpart_pq = nullptr, *hpart_rz = nullptr, *hrz = nullptr;
-  int* hdone = nullptr;
-  int hmax_it = 0;
+  double *hb = nullptr, *hr64 = nullptr, *hlb = nullptr, *hphi = nullptr, *hpart_rr = nullptr;
+  double *fdV[3] = {nullptr, nullptr, nullptr}, *fdVt[3] = {nullptr, nullptr, nullptr};
+  double *fdlam[3] = {nullptr, nullptr, nullptr};
+  double *fdU0 = nullptr, *fdU1 = nullptr;
   double *red_part = nullptr, *red_out = nullptr;
   double *vext = nullptr, *vh_in = nullptr, *vxc_in = nullptr, *vh_out = nullptr, *phi_in = nullptr,
          *phi_out = nullptr, *occ_dev = nullptr, *v0 = nullptr;
@@ -494,6 +492,104 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
 }
 
 
+// Symmetric eigenproblem A = W diag(w) W^T by cyclic Jacobi rotations (A row-major
+// n x n, destroyed; W row-major, eigenvectors in columns).
+void host_jacobi_eig(std::vector<double>& A, int n, std::vector<double>& w, std::vector<double>& W) {
+  W.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) W[(size_t)i * n + i] = 1.0;
+  double norm2 = 0.0;
+  for (double v : A) norm2 += v * v;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+    if (off <= 1e-34 * norm2) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double theta = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * akp - sn * akq;
+          A[(size_t)k * n + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = c * apk - sn * aqk;
+          A[(size_t)q * n + k] = sn * apk + c * aqk;
+        }
+        A[(size_t)p * n + q] = A[(size_t)q * n + p] = 0.0;
+        for (int k = 0; k < n; ++k) {
+          const double wkp = W[(size_t)k * n + p], wkq = W[(size_t)k * n + q];
+          W[(size_t)k * n + p] = c * wkp - sn * wkq;
+          W[(size_t)k * n + q] = sn * wkp + c * wkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+}
+
+// Fast-diagonalisation data of axis d: the interior blocks K_ii, M_ii of the
+// assembled 1-D stiffness and mass give K V = M V diag(lam) with V^T M V = I
+// (M = L L^T, C = L^-1 K L^-T = W diag(lam) W^T, V = L^-T W).
+int fd_axis(efe_handle* h, int d, int nn, const std::vector<double>& Kb, const std::vector<double>& Mb) {
+  const int m = nn - 2;
+  if (m < 1) return EFE_OK;
+  std::vector<double> K((size_t)m * m, 0.0), L((size_t)m * m, 0.0);
+  for (int a = 0; a < m; ++a)
+    for (int o = 0; o < 9; ++o) {
+      const int b = a + o - 4;
+      if (b < 0 || b >= m) continue;
+      K[(size_t)a * m + b] = Kb[(size_t)(a + 1) * 9 + o];
+      L[(size_t)a * m + b] = Mb[(size_t)(a + 1) * 9 + o];
+    }
+  if (host_cholesky_lower(L.data(), m) != 0) {
+    h->err = "1-D mass matrix not positive definite";
+    return EFE_ERR_CHOL;
+  }
+  for (int a = 0; a < m; ++a)
+    for (int b = a + 1; b < m; ++b) L[(size_t)a * m + b] = 0.0;
+  // Y = L^-1 K (columns by forward substitution), C = L^-1 Y^T  (= L^-1 K L^-T, K symmetric)
+  auto fwd = [&](std::vector<double>& X) {
+    for (int c = 0; c < m; ++c)
+      for (int a = 0; a < m; ++a) {
+        double v = X[(size_t)a * m + c];
+        for (int k = 0; k < a; ++k) v -= L[(size_t)a * m + k] * X[(size_t)k * m + c];
+        X[(size_t)a * m + c] = v / L[(size_t)a * m + a];
+      }
+  };
+  fwd(K);
+  std::vector<double> C((size_t)m * m);
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) C[(size_t)a * m + b] = K[(size_t)b * m + a];
+  fwd(C);
+  for (int a = 0; a < m; ++a)
+    for (int b = a + 1; b < m; ++b) {
+      const double v = 0.5 * (C[(size_t)a * m + b] + C[(size_t)b * m + a]);
+      C[(size_t)a * m + b] = C[(size_t)b * m + a] = v;
+    }
+  std::vector<double> lam, W;
+  host_jacobi_eig(C, m, lam, W);
+  // V = L^-T W (back substitution, column by column)
+  for (int c = 0; c < m; ++c)
+    for (int a = m - 1; a >= 0; --a) {
+      double v = W[(size_t)a * m + c];
+      for (int k = a + 1; k < m; ++k) v -= L[(size_t)k * m + a] * W[(size_t)k * m + c];
+      W[(size_t)a * m + c] = v / L[(size_t)a * m + a];
+    }
+  std::vector<double> Wt((size_t)m * m);
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) Wt[(size_t)b * m + a] = W[(size_t)a * m + b];
+  TRY(upload(h, &h->fdV[d], W));
+  TRY(upload(h, &h->fdVt[d], Wt));
+  TRY(upload(h, &h->fdlam[d], lam));
+  return EFE_OK;
+}
+
 // Quadrature leaves, enrichment-value offsets, the assembled 1-D operators of
 // the Hartree stiffness and the node coordinates (self-consistent field).
 int scf_setup_upload(efe_handle* h, const Setup& s) {
@@ -530,38 +626,14 @@ int scf_setup_upload(efe_handle* h, const Setup& s) {
     }
     TRY(upload(h, &h->band[d], K));
     TRY(upload(h, &h->band[3 + d], M));
+    TRY(fd_axis(h, d, nn, K, M));
     xyz.push_back(s.brk[d][0]);
     for (int c = 0; c < s.nc[d]; ++c) {
       const double lo = s.brk[d][c], hc = s.brk[d][c + 1] - s.brk[d][c];
       for (int a = 1; a < NP1; ++a) xyz.push_back(lo + 0.5 * (s.gll_z[a] + 1.0) * hc);
     }
-    // diagonal entries for the Jacobi preconditioner
   }
   TRY(upload(h, &h->node_xyz, xyz));
-  {
-    // diag A = (Kx_ii My_jj Mz_kk + Mx_ii Ky_jj Mz_kk + Mx_ii My_jj Kz_kk) / (4 pi)
-    std::vector<double> kd[3], md[3];
-    for (int d = 0; d < 3; ++d) {
-      kd[d].assign(s.nn[d], 0.0);
-      md[d].assign(s.nn[d], 0.0);
-      for (int c = 0; c < s.nc[d]; ++c) {
-        const double hc = s.brk[d][c + 1] - s.brk[d][c];
-        for (int a = 0; a < NP1; ++a) {
-          kd[d][P * c + a] += (2.0 / hc) * s.K1[a * NP1 + a];
-          md[d][P * c + a] += (hc / 2.0) * s.M1[a * NP1 + a];
-        }
-      }
-    }
-    std::vector<float> dv(s.n_nodes);
-    const double inv4pi = 1.0 / (4.0 * M_PI);
-    for (int64_t g = 0; g < s.n_nodes; ++g) {
-      const int i = (int)(g % s.nn[0]), j = (int)((g / s.nn[0]) % s.nn[1]), k = (int)(g / ((int64_t)s.nn[0] * s.nn[1]));
-      const double dg = inv4pi * (kd[0][i] * md[1][j] * md[2][k] + md[0][i] * kd[1][j] * md[2][k] +
-                                  md[0][i] * md[1][j] * kd[2][k]);
-      dv[g] = (s.Dinv[g] != 0.0) ? (float)(1.0 / dg) : 0.0f;
-    }
-    TRY(upload(h, &h->dinvA, dv));
-  }
   // nuclear repulsion E_ZZ
   h->e_zz = 0.0;
   const int na = (int)s.atom_Z.size();
@@ -607,43 +679,31 @@ EnrDev enr_dev(const efe_handle* h) {
 }
 
 // Hartree work buffers (allocated once)
-int hartree_alloc(efe_handle* h, int max_it) {
+int hartree_alloc(efe_handle* h) {
+  if (h->hb) return EFE_OK;
   const int64_t nn = h->n_nodes;
-  if (!h->hb) {
-    const int64_t nt = stiff_tiles(bands_dev(h));
-    TRY(dalloc(h, &h->hb, nn));
-    TRY(dalloc(h, &h->hr64, nn));
-    TRY(dalloc(h, &h->hphi, nn));
-    TRY(dalloc(h, &h->hlb, std::max<int64_t>(1, h->n_leaf) * NL));
-    TRY(dalloc(h, &h->hr32, nn));
-    TRY(dalloc(h, &h->hz32, nn));
-    TRY(dalloc(h, &h->hp0, nn));
-    TRY(dalloc(h, &h->hp1, nn));
-    TRY(dalloc(h, &h->hq, nn));
-    TRY(dalloc(h, &h->hd, nn));
-    TRY(dalloc(h, &h->hpart_rz0, nt));
-    TRY(dalloc(h, &h->hpart_rr, nt));
-    TRY(dalloc(h, &h->hpart_pq, nt));
-    TRY(dalloc(h, &h->hpart_rz, cg_reduce_blocks()));
-    TRY(dalloc(h, &h->hdone, 1));
-    TRY(dalloc(h, &h->red_part, 64 * (int64_t)cg_reduce_blocks()));
-    TRY(dalloc(h, &h->red_out, 64));
-    CK(cudaMemset(h->hphi, 0, sizeof(double) * nn));
-  }
-  if (max_it + 2 > h->hmax_it) {
-    if (h->hrz) dfree(h, h->hrz);
-    h->hmax_it = max_it + 2;
-    TRY(dalloc(h, &h->hrz, h->hmax_it));
-  }
+  const int64_t nt = stiff_tiles(bands_dev(h));
+  const int64_t nint = std::max<int64_t>(1, (int64_t)(h->mesh.nn[0] - 2) * (h->mesh.nn[1] - 2) * (h->mesh.nn[2] - 2));
+  TRY(dalloc(h, &h->hb, nn));
+  TRY(dalloc(h, &h->hr64, nn));
+  TRY(dalloc(h, &h->hphi, nn));
+  TRY(dalloc(h, &h->hlb, std::max<int64_t>(1, h->n_leaf) * NL));
+  TRY(dalloc(h, &h->hpart_rr, nt));
+  TRY(dalloc(h, &h->fdU0, nint));
+  TRY(dalloc(h, &h->fdU1, nint));
+  TRY(dalloc(h, &h->red_part, 64 * (int64_t)reduce_blocks()));
+  TRY(dalloc(h, &h->red_out, 64));
+  CK(cudaMemset(h->hphi, 0, sizeof(double) * nn));
   return EFE_OK;
 }
 
-// -lap phi / (4 pi) = rho with multipole Dirichlet data: FP64 defect
-// correction around a Jacobi-preconditioned FP32 CG (inner relative
-// reduction 1e-5 of the preconditioned residual norm).
-int hartree_solve(efe_handle* h, const double* rho, double* vh, double* phi, double tol, int max_it, int* iters,
+// -lap phi / (4 pi) = rho with multipole Dirichlet data: load vector, boundary
+// values, then defect correction phi += A_ii^-1 (b - A phi)_i with the exact
+// fast-diagonalisation solve (one correction reaches rounding level; a second
+// runs only if the FP64 residual is still above tol).
+int hartree_solve(efe_handle* h, const double* rho, double* vh, double* phi, double tol, int max_corr, int* iters,
                   double* relres, cudaStream_t st) {
-  TRY(hartree_alloc(h, max_it));
+  TRY(hartree_alloc(h));
   const int64_t nn = h->n_nodes;
   const LeafDev lf = leaf_dev(h);
   const BandsDev bd = bands_dev(h);
@@ -656,27 +716,13 @@ int hartree_solve(efe_handle* h, const double* rho, double* vh, double* phi, dou
   double bb = 0.0;
   CK(cudaMemcpyAsync(&bb, h->red_out + 8, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  CgDev cg;
-  cg.done = h->hdone;
-  cg.part_rz0 = h->hpart_rz0;
-  cg.part_rz = h->hpart_rz;
-  cg.part_pq = h->hpart_pq;
-  cg.rz_hist = h->hrz;
-  cg.tol2 = 1e-10;
-  cg.max_it = max_it;
-  cg.p[0] = h->hp0;
-  cg.p[1] = h->hp1;
-  cg.z = h->hz32;
-  cg.q = h->hq;
-  cg.r = h->hr32;
-  cg.d = h->hd;
-  cg.dinv = h->dinvA;
-  cg.mask = h->mask;
-  int total = 0;
-  double rr = 0.0, rr_prev = -1.0;
-  for (int outer = 0; outer < 40; ++outer) {
-    if (launch_stiff_resid(bd, phi, h->hb, h->mask, h->dinvA, h->hr64, h->hr32, h->hz32, h->hpart_rz0,
-                           h->hpart_rr, st)) {
+  const double* V[3] = {h->fdV[0], h->fdV[1], h->fdV[2]};
+  const double* Vt[3] = {h->fdVt[0], h->fdVt[1], h->fdVt[2]};
+  const double* lam[3] = {h->fdlam[0], h->fdlam[1], h->fdlam[2]};
+  int corr = 0;
+  double rr = 0.0;
+  for (;;) {
+    if (launch_stiff_resid(bd, phi, h->hb, h->mask, h->hr64, h->hpart_rr, st)) {
       h->err = "Hartree residual kernel: shared-memory configuration failed";
       return EFE_ERR_CUDA;
     }
@@ -688,28 +734,13 @@ int hartree_solve(efe_handle* h, const double* rho, double* vh, double* phi, dou
       h->err = "non-finite Hartree residual";
       return EFE_ERR_NAN;
     }
-    if (rr <= tol * tol * bb) break;
-    if (rr_prev >= 0.0 && rr > 0.25 * rr_prev) break;  // stagnation at the FP64 rounding floor
-    rr_prev = rr;
-    CK(cudaMemsetAsync(h->hd, 0, sizeof(float) * nn, st));
-    CK(cudaMemsetAsync(h->hdone, 0, sizeof(int), st));
-    int it = 0, done = 0;
-    while (!done && it <= max_it) {
-      for (int j = 0; j < 32 && it <= max_it; ++j, ++it)
-        if (launch_cg_iteration(bd, cg, it, nn, st)) {
-          h->err = "Hartree CG kernel: shared-memory configuration failed";
-          return EFE_ERR_CUDA;
-        }
-      CKL();
-      CK(cudaMemcpyAsync(&done, h->hdone, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-    }
-    total += done > 0 ? done - 1 : it;
-    launch_add_f32(nn, h->hd, phi, st);
+    if (rr <= tol * tol * bb || corr >= max_corr) break;
+    launch_fd_solve(bd, V, Vt, lam, h->hr64, h->fdU0, h->fdU1, phi, st);
     CKL();
+    ++corr;
   }
   if (relres) *relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-  if (iters) *iters = total;
+  if (iters) *iters = corr;
   launch_leaf_interp(lf, h->n_leaf, h->mesh, h->re, phi, vh, st);
   CKL();
   if (bb > 0.0 && rr > 1e6 * tol * tol * bb) {
@@ -991,11 +1022,18 @@ int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
     h->err = "non-finite potential value";
     return EFE_ERR_NAN;
   }
-  launch_hcc_build(h->re, h->mesh, h->qoff, h->qpts, h->V, h->n_cell, h->Hcc, st);
+  if (launch_hcc_sf(h->re, h->mesh, leaf_dev(h), h->leaf_ptr, h->V, h->n_cell, h->Hcc, st)) {
+    h->err = "cell-matrix kernel: shared-memory configuration failed";
+    return EFE_ERR_CUDA;
+  }
   CKL();
   if (h->nE > 0) {
-    launch_enr_blocks(h->re, h->mesh, h->enr_cells, h->n_enr, h->cf_ptr, h->cf_idx, h->funcs, h->qoff, h->qpts, h->V,
-                      h->blkP_off, h->blkQ_off, h->kmax, h->Pblk, h->Qblk, st);
+    TRY(ensure_eq(h, st));
+    if (launch_enr_sf(h->re, h->mesh, leaf_dev(h), h->leaf_ptr, enr_dev(h), h->enr_cells, h->n_enr, h->V,
+                      h->blkP_off, h->blkQ_off, h->Pblk, h->Qblk, st)) {
+      h->err = "enrichment-block kernel: shared-memory configuration failed";
+      return EFE_ERR_CUDA;
+    }
     CKL();
     launch_gather_sum(h->nnz, h->hec_kin, h->ec_cptr, h->ec_cidx, h->Pblk, h->hec, st);
     launch_permute(h->nnz, h->hec, h->t_perm, h->hecT, st);
@@ -1408,19 +1446,19 @@ int efe_xc_lda(efe_handle* h, const double* rho, double* exc, double* vxc, void*
   return EFE_OK;
 }
 
-int efe_hartree(efe_handle* h, const double* rho, double* vh, double* phi, double tol, int32_t max_iter,
-                int32_t* iters, void* stream) {
-  if (!h || !rho || !vh || !(tol > 0.0) || max_iter < 1) return EFE_ERR_ARG;
+int efe_hartree(efe_handle* h, const double* rho, double* vh, double* phi, double tol, int32_t max_steps,
+                int32_t* steps, void* stream) {
+  if (!h || !rho || !vh || !(tol > 0.0) || max_steps < 1) return EFE_ERR_ARG;
   TRY(set_dev(h));
   cudaStream_t st = S(stream);
-  TRY(hartree_alloc(h, max_iter));
+  TRY(hartree_alloc(h));
   if (!phi) {
     phi = h->hphi;
     CK(cudaMemsetAsync(phi, 0, sizeof(double) * h->n_nodes, st));
   }
   int it = 0;
-  const int rc = hartree_solve(h, rho, vh, phi, tol, max_iter, &it, nullptr, st);
-  if (iters) *iters = it;
+  const int rc = hartree_solve(h, rho, vh, phi, tol, max_steps, &it, nullptr, st);
+  if (steps) *steps = it;
   return rc;
 }
 
@@ -1433,7 +1471,7 @@ int efe_anderson(efe_handle* h, const double* rho_in_hist, const double* rho_out
                  double* rho_next, void* stream) {
   if (!h || !rho_in_hist || !rho_out_hist || !rho_next || n < 1 || n > ANDERSON_MAX) return EFE_ERR_ARG;
   TRY(set_dev(h));
-  TRY(hartree_alloc(h, 1));
+  TRY(hartree_alloc(h));
   HistDev hs;
   hs.n = n;
   for (int k = 0; k < n; ++k) {
@@ -1446,7 +1484,7 @@ int efe_anderson(efe_handle* h, const double* rho_in_hist, const double* rho_out
 int efe_scf_init(efe_handle* h, const efe_scf_params* p, void* stream) {
   if (!h || !p) return EFE_ERR_ARG;
   if (!(p->n_electrons > 0.0) || !(p->kT > 0.0) || !(p->mix_beta > 0.0) || p->mix_beta > 1.0 || p->n_hist < 1 ||
-      p->n_hist > ANDERSON_MAX || !(p->poisson_tol > 0.0) || p->poisson_max_iter < 1 || p->lanczos_k < 2) {
+      p->n_hist > ANDERSON_MAX || !(p->poisson_tol > 0.0) || p->poisson_max_steps < 1 || p->lanczos_k < 2) {
     h->err = "SCF parameters out of range";
     return EFE_ERR_ARG;
   }
@@ -1468,7 +1506,7 @@ int efe_scf_init(efe_handle* h, const efe_scf_params* p, void* stream) {
                             h->vext, st);
   CKL();
   TRY(ensure_eq(h, st));
-  TRY(hartree_alloc(h, p->poisson_max_iter));
+  TRY(hartree_alloc(h));
   h->scfp = *p;
   h->hist_count = 0;
   h->hist_head = 0;
@@ -1493,7 +1531,7 @@ int efe_scf_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, in
   std::memset(res, 0, sizeof(*res));
   // V_eff = V_ext + V_H[rho_in] + v_xc(rho_in)   (Eq. veff)
   int it1 = 0, it2 = 0;
-  TRY(hartree_solve(h, rho_in, h->vh_in, h->phi_in, p.poisson_tol, p.poisson_max_iter, &it1, nullptr, st));
+  TRY(hartree_solve(h, rho_in, h->vh_in, h->phi_in, p.poisson_tol, p.poisson_max_steps, &it1, nullptr, st));
   launch_veff(h->nq, rho_in, h->vext, h->vh_in, h->vxc_in, h->V, st);
   CKL();
   TRY(efe_set_potential(h, h->V, stream));
@@ -1526,7 +1564,7 @@ int efe_scf_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, in
   }
   CK(cudaMemcpyAsync(h->occ_dev, fv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
   TRY(efe_density(h, X, ldx, N, h->occ_dev, rho_out, stream));
-  TRY(hartree_solve(h, rho_out, h->vh_out, h->phi_out, p.poisson_tol, p.poisson_max_iter, &it2, nullptr, st));
+  TRY(hartree_solve(h, rho_out, h->vh_out, h->phi_out, p.poisson_tol, p.poisson_max_steps, &it2, nullptr, st));
   launch_scf_sums(h->qpts, h->nq, rho_in, rho_out, h->vh_in, h->vxc_in, h->vh_out, h->red_part, h->red_out + 16, st);
   CKL();
   double sums[5];
@@ -1544,7 +1582,7 @@ int efe_scf_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, in
   res->total = res->band - res->double_counting + res->hartree + res->xc + res->zz;
   res->fermi_level = mu;
   res->upper_bound = b;
-  res->poisson_iters = it1 + it2;
+  res->poisson_steps = it1 + it2;
   res->filter_passes = passes;
   if (eig) std::memcpy(eig, h->ritz.data(), sizeof(double) * N);
   if (occ) std::memcpy(occ, fv.data(), sizeof(double) * N);

@@ -23,29 +23,6 @@ namespace {
 
 inline unsigned grid1(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-__device__ __forceinline__ void lagrange_dev(const double* z, double xi, double* l) {
-#pragma unroll
-  for (int a = 0; a < NP1; ++a) {
-    double v = 1.0;
-#pragma unroll
-    for (int b = 0; b < NP1; ++b)
-      if (b != a) v *= (xi - z[b]) / (z[a] - z[b]);
-    l[a] = v;
-  }
-}
-
-__device__ __forceinline__ void cell_geom(const MeshDev& m, int64_t e, int* ijk, double* lo, double* h) {
-  ijk[0] = (int)(e % m.nc[0]);
-  ijk[1] = (int)((e / m.nc[0]) % m.nc[1]);
-  ijk[2] = (int)(e / ((int64_t)m.nc[0] * m.nc[1]));
-  const double* bx = m.brk;
-  const double* by = bx + m.nc[0] + 1;
-  const double* bz = by + m.nc[1] + 1;
-  lo[0] = bx[ijk[0]]; h[0] = bx[ijk[0] + 1] - lo[0];
-  lo[1] = by[ijk[1]]; h[1] = by[ijk[1] + 1] - lo[1];
-  lo[2] = bz[ijk[2]]; h[2] = bz[ijk[2] + 1] - lo[2];
-}
-
 // ---------------------------------------------------------------------------
 // set_potential
 // ---------------------------------------------------------------------------
@@ -73,155 +50,6 @@ __global__ void k_potential(const double* __restrict__ qpts, int64_t nq, const d
 __global__ void k_check_finite(const double* __restrict__ x, int64_t n, int* flag) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (!isfinite(x[i])) *flag = 1;
-}
-
-// H^cc_e = 1/2 int grad N_j . grad N_k (closed form on the axis-aligned cell)
-//        + sum_q w_q V_q N_j(x_q) N_k(x_q)           (Eq. Hcc)
-// One CTA per cell; the potential part is a 125 x nq x 125 product tiled in
-// 8 x 8 register blocks over a 128 x 128 padded output.
-__global__ void __launch_bounds__(256) k_hcc_build(RefElem re, MeshDev m, const int64_t* __restrict__ qoff,
-                                                   const double* __restrict__ qpts, const double* __restrict__ V,
-                                                   double* __restrict__ Hcc) {
-  const int64_t e = blockIdx.x;
-  int ijk[3];
-  double lo[3], h[3];
-  cell_geom(m, e, ijk, lo, h);
-  __shared__ double Bs[16][128];
-  __shared__ double Bw[16][128];
-  __shared__ double L[16][3][NP1];
-  const int tid = threadIdx.x;
-  const int ty = tid / 16, tx = tid % 16;
-  double acc[8][8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
-  const int64_t qb = qoff[e], qe = qoff[e + 1];
-  for (int64_t q0 = qb; q0 < qe; q0 += 16) {
-    const int np = (int)min((int64_t)16, qe - q0);
-    if (tid < 48) {
-      const int p = tid / 3, d = tid % 3;
-      if (p < np) {
-        const double xi = 2.0 * (qpts[4 * (q0 + p) + d] - lo[d]) / h[d] - 1.0;
-        lagrange_dev(re.z, xi, L[p][d]);
-      }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < 16 * 128; idx += 256) {
-      const int p = idx / 128, jl = idx % 128;
-      double b = 0.0, bw = 0.0;
-      if (p < np && jl < NL) {
-        b = L[p][0][jl % NP1] * L[p][1][(jl / NP1) % NP1] * L[p][2][jl / (NP1 * NP1)];
-        bw = b * qpts[4 * (q0 + p) + 3] * V[q0 + p];
-      }
-      Bs[p][jl] = b;
-      Bw[p][jl] = bw;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int p = 0; p < 16; ++p) {
-      double ar[8], bc[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) ar[i] = Bw[p][ty * 8 + i];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) bc[j] = Bs[p][tx * 8 + j];
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fma(ar[i], bc[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-  const double cx = h[1] * h[2] / (2.0 * h[0]), cy = h[0] * h[2] / (2.0 * h[1]), cz = h[0] * h[1] / (2.0 * h[2]);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int r = ty * 8 + i;
-    if (r >= NL) continue;
-    const int ra = r % NP1, rb = (r / NP1) % NP1, rc = r / (NP1 * NP1);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int c = tx * 8 + j;
-      if (c >= NL) continue;
-      const int ca = c % NP1, cb = (c / NP1) % NP1, cc = c / (NP1 * NP1);
-      const double kin =
-          0.5 * (cx * re.K1[ra * NP1 + ca] * re.M1[rb * NP1 + cb] * re.M1[rc * NP1 + cc] +
-                 cy * re.M1[ra * NP1 + ca] * re.K1[rb * NP1 + cb] * re.M1[rc * NP1 + cc] +
-                 cz * re.M1[ra * NP1 + ca] * re.M1[rb * NP1 + cb] * re.K1[rc * NP1 + cc]);
-      Hcc[e * (int64_t)(NL * NL) + r * NL + c] = kin + acc[i][j];
-    }
-  }
-}
-
-// Potential parts of the enrichment blocks on one enriched cell:
-//   P[a][j] = sum_q w V N_a N_j  (Eq. Hec),   Q[a][b] = sum_q w V N_a N_b  (Eq. Hee)
-__global__ void __launch_bounds__(128) k_enr_blocks(RefElem re, MeshDev m, const int32_t* __restrict__ enr_cells,
-                                                    const int32_t* __restrict__ cf_ptr,
-                                                    const int32_t* __restrict__ cf_idx,
-                                                    const DevFunc* __restrict__ funcs,
-                                                    const int64_t* __restrict__ qoff,
-                                                    const double* __restrict__ qpts, const double* __restrict__ V,
-                                                    const int64_t* __restrict__ blkP_off,
-                                                    const int64_t* __restrict__ blkQ_off, int kmax,
-                                                    double* __restrict__ Pblk, double* __restrict__ Qblk) {
-  extern __shared__ double sm[];
-  const int ei = blockIdx.x;
-  const int64_t e = enr_cells[ei];
-  const int k = cf_ptr[ei + 1] - cf_ptr[ei];
-  const int32_t* fl = cf_idx + cf_ptr[ei];
-  int ijk[3];
-  double lo[3], h[3];
-  cell_geom(m, e, ijk, lo, h);
-  constexpr int CH = 32;
-  double* Bsm = sm;                       // CH * NL
-  double* Esm = Bsm + CH * NL;            // CH * kmax
-  double* wV = Esm + CH * kmax;           // CH
-  double* Lsm = wV + CH;                  // CH * 3 * NP1
-  double* Pacc = Lsm + CH * 3 * NP1;      // kmax * NL
-  double* Qacc = Pacc + kmax * NL;        // kmax * kmax
-  const int tid = threadIdx.x;
-  for (int i = tid; i < k * NL; i += blockDim.x) Pacc[i] = 0.0;
-  for (int i = tid; i < k * k; i += blockDim.x) Qacc[i] = 0.0;
-  const int64_t qb = qoff[e], qe = qoff[e + 1];
-  for (int64_t q0 = qb; q0 < qe; q0 += CH) {
-    const int np = (int)min((int64_t)CH, qe - q0);
-    __syncthreads();
-    if (tid < CH * 3) {
-      const int p = tid / 3, d = tid % 3;
-      if (p < np) lagrange_dev(re.z, 2.0 * (qpts[4 * (q0 + p) + d] - lo[d]) / h[d] - 1.0, Lsm + (p * 3 + d) * NP1);
-    }
-    if (tid < CH) wV[tid] = (tid < np) ? qpts[4 * (q0 + tid) + 3] * V[q0 + tid] : 0.0;
-    for (int idx = tid; idx < CH * k; idx += blockDim.x) {
-      const int p = idx / k, a = idx % k;
-      double v = 0.0;
-      if (p < np) {
-        const double* x = qpts + 4 * (q0 + p);
-        v = eval_func_value(funcs[fl[a]], x[0], x[1], x[2]);
-      }
-      Esm[p * kmax + a] = v;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < CH * NL; idx += blockDim.x) {
-      const int p = idx / NL, jl = idx % NL;
-      const double* Lp = Lsm + p * 3 * NP1;
-      Bsm[idx] = (p < np) ? Lp[jl % NP1] * Lp[NP1 + (jl / NP1) % NP1] * Lp[2 * NP1 + jl / (NP1 * NP1)] : 0.0;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < k * NL; idx += blockDim.x) {
-      const int a = idx / NL, jl = idx % NL;
-      double s = 0.0;
-      for (int p = 0; p < np; ++p) s = fma(wV[p] * Esm[p * kmax + a], Bsm[p * NL + jl], s);
-      Pacc[idx] += s;
-    }
-    for (int idx = tid; idx < k * k; idx += blockDim.x) {
-      const int a = idx / k, b = idx % k;
-      double s = 0.0;
-      for (int p = 0; p < np; ++p) s = fma(wV[p] * Esm[p * kmax + a], Esm[p * kmax + b], s);
-      Qacc[idx] += s;
-    }
-  }
-  __syncthreads();
-  for (int i = tid; i < k * NL; i += blockDim.x) Pblk[blkP_off[ei] + i] = Pacc[i];
-  for (int i = tid; i < k * k; i += blockDim.x) Qblk[blkQ_off[ei] + i] = Qacc[i];
 }
 
 __global__ void k_gather_sum(int64_t n, const double* __restrict__ base, const int64_t* __restrict__ cptr,
@@ -613,9 +441,14 @@ constexpr int GT = 48;  // output tile (16 x 16 threads, 3 x 3 each)
 __global__ void __launch_bounds__(256) k_gemm_nn(int64_t M, int Nc, int K, double alpha,
                                                  const double* __restrict__ A, int64_t lda,
                                                  const double* __restrict__ B, int64_t ldb, double beta,
-                                                 double* __restrict__ C, int64_t ldc) {
+                                                 double* __restrict__ C, int64_t ldc, int64_t sA, int64_t sB,
+                                                 int64_t sC) {
   __shared__ double As[16][GT + 1];
   __shared__ double Bs[16][GT + 1];
+  // batch member blockIdx.z (strides 0 for a single product)
+  A += blockIdx.z * sA;
+  B += blockIdx.z * sB;
+  C += blockIdx.z * sC;
   const int64_t row0 = (int64_t)blockIdx.x * GT;
   const int col0 = blockIdx.y * GT;
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
@@ -980,25 +813,6 @@ void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st)
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-void launch_hcc_build(const RefElem& re, const MeshDev& m, const int64_t* qoff, const double* qpts,
-                      const double* V, int64_t n_cell, double* Hcc, cudaStream_t st) {
-  if (n_cell <= 0) return;
-  k_hcc_build<<<(unsigned)n_cell, 256, 0, st>>>(re, m, qoff, qpts, V, Hcc);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-}
-
-void launch_enr_blocks(const RefElem& re, const MeshDev& m, const int32_t* enr_cells, int64_t n_enr,
-                       const int32_t* cf_ptr, const int32_t* cf_idx, const DevFunc* funcs, const int64_t* qoff,
-                       const double* qpts, const double* V, const int64_t* blkP_off, const int64_t* blkQ_off,
-                       int kmax, double* Pblk, double* Qblk, cudaStream_t st) {
-  if (n_enr <= 0) return;
-  const size_t smem = sizeof(double) * (32 * NL + 32 * kmax + 32 + 32 * 3 * NP1 + kmax * NL + kmax * kmax);
-  cudaFuncSetAttribute(k_enr_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_enr_blocks<<<(unsigned)n_enr, 128, smem, st>>>(re, m, enr_cells, cf_ptr, cf_idx, funcs, qoff, qpts, V, blkP_off,
-                                                   blkQ_off, kmax, Pblk, Qblk);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-}
-
 void launch_gather_sum(int64_t n_out, const double* base, const int64_t* cptr, const int64_t* cidx,
                        const double* blk, double* out, cudaStream_t st) {
   if (n_out <= 0) return;
@@ -1137,7 +951,16 @@ void launch_gemm_nn(int64_t M, int Nc, int K, double alpha, const double* A, int
                     int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st) {
   if (M <= 0 || Nc <= 0) return;
   dim3 g((unsigned)((M + GT - 1) / GT), (unsigned)((Nc + GT - 1) / GT));
-  k_gemm_nn<<<g, 256, 0, st>>>(M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  k_gemm_nn<<<g, 256, 0, st>>>(M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, 0, 0);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_gemm_nn_batched(int64_t M, int Nc, int K, const double* A, int64_t lda, int64_t sA, const double* B,
+                            int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC, int batch,
+                            cudaStream_t st) {
+  if (M <= 0 || Nc <= 0 || batch <= 0) return;
+  dim3 g((unsigned)((M + GT - 1) / GT), (unsigned)((Nc + GT - 1) / GT), (unsigned)batch);
+  k_gemm_nn<<<g, 256, 0, st>>>(M, Nc, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, sA, sB, sC);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 

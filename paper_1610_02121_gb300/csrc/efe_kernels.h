@@ -30,12 +30,6 @@ void launch_potential_analytic(const double* qpts, int64_t nq, const double* axy
                                int nuclear, const double* gA, const double* gs, const double* gc, int nt,
                                double omega, double* V, cudaStream_t st);
 void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st);
-void launch_hcc_build(const RefElem& re, const MeshDev& m, const int64_t* qoff, const double* qpts,
-                      const double* V, int64_t n_cell, double* Hcc, cudaStream_t st);
-void launch_enr_blocks(const RefElem& re, const MeshDev& m, const int32_t* enr_cells, int64_t n_enr,
-                       const int32_t* cf_ptr, const int32_t* cf_idx, const DevFunc* funcs, const int64_t* qoff,
-                       const double* qpts, const double* V, const int64_t* blkP_off, const int64_t* blkQ_off,
-                       int kmax, double* Pblk, double* Qblk, cudaStream_t st);
 void launch_gather_sum(int64_t n_out, const double* base, const int64_t* cptr, const int64_t* cidx,
                        const double* blk, double* out, cudaStream_t st);
 void launch_permute(int64_t n, const double* src, const int64_t* perm, double* dst, cudaStream_t st);
@@ -119,6 +113,10 @@ int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int*
 // C[M x Nc] = alpha * A[M x K] B[K x Nc] + beta * C   (row-major, lda/ldb/ldc)
 void launch_gemm_nn(int64_t M, int Nc, int K, double alpha, const double* A, int64_t lda, const double* B,
                     int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st);
+// C_b = A_b B_b for b < batch (members at strides sA, sB, sC elements); grid.y = ceil(Nc / 48) <= 65535
+void launch_gemm_nn_batched(int64_t M, int Nc, int K, const double* A, int64_t lda, int64_t sA, const double* B,
+                            int64_t ldb, int64_t sB, double* C, int64_t ldc, int64_t sC, int batch,
+                            cudaStream_t st);
 // C[Na x Nb] = A^T B with A[K x Na], B[K x Nb], K large (split-K, deterministic reduce)
 // sym: the product is symmetric in exact arithmetic (A^T A, Q^T H Q, Q^T M Q): only
 // tiles on or above the diagonal are formed and the rest mirrored
@@ -167,20 +165,6 @@ struct BandsDev {         // assembled 1-D stiffness / exact mass, 9 entries per
   int nn[3];
 };
 
-struct CgDev {            // device state of the inner FP32 conjugate-gradient solve
-  int* done;              // 0 while running, else (last iteration + 1)
-  const double* part_rz0; // r.z partials of the residual kernel (one per tile)
-  double* part_rz;        // r.z partials of the update kernel
-  double* part_pq;        // p.q partials (one per tile)
-  double* rz_hist;        // r.z per iteration
-  double tol2;            // stop when r.z <= tol2 * (r.z)_0
-  int max_it;
-  float* p[2];
-  float *z, *q, *r, *d;
-  const float* dinv;      // inverse diagonal of A (0 on Dirichlet nodes)
-  const double* mask;     // 1 interior, 0 Dirichlet
-};
-
 struct HistDev {          // Anderson history, oldest first
   const double* rin[ANDERSON_MAX];
   const double* rout[ANDERSON_MAX];
@@ -202,12 +186,20 @@ void launch_hartree_load(const LeafDev& lf, int64_t n_leaf, const MeshDev& m, co
                          double* lb, double* b, cudaStream_t st);
 void launch_enr_values(const EnrDev& en, const int32_t* enr_cells, const int64_t* qoff, const double* qpts,
                        const DevFunc* funcs, int64_t n_enr, cudaStream_t st);
+// potential parts of H^cc_e (all cells) and of the enrichment blocks P, Q (enriched cells)
+int launch_hcc_sf(const RefElem& re, const MeshDev& m, const LeafDev& lf, const int64_t* leaf_ptr, const double* V,
+                  int64_t n_cell, double* Hcc, cudaStream_t st);
+int launch_enr_sf(const RefElem& re, const MeshDev& m, const LeafDev& lf, const int64_t* leaf_ptr, const EnrDev& en,
+                  const int32_t* enr_cells, int64_t n_enr, const double* V, const int64_t* blkP_off,
+                  const int64_t* blkQ_off, double* Pblk, double* Qblk, cudaStream_t st);
 int64_t stiff_tiles(const BandsDev& bd);
-int cg_reduce_blocks();
-int launch_stiff_resid(const BandsDev& bd, const double* phi, const double* b, const double* mask, const float* dinv,
-                       double* r64, float* r32, float* z32, double* part_rz, double* part_rr, cudaStream_t st);
-int launch_cg_iteration(const BandsDev& bd, const CgDev& cg, int it, int64_t n, cudaStream_t st);
-void launch_add_f32(int64_t n, const float* d, double* phi, cudaStream_t st);
+int reduce_blocks();
+// r = mask (b - A phi), partials of |r|^2 per tile
+int launch_stiff_resid(const BandsDev& bd, const double* phi, const double* b, const double* mask, double* r64,
+                       double* part_rr, cudaStream_t st);
+// phi_interior += A_ii^-1 r_interior by fast diagonalisation (U0, U1: interior-sized work arrays)
+void launch_fd_solve(const BandsDev& bd, const double* const* V, const double* const* Vt, const double* const* lam,
+                     const double* r, double* U0, double* U1, double* phi, cudaStream_t st);
 void launch_moments(const double* qpts, const double* rho, int64_t nq, double* part, double* mom, cudaStream_t st);
 void launch_finish(const double* part, int nb, int nv, double* out, cudaStream_t st);
 void launch_hartree_bc(const MeshDev& m, const double* node_xyz, const double* mask, const double* mom,

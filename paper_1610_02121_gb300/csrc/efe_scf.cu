@@ -4,13 +4,15 @@
 //     tensor Gauss boxes ("leaves") that make up every cell's rule;
 //   * the Hartree problem -lap V_H / (4 pi) = rho (Eq. Poisson) in the
 //     classical basis (Sec. III.A): load vector b_j = int rho N_j, Dirichlet
-//     data from the monopole + dipole of rho, and a Jacobi-preconditioned CG
-//     whose inner iterations run in FP32 inside an FP64 defect correction;
+//     data from the monopole + dipole of rho, the FP64 residual on the node
+//     grid, and an exact solve of the interior block by fast diagonalisation
+//     (the stiffness of a tensor-product mesh is a Kronecker sum of 1-D
+//     operators; the dense mode products run as FP64 GEMMs);
 //   * LDA exchange-correlation (Ceperley-Alder in the Perdew-Zunger 1981
 //     parametrisation), V_eff = V_ext + V_H + V_xc (Eq. veff);
 //   * energy integrals and n-stage Anderson mixing of rho.
 // All reductions use fixed-order block partials: results are bitwise
-// reproducible run to run.  FP64 is the arithmetic except inside the inner CG.
+// reproducible run to run.  FP64 throughout.
 #include <math.h>
 
 #include "efe_func.h"
@@ -408,13 +410,10 @@ __device__ __forceinline__ int64_t node_of(const BandsDev& bd, int i, int j, int
   return (int64_t)i + (int64_t)bd.nn[0] * ((int64_t)j + (int64_t)bd.nn[1] * k);
 }
 
-// FP64 residual of the defect correction: r = mask (b - A phi); r32 = (float) r,
-// z32 = Dinv r32; partials of r32 . z32 (the inner CG's first rz) and |r|^2.
+// FP64 residual r = mask (b - A phi) on the node grid and partials of |r|^2
 __global__ void __launch_bounds__(256) k_stiff_resid(BandsDev bd, const double* __restrict__ phi,
                                                      const double* __restrict__ b, const double* __restrict__ mask,
-                                                     const float* __restrict__ dinv, double* __restrict__ r64,
-                                                     float* __restrict__ r32, float* __restrict__ z32,
-                                                     double* __restrict__ part_rz, double* __restrict__ part_rr) {
+                                                     double* __restrict__ r64, double* __restrict__ part_rr) {
   extern __shared__ __align__(16) unsigned char smraw[];
   StiffSmem<double>& s = *reinterpret_cast<StiffSmem<double>*>(smraw);
   int i0, j0, k0;
@@ -429,7 +428,7 @@ __global__ void __launch_bounds__(256) k_stiff_resid(BandsDev bd, const double* 
   __syncthreads();
   double y[STILE / 256];
   stiff_tile<double>(bd, i0, j0, k0, s, y);
-  double rz = 0.0, rr = 0.0;
+  double rr = 0.0;
 #pragma unroll
   for (int r = 0; r < STILE / 256; ++r) {
     const int t = threadIdx.x + 256 * r;
@@ -437,105 +436,38 @@ __global__ void __launch_bounds__(256) k_stiff_resid(BandsDev bd, const double* 
     if (i < bd.nn[0] && j < bd.nn[1] && k < bd.nn[2]) {
       const int64_t g = node_of(bd, i, j, k);
       const double rv = mask[g] * (b[g] - y[r]);
-      const float rf = (float)rv;
-      const float zf = dinv[g] * rf;
       r64[g] = rv;
-      r32[g] = rf;
-      z32[g] = zf;
-      rz += (double)rf * (double)zf;
       rr += rv * rv;
     }
   }
-  rz = block_sum(rz, s.red);
   rr = block_sum(rr, s.red);
-  if (threadIdx.x == 0) {
-    part_rz[tile] = rz;
-    part_rr[tile] = rr;
-  }
+  if (threadIdx.x == 0) part_rr[tile] = rr;
 }
 
-// Inner CG, first half of iteration it:  rz_it from the previous partials;
-// stop (every block agrees) when rz_it <= tol2 rz_0 or it == max_it;
-// p_it = z + (rz_it / rz_{it-1}) p_{it-1};  q = mask A p_it;  partials of p . q.
-__global__ void __launch_bounds__(256) k_cg_a(BandsDev bd, CgDev cg, int it, int n_prev_part) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  StiffSmem<float>& s = *reinterpret_cast<StiffSmem<float>*>(smraw);
-  if (*cg.done) return;
-  const double rz = sum_partials(it == 0 ? cg.part_rz0 : cg.part_rz, n_prev_part, s.red);
-  const double rz0 = it == 0 ? rz : cg.rz_hist[0];
-  if (blockIdx.x == 0 && threadIdx.x == 0) cg.rz_hist[it] = rz;
-  if (!(rz > cg.tol2 * rz0) || it >= cg.max_it) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *cg.done = it + 1;
-    return;
-  }
-  const float beta = it == 0 ? 0.0f : (float)(rz / cg.rz_hist[it - 1]);
-  const float* pold = cg.p[(it + 1) & 1];
-  float* pnew = cg.p[it & 1];
-  int i0, j0, k0;
-  int64_t tile;
-  tile_origin(bd, &i0, &j0, &k0, &tile);
-  for (int t = threadIdx.x; t < HZW * HYW * HXW; t += blockDim.x) {
-    const int ii = t % HXW, jj = (t / HXW) % HYW, kk = t / (HXW * HYW);
-    const int gi = i0 - 4 + ii, gj = j0 - 4 + jj, gk = k0 - 4 + kk;
-    const bool ok = gi >= 0 && gj >= 0 && gk >= 0 && gi < bd.nn[0] && gj < bd.nn[1] && gk < bd.nn[2];
-    float v = 0.0f;
-    if (ok) {
-      const int64_t g = node_of(bd, gi, gj, gk);
-      v = it == 0 ? cg.z[g] : fmaf(beta, pold[g], cg.z[g]);
-    }
-    s.x[t] = v;
-  }
-  __syncthreads();
-  float pv[STILE / 256];
-#pragma unroll
-  for (int r = 0; r < STILE / 256; ++r) {
-    const int t = threadIdx.x + 256 * r;
-    const int i = t % TX, j = (t / TX) % TY, k = t / (TX * TY);
-    pv[r] = s.x[((k + 4) * HYW + j + 4) * HXW + i + 4];
-  }
-  float y[STILE / 256];
-  stiff_tile<float>(bd, i0, j0, k0, s, y);
-  double pq = 0.0;
-#pragma unroll
-  for (int r = 0; r < STILE / 256; ++r) {
-    const int t = threadIdx.x + 256 * r;
-    const int i = i0 + t % TX, j = j0 + (t / TX) % TY, k = k0 + t / (TX * TY);
-    if (i < bd.nn[0] && j < bd.nn[1] && k < bd.nn[2]) {
-      const int64_t g = node_of(bd, i, j, k);
-      const float q = (float)cg.mask[g] * y[r];
-      pnew[g] = pv[r];
-      cg.q[g] = q;
-      pq += (double)pv[r] * (double)q;
-    }
-  }
-  pq = block_sum(pq, s.red);
-  if (threadIdx.x == 0) cg.part_pq[tile] = pq;
+// interior nodes (1 .. nn_d - 2 on every axis) <-> compact array U[k][j][i]
+__global__ void k_fd_gather(BandsDev bd, const double* __restrict__ r, double* __restrict__ U) {
+  const int mi = bd.nn[0] - 2, mj = bd.nn[1] - 2, mk = bd.nn[2] - 2;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)mi * mj * mk) return;
+  const int i = (int)(t % mi), j = (int)((t / mi) % mj), k = (int)(t / ((int64_t)mi * mj));
+  U[t] = r[node_of(bd, i + 1, j + 1, k + 1)];
 }
 
-// Inner CG, second half: alpha = rz_it / (p . q); d += alpha p; r -= alpha q;
-// z = Dinv r; partials of r . z.
-__global__ void __launch_bounds__(256) k_cg_b(CgDev cg, int it, int n_tiles, int64_t n) {
-  __shared__ double red[256];
-  if (*cg.done) return;
-  const double pq = sum_partials(cg.part_pq, n_tiles, red);
-  const float alpha = (float)(cg.rz_hist[it] / pq);
-  const float* p = cg.p[it & 1];
-  double rz = 0.0;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-    cg.d[g] = fmaf(alpha, p[g], cg.d[g]);
-    const float r = fmaf(-alpha, cg.q[g], cg.r[g]);
-    const float z = cg.dinv[g] * r;
-    cg.r[g] = r;
-    cg.z[g] = z;
-    rz += (double)r * (double)z;
-  }
-  rz = block_sum(rz, red);
-  if (threadIdx.x == 0) cg.part_rz[blockIdx.x] = rz;
+__global__ void k_fd_scatter_add(BandsDev bd, const double* __restrict__ U, double* __restrict__ phi) {
+  const int mi = bd.nn[0] - 2, mj = bd.nn[1] - 2, mk = bd.nn[2] - 2;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)mi * mj * mk) return;
+  const int i = (int)(t % mi), j = (int)((t / mi) % mj), k = (int)(t / ((int64_t)mi * mj));
+  phi[node_of(bd, i + 1, j + 1, k + 1)] += U[t];
 }
 
-__global__ void k_add_f32(int64_t n, const float* __restrict__ d, double* __restrict__ phi) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g < n) phi[g] += (double)d[g];
+// U[k][j][i] *= 4 pi / (lx_i + ly_j + lz_k)   (inverse of the diagonalised operator)
+__global__ void k_fd_scale(int mi, int mj, int mk, const double* __restrict__ lx, const double* __restrict__ ly,
+                           const double* __restrict__ lz, double* __restrict__ U) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)mi * mj * mk) return;
+  const int i = (int)(t % mi), j = (int)((t / mi) % mj), k = (int)(t / ((int64_t)mi * mj));
+  U[t] *= 12.566370614359172954 / (lx[i] + ly[j] + lz[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -708,6 +640,183 @@ __global__ void k_scale_f64(int64_t n, double* __restrict__ x, const double* __r
   if (i < n) x[i] *= target / num[0];
 }
 
+
+// ---------------------------------------------------------------------------
+// Potential parts of the Hamiltonian blocks by sum factorisation over the
+// quadrature leaves (set_potential, Eqs. Hcc, Hec, Hee).
+//
+// H^cc_e[(a,b,c),(a',b',c')] = kinetic (closed form) +
+//   sum_q w V  Lx[a] Lx[a'] Ly[b] Ly[b'] Lz[c] Lz[c']
+// depends on the index pairs only through the symmetric products
+// Lx[a]Lx[a'] (15 pairs per axis): a 15 x 15 x 15 tensor per cell, formed
+// leaf by leaf in three passes (15 n^3 + 225 n^2 + 3375 n FMAs for an n^3
+// leaf, against 15625 n^3 for the dense B^T diag(wV) B), then expanded.
+__constant__ int c_pa[15] = {0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 2, 2, 3, 3, 4};
+__constant__ int c_pb[15] = {0, 1, 2, 3, 4, 1, 2, 3, 4, 2, 3, 4, 3, 4, 4};
+
+__device__ __forceinline__ int pair_index(int a, int b) {
+  if (a > b) { const int t = a; a = b; b = t; }
+  return a * NP1 - a * (a - 1) / 2 + (b - a);
+}
+
+__global__ void __launch_bounds__(256) k_hcc_sf(RefElem re, MeshDev m, LeafDev lf, const int64_t* __restrict__ leaf_ptr,
+                                                const double* __restrict__ V, double* __restrict__ Hcc) {
+  extern __shared__ __align__(16) double sm[];
+  const int nm = lf.nmax;
+  double* S = sm;                          // 15^3
+  double* L = S + 3375;                    // 3 x nm x 5
+  double* Pp = L + 3 * nm * NP1;           // 3 x nm x 15
+  double* u = Pp + 3 * nm * 15;            // nm^3
+  double* T1 = u + nm * nm * nm;           // 15 x nm^2
+  double* T2 = T1 + 15 * nm * nm;          // 225 x nm
+  const int64_t e = blockIdx.x;
+  int ijk[3];
+  double lo[3], h[3];
+  cell_box(m, e, ijk, lo, h);
+  for (int t = threadIdx.x; t < 3375; t += blockDim.x) S[t] = 0.0;
+  for (int64_t l = leaf_ptr[e]; l < leaf_ptr[e + 1]; ++l) {
+    const int n = lf.n[l];
+    const int64_t off = lf.off[l];
+    const int np = n * n * n;
+    __syncthreads();
+    leaf_lagrange(re, lf.qpts, off, n, nm, lo, h, L);
+    for (int p = threadIdx.x; p < np; p += blockDim.x) u[p] = lf.qpts[4 * (off + p) + 3] * V[off + p];
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * n * 15; t += blockDim.x) {
+      const int d = t / (n * 15), i = (t / 15) % n, al = t % 15;
+      const double* Li = L + (d * nm + i) * NP1;
+      Pp[(d * nm + i) * 15 + al] = Li[c_pa[al]] * Li[c_pb[al]];
+    }
+    __syncthreads();
+    // T1[al][iy][iz] = sum_ix Px[ix][al] u[ix][iy][iz]
+    for (int t = threadIdx.x; t < 15 * n * n; t += blockDim.x) {
+      const int al = t / (n * n), r = t % (n * n), iy = r / n, iz = r % n;
+      const double* ur = u + n * (iy + n * iz);
+      double sacc = 0.0;
+      for (int ix = 0; ix < n; ++ix) sacc = fma(Pp[ix * 15 + al], ur[ix], sacc);
+      T1[t] = sacc;
+    }
+    __syncthreads();
+    // T2[al][be][iz] = sum_iy Py[iy][be] T1[al][iy][iz]
+    for (int t = threadIdx.x; t < 225 * n; t += blockDim.x) {
+      const int ab = t / n, iz = t % n, al = ab / 15, be = ab % 15;
+      double sacc = 0.0;
+      for (int iy = 0; iy < n; ++iy) sacc = fma(Pp[(nm + iy) * 15 + be], T1[al * n * n + iy * n + iz], sacc);
+      T2[ab * nm + iz] = sacc;
+    }
+    __syncthreads();
+    // S[al][be][ga] += sum_iz Pz[iz][ga] T2[al][be][iz]
+    for (int t = threadIdx.x; t < 3375; t += blockDim.x) {
+      const int ab = t / 15, ga = t % 15;
+      double sacc = 0.0;
+      for (int iz = 0; iz < n; ++iz) sacc = fma(Pp[(2 * nm + iz) * 15 + ga], T2[ab * nm + iz], sacc);
+      S[t] += sacc;
+    }
+  }
+  __syncthreads();
+  const double cx = h[1] * h[2] / (2.0 * h[0]), cy = h[0] * h[2] / (2.0 * h[1]), cz = h[0] * h[1] / (2.0 * h[2]);
+  double* He = Hcc + e * (int64_t)(NL * NL);
+  for (int idx = threadIdx.x; idx < NL * NL; idx += blockDim.x) {
+    const int r = idx / NL, c = idx % NL;
+    const int ra = r % NP1, rb = (r / NP1) % NP1, rc = r / (NP1 * NP1);
+    const int ca = c % NP1, cb = (c / NP1) % NP1, cc = c / (NP1 * NP1);
+    const double kin =
+        0.5 * (cx * re.K1[ra * NP1 + ca] * re.M1[rb * NP1 + cb] * re.M1[rc * NP1 + cc] +
+               cy * re.M1[ra * NP1 + ca] * re.K1[rb * NP1 + cb] * re.M1[rc * NP1 + cc] +
+               cz * re.M1[ra * NP1 + ca] * re.M1[rb * NP1 + cb] * re.K1[rc * NP1 + cc]);
+    He[idx] = kin + S[(pair_index(ra, ca) * 15 + pair_index(rb, cb)) * 15 + pair_index(rc, cc)];
+  }
+}
+
+// Potential blocks of one enriched cell (Eqs. Hec, Hee):
+//   P[a][j] = sum_q w V E_a N_j   (per leaf and function: the load-vector passes)
+//   Q[a][b] = sum_q w V E_a E_b   (a <= b, mirrored)
+// accumulated in place in the cell's own output blocks (thread-owned entries).
+constexpr int ENR_G = 8;   // functions per pass
+
+__global__ void __launch_bounds__(256) k_enr_sf(RefElem re, MeshDev m, LeafDev lf, const int64_t* __restrict__ leaf_ptr,
+                                                EnrDev en, const int32_t* __restrict__ enr_cells,
+                                                const double* __restrict__ V, const int64_t* __restrict__ blkP_off,
+                                                const int64_t* __restrict__ blkQ_off, double* __restrict__ Pblk,
+                                                double* __restrict__ Qblk) {
+  extern __shared__ __align__(16) double sm[];
+  const int nm = lf.nmax;
+  double* L = sm;                                  // 3 x nm x 5
+  double* wv = L + 3 * nm * NP1;                   // nm^3
+  double* U = wv + nm * nm * nm;                   // G x nm^3
+  double* S2 = U + ENR_G * nm * nm * nm;           // G x nm^2 x 5
+  double* S1 = S2 + ENR_G * nm * nm * 5;           // G x nm x 25
+  const int ei = blockIdx.x;
+  const int64_t e = enr_cells[ei];
+  const int k = en.cf_ptr[ei + 1] - en.cf_ptr[ei];
+  const double* E = en.Eq + en.eq_off[ei];         // [point of the cell][function]
+  double* P = Pblk + blkP_off[ei];
+  double* Q = Qblk + blkQ_off[ei];
+  int ijk[3];
+  double lo[3], h[3];
+  cell_box(m, e, ijk, lo, h);
+  for (int t = threadIdx.x; t < k * NL; t += blockDim.x) P[t] = 0.0;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) Q[t] = 0.0;
+  const int64_t q0 = en.qoff[e];
+  for (int64_t l = leaf_ptr[e]; l < leaf_ptr[e + 1]; ++l) {
+    const int n = lf.n[l];
+    const int64_t off = lf.off[l];
+    const int64_t p0 = off - q0;
+    const int np = n * n * n;
+    __syncthreads();
+    leaf_lagrange(re, lf.qpts, off, n, nm, lo, h, L);
+    for (int p = threadIdx.x; p < np; p += blockDim.x) wv[p] = lf.qpts[4 * (off + p) + 3] * V[off + p];
+    __syncthreads();
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+      const int a = t / k, b = t % k;
+      if (a > b) continue;
+      const double* Ep = E + p0 * k;
+      double sacc = 0.0;
+      for (int p = 0; p < np; ++p) sacc = fma(wv[p] * Ep[(int64_t)p * k + a], Ep[(int64_t)p * k + b], sacc);
+      Q[t] += sacc;
+    }
+    for (int a0 = 0; a0 < k; a0 += ENR_G) {
+      const int g = min(ENR_G, k - a0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < g * np; t += blockDim.x) {
+        const int gi = t / np, p = t % np;
+        U[gi * np + p] = wv[p] * E[(p0 + p) * k + a0 + gi];
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < g * n * n * 5; t += blockDim.x) {
+        const int gi = t / (n * n * 5), r = t % (n * n * 5);
+        const int c = r % 5, iy = (r / 5) % n, ix = r / (5 * n);
+        const double* ug = U + gi * np;
+        double sacc = 0.0;
+        for (int iz = 0; iz < n; ++iz) sacc = fma(L[(2 * nm + iz) * NP1 + c], ug[ix + n * (iy + n * iz)], sacc);
+        S2[gi * nm * nm * 5 + r] = sacc;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < g * n * 25; t += blockDim.x) {
+        const int gi = t / (n * 25), r = t % (n * 25);
+        const int c = r % 5, b = (r / 5) % 5, ix = r / 25;
+        double sacc = 0.0;
+        for (int iy = 0; iy < n; ++iy)
+          sacc = fma(L[(nm + iy) * NP1 + b], S2[gi * nm * nm * 5 + (ix * n + iy) * 5 + c], sacc);
+        S1[gi * nm * 25 + r] = sacc;
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < g * NL; t += blockDim.x) {
+        const int gi = t / NL, jl = t % NL;
+        const int a = jl % NP1, b = (jl / NP1) % NP1, c = jl / (NP1 * NP1);
+        double sacc = 0.0;
+        for (int ix = 0; ix < n; ++ix) sacc = fma(L[ix * NP1 + a], S1[gi * nm * 25 + ix * 25 + b * 5 + c], sacc);
+        P[(a0 + gi) * NL + jl] += sacc;
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int a = t / k, b = t % k;
+    if (a > b) Q[t] = Q[b * k + a];
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -762,14 +871,46 @@ void launch_enr_values(const EnrDev& en, const int32_t* enr_cells, const int64_t
   g_launches++;
 }
 
+int launch_hcc_sf(const RefElem& re, const MeshDev& m, const LeafDev& lf, const int64_t* leaf_ptr, const double* V,
+                  int64_t n_cell, double* Hcc, cudaStream_t st) {
+  if (n_cell <= 0) return 0;
+  const int nm = lf.nmax;
+  const size_t sm = sizeof(double) * (3375 + 3 * nm * NP1 + 3 * nm * 15 + nm * nm * nm + 15 * nm * nm + 225 * nm);
+  static size_t set = 0;
+  if (sm > set) {
+    if (cudaFuncSetAttribute(k_hcc_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 1;
+    set = sm;
+  }
+  k_hcc_sf<<<(unsigned)n_cell, 256, sm, st>>>(re, m, lf, leaf_ptr, V, Hcc);
+  g_launches++;
+  return 0;
+}
+
+int launch_enr_sf(const RefElem& re, const MeshDev& m, const LeafDev& lf, const int64_t* leaf_ptr, const EnrDev& en,
+                  const int32_t* enr_cells, int64_t n_enr, const double* V, const int64_t* blkP_off,
+                  const int64_t* blkQ_off, double* Pblk, double* Qblk, cudaStream_t st) {
+  if (n_enr <= 0) return 0;
+  const int nm = lf.nmax;
+  const size_t sm = sizeof(double) * (3 * nm * NP1 + nm * nm * nm + ENR_G * nm * nm * nm + ENR_G * nm * nm * 5 +
+                                      ENR_G * nm * 25);
+  static size_t set = 0;
+  if (sm > set) {
+    if (cudaFuncSetAttribute(k_enr_sf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 1;
+    set = sm;
+  }
+  k_enr_sf<<<(unsigned)n_enr, 256, sm, st>>>(re, m, lf, leaf_ptr, en, enr_cells, V, blkP_off, blkQ_off, Pblk, Qblk);
+  g_launches++;
+  return 0;
+}
+
 int64_t stiff_tiles(const BandsDev& bd) {
   return (int64_t)((bd.nn[0] + TX - 1) / TX) * ((bd.nn[1] + TY - 1) / TY) * ((bd.nn[2] + TZ - 1) / TZ);
 }
 
-int cg_reduce_blocks() { return NB_RED; }
+int reduce_blocks() { return NB_RED; }
 
-int launch_stiff_resid(const BandsDev& bd, const double* phi, const double* b, const double* mask, const float* dinv,
-                       double* r64, float* r32, float* z32, double* part_rz, double* part_rr, cudaStream_t st) {
+int launch_stiff_resid(const BandsDev& bd, const double* phi, const double* b, const double* mask, double* r64,
+                       double* part_rr, cudaStream_t st) {
   const size_t sm = sizeof(StiffSmem<double>);
   static bool set = false;
   if (!set) {
@@ -777,28 +918,31 @@ int launch_stiff_resid(const BandsDev& bd, const double* phi, const double* b, c
       return 1;
     set = true;
   }
-  k_stiff_resid<<<(unsigned)stiff_tiles(bd), 256, sm, st>>>(bd, phi, b, mask, dinv, r64, r32, z32, part_rz, part_rr);
+  k_stiff_resid<<<(unsigned)stiff_tiles(bd), 256, sm, st>>>(bd, phi, b, mask, r64, part_rr);
   g_launches++;
   return 0;
 }
 
-int launch_cg_iteration(const BandsDev& bd, const CgDev& cg, int it, int64_t n, cudaStream_t st) {
-  const size_t sm = sizeof(StiffSmem<float>);
-  static bool set = false;
-  if (!set) {
-    if (cudaFuncSetAttribute(k_cg_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return 1;
-    set = true;
-  }
-  const int64_t nt = stiff_tiles(bd);
-  k_cg_a<<<(unsigned)nt, 256, sm, st>>>(bd, cg, it, it == 0 ? (int)nt : NB_RED);
-  k_cg_b<<<NB_RED, 256, 0, st>>>(cg, it, (int)nt, n);
-  g_launches += 2;
-  return 0;
-}
-
-void launch_add_f32(int64_t n, const float* d, double* phi, cudaStream_t st) {
-  k_add_f32<<<nblk(n, 256), 256, 0, st>>>(n, d, phi);
-  g_launches++;
+// interior solve A_ii d = r_i by fast diagonalisation; phi_i += d.
+// V[d] (m x m, row-major, V^T M V = I, V^T K V = diag(lam)), Vt[d] = V[d]^T.
+void launch_fd_solve(const BandsDev& bd, const double* const* V, const double* const* Vt, const double* const* lam,
+                     const double* r, double* U0, double* U1, double* phi, cudaStream_t st) {
+  const int mi = bd.nn[0] - 2, mj = bd.nn[1] - 2, mk = bd.nn[2] - 2;
+  const int64_t n = (int64_t)mi * mj * mk;
+  if (n <= 0) return;
+  const int64_t sl = (int64_t)mi * mj;
+  k_fd_gather<<<nblk(n, 256), 256, 0, st>>>(bd, r, U0);
+  // forward transform u = (Vx (x) Vy (x) Vz)^T r
+  launch_gemm_nn_batched((int64_t)mj * mk, mi, mi, U0, mi, 0, V[0], mi, 0, U1, mi, 0, 1, st);
+  launch_gemm_nn_batched(mj, mi, mj, Vt[1], mj, 0, U1, mi, sl, U0, mi, sl, mk, st);
+  launch_gemm_nn_batched(mk, (int)sl, mk, Vt[2], mk, 0, U0, sl, 0, U1, sl, 0, 1, st);
+  k_fd_scale<<<nblk(n, 256), 256, 0, st>>>(mi, mj, mk, lam[0], lam[1], lam[2], U1);
+  // back transform d = (Vx (x) Vy (x) Vz) u
+  launch_gemm_nn_batched(mk, (int)sl, mk, V[2], mk, 0, U1, sl, 0, U0, sl, 0, 1, st);
+  launch_gemm_nn_batched(mj, mi, mj, V[1], mj, 0, U0, mi, sl, U1, mi, sl, mk, st);
+  launch_gemm_nn_batched((int64_t)mj * mk, mi, mi, U1, mi, 0, Vt[0], mi, 0, U0, mi, 0, 1, st);
+  k_fd_scatter_add<<<nblk(n, 256), 256, 0, st>>>(bd, U0, phi);
+  g_launches += 4;
 }
 
 void launch_moments(const double* qpts, const double* rho, int64_t nq, double* part, double* mom, cudaStream_t st) {
