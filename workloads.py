@@ -281,3 +281,36 @@ def random_block(system, N, seed=5, scale=1.0):
 def lanczos_start(system, seed=9):
     """Seeded start vector for the spectral upper-bound Lanczos run."""
     return random_block(system, 1, seed=seed)[:, 0].copy()
+
+def sad_shells(Z):
+    """Occupied shells (n, zeta, electrons) of a neutral atom for the superposition-
+    of-atomic-densities start: 1s, 2s2p, 3s3p with Slater's-rules exponents
+    (published screening constants 0.30 / 0.35 / 0.85 / 1.0)."""
+    Z = int(Z)
+    out = [(1, Z - 0.30 if Z > 1 else 1.0, float(min(Z, 2)))]
+    if Z > 2:
+        n2 = min(Z - 2, 8)
+        out.append((2, (Z - (2 * 0.85 + (n2 - 1) * 0.35)) / 2.0, float(n2)))
+    if Z > 10:
+        n3 = min(Z - 10, 8)
+        out.append((3, (Z - (2 * 1.0 + 8 * 0.85 + (n3 - 1) * 0.35)) / 3.0, float(n3)))
+    return out
+
+
+def random_cluster(n_atoms, species, seed, min_dist=3.0, density=0.012, h_min=1.0, h_max=3.5, pad=8.0,
+                   r_c=4.0, tau=1e-8, max_depth=7):
+    """Random non-overlapping cluster: Z drawn from `species`, positions uniform in a
+    cube sized for about `density` atoms per bohr^3 with rejection to >= min_dist
+    bohr spacing; graded degree-4 mesh, Slater 1s/2s/2p enrichment, no extra potential."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    side = (n_atoms / density) ** (1.0 / 3.0)
+    pos = []
+    while len(pos) < n_atoms:
+        c = rng.uniform(0.0, side, size=3)
+        if all(np.linalg.norm(c - q) >= min_dist for q in pos):
+            pos.append(c)
+    atoms = np.round(np.array(pos), 3)
+    Z = rng.choice(np.asarray(species, dtype=np.float64), size=n_atoms)
+    sysd = _cluster_system(atoms, Z, h_min, h_max, pad, r_c, seed + 1000, seed + 2000, 0, tau, max_depth,
+                           name=f"cluster{n_atoms}_s{seed}")
+    return sysd
