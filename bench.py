@@ -63,6 +63,13 @@ def workload(name):
     return W.hydrogen(), 8, 20
 
 
+WORKLOAD_TEXT = {
+    "si16": "16-atom Si-like cluster (Z=14, diamond a=10.26), graded degree-4 mesh",
+    "si16s": "16-atom Si-like cluster (Z=14, diamond a=10.26), coarser graded degree-4 mesh (h 1.6-4.0 bohr)",
+    "hydrogen": "hydrogen Z=1, 6x6x6 cells",
+}
+
+
 def filter_flops(n_cell, nnz, nE, N, m):
     """Algorithmic flops of m filter degrees: cell products 2*125^2*N per cell,
     four sparse enrichment products 2*nnz*N, H^ee and S^-1 products 2*nE^2*N each."""
@@ -283,9 +290,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": prec if prec != "fp64" else "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: " + ("16-atom Si-like cluster (Z=14, diamond a=10.26), "
-                                                           "graded degree-4 mesh" if args.workload == "si16"
-                                                           else "hydrogen Z=1, 6x6x6 cells"),
+            "config": {"workload": f"{args.workload}: " + WORKLOAD_TEXT[args.workload],
                        "nodes": G.n_nodes, "cells": G.n_cells, "n_enrich": G.n_enrich, "n_coupling": G.n_coupling, "N": N, "m": m,
                        "fp64_tail": args.fp64_tail if prec != "fp64" else 0,
                        "fp64_engine": args.fp64_engine if prec != "fp64" else "dfma",

@@ -272,9 +272,11 @@ typedef struct {
 
 /* rho(x_q) = 2 sum_i occ_i psi_i(x_q)^2 (Eq. Rho) at every quadrature point,
  * psi_i the FE function with coefficients X[:, i] (X layout, N columns).
- * occ: N FP64 device values.  rho: Q layout, written. */
+ * occ: N FP64 device values.  rho: Q layout, written.  precision:
+ * EFE_PREC_FP64, or EFE_PREC_FP32 (orbital values in FP32 arithmetic, the
+ * squares and their sums in FP64; efe_scf_step uses it in the mixed modes). */
 int efe_density(efe_handle* h, const double* X, int64_t ldx, int32_t N, const double* occ, double* rho,
-                void* stream);
+                int32_t precision, void* stream);
 
 /* LDA energy per electron eps_xc(rho) and potential v_xc = d(rho eps_xc)/d rho
  * at every point (Q layout); exc or vxc may be NULL.  rho is clamped below at
@@ -313,7 +315,8 @@ int efe_scf_init(efe_handle* h, const efe_scf_params* params, void* stream);
  * V_eff(rho_in) -> efe_set_potential -> Lanczos bound b -> `passes` x
  * (degree-m filter + Rayleigh-Ritz; multiple passes re-orthonormalise between
  * them, Sec. VI.B.2) -> occupations -> rho_out -> V_H[rho_out] -> energies ->
- * Anderson.  rho_in (Q layout) is read and then overwritten with the next
+ * Anderson.  In the mixed precisions the density's orbital values are FP32
+ * (efe_density).  rho_in (Q layout) is read and then overwritten with the next
  * mixed input density; rho_out (Q layout) is written.  eig, occ: N host
  * values written (may be NULL); res: the energies.  The first step after
  * efe_scf_init runs a Rayleigh-Ritz step on X first to obtain the filter
@@ -321,6 +324,84 @@ int efe_scf_init(efe_handle* h, const efe_scf_params* params, void* stream);
 int efe_scf_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, int32_t passes, int32_t precision,
                  int32_t fp64_tail, double* rho_in, double* rho_out, double* eig, double* occ, efe_scf_result* res,
                  void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned initial density (not in the paper; the SCF of Sec. V needs a
+ * starting rho_in).  Plain start: superposition of atomic densities (SAD)
+ * from normalised Slater shells.  Learned start: rho = (rho_sad + floor)
+ * exp(y) - floor (clipped at 0, rescaled to N_e) with y the output of a fully
+ * connected network on atom-centred descriptors at each quadrature point.
+ * Training and inference run on the device through the calls below.
+ * precision arguments: EFE_PREC_FP32 (training / inference) or EFE_PREC_FP64
+ * (checks); arrays are then float or double.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t n_shells;          /* 1 .. 3 */
+  int32_t n[3];              /* principal quantum numbers (radial r^(n-1) exp(-zeta r)) */
+  double zeta[3];
+  double occ[3];             /* electrons per shell */
+} efe_atom_shells;
+
+/* rho_sad at the points (Q layout), one efe_atom_shells per atom (host array,
+ * n_atoms entries, atom order of efe_create); scaled to n_electrons
+ * electrons on the quadrature if n_electrons > 0. */
+int efe_sad_density(efe_handle* h, const efe_atom_shells* shells, double n_electrons, double* rho, void* stream);
+
+typedef struct {
+  int32_t n_species;         /* species slots, 1 .. 4 */
+  double species_Z[4];       /* an atom with charge species_Z[s] uses slot s */
+  int32_t n_radial;          /* radial centres, 1 .. 16 */
+  double radial_mu[16];
+  double radial_sigma;
+  int32_t n_ang;             /* angular bands, 0 .. 8 */
+  double ang_mu[8];
+  double ang_sigma;
+  double r_cut;              /* smooth cutoff (1 + cos(pi r / r_cut)) / 2 */
+  int32_t standardise;       /* 1: feature f is written as (f - offset[f]) * scale[f] */
+  double offset[96];
+  double scale[96];
+} efe_desc_params;
+
+/* Descriptors at every point: D (n_qpoints x F row-major, F = n_species *
+ * (n_radial + n_ang)) with, per species slot s, the radial features
+ * sum_I exp(-(r_I - mu_k)^2 / (2 sigma^2)) fc(r_I) and the angular features
+ * |sum_I exp(-(r_I - mu_k)^2 / (2 sigma_a^2)) fc(r_I) (x - R_I) / r_I|^2. */
+int efe_descriptors(efe_handle* h, const efe_desc_params* p, void* D, int32_t precision, void* stream);
+
+/* rho = max((rho_sad + floor) exp(y) - floor, 0), rescaled to n_electrons
+ * (Q layout; y float or double per precision). */
+int efe_learned_density(efe_handle* h, const double* rho_sad, const void* y, double floor, double n_electrons,
+                        double* rho, int32_t precision, void* stream);
+
+/* Regression target y = log(rho + floor) - log(rho_sad + floor) at the points. */
+int efe_density_log_ratio(efe_handle* h, const double* rho, const double* rho_sad, double floor, void* y,
+                          int32_t precision, void* stream);
+
+/* Fully connected network: n_layers linear layers dims[0] -> ... -> dims[n_layers]
+ * (dims[n_layers] = 1), SiLU after every layer but the last.  Parameters are
+ * one flat array: for each layer W (dims[l+1] x dims[l], row-major) then b. */
+typedef struct {
+  int32_t n_layers;          /* 1 .. 8 */
+  int32_t dims[9];
+} efe_mlp_shape;
+
+int64_t efe_mlp_param_count(const efe_mlp_shape* s);
+/* elements of the forward work array (pre-activations and activations) for n rows */
+int64_t efe_mlp_work_elems(const efe_mlp_shape* s, int64_t n);
+/* elements of the backward scratch array for n rows */
+int64_t efe_mlp_scratch_elems(const efe_mlp_shape* s, int64_t n);
+/* y (n) = net(X (n x dims[0])); work keeps what the backward pass needs */
+int efe_mlp_forward(const efe_mlp_shape* s, const void* params, const void* X, int64_t n, void* y, void* work,
+                    int32_t precision, void* stream);
+/* grads = d(sum_i dy_i y_i)/d params for the X, work of the last forward call */
+int efe_mlp_backward(const efe_mlp_shape* s, const void* params, const void* X, int64_t n, const void* work,
+                     const void* dy, void* grads, void* scratch, int32_t precision, void* stream);
+/* loss = sum c (yh - y)^2 / sum c (host), dy = d loss / d yh (device) */
+int efe_wmse(const void* yh, const void* y, const void* c, int64_t n, void* dy, double* loss, int32_t precision,
+             void* stream);
+/* one Adam step (Kingma & Ba) on n parameters with moments m, v; t counts from 1 */
+int efe_adam(void* p, const void* g, void* m, void* v, int64_t n, double lr, double beta1, double beta2, double eps,
+             int32_t t, int32_t precision, void* stream);
 
 #ifdef __cplusplus
 }

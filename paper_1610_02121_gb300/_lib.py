@@ -23,7 +23,10 @@ SYMBOLS = ["efe_create", "efe_destroy", "efe_last_error", "efe_sizes", "efe_qpoi
            "efe_set_potential_analytic", "efe_reserve", "efe_apply_H", "efe_apply_M", "efe_apply_Minv",
            "efe_upper_bound", "efe_chfsi_step", "efe_rayleigh_ritz", "efe_enable_timing", "efe_kernel_stats",
            "efe_launch_count", "efe_apply_M_noalloc", "efe_set_fp64_engine", "efe_density", "efe_xc_lda",
-           "efe_hartree", "efe_fermi", "efe_anderson", "efe_scf_init", "efe_scf_step"]
+           "efe_hartree", "efe_fermi", "efe_anderson", "efe_scf_init", "efe_scf_step", "efe_sad_density",
+           "efe_descriptors", "efe_learned_density", "efe_density_log_ratio", "efe_mlp_param_count",
+           "efe_mlp_work_elems", "efe_mlp_scratch_elems", "efe_mlp_forward", "efe_mlp_backward", "efe_wmse",
+           "efe_adam"]
 
 
 class EfeError(RuntimeError):
@@ -68,6 +71,21 @@ class ScfResult(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class AtomShells(C.Structure):
+    _fields_ = [("n_shells", C.c_int32), ("n", C.c_int32 * 3), ("zeta", C.c_double * 3), ("occ", C.c_double * 3)]
+
+
+class DescParams(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("species_Z", C.c_double * 4), ("n_radial", C.c_int32),
+                ("radial_mu", C.c_double * 16), ("radial_sigma", C.c_double), ("n_ang", C.c_int32),
+                ("ang_mu", C.c_double * 8), ("ang_sigma", C.c_double), ("r_cut", C.c_double),
+                ("standardise", C.c_int32), ("offset", C.c_double * 96), ("scale", C.c_double * 96)]
+
+
+class MlpShape(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("dims", C.c_int32 * 9)]
+
+
 KB_HA_PER_K = 3.166811563e-6   # Boltzmann constant (Ha/K)
 
 
@@ -99,18 +117,31 @@ def load(path=LIB_PATH):
         "efe_launch_count": [P64],
         "efe_apply_M_noalloc": [vp, vp, i64, i32, vp, i64, vp],
         "efe_set_fp64_engine": [vp, i32],
-        "efe_density": [vp, vp, i64, i32, vp, vp, vp],
+        "efe_density": [vp, vp, i64, i32, vp, vp, i32, vp],
         "efe_xc_lda": [vp, vp, vp, vp, vp],
         "efe_hartree": [vp, vp, vp, vp, dbl, i32, C.POINTER(C.c_int32), vp],
         "efe_fermi": [PD, i32, dbl, dbl, PD, PD],
         "efe_anderson": [vp, vp, vp, i32, dbl, vp, vp],
         "efe_scf_init": [vp, C.POINTER(ScfParams), vp],
         "efe_scf_step": [vp, vp, i64, i32, i32, i32, i32, i32, vp, vp, PD, PD, C.POINTER(ScfResult), vp],
+        "efe_sad_density": [vp, C.POINTER(AtomShells), dbl, vp, vp],
+        "efe_descriptors": [vp, C.POINTER(DescParams), vp, i32, vp],
+        "efe_learned_density": [vp, vp, vp, dbl, dbl, vp, i32, vp],
+        "efe_density_log_ratio": [vp, vp, vp, dbl, vp, i32, vp],
+        "efe_mlp_param_count": [C.POINTER(MlpShape)],
+        "efe_mlp_work_elems": [C.POINTER(MlpShape), i64],
+        "efe_mlp_scratch_elems": [C.POINTER(MlpShape), i64],
+        "efe_mlp_forward": [C.POINTER(MlpShape), vp, vp, i64, vp, vp, i32, vp],
+        "efe_mlp_backward": [C.POINTER(MlpShape), vp, vp, i64, vp, vp, vp, vp, i32, vp],
+        "efe_wmse": [vp, vp, vp, i64, vp, PD, i32, vp],
+        "efe_adam": [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, i32, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = C.c_char_p if name == "efe_last_error" else C.c_int
+        f.restype = (C.c_char_p if name == "efe_last_error" else
+                     C.c_int64 if name in ("efe_mlp_param_count", "efe_mlp_work_elems", "efe_mlp_scratch_elems")
+                     else C.c_int)
     return lib
 
 
@@ -312,14 +343,15 @@ class System:
         assert t.is_cuda and t.dtype == self._torch.float64 and t.is_contiguous() and t.numel() == self.n_qpoints
         return C.c_void_p(t.data_ptr())
 
-    def density(self, X, occ, rho=None):
-        """rho = 2 sum_i occ_i psi_i^2 at the quadrature points (Eq. Rho)."""
+    def density(self, X, occ, rho=None, precision="fp64"):
+        """rho = 2 sum_i occ_i psi_i^2 at the quadrature points (Eq. Rho); precision "fp64" or
+        "fp32" (orbital values in FP32, squares and sums in FP64)."""
         px, ldx, N = self._block(X)
         occ = self._torch.as_tensor(occ, dtype=self._torch.float64, device=X.device).contiguous()
         if rho is None:
             rho = self._torch.empty(self.n_qpoints, dtype=self._torch.float64, device=X.device)
         self._check(self.L.efe_density(self.h, px, ldx, N, C.c_void_p(occ.data_ptr()), self._qvec(rho),
-                                       self._stream()))
+                                       PREC[precision], self._stream()))
         return rho
 
     def xc_lda(self, rho):
@@ -368,6 +400,42 @@ class System:
         out["occ"] = occ
         return out
 
+    # -- learned initial density -------------------------------------------------
+    def sad_density(self, shells, n_electrons=0.0):
+        """Superposition of atomic densities; shells[I] = [(n, zeta, electrons), ...] per atom."""
+        arr = (AtomShells * max(1, len(shells)))()
+        for i, sh in enumerate(shells):
+            arr[i].n_shells = len(sh)
+            for k, (n, z, o) in enumerate(sh):
+                arr[i].n[k] = int(n)
+                arr[i].zeta[k] = float(z)
+                arr[i].occ[k] = float(o)
+        rho = self._torch.empty(self.n_qpoints, dtype=self._torch.float64, device="cuda")
+        self._check(self.L.efe_sad_density(self.h, arr, float(n_electrons), self._qvec(rho), self._stream()))
+        return rho
+
+    def descriptors(self, params, precision="fp32"):
+        dt = self._torch.float32 if precision == "fp32" else self._torch.float64
+        nf = params.n_species * (params.n_radial + params.n_ang)
+        D = self._torch.empty((self.n_qpoints, nf), dtype=dt, device="cuda")
+        self._check(self.L.efe_descriptors(self.h, C.byref(params), C.c_void_p(D.data_ptr()), PREC[precision],
+                                           self._stream()))
+        return D
+
+    def learned_density(self, rho_sad, y, floor, n_electrons):
+        prec = "fp32" if y.dtype == self._torch.float32 else "fp64"
+        rho = self._torch.empty_like(rho_sad)
+        self._check(self.L.efe_learned_density(self.h, self._qvec(rho_sad), C.c_void_p(y.data_ptr()), float(floor),
+                                               float(n_electrons), self._qvec(rho), PREC[prec], self._stream()))
+        return rho
+
+    def density_log_ratio(self, rho, rho_sad, floor, precision="fp32"):
+        dt = self._torch.float32 if precision == "fp32" else self._torch.float64
+        y = self._torch.empty(self.n_qpoints, dtype=dt, device="cuda")
+        self._check(self.L.efe_density_log_ratio(self.h, self._qvec(rho), self._qvec(rho_sad), float(floor),
+                                                 C.c_void_p(y.data_ptr()), PREC[precision], self._stream()))
+        return y
+
     def set_fp64_engine(self, engine):
         """0: FP64 DFMA products; 1 (or "tensor"): FP64-grade products on the BF16 tensor cores."""
         e = {"dfma": 0, "tensor": 1}.get(engine, engine)
@@ -382,3 +450,84 @@ class System:
         cc = C.c_int64()
         self._check(self.L.efe_kernel_stats(self.h, C.byref(n), C.byref(ms), C.byref(cc), int(bool(reset))))
         return n.value, ms.value, cc.value
+
+
+class Mlp:
+    """Fully connected network on the device (SiLU hidden layers, scalar output):
+    flat parameter tensor, forward / backward / Adam through the C ABI."""
+
+    def __init__(self, dims, precision="fp32", params=None, seed=0):
+        import torch
+        self._torch = torch
+        self.L = lib()
+        self.dims = list(dims)
+        self.shape = MlpShape(len(dims) - 1, (C.c_int32 * 9)(*(list(dims) + [0] * (9 - len(dims)))))
+        self.prec = precision
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.n_params = self.L.efe_mlp_param_count(C.byref(self.shape))
+        if self.n_params < 0:
+            raise EfeError(1, "invalid network shape")
+        if params is None:
+            rng = np.random.Generator(np.random.PCG64(seed))
+            parts = []
+            for a, b in zip(dims[:-1], dims[1:]):
+                lim = 1.0 / np.sqrt(a)
+                parts.append(rng.uniform(-lim, lim, size=a * b))
+                parts.append(np.zeros(b))
+            params = np.concatenate(parts)
+        self.params = torch.as_tensor(np.asarray(params), dtype=self.dtype).cuda().contiguous()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.t = 0
+        self._n = -1
+
+    def _bufs(self, n):
+        if n > self._n:
+            t = self._torch
+            self.work = t.empty(self.L.efe_mlp_work_elems(C.byref(self.shape), n), dtype=self.dtype, device="cuda")
+            self.scratch = t.empty(self.L.efe_mlp_scratch_elems(C.byref(self.shape), n), dtype=self.dtype,
+                                   device="cuda")
+            self._n = n
+
+    def _stream(self):
+        return C.c_void_p(self._torch.cuda.current_stream().cuda_stream)
+
+    def _chk(self, rc, what):
+        if rc != EFE_OK:
+            raise EfeError(rc, what)
+
+    def forward(self, X):
+        n = X.shape[0]
+        self._bufs(n)
+        y = self._torch.empty(n, dtype=self.dtype, device="cuda")
+        self._chk(self.L.efe_mlp_forward(C.byref(self.shape), C.c_void_p(self.params.data_ptr()),
+                                         C.c_void_p(X.data_ptr()), n, C.c_void_p(y.data_ptr()),
+                                         C.c_void_p(self.work.data_ptr()), PREC[self.prec], self._stream()),
+                  "efe_mlp_forward")
+        return y
+
+    def backward(self, X, dy):
+        """Gradients of sum dy * y for the X of the last forward call."""
+        n = X.shape[0]
+        g = self._torch.empty_like(self.params)
+        self._chk(self.L.efe_mlp_backward(C.byref(self.shape), C.c_void_p(self.params.data_ptr()),
+                                          C.c_void_p(X.data_ptr()), n, C.c_void_p(self.work.data_ptr()),
+                                          C.c_void_p(dy.data_ptr()), C.c_void_p(g.data_ptr()),
+                                          C.c_void_p(self.scratch.data_ptr()), PREC[self.prec], self._stream()),
+                  "efe_mlp_backward")
+        return g
+
+    def wmse(self, yh, y, c):
+        dy = self._torch.empty_like(yh)
+        loss = C.c_double()
+        self._chk(self.L.efe_wmse(C.c_void_p(yh.data_ptr()), C.c_void_p(y.data_ptr()), C.c_void_p(c.data_ptr()),
+                                  yh.numel(), C.c_void_p(dy.data_ptr()), C.byref(loss), PREC[self.prec],
+                                  self._stream()), "efe_wmse")
+        return loss.value, dy
+
+    def adam(self, g, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.t += 1
+        self._chk(self.L.efe_adam(C.c_void_p(self.params.data_ptr()), C.c_void_p(g.data_ptr()),
+                                  C.c_void_p(self.m.data_ptr()), C.c_void_p(self.v.data_ptr()), self.n_params,
+                                  float(lr), float(b1), float(b2), float(eps), self.t, PREC[self.prec],
+                                  self._stream()), "efe_adam")

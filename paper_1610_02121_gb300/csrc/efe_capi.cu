@@ -198,7 +198,7 @@ int reserve(efe_handle* h, int N) {
   TRY(dalloc(h, &h->xe, std::max<int64_t>(1, h->nE) * N));
   TRY(dalloc(h, &h->rb, std::max<int64_t>(1, h->nE) * N));
   TRY(dalloc(h, &h->part, std::max<int64_t>(1, h->nseg) * N));
-  TRY(dalloc(h, &h->small, 16 * (int64_t)N * N + 8 * (int64_t)N));
+  TRY(dalloc(h, &h->small, 24 * (int64_t)N * N + 8 * (int64_t)N));
   h->tnwork_elems = gemm_tn_work_elems(R, N, N);
   TRY(dalloc(h, &h->tnwork, h->tnwork_elems));
   TRY(dalloc(h, &h->rpart, ((R + 2047) / 2048 + 1) * (int64_t)N));
@@ -1282,6 +1282,55 @@ int gemm_tall(efe_handle* h, int64_t rows, int N, const double* A, int64_t lda, 
   return EFE_OK;
 }
 
+// Dense symmetric eigenproblem C = V diag(w) V^T of Rayleigh-Ritz (N x N, FP64).
+// FP64 rotations run at the FP64 rate of one SM, so C is first diagonalised in
+// FP32 (to a relative off-diagonal size ~1e-6); the FP32 vectors are made
+// orthonormal in FP64 (Q = V32 L^-T, L L^T = V32^T V32), C' = Q^T C Q is then
+// nearly diagonal and FP64 Jacobi finishes it in two or three sweeps
+// (quadratic convergence); V = Q V'.  Falls back to FP64 Jacobi from scratch
+// if the FP32 stage fails.  Scratch: 9 N x N blocks at E.
+int sym_eig(efe_handle* h, const double* C, int N, double* V, double* w, double* E, cudaStream_t st) {
+  const int64_t NN = (int64_t)N * N;
+  float* C32 = reinterpret_cast<float*>(E);
+  float* V32 = C32 + NN;
+  double* Q0 = E + NN;
+  double* G = Q0 + NN;
+  double* Li = G + NN;
+  double* LiT = Li + NN;
+  double* Q = LiT + NN;
+  double* T1 = Q + NN;
+  double* C2 = T1 + NN;
+  double* V2 = C2 + NN;
+  float* w32 = reinterpret_cast<float*>(V);  // scratch until V is written
+  CK(cudaMemsetAsync(h->info + 1, 0, 2 * sizeof(int), st));
+  launch_f64_to_f32_rows(N, C, N, C32, N, N, st);
+  launch_jacobi_f32(C32, N, N, V32, N, w32, 60, h->info + 2, st);
+  launch_f32_to_f64_rows(N, V32, N, Q0, N, N, st);
+  launch_gemm_tn(N, N, N, Q0, N, Q0, N, G, N, h->tnwork, h->tnwork_elems, st, true);
+  launch_symmetrize(G, N, N, st);
+  launch_chol(G, N, N, h->info + 2, st);
+  CKL();
+  int inf = 0;
+  CK(cudaMemcpyAsync(&inf, h->info + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (inf) {  // FP32 stage unusable: plain FP64 Jacobi
+    CK(cudaMemcpyAsync(C2, C, sizeof(double) * NN, cudaMemcpyDeviceToDevice, st));
+    launch_jacobi(C2, N, N, V, N, w, 60, h->info + 1, st);
+    CKL();
+    return EFE_OK;
+  }
+  launch_trinv_lower(G, N, N, Li, N, st);
+  launch_transpose(Li, N, N, LiT, N, st);
+  launch_gemm_nn(N, N, N, 1.0, Q0, N, LiT, N, 0.0, Q, N, st);
+  launch_gemm_tn(N, N, N, Q, N, C, N, T1, N, h->tnwork, h->tnwork_elems, st, false);
+  launch_gemm_nn(N, N, N, 1.0, T1, N, Q, N, 0.0, C2, N, st);
+  launch_symmetrize(C2, N, N, st);
+  launch_jacobi(C2, N, N, V2, N, w, 40, h->info + 1, st);
+  launch_gemm_nn(N, N, N, 1.0, Q, N, V2, N, 0.0, V, N, st);
+  CKL();
+  return EFE_OK;
+}
+
 int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* eig_host, double* resid_host,
                       void* stream) {
   if (!h || !eig_host) return EFE_ERR_ARG;
@@ -1311,6 +1360,7 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   double* wv = Psi + NN;
   double* eps = wv + N;
   double* res = eps + N;
+  double* E0 = res + N + 5 * (int64_t)N;   // eigensolver scratch: 9 blocks
   double *Q = h->B1, *HQ = h->B2, *MQ = h->W;
   int inf[2] = {0, 0};
   // Cholesky-QR: G = X^T X = L L^T, Q = X L^-T
@@ -1350,7 +1400,7 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   launch_gemm_nn(N, N, N, 1.0, Lminv, N, Hp, N, 0.0, T1, N, st);
   launch_gemm_nn(N, N, N, 1.0, T1, N, LminvT, N, 0.0, C, N, st);
   launch_symmetrize(C, N, N, st);
-  launch_jacobi(C, N, N, Vj, N, wv, 40, h->info + 1, st);
+  TRY(sym_eig(h, C, N, Vj, wv, E0, st));
   launch_sort_eig(wv, Vj, N, N, eps, Z, N, st);
   launch_gemm_nn(N, N, N, 1.0, LminvT, N, Z, N, 0.0, Psi, N, st);
   // rotation and residuals
@@ -1425,12 +1475,17 @@ int efe_kernel_stats(efe_handle* h, int64_t* launches, double* total_ms, int64_t
 // ---------------------------------------------------------------------------
 // self-consistent field
 int efe_density(efe_handle* h, const double* X, int64_t ldx, int32_t N, const double* occ, double* rho,
-                void* stream) {
+                int32_t precision, void* stream) {
   if (!h || !X || !occ || !rho || N < 1 || ldx < N) return EFE_ERR_ARG;
+  if (precision != EFE_PREC_FP64 && precision != EFE_PREC_FP32) {
+    h->err = "density precision must be EFE_PREC_FP64 or EFE_PREC_FP32";
+    return EFE_ERR_ARG;
+  }
   TRY(set_dev(h));
   cudaStream_t st = S(stream);
   TRY(ensure_eq(h, st));
-  if (launch_leaf_density(leaf_dev(h), h->n_leaf, h->mesh, h->re, enr_dev(h), h->kmax, X, ldx, N, occ, rho, st)) {
+  if (launch_leaf_density(leaf_dev(h), h->n_leaf, h->mesh, h->re, enr_dev(h), h->kmax, X, ldx, N, occ, rho,
+                          precision == EFE_PREC_FP32, st)) {
     h->err = "density kernel: shared-memory request too large (enrichment functions per cell)";
     return EFE_ERR_ARG;
   }
@@ -1563,7 +1618,8 @@ int efe_scf_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, in
     h->occ_cap = N;
   }
   CK(cudaMemcpyAsync(h->occ_dev, fv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
-  TRY(efe_density(h, X, ldx, N, h->occ_dev, rho_out, stream));
+  TRY(efe_density(h, X, ldx, N, h->occ_dev, rho_out, precision == EFE_PREC_FP64 ? EFE_PREC_FP64 : EFE_PREC_FP32,
+                  stream));
   TRY(hartree_solve(h, rho_out, h->vh_out, h->phi_out, p.poisson_tol, p.poisson_max_steps, &it2, nullptr, st));
   launch_scf_sums(h->qpts, h->nq, rho_in, rho_out, h->vh_in, h->vxc_in, h->vh_out, h->red_part, h->red_out + 16, st);
   CKL();
@@ -1671,3 +1727,232 @@ extern "C" int efe_apply_M_noalloc(efe_handle* h, const double* X, int64_t ldx, 
   CKL();
   return EFE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Learned initial density: SAD start, descriptors, network, loss, optimiser.
+// The loss reduction uses a file-scope device array (no handle needed).
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_learn_red[2 * 1024 + 8];
+
+namespace {
+std::mutex g_learn_mu;
+double* g_learn_ptr[256] = {nullptr};
+
+double* learn_red(int dev) {
+  if (dev < 0 || dev >= 256) return nullptr;
+  std::lock_guard<std::mutex> lk(g_learn_mu);
+  if (!g_learn_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_learn_red) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_learn_ptr[dev] = (double*)p;
+  }
+  return g_learn_ptr[dev];
+}
+
+bool valid_shape(const efe_mlp_shape* s) {
+  if (!s || s->n_layers < 1 || s->n_layers > 8) return false;
+  for (int l = 0; l <= s->n_layers; ++l)
+    if (s->dims[l] < 1 || s->dims[l] > 4096) return false;
+  return s->dims[s->n_layers] == 1;
+}
+
+bool valid_prec(int32_t p) { return p == EFE_PREC_FP32 || p == EFE_PREC_FP64; }
+}  // namespace
+
+extern "C" {
+
+int efe_sad_density(efe_handle* h, const efe_atom_shells* shells, double n_electrons, double* rho, void* stream) {
+  if (!h || !shells || !rho) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  std::vector<SadShellDev> sd(std::max(1, h->n_atoms));
+  for (int a = 0; a < h->n_atoms; ++a) {
+    const efe_atom_shells& s = shells[a];
+    if (s.n_shells < 1 || s.n_shells > 3) {
+      h->err = "efe_atom_shells.n_shells must be 1 .. 3";
+      return EFE_ERR_ARG;
+    }
+    sd[a].n_shells = s.n_shells;
+    for (int k = 0; k < s.n_shells; ++k) {
+      if (s.n[k] < 1 || s.n[k] > 7 || !(s.zeta[k] > 0.0) || !(s.occ[k] >= 0.0)) {
+        h->err = "bad Slater shell (n in 1..7, zeta > 0, occ >= 0)";
+        return EFE_ERR_ARG;
+      }
+      double fact = 1.0;
+      for (int i = 2; i <= 2 * s.n[k]; ++i) fact *= i;
+      sd[a].n[k] = s.n[k];
+      sd[a].zeta[k] = s.zeta[k];
+      sd[a].occ[k] = s.occ[k];
+      sd[a].c[k] = sqrt(pow(2.0 * s.zeta[k], 2 * s.n[k] + 1) / fact);
+    }
+  }
+  cudaStream_t st = S(stream);
+  SadShellDev* dsh = nullptr;
+  TRY(dalloc(h, &dsh, (int64_t)sd.size()));
+  CK(cudaMemcpyAsync(dsh, sd.data(), sizeof(SadShellDev) * sd.size(), cudaMemcpyHostToDevice, st));
+  launch_sad(h->qpts, h->nq, h->axyz, h->n_atoms, dsh, rho, st);
+  if (n_electrons > 0.0) {
+    double* red = learn_red(h->dev);
+    if (!red) {
+      h->err = "reduction scratch unavailable";
+      return EFE_ERR_CUDA;
+    }
+    launch_scale_count(h->qpts, h->nq, n_electrons, rho, red, st);
+  }
+  CKL();
+  CK(cudaStreamSynchronize(st));
+  dfree(h, dsh);
+  return EFE_OK;
+}
+
+int efe_descriptors(efe_handle* h, const efe_desc_params* p, void* D, int32_t precision, void* stream) {
+  if (!h || !p || !D || !valid_prec(precision)) return EFE_ERR_ARG;
+  if (p->n_species < 1 || p->n_species > DESC_MAX_SPECIES || p->n_radial < 1 || p->n_radial > DESC_MAX_RADIAL ||
+      p->n_ang < 0 || p->n_ang > DESC_MAX_ANG || !(p->radial_sigma > 0.0) || !(p->r_cut > 0.0) ||
+      (p->n_ang > 0 && !(p->ang_sigma > 0.0))) {
+    h->err = "descriptor parameters out of range";
+    return EFE_ERR_ARG;
+  }
+  TRY(set_dev(h));
+  DescDev dd;
+  dd.n_species = p->n_species;
+  dd.n_radial = p->n_radial;
+  dd.n_ang = p->n_ang;
+  for (int k = 0; k < DESC_MAX_RADIAL; ++k) dd.radial_mu[k] = k < p->n_radial ? p->radial_mu[k] : 0.0;
+  for (int k = 0; k < DESC_MAX_ANG; ++k) dd.ang_mu[k] = k < p->n_ang ? p->ang_mu[k] : 0.0;
+  dd.radial_sigma = p->radial_sigma;
+  dd.ang_sigma = p->ang_sigma;
+  dd.r_cut = p->r_cut;
+  dd.standardise = p->standardise ? 1 : 0;
+  const int nfeat = p->n_species * (p->n_radial + p->n_ang);
+  for (int f = 0; f < DESC_MAX_SPECIES * (DESC_MAX_RADIAL + DESC_MAX_ANG); ++f) {
+    dd.offset[f] = (p->standardise && f < nfeat) ? p->offset[f] : 0.0;
+    dd.scale[f] = (p->standardise && f < nfeat) ? p->scale[f] : 1.0;
+  }
+  // species slot of every atom (-1: not described)
+  std::vector<double> Z(h->n_atoms);
+  if (h->n_atoms > 0) CK(cudaMemcpy(Z.data(), h->aZ, sizeof(double) * h->n_atoms, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> slot(std::max(1, h->n_atoms), -1);
+  for (int a = 0; a < h->n_atoms; ++a)
+    for (int s = 0; s < p->n_species; ++s)
+      if (fabs(Z[a] - p->species_Z[s]) < 1e-9) slot[a] = s;
+  cudaStream_t st = S(stream);
+  int32_t* dslot = nullptr;
+  TRY(dalloc(h, &dslot, (int64_t)slot.size()));
+  CK(cudaMemcpyAsync(dslot, slot.data(), sizeof(int32_t) * slot.size(), cudaMemcpyHostToDevice, st));
+  if (precision == EFE_PREC_FP32)
+    launch_descriptors<float>(h->qpts, h->nq, h->axyz, dslot, h->n_atoms, dd, (float*)D, st);
+  else
+    launch_descriptors<double>(h->qpts, h->nq, h->axyz, dslot, h->n_atoms, dd, (double*)D, st);
+  CKL();
+  CK(cudaStreamSynchronize(st));
+  dfree(h, dslot);
+  return EFE_OK;
+}
+
+int efe_learned_density(efe_handle* h, const double* rho_sad, const void* y, double floor, double n_electrons,
+                        double* rho, int32_t precision, void* stream) {
+  if (!h || !rho_sad || !y || !rho || !(floor > 0.0) || !valid_prec(precision)) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  cudaStream_t st = S(stream);
+  if (precision == EFE_PREC_FP32)
+    launch_apply_correction<float>(h->nq, rho_sad, (const float*)y, floor, rho, st);
+  else
+    launch_apply_correction<double>(h->nq, rho_sad, (const double*)y, floor, rho, st);
+  if (n_electrons > 0.0) {
+    double* red = learn_red(h->dev);
+    if (!red) {
+      h->err = "reduction scratch unavailable";
+      return EFE_ERR_CUDA;
+    }
+    launch_scale_count(h->qpts, h->nq, n_electrons, rho, red, st);
+  }
+  CKL();
+  return EFE_OK;
+}
+
+int efe_density_log_ratio(efe_handle* h, const double* rho, const double* rho_sad, double floor, void* y,
+                          int32_t precision, void* stream) {
+  if (!h || !rho || !rho_sad || !y || !(floor > 0.0) || !valid_prec(precision)) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  cudaStream_t st = S(stream);
+  if (precision == EFE_PREC_FP32)
+    launch_log_ratio<float>(h->nq, rho, rho_sad, floor, (float*)y, st);
+  else
+    launch_log_ratio<double>(h->nq, rho, rho_sad, floor, (double*)y, st);
+  CKL();
+  return EFE_OK;
+}
+
+int64_t efe_mlp_param_count(const efe_mlp_shape* s) {
+  return valid_shape(s) ? mlp_param_count(s->dims, s->n_layers) : -1;
+}
+
+int64_t efe_mlp_work_elems(const efe_mlp_shape* s, int64_t n) {
+  return valid_shape(s) && n >= 0 ? mlp_work_elems(s->dims, s->n_layers, n) : -1;
+}
+
+int64_t efe_mlp_scratch_elems(const efe_mlp_shape* s, int64_t n) {
+  return valid_shape(s) && n >= 0 ? mlp_scratch_elems(s->dims, s->n_layers, n) : -1;
+}
+
+int efe_mlp_forward(const efe_mlp_shape* s, const void* params, const void* X, int64_t n, void* y, void* work,
+                    int32_t precision, void* stream) {
+  if (!valid_shape(s) || !params || !X || !y || !work || n < 1 || !valid_prec(precision)) return EFE_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == EFE_PREC_FP32)
+    mlp_forward<float>(s->dims, s->n_layers, (const float*)params, (const float*)X, n, (float*)y, (float*)work, st);
+  else
+    mlp_forward<double>(s->dims, s->n_layers, (const double*)params, (const double*)X, n, (double*)y,
+                        (double*)work, st);
+  return cudaGetLastError() == cudaSuccess ? EFE_OK : EFE_ERR_CUDA;
+}
+
+int efe_mlp_backward(const efe_mlp_shape* s, const void* params, const void* X, int64_t n, const void* work,
+                     const void* dy, void* grads, void* scratch, int32_t precision, void* stream) {
+  if (!valid_shape(s) || !params || !X || !work || !dy || !grads || !scratch || n < 1 || !valid_prec(precision))
+    return EFE_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == EFE_PREC_FP32)
+    mlp_backward<float>(s->dims, s->n_layers, (const float*)params, (const float*)X, n, (const float*)work,
+                        (const float*)dy, (float*)grads, (float*)scratch, st);
+  else
+    mlp_backward<double>(s->dims, s->n_layers, (const double*)params, (const double*)X, n, (const double*)work,
+                         (const double*)dy, (double*)grads, (double*)scratch, st);
+  return cudaGetLastError() == cudaSuccess ? EFE_OK : EFE_ERR_CUDA;
+}
+
+int efe_wmse(const void* yh, const void* y, const void* c, int64_t n, void* dy, double* loss, int32_t precision,
+             void* stream) {
+  if (!yh || !y || !c || !dy || n < 1 || !valid_prec(precision)) return EFE_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return EFE_ERR_CUDA;
+  double* red = learn_red(dev);
+  if (!red) return EFE_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* stats = red + 2 * 1024;
+  if (precision == EFE_PREC_FP32)
+    launch_wmse<float>((const float*)yh, (const float*)y, (const float*)c, n, (float*)dy, red, stats, st);
+  else
+    launch_wmse<double>((const double*)yh, (const double*)y, (const double*)c, n, (double*)dy, red, stats, st);
+  if (loss) {
+    if (cudaMemcpyAsync(loss, stats, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) return EFE_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return EFE_ERR_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? EFE_OK : EFE_ERR_CUDA;
+}
+
+int efe_adam(void* p, const void* g, void* m, void* v, int64_t n, double lr, double beta1, double beta2, double eps,
+             int32_t t, int32_t precision, void* stream) {
+  if (!p || !g || !m || !v || n < 1 || t < 1 || !valid_prec(precision) || !(lr > 0.0)) return EFE_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == EFE_PREC_FP32)
+    launch_adam<float>(n, (float*)p, (const float*)g, (float*)m, (float*)v, lr, beta1, beta2, eps, t, st);
+  else
+    launch_adam<double>(n, (double*)p, (const double*)g, (double*)m, (double*)v, lr, beta1, beta2, eps, t, st);
+  return cudaGetLastError() == cudaSuccess ? EFE_OK : EFE_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -621,17 +621,20 @@ __global__ void k_symmetrize(double* A, int n, int lda) {
 
 // Parallel cyclic Jacobi (round-robin pairing) for a symmetric n x n matrix in
 // one CTA: A <- J^T A J with disjoint rotations per round, V <- V J.
-template <bool SMEM>
-__global__ void __launch_bounds__(1024) k_jacobi(double* Ag, int n, int ldag, double* V, int ldv, double* w,
-                                                 int max_sweeps, int* info) {
-  __shared__ double cs[1024], sn[1024];
+// T = double, or float for the pre-diagonalisation of the mixed eigensolver;
+// stops when the off-diagonal square sum is <= tol2 times the total.
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(1024) k_jacobi(T* Ag, int n, int ldag, T* V, int ldv, T* w, int max_sweeps,
+                                                 double tol2, int* info) {
+  __shared__ T cs[1024], sn[1024];
   __shared__ int pp[1024], qq[1024];
   __shared__ double red[2][32];
   __shared__ int done;
-  extern __shared__ double As_dyn[];
+  extern __shared__ double As_raw[];
+  T* As_dyn = reinterpret_cast<T*>(As_raw);
   const int tid = threadIdx.x, bd = blockDim.x;
   // the working matrix lives in shared memory when it fits (n <= 150), else in global memory
-  double* A = SMEM ? As_dyn : Ag;
+  T* A = SMEM ? As_dyn : Ag;
   const int lda = SMEM ? n : ldag;
   if (SMEM) {
     for (int64_t t = tid; t < (int64_t)n * n; t += bd) As_dyn[t] = Ag[(t / n) * (int64_t)ldag + t % n];
@@ -639,14 +642,14 @@ __global__ void __launch_bounds__(1024) k_jacobi(double* Ag, int n, int ldag, do
   }
   const int n2 = n + (n & 1);
   const int np = n2 / 2;
-  for (int64_t t = tid; t < (int64_t)n * n; t += bd) V[(t / n) * ldv + t % n] = (t / n == t % n) ? 1.0 : 0.0;
+  for (int64_t t = tid; t < (int64_t)n * n; t += bd) V[(t / n) * ldv + t % n] = (t / n == t % n) ? T(1) : T(0);
   if (tid == 0) done = 0;
   int sweep = 0;
   for (; sweep <= max_sweeps; ++sweep) {
     __syncthreads();
     double off = 0.0, tot = 0.0;
     for (int64_t t = tid; t < (int64_t)n * n; t += bd) {
-      const double a = A[(t / n) * lda + t % n];
+      const double a = (double)A[(t / n) * lda + t % n];
       tot += a * a;
       if (t / n != t % n) off += a * a;
     }
@@ -659,7 +662,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(double* Ag, int n, int ldag, do
     if (tid == 0) {
       double so = 0.0, st = 0.0;
       for (int i = 0; i < (bd + 31) / 32; ++i) { so += red[0][i]; st += red[1][i]; }
-      done = (so <= 1e-30 * st) ? 1 : 0;
+      done = (so <= tol2 * st) ? 1 : 0;
     }
     __syncthreads();
     if (done || sweep == max_sweeps) break;
@@ -670,13 +673,13 @@ __global__ void __launch_bounds__(1024) k_jacobi(double* Ag, int n, int ldag, do
         const int pl2 = (s2 == 0) ? 0 : ((s2 - 1 + r) % (n2 - 1)) + 1;
         const int p = min(pl1, pl2), q = max(pl1, pl2);
         if (q >= n) { pp[k] = -1; continue; }
-        const double apq = A[(int64_t)p * lda + q];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
-          const double app = A[(int64_t)p * lda + p], aqq = A[(int64_t)q * lda + q];
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
+        const T apq = A[(int64_t)p * lda + q];
+        T c = T(1), s = T(0);
+        if (apq != T(0)) {
+          const T app = A[(int64_t)p * lda + p], aqq = A[(int64_t)q * lda + q];
+          const T tau = (aqq - app) / (T(2) * apq);
+          const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+          c = T(1) / sqrt(T(1) + t * t);
           s = t * c;
         }
         pp[k] = p; qq[k] = q; cs[k] = c; sn[k] = s;
@@ -687,13 +690,13 @@ __global__ void __launch_bounds__(1024) k_jacobi(double* Ag, int n, int ldag, do
         const int p = pp[k];
         if (p < 0) continue;
         const int q = qq[k];
-        const double c = cs[k], s = sn[k];
-        double* Ai = A + (int64_t)i * lda;
-        const double aip = Ai[p], aiq = Ai[q];
+        const T c = cs[k], s = sn[k];
+        T* Ai = A + (int64_t)i * lda;
+        const T aip = Ai[p], aiq = Ai[q];
         Ai[p] = c * aip - s * aiq;
         Ai[q] = s * aip + c * aiq;
-        double* Vi = V + (int64_t)i * ldv;
-        const double vip = Vi[p], viq = Vi[q];
+        T* Vi = V + (int64_t)i * ldv;
+        const T vip = Vi[p], viq = Vi[q];
         Vi[p] = c * vip - s * viq;
         Vi[q] = s * vip + c * viq;
       }
@@ -703,8 +706,8 @@ __global__ void __launch_bounds__(1024) k_jacobi(double* Ag, int n, int ldag, do
         const int p = pp[k];
         if (p < 0) continue;
         const int q = qq[k];
-        const double c = cs[k], s = sn[k];
-        const double apj = A[(int64_t)p * lda + j], aqj = A[(int64_t)q * lda + j];
+        const T c = cs[k], s = sn[k];
+        const T apj = A[(int64_t)p * lda + j], aqj = A[(int64_t)q * lda + j];
         A[(int64_t)p * lda + j] = c * apj - s * aqj;
         A[(int64_t)q * lda + j] = s * apj + c * aqj;
       }
@@ -712,8 +715,8 @@ __global__ void __launch_bounds__(1024) k_jacobi(double* Ag, int n, int ldag, do
       for (int k = tid; k < np; k += bd) {
         const int p = pp[k];
         if (p < 0) continue;
-        A[(int64_t)p * lda + qq[k]] = 0.0;
-        A[(int64_t)qq[k] * lda + p] = 0.0;
+        A[(int64_t)p * lda + qq[k]] = T(0);
+        A[(int64_t)qq[k] * lda + p] = T(0);
       }
       __syncthreads();
     }
@@ -1003,16 +1006,27 @@ void launch_symmetrize(double* A, int n, int lda, cudaStream_t st) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-void launch_jacobi(double* A, int n, int lda, double* V, int ldv, double* w, int max_sweeps, int* info,
-                   cudaStream_t st) {
-  const size_t smem = sizeof(double) * (size_t)n * n;
+template <typename T>
+void launch_jacobi_t(T* A, int n, int lda, T* V, int ldv, T* w, int max_sweeps, double tol2, int* info,
+                     cudaStream_t st) {
+  const size_t smem = sizeof(T) * (size_t)n * n;
   if (smem <= 180 * 1024) {
-    cudaFuncSetAttribute(k_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_jacobi<true><<<1, 1024, smem, st>>>(A, n, lda, V, ldv, w, max_sweeps, info);
+    cudaFuncSetAttribute(k_jacobi<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobi<T, true><<<1, 1024, smem, st>>>(A, n, lda, V, ldv, w, max_sweeps, tol2, info);
   } else {
-    k_jacobi<false><<<1, 1024, 0, st>>>(A, n, lda, V, ldv, w, max_sweeps, info);
+    k_jacobi<T, false><<<1, 1024, 0, st>>>(A, n, lda, V, ldv, w, max_sweeps, tol2, info);
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_jacobi(double* A, int n, int lda, double* V, int ldv, double* w, int max_sweeps, int* info,
+                   cudaStream_t st) {
+  launch_jacobi_t<double>(A, n, lda, V, ldv, w, max_sweeps, 1e-30, info, st);
+}
+
+void launch_jacobi_f32(float* A, int n, int lda, float* V, int ldv, float* w, int max_sweeps, int* info,
+                       cudaStream_t st) {
+  launch_jacobi_t<float>(A, n, lda, V, ldv, w, max_sweeps, 1e-12, info, st);
 }
 
 void launch_sort_eig(const double* w, const double* V, int n, int ldv, double* ws, double* Vs, int ldvs,

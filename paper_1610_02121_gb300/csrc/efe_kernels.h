@@ -6,6 +6,7 @@
 
 #include "efe_internal.h"
 
+#include <algorithm>
 #include <atomic>
 
 namespace efe {
@@ -129,6 +130,9 @@ void launch_transpose(const double* A, int n, int lda, double* B, int ldb, cudaS
 void launch_symmetrize(double* A, int n, int lda, cudaStream_t st);
 void launch_jacobi(double* A, int n, int lda, double* V, int ldv, double* w, int max_sweeps, int* info,
                    cudaStream_t st);
+// FP32 cyclic Jacobi to a relative off-diagonal size of 1e-6 (pre-diagonalisation)
+void launch_jacobi_f32(float* A, int n, int lda, float* V, int ldv, float* w, int max_sweeps, int* info,
+                       cudaStream_t st);
 void launch_sort_eig(const double* w, const double* V, int n, int ldv, double* ws, double* Vs, int ldvs,
                      cudaStream_t st);
 // per-column ||HX - eps MX||^2 partial sums, then sqrt
@@ -175,8 +179,9 @@ struct AndersonCoef {
   double t[ANDERSON_MAX];
 };
 
+// fp32: orbital values in FP32 arithmetic (mixed mode); rho and its orbital sums stay FP64
 int launch_leaf_density(const LeafDev& lf, int64_t n_leaf, const MeshDev& m, const RefElem& re, const EnrDev& en,
-                        int kmax, const double* X, int64_t ldx, int N, const double* occ, double* rho,
+                        int kmax, const double* X, int64_t ldx, int N, const double* occ, double* rho, bool fp32,
                         cudaStream_t st);
 size_t leaf_density_smem(int nm, int kmax);
 void launch_leaf_interp(const LeafDev& lf, int64_t n_leaf, const MeshDev& m, const RefElem& re, const double* phi,
@@ -215,5 +220,52 @@ void launch_anderson_gram(const double* qpts, int64_t nq, const HistDev& hs, dou
 void launch_anderson_mix(int64_t nq, const HistDev& hs, const AndersonCoef& th, double beta, double* out,
                          cudaStream_t st);
 void launch_scale_to(int64_t n, double* x, const double* num, double target, cudaStream_t st);
+
+// ---- learned initial density (efe_learn.cu) ----
+constexpr int DESC_MAX_SPECIES = 4, DESC_MAX_RADIAL = 16, DESC_MAX_ANG = 8;
+
+struct DescDev {
+  int n_species, n_radial, n_ang;
+  double radial_mu[DESC_MAX_RADIAL];
+  double radial_sigma;
+  double ang_mu[DESC_MAX_ANG];
+  double ang_sigma;
+  double r_cut;
+  int standardise;
+  double offset[DESC_MAX_SPECIES * (DESC_MAX_RADIAL + DESC_MAX_ANG)];
+  double scale[DESC_MAX_SPECIES * (DESC_MAX_RADIAL + DESC_MAX_ANG)];
+};
+
+struct SadShellDev {      // one atom: up to three Slater shells
+  int n_shells;
+  int n[3];
+  double zeta[3], occ[3], c[3];   // c: radial normalisation constant
+};
+
+void launch_sad(const double* qpts, int64_t nq, const double* axyz, int na, const SadShellDev* sh, double* rho,
+                cudaStream_t st);
+template <typename T>
+void launch_descriptors(const double* qpts, int64_t nq, const double* axyz, const int32_t* slot, int na,
+                        const DescDev& p, T* D, cudaStream_t st);
+int64_t mlp_param_count(const int* dims, int nl);
+int64_t mlp_work_elems(const int* dims, int nl, int64_t n);
+int64_t mlp_scratch_elems(const int* dims, int nl, int64_t n);
+template <typename T>
+void mlp_forward(const int* dims, int nl, const T* params, const T* X, int64_t n, T* y, T* work, cudaStream_t st);
+template <typename T>
+void mlp_backward(const int* dims, int nl, const T* params, const T* X, int64_t n, const T* work, const T* dy,
+                  T* grads, T* scratch, cudaStream_t st);
+template <typename T>
+void launch_wmse(const T* yh, const T* y, const T* c, int64_t n, T* dy, double* part, double* stats, cudaStream_t st);
+template <typename T>
+void launch_adam(int64_t n, T* p, const T* g, T* m, T* v, double lr, double b1, double b2, double eps, int t,
+                 cudaStream_t st);
+template <typename T>
+void launch_apply_correction(int64_t n, const double* rs, const T* y, double floor, double* rho, cudaStream_t st);
+template <typename T>
+void launch_log_ratio(int64_t n, const double* rho, const double* rs, double floor, T* y, cudaStream_t st);
+// x *= target / sum_q w_q x_q
+void launch_scale_count(const double* qpts, int64_t nq, double target, double* x, double* part, cudaStream_t st);
+int learn_reduce_blocks();
 
 }  // namespace efe

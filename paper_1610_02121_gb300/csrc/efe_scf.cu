@@ -93,6 +93,9 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
 // One CTA per leaf.  Per CW-column pass: X_e (125 x CW) -> T1 = Lx X_e ->
 // T2 = Ly T1 -> psi = Lz T2 (+ enrichment) with 2730 FMAs per column on a
 // 6^3 leaf instead of 27000 for the dense 216 x 125 basis matrix.
+// T: arithmetic of the orbital values (double, or float in the mixed mode);
+// 2 f psi^2 and its sums over orbitals are always FP64.
+template <typename T>
 __global__ void __launch_bounds__(LT) k_leaf_density(LeafDev lf, MeshDev m, RefElem re, EnrDev en,
                                                      const double* __restrict__ X, int64_t ldx, int N,
                                                      const double* __restrict__ occ, double* __restrict__ rho) {
@@ -105,10 +108,10 @@ __global__ void __launch_bounds__(LT) k_leaf_density(LeafDev lf, MeshDev m, RefE
   const int nm = lf.nmax;
   double* L = sm;                                   // 3 x nm x 5
   double* racc = L + 3 * nm * NP1;                  // nm^3
-  double* Xs = racc + nm * nm * nm;                 // 125 x CW
-  double* T1 = Xs + NL * CW;                        // n x 25 x CW
-  double* T2 = T1 + nm * 25 * CW;                   // n x n x 5 x CW
-  double* Xes = T2 + nm * nm * 5 * CW;              // kmax x CW
+  T* Xs = reinterpret_cast<T*>(racc + nm * nm * nm);  // 125 x CW
+  T* T1 = Xs + NL * CW;                             // n x 25 x CW
+  T* T2 = T1 + nm * 25 * CW;                        // n x n x 5 x CW
+  T* Xes = T2 + nm * nm * 5 * CW;                   // kmax x CW
   __shared__ int64_t gnode[NL];
   int ijk[3];
   double lo[3], h[3];
@@ -127,30 +130,30 @@ __global__ void __launch_bounds__(LT) k_leaf_density(LeafDev lf, MeshDev m, RefE
     __syncthreads();
     for (int t = threadIdx.x; t < NL * CW; t += blockDim.x) {
       const int r = t / CW, c = t % CW;
-      Xs[t] = (c0 + c < N) ? X[gnode[r] * ldx + c0 + c] : 0.0;
+      Xs[t] = (c0 + c < N) ? (T)X[gnode[r] * ldx + c0 + c] : T(0);
     }
     for (int t = threadIdx.x; t < ke * CW; t += blockDim.x) {
       const int a = t / CW, c = t % CW;
-      Xes[t] = (c0 + c < N) ? X[(en.n_nodes + fl[a]) * ldx + c0 + c] : 0.0;
+      Xes[t] = (c0 + c < N) ? (T)X[(en.n_nodes + fl[a]) * ldx + c0 + c] : T(0);
     }
     __syncthreads();
     // T1[ix][b + 5c][col] = sum_a Lx[ix][a] X[a + 5b + 25c][col]
     for (int t = threadIdx.x; t < n * 25 * CW; t += blockDim.x) {
       const int col = t % CW, bc = (t / CW) % 25, ix = t / (25 * CW);
-      const double* xr = Xs + (bc * NP1) * CW + col;
-      double s = 0.0;
+      const T* xr = Xs + (bc * NP1) * CW + col;
+      T s = T(0);
 #pragma unroll
-      for (int a = 0; a < NP1; ++a) s = fma(Lx[ix * NP1 + a], xr[a * CW], s);
+      for (int a = 0; a < NP1; ++a) s = fma((T)Lx[ix * NP1 + a], xr[a * CW], s);
       T1[t] = s;
     }
     __syncthreads();
     // T2[ix][iy][c][col] = sum_b Ly[iy][b] T1[ix][b + 5c][col]
     for (int t = threadIdx.x; t < n * n * 5 * CW; t += blockDim.x) {
       const int col = t % CW, c = (t / CW) % 5, iy = (t / (5 * CW)) % n, ix = t / (5 * CW * n);
-      const double* tr = T1 + (ix * 25 + c * NP1) * CW + col;
-      double s = 0.0;
+      const T* tr = T1 + (ix * 25 + c * NP1) * CW + col;
+      T s = T(0);
 #pragma unroll
-      for (int b = 0; b < NP1; ++b) s = fma(Ly[iy * NP1 + b], tr[b * CW], s);
+      for (int b = 0; b < NP1; ++b) s = fma((T)Ly[iy * NP1 + b], tr[b * CW], s);
       T2[t] = s;
     }
     __syncthreads();
@@ -161,13 +164,14 @@ __global__ void __launch_bounds__(LT) k_leaf_density(LeafDev lf, MeshDev m, RefE
       const bool act = t < np * CW;
       const int col = t % CW, p = act ? t / CW : 0;
       const int ix = p % n, iy = (p / n) % n, iz = p / (n * n);
-      const double* tr = T2 + ((ix * n + iy) * 5) * CW + col;
-      double psi = 0.0;
+      const T* tr = T2 + ((ix * n + iy) * 5) * CW + col;
+      T psi = T(0);
 #pragma unroll
-      for (int c = 0; c < NP1; ++c) psi = fma(Lz[iz * NP1 + c], tr[c * CW], psi);
-      for (int a = 0; a < ke; ++a) psi = fma(Eq[(int64_t)p * ke + a], Xes[a * CW + col], psi);
+      for (int c = 0; c < NP1; ++c) psi = fma((T)Lz[iz * NP1 + c], tr[c * CW], psi);
+      for (int a = 0; a < ke; ++a) psi = fma((T)Eq[(int64_t)p * ke + a], Xes[a * CW + col], psi);
       const double f = (act && c0 + col < N) ? occ[c0 + col] : 0.0;
-      double v = 2.0 * f * psi * psi;
+      const double pd = (double)psi;
+      double v = 2.0 * f * pd * pd;
       // fixed-order sum over the CW lanes of this point (CW divides 32)
 #pragma unroll
       for (int s = CW / 2; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
@@ -826,18 +830,24 @@ size_t leaf_density_smem(int nm, int kmax) {
 }
 
 int launch_leaf_density(const LeafDev& lf, int64_t n_leaf, const MeshDev& m, const RefElem& re, const EnrDev& en,
-                        int kmax, const double* X, int64_t ldx, int N, const double* occ, double* rho,
+                        int kmax, const double* X, int64_t ldx, int N, const double* occ, double* rho, bool fp32,
                         cudaStream_t st) {
   if (n_leaf <= 0) return 0;
   const size_t sm = leaf_density_smem(lf.nmax, kmax);
   if (sm > 227 * 1024) return 1;
-  static size_t set = 0;
+  static size_t set64 = 0, set32 = 0;
+  size_t& set = fp32 ? set32 : set64;
   if (sm > set) {
-    if (cudaFuncSetAttribute(k_leaf_density, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-      return 1;
+    const cudaError_t e =
+        fp32 ? cudaFuncSetAttribute(k_leaf_density<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+             : cudaFuncSetAttribute(k_leaf_density<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return 1;
     set = sm;
   }
-  k_leaf_density<<<(unsigned)n_leaf, LT, sm, st>>>(lf, m, re, en, X, ldx, N, occ, rho);
+  if (fp32)
+    k_leaf_density<float><<<(unsigned)n_leaf, LT, sm, st>>>(lf, m, re, en, X, ldx, N, occ, rho);
+  else
+    k_leaf_density<double><<<(unsigned)n_leaf, LT, sm, st>>>(lf, m, re, en, X, ldx, N, occ, rho);
   g_launches++;
   return 0;
 }

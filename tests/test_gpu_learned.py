@@ -1,0 +1,153 @@
+"""GPU parity of the learned-initial-density kernels against the FP64 oracle, and
+the gain of the trained network over the plain superposition start.
+
+FP64 check mode: SAD, descriptors, network forward/backward, loss and Adam
+agree with the oracle to rounding (1e-10 relative; the oracle's gradients are
+themselves pinned against finite differences).  FP32 mode: 1e-4 relative."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_util import cuda_available, gpu_system, to_dev, torch
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not cuda_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    s = W.tiny(seed=11)
+    G = gpu_system(s)
+    return s, G, G.qpoints().cpu().numpy()
+
+
+def _slots(Z):
+    from paper_1610_02121_gb300 import learned as LR
+    return np.array([LR.SPECIES.index(float(z)) if float(z) in LR.SPECIES else -1 for z in Z])
+
+
+def test_sad_parity(tiny):
+    from oracle import learned as OL
+    s, G, q = tiny
+    shells = [W.sad_shells(z) for z in s["Z"]]
+    rho = G.sad_density(shells).cpu().numpy()
+    ref = OL.sad_density(q[:, :3], s["atoms"], shells)
+    assert np.abs(rho - ref).max() <= 1e-12 * np.abs(ref).max()
+    ne = float(sum(s["Z"]))
+    rho_n = G.sad_density(shells, ne).cpu().numpy()
+    assert abs(np.sum(q[:, 3] * rho_n) - ne) < 1e-10 * ne
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_descriptor_parity(tiny, prec, tol):
+    from oracle import learned as OL
+    from paper_1610_02121_gb300 import learned as LR
+    s, G, q = tiny
+    D = G.descriptors(LR.desc_params(), precision=prec).double().cpu().numpy()
+    # the oracle's species slots follow the same order (1, 6, 8, 14); tiny holds Z = 1, 2
+    slots = _slots(s["Z"])
+    keep = slots >= 0
+    ref = OL.descriptors(q[:, :3], s["atoms"][keep], slots[keep])
+    assert D.shape == ref.shape
+    assert np.abs(D - ref).max() <= tol * max(1.0, np.abs(ref).max())
+
+
+def _net(prec, seed=3, dims=(64, 32, 32, 32, 1)):
+    from oracle import learned as OL
+    from paper_1610_02121_gb300._lib import Mlp
+    P = OL.init_params(list(dims), seed=seed)
+    rng = np.random.default_rng(seed)
+    for l in range(1, len(P), 2):
+        P[l] = rng.standard_normal(P[l].shape) * 0.1
+    flat = np.concatenate([p.reshape(-1) for p in P])
+    return P, Mlp(list(dims), precision=prec, params=flat)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_mlp_forward_backward_parity(prec, tol):
+    from oracle import learned as OL
+    P, net = _net(prec)
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((1000, 64))
+    dy = rng.standard_normal(1000)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Xd = torch.as_tensor(X, dtype=dt, device="cuda").contiguous()
+    y = net.forward(Xd).double().cpu().numpy()
+    y_ref, pre = OL.forward(P, X)
+    assert np.abs(y - y_ref).max() <= tol * np.abs(y_ref).max()
+    g = net.backward(Xd, torch.as_tensor(dy, dtype=dt, device="cuda")).double().cpu().numpy()
+    g_ref = np.concatenate([x.reshape(-1) for x in OL.backward(P, X, pre, dy)])
+    gtol = 1e-10 if prec == "fp64" else 1e-3
+    assert np.abs(g - g_ref).max() <= gtol * np.abs(g_ref).max()
+
+
+def test_wmse_and_adam_parity():
+    from oracle import learned as OL
+    P, net = _net("fp64")
+    rng = np.random.default_rng(9)
+    n = 777
+    yh, y, c = rng.standard_normal(n), rng.standard_normal(n), rng.uniform(0.1, 2, n)
+    loss, dy = net.wmse(*(torch.as_tensor(a, device="cuda") for a in (yh, y, c)))
+    l_ref, dy_ref = OL.wmse(yh, y, c)
+    assert abs(loss - l_ref) < 1e-12 * l_ref
+    np.testing.assert_allclose(dy.cpu().numpy(), dy_ref, rtol=1e-12, atol=1e-15)
+    p0 = net.params.cpu().numpy().copy()
+    g = rng.standard_normal(p0.size)
+    m, v = np.zeros_like(p0), np.zeros_like(p0)
+    pr = p0.copy()
+    for t in (1, 2, 3):
+        net.adam(torch.as_tensor(g * t, device="cuda"), lr=1e-2)
+        OL.adam_step(pr, g * t, m, v, t, lr=1e-2)
+    np.testing.assert_allclose(net.params.cpu().numpy(), pr, rtol=1e-12, atol=1e-14)
+
+
+def test_learned_density_inverts_log_ratio(tiny):
+    s, G, q = tiny
+    shells = [W.sad_shells(z) for z in s["Z"]]
+    ne = float(sum(s["Z"]))
+    rs = G.sad_density(shells, ne)
+    r = np.sqrt(np.sum((q[:, :3] - s["atoms"][0]) ** 2, axis=1))
+    rho = to_dev(np.exp(-r) * 0.3)
+    y = G.density_log_ratio(rho, rs, 1e-6, precision="fp64")
+    back = G.learned_density(rs, y, 1e-6, 0.0).cpu().numpy()
+    np.testing.assert_allclose(back, rho.cpu().numpy(), rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.slow
+def test_learned_start_gain():
+    """Train on the converged densities of small C/O clusters, then start a held-out
+    cluster from SAD and from the learned density: both reach the same energy
+    (within 1e-5 Ha/atom) and the learned start needs no more SCF iterations."""
+    from paper_1610_02121_gb300 import learned as LR
+    m = 12
+    train = [W.random_cluster(4, [6, 8], seed=s, h_min=1.2, h_max=4.0, pad=7.0) for s in (11, 12, 13)]
+    rows = []
+    model = LR.DensityModel(seed=1)
+    raw = []
+    for s in train:
+        G = gpu_system(s)
+        ne = float(np.sum(s["Z"]))
+        N = int(ne / 2) + 10
+        X = to_dev(W.initial_block(s, N, seed=1))
+        rs = G.sad_density([W.sad_shells(z) for z in s["Z"]], ne)
+        res, its, rho = LR.scf_to_convergence(G, X, rs.clone(), ne, m)
+        D = G.descriptors(LR.desc_params(), precision="fp32")
+        raw.append((G, rho, rs, D))
+    model.set_standardisation(torch.cat([d for (_, _, _, d) in raw])[::97])
+    for k, (G, rho, rs, _) in enumerate(raw):
+        rows.append(LR.training_rows(G, rho, rs, model.descriptors(G), 200000, seed=k))
+    D = torch.cat([r[0] for r in rows])
+    y = torch.cat([r[1] for r in rows])
+    c = torch.cat([r[2] for r in rows])
+    losses = model.fit(D, y, c, steps=800)
+    assert losses[-1] < 0.5 * losses[0]
+    s = W.random_cluster(5, [6, 8], seed=21, h_min=1.2, h_max=4.0, pad=7.0)
+    G = gpu_system(s)
+    ne = float(np.sum(s["Z"]))
+    N = int(ne / 2) + 10
+    rs = G.sad_density([W.sad_shells(z) for z in s["Z"]], ne)
+    r_sad, it_sad, _ = LR.scf_to_convergence(G, to_dev(W.initial_block(s, N, seed=1)), rs.clone(), ne, m)
+    r_ml, it_ml, _ = LR.scf_to_convergence(G, to_dev(W.initial_block(s, N, seed=1)), model.start_density(G, rs, ne),
+                                           ne, m)
+    n_atoms = len(s["Z"])
+    assert abs(r_sad["total"] - r_ml["total"]) < 1e-5 * n_atoms
+    assert it_ml <= it_sad, (it_ml, it_sad)

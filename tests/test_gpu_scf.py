@@ -76,6 +76,16 @@ def test_density_parity(tiny, N):
     assert np.abs(rho - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+def test_density_fp32_orbital_values(tiny):
+    """Mixed mode: FP32 orbital values, FP64 squares and sums -> FP32-level agreement."""
+    from oracle import scf as S
+    X = W.random_block(tiny.s, 37, seed=5)
+    occ = np.random.default_rng(3).uniform(0.0, 1.0, 37)
+    rho = tiny.G.density(to_dev(X), occ, precision="fp32").cpu().numpy()
+    ref = tiny.to_gpu_order(S.density(tiny.qc, X, occ))
+    assert np.abs(rho - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
 def test_density_classical_only(ho):
     from oracle import scf as S
     X = W.random_block(ho.s, 5, seed=3)
