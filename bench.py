@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-scf", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
     p.add_argument("--scf-steps", type=int, default=3)
     p.add_argument("--workload", default="si16", choices=["si16", "si16s", "hydrogen"])
     return p.parse_args()
@@ -159,6 +160,56 @@ def cpu_sample(system, N, steps=None, min_seconds=10.0):
             f"({d.n_cell} cells) of the same mesh and potential; {n} applies, {el:.1f} s; "
             "TFLOP/s by the same algorithmic count")
     return flops / dt / 1e12, dt, desc
+
+
+def batch_section(P, torch, stream, n_sys=8, m=20, steps=3):
+    import math
+    rng = np.random.default_rng(5)
+    Gs, Xs, Ns, flops, tiles, nodes = [], [], [], 0.0, [], []
+    for i in range(n_sys):
+        na = int(rng.integers(1, 7))
+        s = W.random_cluster(na, [1, 6, 8, 14], seed=500 + i, h_min=1.2, h_max=4.0, pad=7.0)
+        G = P.System(s)
+        G.set_potential_analytic()
+        ne = float(np.sum(s["Z"]))
+        N = int(math.ceil(0.6 * ne)) + 8
+        X = torch.from_numpy(W.initial_block(s, N, seed=1)).cuda()
+        G.rayleigh_ritz(X)
+        tile, _ = G.autotune(N, "tf32x3")
+        Gs.append(G)
+        Xs.append(X)
+        Ns.append(N)
+        tiles.append(tile)
+        nodes.append(G.n_nodes)
+        flops += filter_flops(G.n_cells, G.n_coupling, G.n_enrich, N, m)
+    a, b, a0 = [], [], []
+    for G, X in zip(Gs, Xs):
+        e, _ = G.rayleigh_ritz(X)
+        a.append(e.max())
+        a0.append(e.min())
+        b.append(G.upper_bound(X[:, -1].contiguous(), 10))
+    B = P.Batch(Gs)
+    out = {}
+    for mode in (True, False):
+        Xw = [x.clone() for x in Xs]
+        B.chfsi_step(Xw, m, a, b, a0, precision="tf32x3", fp64_tail=2, graph=mode)   # warm-up / recording
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        s0.record(stream)
+        for _ in range(steps):
+            B.chfsi_step(Xw, m, a, b, a0, precision="tf32x3", fp64_tail=2, graph=mode)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        out[mode] = (time.perf_counter() - t0) / steps
+    nn, kn = B.graph_nodes()
+    B.close()
+    return {"systems": n_sys, "nodes": nodes, "N": Ns, "m": m, "precision": "tf32x3, FP64 tail 2",
+            "graph_s_per_step": out[True], "sequential_s_per_step": out[False],
+            "graph_speedup": out[False] / out[True], "graph_tflops": flops / out[True] / 1e12,
+            "graph_nodes": nn, "graph_kernel_nodes": kn, "autotuned_tiles": tiles,
+            "step": "one filter step of every system (no Rayleigh-Ritz), host wall clock incl. graph launch"}
 
 
 def run_reference(args):
@@ -360,6 +411,11 @@ def main():
                        "total_energy_Ha": [h["total"] for h in [r0] + hist],
                        "drho": [h["drho"] for h in [r0] + hist],
                        "start": "density of the Rayleigh-Ritz-rotated atomic-orbital block, renormalised to N_e"}
+    # many small systems (1-6 atoms, Z in {1, 6, 8, 14}, own graded meshes, N = ceil(0.6 N_e) + 8):
+    # one ChFSI filter step of every system as one CUDA graph vs the same steps launched
+    # one system after another; column tiles of the cell kernel picked by the autotuner
+    if not args.no_batch and rank == 0:
+        line["batch"] = batch_section(P, torch, stream)
     if not args.no_cpu and rank == 0 and world == 1:
         v, dt, desc = cpu_sample(system, N)
         line["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)),

@@ -403,6 +403,36 @@ int efe_wmse(const void* yh, const void* y, const void* c, int64_t n, void* dy, 
 int efe_adam(void* p, const void* g, void* m, void* v, int64_t n, double lr, double beta1, double beta2, double eps,
              int32_t t, int32_t precision, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Autotuner and batched systems
+ * ------------------------------------------------------------------------ */
+/* Times the tensor-core cell kernel's column tiles (64, 96, 160) on one full
+ * cell apply for N columns in the given mixed precision (EFE_PREC_TF32 or
+ * EFE_PREC_TF32X3) and keeps the fastest for this handle and N; tile_out: the
+ * choice (host, may be NULL); ms_out: the three times in ms (host, may be NULL).
+ * Needs a potential. */
+int efe_autotune(efe_handle* h, int32_t N, int32_t precision, int32_t* tile_out, double* ms_out);
+
+/* A batch of independent systems (handles on one device) whose ChFSI filter
+ * steps run as one CUDA graph: each system's kernel sequence is a branch of
+ * the graph, recorded once per (X pointers, ld, N, m, precision, fp64_tail)
+ * and replayed; the recurrence coefficients of every system are copied by
+ * nodes of the graph from pinned staging buffers refreshed before each launch,
+ * so new filter bounds need no new recording.  The handles stay owned by the
+ * caller and must outlive the batch. */
+typedef struct efe_batch efe_batch;
+int efe_batch_create(efe_handle* const* systems, int32_t n, efe_batch** out);
+int efe_batch_destroy(efe_batch* b);
+const char* efe_batch_last_error(const efe_batch* b);
+/* graph size of the last recording (host, may be NULL) */
+int efe_batch_graph_nodes(const efe_batch* b, int64_t* nodes, int64_t* kernel_nodes);
+/* One efe_chfsi_step per system i (X[i], ldx[i], N[i], a[i], b[i], a0[i]; host
+ * arrays of n entries).  use_graph = 0 runs the steps one after another on
+ * `stream` (reference path); 1 replays the recorded graph.  Synchronises. */
+int efe_batch_chfsi_step(efe_batch* b, double* const* X, const int64_t* ldx, const int32_t* N, int32_t m,
+                         const double* a, const double* bnd, const double* a0, int32_t precision, int32_t fp64_tail,
+                         int32_t use_graph, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

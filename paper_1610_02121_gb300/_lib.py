@@ -26,7 +26,8 @@ SYMBOLS = ["efe_create", "efe_destroy", "efe_last_error", "efe_sizes", "efe_qpoi
            "efe_hartree", "efe_fermi", "efe_anderson", "efe_scf_init", "efe_scf_step", "efe_sad_density",
            "efe_descriptors", "efe_learned_density", "efe_density_log_ratio", "efe_mlp_param_count",
            "efe_mlp_work_elems", "efe_mlp_scratch_elems", "efe_mlp_forward", "efe_mlp_backward", "efe_wmse",
-           "efe_adam"]
+           "efe_adam", "efe_autotune", "efe_batch_create", "efe_batch_destroy", "efe_batch_last_error",
+           "efe_batch_graph_nodes", "efe_batch_chfsi_step"]
 
 
 class EfeError(RuntimeError):
@@ -135,11 +136,17 @@ def load(path=LIB_PATH):
         "efe_mlp_backward": [C.POINTER(MlpShape), vp, vp, i64, vp, vp, vp, vp, i32, vp],
         "efe_wmse": [vp, vp, vp, i64, vp, PD, i32, vp],
         "efe_adam": [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, i32, i32, vp],
+        "efe_autotune": [vp, i32, i32, C.POINTER(C.c_int32), PD],
+        "efe_batch_create": [C.POINTER(vp), i32, C.POINTER(vp)],
+        "efe_batch_destroy": [vp],
+        "efe_batch_last_error": [vp],
+        "efe_batch_graph_nodes": [vp, P64, P64],
+        "efe_batch_chfsi_step": [vp, C.POINTER(vp), P64, C.POINTER(C.c_int32), i32, PD, PD, PD, i32, i32, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = (C.c_char_p if name == "efe_last_error" else
+        f.restype = (C.c_char_p if name in ("efe_last_error", "efe_batch_last_error") else
                      C.c_int64 if name in ("efe_mlp_param_count", "efe_mlp_work_elems", "efe_mlp_scratch_elems")
                      else C.c_int)
     return lib
@@ -436,6 +443,13 @@ class System:
                                                  C.c_void_p(y.data_ptr()), PREC[precision], self._stream()))
         return y
 
+    def autotune(self, N, precision="tf32x3"):
+        """Pick the tensor-core cell kernel's column tile for N columns; returns (tile, ms per tile)."""
+        t = C.c_int32()
+        ms = np.zeros(3)
+        self._check(self.L.efe_autotune(self.h, int(N), PREC[precision], C.byref(t), _dptr(ms)))
+        return t.value, ms
+
     def set_fp64_engine(self, engine):
         """0: FP64 DFMA products; 1 (or "tensor"): FP64-grade products on the BF16 tensor cores."""
         e = {"dfma": 0, "tensor": 1}.get(engine, engine)
@@ -531,3 +545,49 @@ class Mlp:
                                   C.c_void_p(self.m.data_ptr()), C.c_void_p(self.v.data_ptr()), self.n_params,
                                   float(lr), float(b1), float(b2), float(eps), self.t, PREC[self.prec],
                                   self._stream()), "efe_adam")
+
+
+class Batch:
+    """Independent systems whose ChFSI filter steps run as one CUDA graph."""
+
+    def __init__(self, systems):
+        self.L = lib()
+        self.systems = list(systems)
+        arr = (C.c_void_p * len(self.systems))(*[s.h.value for s in self.systems])
+        b = C.c_void_p()
+        rc = self.L.efe_batch_create(arr, len(self.systems), C.byref(b))
+        self.b = b
+        if rc != EFE_OK:
+            msg = self.L.efe_batch_last_error(b).decode() if b.value else "efe_batch_create failed"
+            self.close()
+            raise EfeError(rc, msg)
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            self.L.efe_batch_destroy(self.b)
+            self.b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def chfsi_step(self, Xs, m, a, b, a0, precision="fp64", fp64_tail=0, graph=True):
+        import torch
+        n = len(self.systems)
+        ptr = (C.c_void_p * n)(*[X.data_ptr() for X in Xs])
+        ld = np.array([X.stride(0) for X in Xs], dtype=np.int64)
+        N = np.array([X.shape[1] for X in Xs], dtype=np.int32)
+        av, bv, a0v = (np.ascontiguousarray(v, dtype=np.float64) for v in (a, b, a0))
+        rc = self.L.efe_batch_chfsi_step(self.b, ptr, ld.ctypes.data_as(C.POINTER(C.c_int64)),
+                                         N.ctypes.data_as(C.POINTER(C.c_int32)), int(m), _dptr(av), _dptr(bv),
+                                         _dptr(a0v), PREC[precision], int(fp64_tail), int(bool(graph)),
+                                         C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if rc != EFE_OK:
+            raise EfeError(rc, self.L.efe_batch_last_error(self.b).decode())
+
+    def graph_nodes(self):
+        a, k = C.c_int64(), C.c_int64()
+        self.L.efe_batch_graph_nodes(self.b, C.byref(a), C.byref(k))
+        return a.value, k.value

@@ -51,12 +51,14 @@ struct efe_handle {
   float* Hcc32 = nullptr;
   float *As1 = nullptr, *As2 = nullptr;  // TF32 split images of H^cc_e (chunk-major)
   int tc_mode = 0;          // 1: TF32 tcgen05 cell products, 2: 3-term split TF32 (FP32-grade)
+  int tc_tile = 0, tc_tile_N = 0;  // autotuned column tile of the tensor-core cell kernel for N
   int n_sm = 148;
   int fp64_engine = 0;      // 0: FP64 DFMA products; 1: FP64-grade products on the BF16 tensor cores
   int* hexp = nullptr;      // per-cell row exponents of H^cc_e (tensor-core FP64 products)
   int* oz_fexp = nullptr;   // per-column exponents (N)
   int* oz_bexp = nullptr;   // per-column exponents of small right-hand matrices (N)
   int* oz_aexp = nullptr;   // per-row exponents of tall left-hand matrices (rows)
+  int2* oz_pairs = nullptr; // tile pairs of the tensor-core A^T B products
   bool time_this = false;   // the cell-apply timer records only the filter's mixed-precision launches
   DevFunc* funcs = nullptr;
   int32_t *enr_cells = nullptr, *cf_ptr = nullptr, *cf_idx = nullptr;
@@ -89,7 +91,18 @@ struct efe_handle {
   int Nres32 = 0, ld32 = 0, npc = 0, ncb = 0;
   float *Yf[3] = {nullptr, nullptr, nullptr}, *Wf = nullptr, *cpart = nullptr;
   float *mecT32 = nullptr, *hecT32 = nullptr;
+  // dense FP32 tiles of the pattern over blocks of pattern nodes (mixed filter)
+  int64_t cb_nblk = 0, cb_nslots = 0;
+  int64_t *cb_slot_off = nullptr, *cb_pos = nullptr;
+  int32_t* cb_slots = nullptr;
+  float *tileH = nullptr, *tileM = nullptr;
   double* Ye[3] = {nullptr, nullptr, nullptr};
+  // Chebyshev coefficients {alpha, c, beta} per degree: pinned host staging and device copy
+  double* coefh = nullptr;
+  double* coefd = nullptr;
+  int coef_cap = 0;
+  cudaEvent_t coef_ev = nullptr;
+  bool coef_pending = false;
   // self-consistent field (Sec. V): quadrature leaves, Hartree operator, SCF state
   int64_t n_leaf = 0;
   int leaf_nmax = 1;
@@ -204,8 +217,10 @@ int reserve(efe_handle* h, int N) {
   TRY(dalloc(h, &h->rpart, ((R + 2047) / 2048 + 1) * (int64_t)N));
   dfree(h, h->oz_fexp);
   dfree(h, h->oz_bexp);
+  dfree(h, h->oz_pairs);
   TRY(dalloc(h, &h->oz_fexp, N));
   TRY(dalloc(h, &h->oz_bexp, N));
+  TRY(dalloc(h, &h->oz_pairs, oz_gram_max_pairs(N, N)));
   h->Nres = N;
   return EFE_OK;
 }
@@ -225,7 +240,8 @@ int reserve32(efe_handle* h, int N) {
   }
   TRY(dalloc(h, &h->Wf, h->n_nodes * ld));
   CK(cudaMemset(h->Wf, 0, sizeof(float) * h->n_nodes * ld));
-  h->npc = (int)std::max<int64_t>(32, (h->n_tn + 4 * h->n_sm - 1) / (4 * h->n_sm));
+  // node blocks per CTA of the coupling kernels: about four CTAs per SM
+  h->npc = (int)std::max<int64_t>(1, (h->cb_nblk + 4 * h->n_sm - 1) / (4 * h->n_sm));
   h->ncb = coup_nblocks(std::max<int64_t>(1, h->n_tn), h->npc);
   TRY(dalloc(h, &h->cpart, (int64_t)h->ncb * std::max<int64_t>(1, h->nE) * N));
   h->ld32 = ld;
@@ -307,7 +323,7 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
     } else {
       if (tc) {
         if (launch_cell_tc3(h->As1, h->As2, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N,
-                            h->tc_mode == 2, h->n_sm, h->info + 4, st)) {
+                            h->tc_mode == 2, h->n_sm, h->info + 4, st, h->tc_tile_N == N ? h->tc_tile : 0)) {
           h->err = "tensor-core cell kernel needs 16-byte aligned rows";
           return EFE_ERR_ARG;
         }
@@ -395,16 +411,16 @@ int apply_Minv_impl(efe_handle* h, const double* X, int64_t ldx, int N, double* 
 
 // --- one filter degree in FP64: Ynew = alpha (H~ Ycur - c Ycur) + beta Yprev ---
 int degree_f64(efe_handle* h, const double* Yc, int64_t ldc, const double* Yp, int64_t ldp, double* Yn, int64_t ldn,
-               double alpha, double cc, double beta, int N, cudaStream_t st) {
+               const double* coef, int N, cudaStream_t st) {
   const int64_t nn = h->n_nodes;
   double* Wc = h->W;
   double* We = h->W + nn * N;
   TRY(apply_H_generic<double>(h, Yc, ldc, Yc + nn * ldc, ldc, Wc, N, We, N, N, st, h->Hcc));
   TRY(minv_core<double>(h, Wc, N, We, N, N, st));
-  launch_cheb_combine<double>(nn, h->Dinv, Wc, N, Yc, ldc, Yp, ldp, Yn, ldn, alpha, cc, beta, N, st);
+  launch_cheb_combine<double>(nn, h->Dinv, Wc, N, Yc, ldc, Yp, ldp, Yn, ldn, coef, N, st);
   if (h->nE > 0)
     launch_cheb_combine<double>(h->nE, nullptr, h->xe, N, Yc + nn * ldc, ldc, Yp ? Yp + nn * ldp : nullptr, ldp,
-                                Yn + nn * ldn, ldn, alpha, cc, beta, N, st);
+                                Yn + nn * ldn, ldn, coef, N, st);
   CKL();
   return EFE_OK;
 }
@@ -413,7 +429,7 @@ int degree_f64(efe_handle* h, const double* Yc, int64_t ldc, const double* Yp, i
 // Classical rows use the padded leading dimension ld32; the enrichment
 // coupling runs node-major with FP32 products and FP64 cross-block sums.
 int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Yp, const double* Ype, float* Yn,
-               double* Yne, double alpha, double cc, double beta, int N, cudaStream_t st) {
+               double* Yne, const double* coef, int N, cudaStream_t st) {
   const int64_t nn = h->n_nodes;
   const int ld = h->ld32;
   double* We = h->W;  // nE x N FP64 scratch
@@ -423,20 +439,20 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
   h->time_this = false;
   if (h->nE > 0) {
     const int nE = (int)h->nE;
-    if ((int64_t)nE * N * 4 <= 160 * 1024 && h->kmax <= 64) {
-      launch_coup_cols<float>(h->n_tn, h->npc, h->t_nodes, h->t_ptr, h->t_col, h->hecT32, 1.f, Yce, N, nE, N, h->Wf,
-                              ld, st);
-      launch_coup_rows<float>(h->n_tn, h->npc, h->t_nodes, h->t_ptr, h->t_col, h->hecT32, nullptr, Yc, ld, nE, N,
-                              h->cpart, st);
+    if (coup_smem(nE, N, true) <= 200 * 1024) {
+      launch_coup_cols<float>(h->n_tn, h->npc, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, 1.f, Yce, N, nE,
+                              N, h->Wf, ld, st);
+      launch_coup_rows<float>(h->n_tn, h->npc, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, nullptr, Yc, ld,
+                              nE, N, h->cpart, st);
       launch_coup_reduce(h->ncb, nE, N, h->cpart, 1.0, nullptr, 0, 0.0, We, N, st);
       launch_gemm_nn(nE, N, nE, 1.0, h->Hee, nE, Yce, N, 1.0, We, N, st);
       // block-wise inverse: r = We - M^ec D^-1 Wc, x_e = S^-1 r, Wc -= M^ec^T x_e
-      launch_coup_rows<float>(h->n_tn, h->npc, h->t_nodes, h->t_ptr, h->t_col, h->mecT32, h->Dinv, h->Wf, ld, nE, N,
-                              h->cpart, st);
+      launch_coup_rows<float>(h->n_tn, h->npc, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, h->Dinv, h->Wf,
+                              ld, nE, N, h->cpart, st);
       launch_coup_reduce(h->ncb, nE, N, h->cpart, -1.0, We, N, 1.0, h->rb, N, st);
       launch_gemm_nn(nE, N, nE, 1.0, h->Sinv, nE, h->rb, N, 0.0, h->xe, N, st);
-      launch_coup_cols<float>(h->n_tn, h->npc, h->t_nodes, h->t_ptr, h->t_col, h->mecT32, -1.f, h->xe, N, nE, N,
-                              h->Wf, ld, st);
+      launch_coup_cols<float>(h->n_tn, h->npc, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, -1.f, h->xe, N,
+                              nE, N, h->Wf, ld, st);
     } else {
       launch_spmm_nodes<float>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->hecT, 1.0, Yce, N, h->Wf, ld, N, st);
       launch_spmm_segments<float>(h->nseg, h->seg_start, h->seg_end, h->ec_col, h->hec, nullptr, Yc, ld, h->part, N,
@@ -446,8 +462,8 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
       TRY(minv_core<float>(h, h->Wf, ld, We, N, N, st));
     }
   }
-  launch_cheb_combine_f4(nn, ld, h->Dinv, h->Wf, Yc, Yp, Yn, alpha, cc, beta, st);
-  if (h->nE > 0) launch_cheb_combine<double>(h->nE, nullptr, h->xe, N, Yce, N, Ype, N, Yne, N, alpha, cc, beta, N, st);
+  launch_cheb_combine_f4(nn, ld, h->Dinv, h->Wf, Yc, Yp, Yn, coef, st);
+  if (h->nE > 0) launch_cheb_combine<double>(h->nE, nullptr, h->xe, N, Yce, N, Ype, N, Yne, N, coef, N, st);
   CKL();
   return EFE_OK;
 }
@@ -964,6 +980,39 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
     launch_permute(h->nnz, h->mec, h->t_perm, h->mecT, 0);
     launch_to_f32(h->mecT, h->mecT32, h->nnz, 0);
     CKL();
+    {
+      // blocks of consecutive pattern nodes: their function slots and the tile
+      // position of every pattern entry
+      const int B = coup_block_nodes();
+      const int64_t nblk = (h->n_tn + B - 1) / B;
+      std::vector<int64_t> soff(nblk + 1, 0), pos(h->nnz);
+      std::vector<int32_t> slots;
+      std::vector<int32_t> fs;
+      for (int64_t b = 0; b < nblk; ++b) {
+        const int64_t r0 = b * B, r1 = std::min<int64_t>(h->n_tn, r0 + B);
+        fs.assign(s.t_col.begin() + s.t_ptr[r0], s.t_col.begin() + s.t_ptr[r1]);
+        std::sort(fs.begin(), fs.end());
+        fs.erase(std::unique(fs.begin(), fs.end()), fs.end());
+        for (int64_t r = r0; r < r1; ++r)
+          for (int64_t q = s.t_ptr[r]; q < s.t_ptr[r + 1]; ++q) {
+            const int64_t k = std::lower_bound(fs.begin(), fs.end(), s.t_col[q]) - fs.begin();
+            pos[q] = (soff[b] + k) * B + (r - r0);
+          }
+        slots.insert(slots.end(), fs.begin(), fs.end());
+        soff[b + 1] = soff[b] + (int64_t)fs.size();
+      }
+      h->cb_nblk = nblk;
+      h->cb_nslots = soff[nblk];
+      TRY(upload(h, &h->cb_slot_off, soff));
+      TRY(upload(h, &h->cb_slots, slots));
+      TRY(upload(h, &h->cb_pos, pos));
+      TRY(dalloc(h, &h->tileM, h->cb_nslots * B));
+      TRY(dalloc(h, &h->tileH, h->cb_nslots * B));
+      CK(cudaMemset(h->tileM, 0, sizeof(float) * h->cb_nslots * B));
+      CK(cudaMemset(h->tileH, 0, sizeof(float) * h->cb_nslots * B));
+      launch_tile_scatter(h->nnz, h->cb_pos, h->mecT32, h->tileM, 0);
+      CKL();
+    }
     TRY(upload(h, &h->Mee, s.Mee));
     TRY(upload(h, &h->Hee_kin, s.Hee_kin));
     TRY(dalloc(h, &h->Hee, h->nE * h->nE));
@@ -978,6 +1027,9 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
 int efe_destroy(efe_handle* h) {
   if (!h) return EFE_OK;
   cudaSetDevice(h->dev);
+  if (h->coef_ev) cudaEventSynchronize(h->coef_ev);
+  if (h->coefh) cudaFreeHost(h->coefh);
+  if (h->coef_ev) cudaEventDestroy(h->coef_ev);
   for (void* p : h->allocs) cudaFree(p);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -1038,6 +1090,7 @@ int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
     launch_gather_sum(h->nnz, h->hec_kin, h->ec_cptr, h->ec_cidx, h->Pblk, h->hec, st);
     launch_permute(h->nnz, h->hec, h->t_perm, h->hecT, st);
     launch_to_f32(h->hecT, h->hecT32, h->nnz, st);
+    launch_tile_scatter(h->nnz, h->cb_pos, h->hecT32, h->tileH, st);
     launch_gather_sum(h->nE * h->nE, h->Hee_kin, h->ee_cptr, h->ee_cidx, h->Qblk, h->Hee, st);
     launch_symmetrize(h->Hee, (int)h->nE, (int)h->nE, st);
     CKL();
@@ -1174,9 +1227,63 @@ int efe_upper_bound(efe_handle* h, const double* v0, int32_t k, double* b_out, v
   return EFE_OK;
 }
 
-int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, double a, double b, double a0,
-                   int32_t precision, int32_t fp64_tail, void* stream) {
-  if (!h) return EFE_ERR_ARG;
+// Scaled three-term recurrence coefficients of degrees 1..m (Sec. V):
+// Y_k = alpha_k (H~ Y_{k-1} - c Y_{k-1}) + beta_k Y_{k-2}.
+static void fill_coefs(double* out, int m, double a, double b, double a0) {
+  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+  const double s1 = e / (a0 - c);
+  double sig = s1;
+  for (int k = 1; k <= m; ++k) {
+    double al, be;
+    if (k == 1) {
+      al = s1 / e;
+      be = 0.0;
+    } else {
+      const double sn = 1.0 / (2.0 / s1 - sig);
+      al = 2.0 * sn / e;
+      be = -sig * sn;
+      sig = sn;
+    }
+    out[3 * (k - 1)] = al;
+    out[3 * (k - 1) + 1] = c;
+    out[3 * (k - 1) + 2] = be;
+  }
+}
+
+// Stage the recurrence coefficients of the m degrees ({alpha, c, beta} each) in
+// pinned host memory and copy them to the device.  Outside a graph capture the
+// previous copy is waited for first, so the staging buffer is never rewritten
+// while a copy reads it; inside a capture the copy becomes a graph node that
+// reads the staging buffer at every launch (the caller refreshes it).
+static int stage_coefs(efe_handle* h, int m, double a, double b, double a0, cudaStream_t st, bool in_graph) {
+  if (m > h->coef_cap) {
+    if (in_graph) {
+      h->err = "coefficient buffers must exist before a graph capture";
+      return EFE_ERR_STATE;
+    }
+    if (h->coef_ev) CK(cudaEventSynchronize(h->coef_ev));
+    if (h->coefh) cudaFreeHost(h->coefh);
+    dfree(h, h->coefd);
+    h->coefh = nullptr;
+    CK(cudaMallocHost(&h->coefh, sizeof(double) * 3 * m));
+    TRY(dalloc(h, &h->coefd, 3 * (int64_t)m));
+    h->coef_cap = m;
+    if (!h->coef_ev) CK(cudaEventCreateWithFlags(&h->coef_ev, cudaEventDisableTiming));
+  }
+  if (!in_graph && h->coef_pending) CK(cudaEventSynchronize(h->coef_ev));
+  fill_coefs(h->coefh, m, a, b, a0);
+  CK(cudaMemcpyAsync(h->coefd, h->coefh, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, st));
+  if (!in_graph) {
+    CK(cudaEventRecord(h->coef_ev, st));
+    h->coef_pending = true;
+  }
+  return EFE_OK;
+}
+
+// Enqueue one ChFSI filter step on `st` without any host synchronisation
+// (graph-capturable when in_graph and the workspaces already exist).
+static int chfsi_enqueue(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, double a, double b,
+                         double a0, int32_t precision, int32_t fp64_tail, cudaStream_t st, bool in_graph) {
   TRY(check_block(h, X, ldx, N));
   if (m < 1 || !(b > a) || !(a > a0) || !is_finite_d(a) || !is_finite_d(b) || !is_finite_d(a0) || fp64_tail < 0) {
     h->err = "bad filter parameters (need m >= 1, a0 < a < b, finite)";
@@ -1187,26 +1294,18 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
     h->err = "precision mode not available in this build";
     return EFE_ERR_ARG;
   }
-  TRY(set_dev(h));
-  TRY(reserve(h, N));
-  cudaStream_t st = S(stream);
-  const int64_t nn = h->n_nodes;
-  const double e = 0.5 * (b - a), c = 0.5 * (b + a);
-  const double s1 = e / (a0 - c);
-  double sig = s1;
-  // coefficients of degree k (1-based): Ynew = alpha (H~ Ycur - c Ycur) + beta Yprev
-  auto coef = [&](int k, double* alpha, double* beta) {
-    if (k == 1) {
-      *alpha = s1 / e;
-      *beta = 0.0;
-      return;
-    }
-    const double sn = 1.0 / (2.0 / s1 - sig);
-    *alpha = 2.0 * sn / e;
-    *beta = -sig * sn;
-    sig = sn;
-  };
   const int n_low = (precision == EFE_PREC_FP64) ? 0 : std::max(0, m - fp64_tail);
+  if (in_graph) {
+    if (N > h->Nres || (n_low > 0 && N > h->Nres32)) {
+      h->err = "workspaces must be reserved before a graph capture";
+      return EFE_ERR_STATE;
+    }
+  } else {
+    TRY(reserve(h, N));
+    if (n_low > 0) TRY(reserve32(h, N));
+  }
+  TRY(stage_coefs(h, m, a, b, a0, st, in_graph));
+  const int64_t nn = h->n_nodes;
   h->tc_mode = (precision == EFE_PREC_TF32) ? 1 : (precision == EFE_PREC_TF32X3 ? 2 : 0);
   CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
   // FP64 buffers: slot 0 = X (user, ldx), 1 = B1, 2 = B2 (ld = N)
@@ -1215,18 +1314,15 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
   int prev = -1, cur = 0;
   int k = 1;
   if (n_low > 0) {
-    TRY(reserve32(h, N));
     // load Y_0 into the low-precision buffers
     launch_f64_to_f32_rows(nn, X, ldx, h->Yf[0], h->ld32, N, st);
     if (h->nE > 0) launch_copy_rows(h->nE, X + nn * ldx, ldx, h->Ye[0], N, N, st);
     CKL();
     int p32 = -1, c32 = 0;
     for (; k <= n_low; ++k) {
-      double al, be;
-      coef(k, &al, &be);
       const int nx = (c32 + 1) % 3 == p32 ? (c32 + 2) % 3 : (c32 + 1) % 3;
       TRY(degree_f32(h, h->Yf[c32], h->Ye[c32], p32 >= 0 ? h->Yf[p32] : nullptr, p32 >= 0 ? h->Ye[p32] : nullptr,
-                     h->Yf[nx], h->Ye[nx], al, c, be, N, st));
+                     h->Yf[nx], h->Ye[nx], h->coefd + 3 * (k - 1), N, st));
       p32 = c32;
       c32 = nx;
     }
@@ -1242,12 +1338,10 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
     CKL();
   }
   for (; k <= m; ++k) {
-    double al, be;
-    coef(k, &al, &be);
     int nx = 0;
     while (nx == cur || nx == prev) ++nx;
     TRY(degree_f64(h, buf[cur], ld[cur], prev >= 0 ? buf[prev] : nullptr, prev >= 0 ? ld[prev] : 0, buf[nx], ld[nx],
-                   al, c, be, N, st));
+                   h->coefd + 3 * (k - 1), N, st));
     prev = cur;
     cur = nx;
   }
@@ -1255,15 +1349,28 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
     launch_copy_rows(h->rows, buf[cur], ld[cur], X, ldx, N, st);
     CKL();
   }
-  if ((n_low > 0 && h->tc_mode) || h->fp64_engine == 1) {
-    int flag = 0;
-    CK(cudaMemcpyAsync(&flag, h->info + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (flag) {
-      h->err = "tensor-core cell kernel: bounded mbarrier wait ran out";
-      return EFE_ERR_TIMEOUT;
-    }
+  return EFE_OK;
+}
+
+static int chfsi_check_flags(efe_handle* h, cudaStream_t st) {
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, h->info + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flag) {
+    h->err = "tensor-core kernel: bounded mbarrier wait ran out";
+    return EFE_ERR_TIMEOUT;
   }
+  return EFE_OK;
+}
+
+int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, double a, double b, double a0,
+                   int32_t precision, int32_t fp64_tail, void* stream) {
+  if (!h) return EFE_ERR_ARG;
+  TRY(set_dev(h));
+  cudaStream_t st = S(stream);
+  TRY(chfsi_enqueue(h, X, ldx, N, m, a, b, a0, precision, fp64_tail, st, false));
+  const int n_low = (precision == EFE_PREC_FP64) ? 0 : std::max(0, m - fp64_tail);
+  if ((n_low > 0 && h->tc_mode) || h->fp64_engine == 1) TRY(chfsi_check_flags(h, st));
   return EFE_OK;
 }
 
@@ -1278,6 +1385,24 @@ int gemm_tall(efe_handle* h, int64_t rows, int N, const double* A, int64_t lda, 
   } else {
     launch_gemm_nn(rows, N, N, 1.0, A, lda, B, N, 0.0, C, ldc, st);
   }
+  CKL();
+  return EFE_OK;
+}
+
+// C (N x N) = A^T B for tall A, B (rows x N): FP64 DFMA split-K, or with the
+// tensor-core FP64 engine the sliced A^T B (exponents per column over all rows).
+int gemm_gram(efe_handle* h, int64_t rows, int N, const double* A, int64_t lda, const double* B, int64_t ldb,
+              double* C, bool sym, cudaStream_t st) {
+  if (h->fp64_engine == 1) {
+    launch_oz_colexp(A, lda, rows, N, h->oz_fexp, st);
+    if (B != A) launch_oz_colexp(B, ldb, rows, N, h->oz_bexp, st);
+    if (launch_oz_gram(rows, N, N, A, lda, h->oz_fexp, B, ldb, B != A ? h->oz_bexp : h->oz_fexp, C, N, sym,
+                       h->tnwork, h->tnwork_elems, h->oz_pairs, h->n_sm, h->info + 4, st) == 0) {
+      CKL();
+      return EFE_OK;
+    }
+  }
+  launch_gemm_tn(rows, N, N, A, lda, B, ldb, C, N, h->tnwork, h->tnwork_elems, st, sym);
   CKL();
   return EFE_OK;
 }
@@ -1364,25 +1489,32 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   double *Q = h->B1, *HQ = h->B2, *MQ = h->W;
   int inf[2] = {0, 0};
   // Cholesky-QR: G = X^T X = L L^T, Q = X L^-T
-  launch_gemm_tn(R, N, N, X, ldx, X, ldx, G, N, h->tnwork, h->tnwork_elems, st, true);
+  CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
+  TRY(gemm_gram(h, R, N, X, ldx, X, ldx, G, true, st));
   launch_symmetrize(G, N, N, st);
   launch_chol(G, N, N, h->info, st);
   CKL();
-  CK(cudaMemcpyAsync(inf, h->info, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (inf[0]) {
-    h->err = "Cholesky-QR breakdown: Gram matrix X^T X is not positive definite (rank-deficient block)";
-    return EFE_ERR_CHOL;
+  {
+    int fl[5] = {0, 0, 0, 0, 0};
+    CK(cudaMemcpyAsync(fl, h->info, sizeof(fl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (fl[4]) {
+      h->err = "tensor-core FP64 product: bounded wait ran out";
+      return EFE_ERR_TIMEOUT;
+    }
+    if (fl[0]) {
+      h->err = "Cholesky-QR breakdown: Gram matrix X^T X is not positive definite (rank-deficient block)";
+      return EFE_ERR_CHOL;
+    }
   }
   launch_trinv_lower(G, N, N, Linv, N, st);
   launch_transpose(Linv, N, N, Rinv, N, st);
-  CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
   TRY(gemm_tall(h, R, N, X, ldx, Rinv, Q, N, st));
   // projections
   TRY(apply_H_impl(h, Q, N, N, HQ, N, st));
   TRY(apply_M_impl(h, Q, N, N, MQ, N, st));
-  launch_gemm_tn(R, N, N, Q, N, HQ, N, Hp, N, h->tnwork, h->tnwork_elems, st, true);
-  launch_gemm_tn(R, N, N, Q, N, MQ, N, Mp, N, h->tnwork, h->tnwork_elems, st, true);
+  TRY(gemm_gram(h, R, N, Q, N, HQ, N, Hp, true, st));
+  TRY(gemm_gram(h, R, N, Q, N, MQ, N, Mp, true, st));
   launch_symmetrize(Hp, N, N, st);
   launch_symmetrize(Mp, N, N, st);
   CK(cudaMemcpyAsync(Lm, Mp, sizeof(double) * NN, cudaMemcpyDeviceToDevice, st));
@@ -1953,6 +2085,274 @@ int efe_adam(void* p, const void* g, void* m, void* v, int64_t n, double lr, dou
   else
     launch_adam<double>(n, (double*)p, (const double*)g, (double*)m, (double*)v, lr, beta1, beta2, eps, t, st);
   return cudaGetLastError() == cudaSuccess ? EFE_OK : EFE_ERR_CUDA;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner of the tensor-core cell kernel and batched multi-system filter steps
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int efe_autotune(efe_handle* h, int32_t N, int32_t precision, int32_t* tile_out, double* ms_out) {
+  if (!h || N < 1 || (precision != EFE_PREC_TF32 && precision != EFE_PREC_TF32X3)) return EFE_ERR_ARG;
+  if (!h->potential_set) {
+    h->err = "no potential set (call efe_set_potential first)";
+    return EFE_ERR_STATE;
+  }
+  TRY(set_dev(h));
+  TRY(reserve(h, N));
+  TRY(reserve32(h, N));
+  cudaStream_t st = nullptr;
+  const int64_t nn = h->n_nodes;
+  CK(cudaMemsetAsync(h->Yf[0], 0, sizeof(float) * nn * h->ld32, st));
+  CK(cudaMemsetAsync(h->Wf, 0, sizeof(float) * nn * h->ld32, st));
+  CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
+  int ntile = 0;
+  const int* tiles = tc3_tiles(&ntile);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 0;
+  double best_ms = 1e300;
+  for (int i = 0; i < ntile; ++i) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {  // rep 0 warms up
+      CK(cudaEventRecord(e0, st));
+      for (int c = 0; c < 8; ++c) {
+        const int64_t nc = h->colour_off[c + 1] - h->colour_off[c];
+        if (nc == 0) continue;
+        if (launch_cell_tc3(h->As1, h->As2, h->colour_cells + h->colour_off[c], nc, h->mesh, h->Yf[0], h->ld32, h->Wf,
+                            h->ld32, N, precision == EFE_PREC_TF32X3, h->n_sm, h->info + 4, st, tiles[i])) {
+          h->err = "tensor-core cell kernel needs 16-byte aligned rows";
+          return EFE_ERR_ARG;
+        }
+      }
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      if (rep == 1 || (rep > 1 && t < ms)) ms = t;
+    }
+    if (ms_out) ms_out[i] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = tiles[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int flag = 0;
+  CK(cudaMemcpy(&flag, h->info + 4, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    h->err = "tensor-core cell kernel: bounded mbarrier wait ran out";
+    return EFE_ERR_TIMEOUT;
+  }
+  h->tc_tile = best;
+  h->tc_tile_N = N;
+  if (tile_out) *tile_out = best;
+  return EFE_OK;
+}
+
+}  // extern "C"
+
+struct efe_batch {
+  std::vector<efe_handle*> hs;
+  int dev = 0;
+  cudaStream_t s0 = nullptr;
+  std::vector<cudaStream_t> st;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernel_nodes = 0, nodes = 0;
+  // what the captured graph was recorded for
+  std::vector<double*> X;
+  std::vector<int64_t> ldx;
+  std::vector<int32_t> N;
+  int m = 0, precision = -1, fp64_tail = -1, engine = -1;
+  std::string err;
+};
+
+namespace {
+void batch_clear_graph(efe_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->X.clear();
+}
+}  // namespace
+
+extern "C" {
+
+int efe_batch_create(efe_handle* const* systems, int32_t n, efe_batch** out) {
+  if (!out || !systems || n < 1) return EFE_ERR_ARG;
+  *out = nullptr;
+  efe_batch* b = new (std::nothrow) efe_batch();
+  if (!b) return EFE_ERR_ALLOC;
+  *out = b;
+  b->dev = systems[0]->dev;
+  for (int i = 0; i < n; ++i) {
+    if (!systems[i] || systems[i]->dev != b->dev) {
+      b->err = "batch systems must be valid handles on one device";
+      return EFE_ERR_ARG;
+    }
+    b->hs.push_back(systems[i]);
+  }
+  if (cudaSetDevice(b->dev) != cudaSuccess || cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    b->err = "stream / event creation failed";
+    return EFE_ERR_CUDA;
+  }
+  b->st.resize(n, nullptr);
+  b->join.resize(n, nullptr);
+  for (int i = 0; i < n; ++i)
+    if (cudaStreamCreateWithFlags(&b->st[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess) {
+      b->err = "stream / event creation failed";
+      return EFE_ERR_CUDA;
+    }
+  return EFE_OK;
+}
+
+int efe_batch_destroy(efe_batch* b) {
+  if (!b) return EFE_OK;
+  cudaSetDevice(b->dev);
+  batch_clear_graph(b);
+  for (auto s : b->st)
+    if (s) cudaStreamDestroy(s);
+  for (auto e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->s0) cudaStreamDestroy(b->s0);
+  delete b;
+  return EFE_OK;
+}
+
+const char* efe_batch_last_error(const efe_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+int efe_batch_graph_nodes(const efe_batch* b, int64_t* nodes, int64_t* kernel_nodes) {
+  if (!b) return EFE_ERR_ARG;
+  if (nodes) *nodes = b->nodes;
+  if (kernel_nodes) *kernel_nodes = b->kernel_nodes;
+  return EFE_OK;
+}
+
+int efe_batch_chfsi_step(efe_batch* b, double* const* X, const int64_t* ldx, const int32_t* N, int32_t m,
+                         const double* a, const double* bnd, const double* a0, int32_t precision, int32_t fp64_tail,
+                         int32_t use_graph, void* stream) {
+  if (!b || !X || !ldx || !N || !a || !bnd || !a0 || m < 1) return EFE_ERR_ARG;
+  const int n = (int)b->hs.size();
+  if (cudaSetDevice(b->dev) != cudaSuccess) return EFE_ERR_CUDA;
+  cudaStream_t caller = (cudaStream_t)stream;
+  auto fail = [&](int i, int rc) {
+    b->err = "system " + std::to_string(i) + ": " + b->hs[i]->err;
+    return rc;
+  };
+  if (!use_graph) {
+    for (int i = 0; i < n; ++i) {
+      const int rc = efe_chfsi_step(b->hs[i], X[i], ldx[i], N[i], m, a[i], bnd[i], a0[i], precision, fp64_tail,
+                                    stream);
+      if (rc != EFE_OK) return fail(i, rc);
+    }
+    return EFE_OK;
+  }
+  const int n_low = (precision == EFE_PREC_FP64) ? 0 : std::max(0, m - fp64_tail);
+  // workspaces and coefficient buffers exist before any capture
+  for (int i = 0; i < n; ++i) {
+    efe_handle* h = b->hs[i];
+    int rc = reserve(h, N[i]);
+    if (rc == EFE_OK && n_low > 0) rc = reserve32(h, N[i]);
+    if (rc != EFE_OK) return fail(i, rc);
+    if (h->coef_cap < m) {
+      rc = stage_coefs(h, m, a[i], bnd[i], a0[i], caller, false);
+      if (rc != EFE_OK) return fail(i, rc);
+    }
+    if (h->coef_pending) cudaEventSynchronize(h->coef_ev);
+    h->coef_pending = false;
+  }
+  bool same = b->exec && b->m == m && b->precision == precision && b->fp64_tail == fp64_tail &&
+              (int)b->X.size() == n && b->engine == b->hs[0]->fp64_engine;
+  for (int i = 0; same && i < n; ++i) same = b->X[i] == X[i] && b->ldx[i] == ldx[i] && b->N[i] == N[i];
+  if (!same) {
+    batch_clear_graph(b);
+    const int64_t l0 = g_launches.load();
+    std::vector<bool> timing(n);
+    for (int i = 0; i < n; ++i) {
+      timing[i] = b->hs[i]->timing;
+      b->hs[i]->timing = false;
+    }
+    if (cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      b->err = "cudaStreamBeginCapture failed";
+      return EFE_ERR_CUDA;
+    }
+    int rc = EFE_OK, bad = -1;
+    cudaEventRecord(b->fork, b->s0);
+    for (int i = 0; i < n && rc == EFE_OK; ++i) {
+      cudaStreamWaitEvent(b->st[i], b->fork, 0);
+      rc = chfsi_enqueue(b->hs[i], X[i], ldx[i], N[i], m, a[i], bnd[i], a0[i], precision, fp64_tail, b->st[i], true);
+      if (rc != EFE_OK) bad = i;
+      cudaEventRecord(b->join[i], b->st[i]);
+      cudaStreamWaitEvent(b->s0, b->join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(b->s0, &graph);
+    for (int i = 0; i < n; ++i) b->hs[i]->timing = timing[i];
+    g_launches.store(l0);  // capture records, it does not launch
+    if (rc != EFE_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(bad, rc);
+    }
+    if (ce != cudaSuccess || !graph) {
+      cudaGetLastError();
+      b->err = std::string("graph capture failed: ") + cudaGetErrorString(ce);
+      return EFE_ERR_CUDA;
+    }
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int64_t nk = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      b->exec = nullptr;
+      b->err = std::string("graph instantiation failed: ") + cudaGetErrorString(ie);
+      return EFE_ERR_CUDA;
+    }
+    b->nodes = (int64_t)nn;
+    b->kernel_nodes = nk;
+    b->X.assign(X, X + n);
+    b->ldx.assign(ldx, ldx + n);
+    b->N.assign(N, N + n);
+    b->m = m;
+    b->precision = precision;
+    b->fp64_tail = fp64_tail;
+    b->engine = b->hs[0]->fp64_engine;
+  }
+  // refresh the staged coefficients (read by the graph's copy nodes), then replay
+  for (int i = 0; i < n; ++i) {
+    fill_coefs(b->hs[i]->coefh, m, a[i], bnd[i], a0[i]);
+    b->hs[i]->tc_mode = (precision == EFE_PREC_TF32) ? 1 : (precision == EFE_PREC_TF32X3 ? 2 : 0);
+  }
+  if (cudaStreamSynchronize(caller) != cudaSuccess || cudaGraphLaunch(b->exec, b->s0) != cudaSuccess) {
+    cudaGetLastError();
+    b->err = "graph launch failed";
+    return EFE_ERR_CUDA;
+  }
+  g_launches += b->kernel_nodes;
+  if (cudaStreamSynchronize(b->s0) != cudaSuccess) {
+    b->err = "graph execution failed";
+    return EFE_ERR_CUDA;
+  }
+  for (int i = 0; i < n; ++i) {
+    const int rc = chfsi_check_flags(b->hs[i], b->s0);
+    if (rc != EFE_OK) return fail(i, rc);
+  }
+  return EFE_OK;
 }
 
 }  // extern "C"

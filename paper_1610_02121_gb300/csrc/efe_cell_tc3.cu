@@ -30,19 +30,21 @@ namespace {
 
 constexpr int T3_M = 128, T3_K = 128, T3_KC = 32, T3_NCH = 4;
 constexpr int T3_STAGES = 2;
-constexpr int T3_TW = 160;                 // column tile
+// column tile (template parameter TW of the kernel): 64, 96 or 160, picked per
+// system and N by the autotuner (efe_autotune); 160 by default
 constexpr int T3_THREADS = 512;
 constexpr int T3_CONV_WARP0 = 2, T3_CONV_WARPS = 6;
 constexpr int T3_EPI_WARP0 = 8, T3_EPI_WARPS = 8;
 constexpr uint32_t T3_TMEM_COLS = 512;     // accumulators at columns 0 and 256
 constexpr long long T3_WAIT = 2000000000LL;
 
+template <int TW>
 struct T3Layout {
   // stage: A1 | A2 | B1 | B2 | Braw      (bytes)
   static constexpr uint32_t A = T3_M * T3_KC * 4;           // 16 KB
-  static constexpr uint32_t B = T3_TW * T3_KC * 4;          // 20 KB
-  static constexpr uint32_t RAW = T3_KC * T3_TW * 4;        // 20 KB
-  static constexpr uint32_t STAGE = 2 * A + 2 * B + RAW;    // 92 KB
+  static constexpr uint32_t B = TW * T3_KC * 4;             // 20 KB at TW = 160
+  static constexpr uint32_t RAW = T3_KC * TW * 4;           // 20 KB at TW = 160
+  static constexpr uint32_t STAGE = 2 * A + 2 * B + RAW;    // 92 KB at TW = 160
   static constexpr uint32_t BARS = T3_STAGES * STAGE;       // barrier area offset
   static constexpr size_t TOTAL = (size_t)BARS + 256;
 };
@@ -120,7 +122,7 @@ __device__ __forceinline__ uint32_t cmo(int row, int k) {
   return (uint32_t)(row >> 3) * 1024u + (uint32_t)(k >> 2) * 128u + (uint32_t)(row & 7) * 16u;
 }
 
-template <bool SPLIT>
+template <bool SPLIT, int TW>
 __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restrict__ A1g, const float* __restrict__ A2g,
                                                             const int32_t* __restrict__ cells, int64_t ncells,
                                                             MeshDev m, const float* __restrict__ Y, int64_t ldy,
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
   if (tid == 0) s_skip = *(volatile int*)err;
   __syncthreads();
   if (s_skip) return;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + T3Layout::BARS);  // [2]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + T3Layout<TW>::BARS);  // [2]
   uint64_t* conv = full + 2;                                          // [2]
   uint64_t* empty = full + 4;                                         // [2]
   uint64_t* accf = full + 6;                                          // [2]
@@ -172,8 +174,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
     for (int64_t t = 0; t < my_items && !*abort_flag; ++t) {
       const int64_t item = blockIdx.x + t * gridDim.x;
       const int64_t e = cells[item / ntiles];
-      const int c0 = (int)(item % ntiles) * T3_TW;
-      const int ncol = min(T3_TW, N - c0);
+      const int c0 = (int)(item % ntiles) * TW;
+      const int ncol = min(TW, N - c0);
       const uint32_t row_bytes = (uint32_t)((ncol + 3) / 4) * 16u;
       for (int kc = 0; kc < T3_NCH; ++kc) {
         const int64_t ch = t * T3_NCH + kc;
@@ -182,18 +184,18 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
           if (lane == 0) { *abort_flag = 1; atomicExch(err, 1); }
           break;
         }
-        unsigned char* S = sm + s * T3Layout::STAGE;
+        unsigned char* S = sm + s * T3Layout<TW>::STAGE;
         const int nrows = min(T3_KC, NL - kc * T3_KC);
         if (lane == 0)
-          bar_expect_tx(full + s, (SPLIT ? 2u : 1u) * T3Layout::A + (uint32_t)nrows * row_bytes);
+          bar_expect_tx(full + s, (SPLIT ? 2u : 1u) * T3Layout<TW>::A + (uint32_t)nrows * row_bytes);
         __syncwarp();
         if (lane == 0) {
-          bulk_g2s(S, A1g + (e * T3_NCH + kc) * (T3_M * T3_KC), T3Layout::A, full + s);
-          if (SPLIT) bulk_g2s(S + T3Layout::A, A2g + (e * T3_NCH + kc) * (T3_M * T3_KC), T3Layout::A, full + s);
+          bulk_g2s(S, A1g + (e * T3_NCH + kc) * (T3_M * T3_KC), T3Layout<TW>::A, full + s);
+          if (SPLIT) bulk_g2s(S + T3Layout<TW>::A, A2g + (e * T3_NCH + kc) * (T3_M * T3_KC), T3Layout<TW>::A, full + s);
         }
         if (lane < nrows) {
           const int64_t g = cell_node(m, e, kc * T3_KC + lane);
-          bulk_g2s(S + 2 * T3Layout::A + 2 * T3Layout::B + (uint32_t)lane * (T3_TW * 4), Y + g * ldy + c0, row_bytes,
+          bulk_g2s(S + 2 * T3Layout<TW>::A + 2 * T3Layout<TW>::B + (uint32_t)lane * (TW * 4), Y + g * ldy + c0, row_bytes,
                    full + s);
         }
         __syncwarp();
@@ -203,8 +205,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
     // ------------------------------------------------------------ MMA issuer
     for (int64_t t = 0; t < my_items && !*abort_flag; ++t) {
       const int64_t item = blockIdx.x + t * gridDim.x;
-      const int c0 = (int)(item % ntiles) * T3_TW;
-      const int ncol = min(T3_TW, N - c0);
+      const int c0 = (int)(item % ntiles) * TW;
+      const int ncol = min(TW, N - c0);
       const int nmma = ((ncol + 15) / 16) * 16;
       const int b = (int)(t & 1);
       bool ok = true;
@@ -217,8 +219,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) break;
         if (lane == 0) {
-          unsigned char* S = sm + s * T3Layout::STAGE;
-          const uint32_t a1 = su32(S), a2 = a1 + T3Layout::A, b1 = a1 + 2 * T3Layout::A, b2 = b1 + T3Layout::B;
+          unsigned char* S = sm + s * T3Layout<TW>::STAGE;
+          const uint32_t a1 = su32(S), a2 = a1 + T3Layout<TW>::A, b1 = a1 + 2 * T3Layout<TW>::A, b2 = b1 + T3Layout<TW>::B;
           const uint32_t d = tmem + (uint32_t)(b * 256);
           const uint32_t id = idesc_tf32(nmma);
 #pragma unroll
@@ -245,8 +247,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
     const int ct = tid - T3_CONV_WARP0 * 32;
     for (int64_t t = 0; t < my_items && !*abort_flag; ++t) {
       const int64_t item = blockIdx.x + t * gridDim.x;
-      const int c0 = (int)(item % ntiles) * T3_TW;
-      const int ncol = min(T3_TW, N - c0);
+      const int c0 = (int)(item % ntiles) * TW;
+      const int ncol = min(TW, N - c0);
       const int nmma = ((ncol + 15) / 16) * 16;
       bool ok = true;
       for (int kc = 0; kc < T3_NCH; ++kc) {
@@ -254,10 +256,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
         const int s = (int)(ch % T3_STAGES);
         ok = bar_wait(full + s, (uint32_t)((ch / T3_STAGES) & 1));
         if (!ok) break;
-        unsigned char* S = sm + s * T3Layout::STAGE;
-        const float* raw = reinterpret_cast<const float*>(S + 2 * T3Layout::A + 2 * T3Layout::B);
-        unsigned char* B1 = S + 2 * T3Layout::A;
-        unsigned char* B2 = B1 + T3Layout::B;
+        unsigned char* S = sm + s * T3Layout<TW>::STAGE;
+        const float* raw = reinterpret_cast<const float*>(S + 2 * T3Layout<TW>::A + 2 * T3Layout<TW>::B);
+        unsigned char* B1 = S + 2 * T3Layout<TW>::A;
+        unsigned char* B2 = B1 + T3Layout<TW>::B;
         const int nrows = min(T3_KC, NL - kc * T3_KC);
         for (int v = ct; v < nmma * 8; v += T3_CONV_WARPS * 32) {
           const int n = v % nmma, kq = v / nmma;
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int kr = kq * 4 + q;
-            y[q] = (kr < nrows && n < ncol) ? raw[kr * T3_TW + n] : 0.f;
+            y[q] = (kr < nrows && n < ncol) ? raw[kr * TW + n] : 0.f;
           }
           float4 h4, l4;
           h4.x = tf32r(y[0]); h4.y = tf32r(y[1]); h4.z = tf32r(y[2]); h4.w = tf32r(y[3]);
@@ -293,8 +295,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
     for (int64_t t = 0; t < my_items && !*abort_flag; ++t) {
       const int64_t item = blockIdx.x + t * gridDim.x;
       const int64_t e = cells[item / ntiles];
-      const int c0 = (int)(item % ntiles) * T3_TW;
-      const int ncol = min(T3_TW, N - c0);
+      const int c0 = (int)(item % ntiles) * TW;
+      const int ncol = min(TW, N - c0);
       const int b = (int)(t & 1);
       if (!bar_wait(accf + b, (uint32_t)((t / 2) & 1))) {
         *abort_flag = 1;
@@ -387,22 +389,44 @@ void launch_build_asplit(const double* Hcc, int64_t n_cell, float* A1, float* A2
 
 // W += H_e Y_e over the cells of one colour.  Y / W: FP32 rows, ld a multiple of 4
 // elements and rows 16-byte aligned (the bulk copies need 16-byte sizes and addresses).
-int launch_cell_tc3(const float* A1, const float* A2, const int32_t* cells, int64_t ncells, const MeshDev& m,
-                    const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
-                    cudaStream_t st) {
-  if (ncells <= 0 || N <= 0) return 0;
-  if ((ldy & 3) || (ldw & 3)) return 1;
-  const int ntiles = (N + T3_TW - 1) / T3_TW;
+namespace {
+template <int TW>
+void tc3_launch(const float* A1, const float* A2, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
+                cudaStream_t st) {
+  const int ntiles = (N + TW - 1) / TW;
   const int64_t items = ncells * ntiles;
   const unsigned grid = (unsigned)(items < n_sm ? items : n_sm);
-  const size_t smem = T3Layout::TOTAL;
+  const size_t smem = T3Layout<TW>::TOTAL;
   if (split) {
-    cudaFuncSetAttribute(k_cell_tc3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cell_tc3<true><<<grid, T3_THREADS, smem, st>>>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err);
+    cudaFuncSetAttribute(k_cell_tc3<true, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cell_tc3<true, TW><<<grid, T3_THREADS, smem, st>>>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err);
   } else {
-    cudaFuncSetAttribute(k_cell_tc3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cell_tc3<false><<<grid, T3_THREADS, smem, st>>>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err);
+    cudaFuncSetAttribute(k_cell_tc3<false, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cell_tc3<false, TW><<<grid, T3_THREADS, smem, st>>>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err);
   }
+}
+}  // namespace
+
+const int* tc3_tiles(int* count) {
+  static const int tiles[3] = {64, 96, 160};
+  *count = 3;
+  return tiles;
+}
+
+int launch_cell_tc3(const float* A1, const float* A2, const int32_t* cells, int64_t ncells, const MeshDev& m,
+                    const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
+                    cudaStream_t st, int tile) {
+  if (ncells <= 0 || N <= 0) return 0;
+  if ((ldy & 3) || (ldw & 3)) return 1;
+  if (tile == 64)
+    tc3_launch<64>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
+  else if (tile == 96)
+    tc3_launch<96>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
+  else if (tile == 160 || tile == 0)
+    tc3_launch<160>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
+  else
+    return 1;
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return 0;
 }

@@ -191,13 +191,15 @@ __global__ void k_seg_reduce(int nrows, const int64_t* __restrict__ row_seg_ptr,
   out[(int64_t)r * ldo + c] = v;
 }
 
+// coef = {alpha, c, beta} of this degree, read from device memory (so a captured
+// graph of the filter stays valid when the filter bounds change)
 template <typename T>
 __global__ void k_cheb_combine(int64_t nrows, const double* __restrict__ rowscale, const T* __restrict__ X,
                                int64_t ldx, const T* __restrict__ Yc, int64_t ldc, const T* __restrict__ Yp,
-                               int64_t ldp, T* __restrict__ Yn, int64_t ldn, double alpha, double cc, double beta,
-                               int N) {
+                               int64_t ldp, T* __restrict__ Yn, int64_t ldn, const double* __restrict__ coef, int N) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= nrows * N) return;
+  const double alpha = coef[0], cc = coef[1], beta = coef[2];
   const int64_t r = idx / N;
   const int c = (int)(idx % N);
   double x = (double)X[r * ldx + c];
@@ -280,60 +282,88 @@ __global__ void __launch_bounds__(256) k_cell_apply_narrow(const T* __restrict__
 }
 
 // Node-major enrichment products (FP32 arithmetic, mixed-precision filter).
-// Nodes are processed in chunks of CH: the chunk's slice of the pattern
-// (function ids and values) is staged in shared memory, then every thread
-// (one vector column) issues the chunk's CH independent row loads before it
-// uses them, so many loads are in flight per thread.
-constexpr int CPL_CH = 32;           // nodes per chunk
-constexpr int CPL_QMAX = CPL_CH * 64; // pattern entries per chunk (<= 64 functions per node)
+// The pattern nodes (the nodes that meet a support) form blocks of CPB
+// consecutive nodes.  The functions touching a block are few (neighbouring
+// nodes lie in the same supports); for each block the set-up lists them
+// ("slots") and the values of H^ec and M^ec are kept as dense FP32 tiles
+// (slots x CPB, slot-major), so a block's product is a small dense GEMM (4 x 4
+// register tiles) over contiguous tile data, and each vector row is read once.
+constexpr int CPB = 32;     // nodes per block
+constexpr int CPF = 64;     // slots per GEMM pass (more: further passes)
 
-// Rows product: part[b][a][c] = sum over the nodes g of CTA b of
-//   sum_{a in pattern(g)} val[g, a] * scale[g] * X[g][c]
-// with the (n_E x N) accumulator in shared memory, so each vector row is read
-// once however many enrichment supports contain its node.
+// tile[pos[q]] = val[q]   (tiles zeroed beforehand)
+__global__ void k_tile_scatter(int64_t nnz, const int64_t* __restrict__ pos, const float* __restrict__ val,
+                               float* __restrict__ tile) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < nnz) tile[pos[q]] = val[q];
+}
+
+// Rows product: part[b][a][c] = sum over the blocks of CTA b of
+//   sum_u tile[slot][u] * scale[g_u] * X[g_u][c]  accumulated at a = f(slot),
+// in a CTA-private (n_E x N) shared-memory array.
 template <typename T>
-__global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, int npc, const int32_t* __restrict__ t_nodes,
-                                                   const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_col,
-                                                   const float* __restrict__ tval, const double* __restrict__ scale,
-                                                   const T* __restrict__ X, int64_t ldx, int nE, int N,
-                                                   float* __restrict__ part) {
-  extern __shared__ float acc[];
-  __shared__ int64_t sg[CPL_CH];
-  __shared__ float ss[CPL_CH];
-  __shared__ int sp[CPL_CH + 1];
-  __shared__ int scol[CPL_QMAX];
-  __shared__ float sval[CPL_QMAX];
+__global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, int bpc, const int32_t* __restrict__ t_nodes,
+                                                   const int64_t* __restrict__ slot_off,
+                                                   const int32_t* __restrict__ slots, const float* __restrict__ tile,
+                                                   const double* __restrict__ scale, const T* __restrict__ X,
+                                                   int64_t ldx, int nE, int N, float* __restrict__ part) {
+  extern __shared__ __align__(16) float smf[];
+  const int ldy = N + 4;
+  float* acc = smf;                                  // nE x N
+  float* Ys = acc + (size_t)nE * N;                  // CPB x ldy
+  float* Ps = Ys + CPB * ldy;                        // CPF x CPB
+  __shared__ int sf[CPF];
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int i = tid; i < nE * N; i += bd) acc[i] = 0.f;
-  const int64_t r0 = (int64_t)blockIdx.x * npc;
-  const int64_t r1 = min(n_tn, r0 + npc);
-  for (int64_t rc = r0; rc < r1; rc += CPL_CH) {
-    const int nn = (int)min((int64_t)CPL_CH, r1 - rc);
-    const int64_t qa = t_ptr[rc];
+  const int64_t nblk = (n_tn + CPB - 1) / CPB;
+  const int64_t b0 = (int64_t)blockIdx.x * bpc, b1 = min(nblk, b0 + bpc);
+  const int ncb = (N + 3) / 4;
+  for (int64_t bb = b0; bb < b1; ++bb) {
+    const int64_t r0 = bb * CPB;
+    const int nb = (int)min((int64_t)CPB, n_tn - r0);
     __syncthreads();
-    if (tid < nn) {
-      const int64_t g = t_nodes[rc + tid];
-      sg[tid] = g;
-      ss[tid] = scale ? (float)scale[g] : 1.f;
+    for (int i = tid; i < CPB * ldy; i += bd) {
+      const int u = i / ldy, c = i % ldy;
+      float v = 0.f;
+      if (u < nb && c < N) {
+        const int64_t g = t_nodes[r0 + u];
+        v = (float)X[g * ldx + c];
+        if (scale) v *= (float)scale[g];
+      }
+      Ys[i] = v;
     }
-    if (tid <= nn) sp[tid] = (int)(t_ptr[rc + tid] - qa);
-    const int nq = (int)(t_ptr[rc + nn] - qa);
-    for (int q = tid; q < nq; q += bd) {
-      scol[q] = t_col[qa + q];
-      sval[q] = tval[qa + q];
-    }
-    __syncthreads();
-    for (int c = tid; c < N; c += bd) {
-      float xv[CPL_CH];
+    const int64_t s0 = slot_off[bb], s1 = slot_off[bb + 1];
+    for (int64_t sp = s0; sp < s1; sp += CPF) {
+      const int nf = (int)min((int64_t)CPF, s1 - sp);
+      __syncthreads();
+      for (int i = tid; i < CPF * CPB; i += bd) Ps[i] = (i < nf * CPB) ? tile[sp * CPB + i] : 0.f;
+      if (tid < nf) sf[tid] = slots[sp + tid];
+      __syncthreads();
+      const int nsb = (nf + 3) / 4;
+      for (int t = tid; t < nsb * ncb; t += bd) {
+        const int sb = t / ncb, cb = t % ncb;
+        float r[4][4] = {};
+#pragma unroll 8
+        for (int u = 0; u < CPB; ++u) {
+          float pv[4], yv[4];
 #pragma unroll
-      for (int u = 0; u < CPL_CH; ++u) xv[u] = (u < nn) ? (float)X[sg[u] * ldx + c] : 0.f;
+          for (int i = 0; i < 4; ++i) pv[i] = Ps[(sb * 4 + i) * CPB + u];
 #pragma unroll
-      for (int u = 0; u < CPL_CH; ++u) {
-        if (u >= nn) break;
-        const float x = ss[u] * xv[u];
-        // each accumulator address (a, c) belongs to thread c alone: plain
-        // read-modify-write, in program order (deterministic)
-        for (int q = sp[u]; q < sp[u + 1]; ++q) acc[scol[q] * N + c] += sval[q] * x;
+          for (int j = 0; j < 4; ++j) yv[j] = Ys[u * ldy + cb * 4 + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) r[i][j] = fmaf(pv[i], yv[j], r[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int sl = sb * 4 + i;
+          if (sl >= nf) break;
+          float* ar = acc + (size_t)sf[sl] * N;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (cb * 4 + j < N) ar[cb * 4 + j] += r[i][j];
+        }
       }
     }
   }
@@ -356,53 +386,69 @@ __global__ void k_coup_reduce(int nb, int nE, int N, const float* __restrict__ p
   out[(int64_t)a * ldo + c] = v;
 }
 
-// Columns product: W[g][c] += sgn * sum_{a in pattern(g)} val[g, a] * Xe[a][c], Xe staged in
-// shared memory as FP32.
+// Columns product: W[g_u][c] += sgn * sum_slot tile[slot][u] * Xe[f(slot)][c]
+// (Xe staged in shared memory as FP32), same block tiles.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_coup_cols(int64_t n_tn, int npc, const int32_t* __restrict__ t_nodes,
-                                                   const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_col,
-                                                   const float* __restrict__ tval, float sgn,
-                                                   const double* __restrict__ Xe, int64_t ldxe, int nE, int N,
-                                                   T* __restrict__ W, int64_t ldw) {
-  extern __shared__ float xs[];
-  __shared__ int64_t sg[CPL_CH];
-  __shared__ int sp[CPL_CH + 1];
-  __shared__ int scol[CPL_QMAX];
-  __shared__ float sval[CPL_QMAX];
+__global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, int bpc, const int32_t* __restrict__ t_nodes,
+                                                   const int64_t* __restrict__ slot_off,
+                                                   const int32_t* __restrict__ slots, const float* __restrict__ tile,
+                                                   float sgn, const double* __restrict__ Xe, int64_t ldxe, int nE,
+                                                   int N, T* __restrict__ W, int64_t ldw) {
+  extern __shared__ __align__(16) float smf[];
+  float* xs = smf;                                   // nE x N
+  float* Ps = xs + (size_t)nE * N;                   // CPF x CPB
+  __shared__ int sf[CPF];
+  __shared__ int64_t sg[CPB];
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int i = tid; i < nE * N; i += bd) xs[i] = (float)Xe[(int64_t)(i / N) * ldxe + i % N];
-  const int64_t r0 = (int64_t)blockIdx.x * npc;
-  const int64_t r1 = min(n_tn, r0 + npc);
-  for (int64_t rc = r0; rc < r1; rc += CPL_CH) {
-    const int nn = (int)min((int64_t)CPL_CH, r1 - rc);
-    const int64_t qa = t_ptr[rc];
+  const int64_t nblk = (n_tn + CPB - 1) / CPB;
+  const int64_t b0 = (int64_t)blockIdx.x * bpc, b1 = min(nblk, b0 + bpc);
+  const int ncb = (N + 3) / 4;
+  for (int64_t bb = b0; bb < b1; ++bb) {
+    const int64_t r0 = bb * CPB;
+    const int nb = (int)min((int64_t)CPB, n_tn - r0);
+    const int64_t s0 = slot_off[bb], s1 = slot_off[bb + 1];
+    // thread t owns output tile (4 nodes x 4 columns); results summed over the slot passes
+    const int ntile = (CPB / 4) * ncb;
+    float r[2][4][4] = {};
     __syncthreads();
-    if (tid < nn) sg[tid] = t_nodes[rc + tid];
-    if (tid <= nn) sp[tid] = (int)(t_ptr[rc + tid] - qa);
-    const int nq = (int)(t_ptr[rc + nn] - qa);
-    for (int q = tid; q < nq; q += bd) {
-      scol[q] = t_col[qa + q];
-      sval[q] = tval[qa + q];
-    }
-    __syncthreads();
-    // NL_LANES node lanes x column threads: every (node, column) is written by one thread
-    constexpr int NLN = 4;
-    const int cthreads = bd / NLN;
-    const int lane_n = tid / cthreads, ct = tid % cthreads;
-    for (int c = ct; c < N; c += cthreads) {
-      float wv[CPL_CH / NLN];
+    if (tid < nb) sg[tid] = t_nodes[r0 + tid];
+    for (int64_t sp = s0; sp < s1; sp += CPF) {
+      const int nf = (int)min((int64_t)CPF, s1 - sp);
+      __syncthreads();
+      for (int i = tid; i < CPF * CPB; i += bd) Ps[i] = (i < nf * CPB) ? tile[sp * CPB + i] : 0.f;
+      if (tid < nf) sf[tid] = slots[sp + tid];
+      __syncthreads();
+      for (int k = 0; k < 2; ++k) {
+        const int t = tid + k * bd;
+        if (t >= ntile) break;
+        const int ub = t / ncb, cb = t % ncb;
+        for (int sl = 0; sl < nf; ++sl) {
+          const float* xr = xs + (size_t)sf[sl] * N + cb * 4;
+          float pv[4], xv[4];
 #pragma unroll
-      for (int v = 0; v < CPL_CH / NLN; ++v) {
-        const int u = v * NLN + lane_n;
-        wv[v] = (u < nn) ? (float)W[sg[u] * ldw + c] : 0.f;
+          for (int i = 0; i < 4; ++i) pv[i] = Ps[sl * CPB + ub * 4 + i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) xv[j] = (cb * 4 + j < N) ? xr[j] : 0.f;
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) r[k][i][j] = fmaf(pv[i], xv[j], r[k][i][j]);
+        }
       }
+    }
+    for (int k = 0; k < 2; ++k) {
+      const int t = tid + k * bd;
+      if (t >= ntile) break;
+      const int ub = t / ncb, cb = t % ncb;
 #pragma unroll
-      for (int v = 0; v < CPL_CH / NLN; ++v) {
-        const int u = v * NLN + lane_n;
-        if (u >= nn) break;
-        float s = 0.f;
-        for (int q = sp[u]; q < sp[u + 1]; ++q) s = fmaf(sval[q], xs[scol[q] * N + c], s);
-        W[sg[u] * ldw + c] = (T)(wv[v] + sgn * s);
+      for (int i = 0; i < 4; ++i) {
+        const int u = ub * 4 + i;
+        if (u >= nb) break;
+        T* wr = W + sg[u] * ldw + cb * 4;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (cb * 4 + j < N) wr[j] = (T)((float)wr[j] + sgn * r[k][i][j]);
       }
     }
   }
@@ -411,10 +457,11 @@ __global__ void __launch_bounds__(1024) k_coup_cols(int64_t n_tn, int npc, const
 // Chebyshev combine on 16-byte aligned FP32 rows (ld multiple of 4): four columns per thread.
 __global__ void k_cheb_combine_f4(int64_t nrows, int ld4, const double* __restrict__ rowscale,
                                   const float4* __restrict__ X, const float4* __restrict__ Yc,
-                                  const float4* __restrict__ Yp, float4* __restrict__ Yn, float alpha, float cc,
-                                  float beta) {
+                                  const float4* __restrict__ Yp, float4* __restrict__ Yn,
+                                  const double* __restrict__ coef) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= nrows * ld4) return;
+  const float alpha = (float)coef[0], cc = (float)coef[1], beta = (float)coef[2];
   const int64_t r = idx / ld4;
   const float sc = rowscale ? (float)rowscale[r] : 1.f;
   const float4 x = X[idx], y = Yc[idx];
@@ -892,19 +939,17 @@ void launch_seg_reduce(int nrows, const int64_t* row_seg_ptr, const double* part
 
 template <typename T>
 void launch_cheb_combine(int64_t nrows, const double* rowscale, const T* Xsrc, int64_t ldx, const T* Ycur,
-                         int64_t ldc, const T* Yprev, int64_t ldp, T* Ynew, int64_t ldn, double alpha, double c,
-                         double beta, int N, cudaStream_t st) {
+                         int64_t ldc, const T* Yprev, int64_t ldp, T* Ynew, int64_t ldn, const double* coef, int N,
+                         cudaStream_t st) {
   if (nrows <= 0 || N <= 0) return;
   k_cheb_combine<T><<<grid1(nrows * N, 256), 256, 0, st>>>(nrows, rowscale, Xsrc, ldx, Ycur, ldc, Yprev, ldp, Ynew,
-                                                           ldn, alpha, c, beta, N);
+                                                           ldn, coef, N);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 template void launch_cheb_combine<double>(int64_t, const double*, const double*, int64_t, const double*, int64_t,
-                                          const double*, int64_t, double*, int64_t, double, double, double, int,
-                                          cudaStream_t);
+                                          const double*, int64_t, double*, int64_t, const double*, int, cudaStream_t);
 template void launch_cheb_combine<float>(int64_t, const double*, const float*, int64_t, const float*, int64_t,
-                                         const float*, int64_t, float*, int64_t, double, double, double, int,
-                                         cudaStream_t);
+                                         const float*, int64_t, float*, int64_t, const double*, int, cudaStream_t);
 
 template <typename T>
 void launch_row_scale(int64_t nrows, const double* rowscale, const T* X, int64_t ldx, T* Y, int64_t ldy, int N,
@@ -1077,18 +1122,34 @@ void launch_cell_apply_narrow_f32(const float* Hcc, const int32_t* cells, int64_
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-int coup_nblocks(int64_t n_tn, int npc) { return (int)((n_tn + npc - 1) / npc); }
+int coup_nblocks(int64_t n_tn, int bpc) {
+  const int64_t nblk = (n_tn + CPB - 1) / CPB;
+  return (int)((nblk + bpc - 1) / bpc);
+}
+
+int coup_block_nodes() { return CPB; }
+
+// shared memory of the node-major kernels: the (n_E x N) array, the rows
+// kernel's CPB x (N + 4) vector tile and one CPF x CPB pattern tile
+size_t coup_smem(int nE, int N, bool rows) {
+  return sizeof(float) * ((size_t)nE * N + (rows ? (size_t)CPB * (N + 4) : 0) + (size_t)CPF * CPB);
+}
+
+void launch_tile_scatter(int64_t nnz, const int64_t* pos, const float* val, float* tile, cudaStream_t st) {
+  if (nnz <= 0) return;
+  k_tile_scatter<<<grid1(nnz, 256), 256, 0, st>>>(nnz, pos, val, tile);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 template <typename T>
-void launch_coup_rows(int64_t n_tn, int npc, const int32_t* t_nodes, const int64_t* t_ptr, const int32_t* t_col,
-                      const float* tval, const double* scale, const T* X, int64_t ldx, int nE, int N, float* part,
+void launch_coup_rows(int64_t n_tn, int bpc, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
+                      const float* tile, const double* scale, const T* X, int64_t ldx, int nE, int N, float* part,
                       cudaStream_t st) {
   if (n_tn <= 0 || N <= 0 || nE <= 0) return;
-  const int nb = coup_nblocks(n_tn, npc);
-  const int t = N >= 256 ? 256 : (N < 64 ? 64 : ((N + 31) / 32) * 32);
-  const size_t smem = sizeof(float) * (size_t)nE * N;
+  const int nb = coup_nblocks(n_tn, bpc);
+  const size_t smem = coup_smem(nE, N, true);
   cudaFuncSetAttribute(k_coup_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_coup_rows<T><<<nb, t, smem, st>>>(n_tn, npc, t_nodes, t_ptr, t_col, tval, scale, X, ldx, nE, N, part);
+  k_coup_rows<T><<<nb, 256, smem, st>>>(n_tn, bpc, t_nodes, slot_off, slots, tile, scale, X, ldx, nE, N, part);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 template void launch_coup_rows<float>(int64_t, int, const int32_t*, const int64_t*, const int32_t*, const float*,
@@ -1102,28 +1163,25 @@ void launch_coup_reduce(int nb, int nE, int N, const float* part, double sgn, co
 }
 
 template <typename T>
-void launch_coup_cols(int64_t n_tn, int npc, const int32_t* t_nodes, const int64_t* t_ptr, const int32_t* t_col,
-                      const float* tval, float sgn, const double* Xe, int64_t ldxe, int nE, int N, T* W, int64_t ldw,
+void launch_coup_cols(int64_t n_tn, int bpc, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
+                      const float* tile, float sgn, const double* Xe, int64_t ldxe, int nE, int N, T* W, int64_t ldw,
                       cudaStream_t st) {
   if (n_tn <= 0 || N <= 0 || nE <= 0) return;
-  const int nb = coup_nblocks(n_tn, npc);
-  const int tc = N >= 256 ? 256 : (N < 64 ? 64 : ((N + 31) / 32) * 32);
-  const int t = 4 * tc;  // four node lanes
-  const size_t smem = sizeof(float) * (size_t)nE * N;
+  const int nb = coup_nblocks(n_tn, bpc);
+  const size_t smem = coup_smem(nE, N, false);
   cudaFuncSetAttribute(k_coup_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_coup_cols<T><<<nb, t, smem, st>>>(n_tn, npc, t_nodes, t_ptr, t_col, tval, sgn, Xe, ldxe, nE, N, W, ldw);
+  k_coup_cols<T><<<nb, 256, smem, st>>>(n_tn, bpc, t_nodes, slot_off, slots, tile, sgn, Xe, ldxe, nE, N, W, ldw);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 template void launch_coup_cols<float>(int64_t, int, const int32_t*, const int64_t*, const int32_t*, const float*,
                                       float, const double*, int64_t, int, int, float*, int64_t, cudaStream_t);
 
 void launch_cheb_combine_f4(int64_t nrows, int ld, const double* rowscale, const float* X, const float* Yc,
-                            const float* Yp, float* Yn, double alpha, double c, double beta, cudaStream_t st) {
+                            const float* Yp, float* Yn, const double* coef, cudaStream_t st) {
   if (nrows <= 0) return;
   const int ld4 = ld / 4;
   k_cheb_combine_f4<<<grid1(nrows * ld4, 256), 256, 0, st>>>(nrows, ld4, rowscale, (const float4*)X,
-                                                            (const float4*)Yc, (const float4*)Yp, (float4*)Yn,
-                                                            (float)alpha, (float)c, (float)beta);
+                                                            (const float4*)Yc, (const float4*)Yp, (float4*)Yn, coef);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 

@@ -47,20 +47,25 @@ void launch_cell_apply_narrow_f64(const double* Hcc, const int32_t* cells, int64
                                   const double* Y, int64_t ldy, double* W, int64_t ldw, int N, cudaStream_t st);
 void launch_cell_apply_narrow_f32(const float* Hcc, const int32_t* cells, int64_t ncells, const MeshDev& m,
                                   const float* Y, int64_t ldy, float* W, int64_t ldw, int N, cudaStream_t st);
-// node-major enrichment products with FP32 arithmetic (mixed-precision filter)
-int coup_nblocks(int64_t n_tn, int npc);
+// node-major enrichment products with FP32 arithmetic (mixed-precision filter) over
+// blocks of coup_block_nodes() pattern nodes: slot_off / slots list the functions of
+// every block, tile holds the values as dense (slots x block) FP32 tiles
+int coup_nblocks(int64_t n_tn, int bpc);   // CTAs for bpc blocks per CTA
+int coup_block_nodes();
+size_t coup_smem(int nE, int N, bool rows);
+void launch_tile_scatter(int64_t nnz, const int64_t* pos, const float* val, float* tile, cudaStream_t st);
 template <typename T>
-void launch_coup_rows(int64_t n_tn, int npc, const int32_t* t_nodes, const int64_t* t_ptr, const int32_t* t_col,
-                      const float* tval, const double* scale, const T* X, int64_t ldx, int nE, int N, float* part,
+void launch_coup_rows(int64_t n_tn, int bpc, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
+                      const float* tile, const double* scale, const T* X, int64_t ldx, int nE, int N, float* part,
                       cudaStream_t st);
 void launch_coup_reduce(int nb, int nE, int N, const float* part, double sgn, const double* base, int64_t ldb,
                         double alpha_base, double* out, int64_t ldo, cudaStream_t st);
 template <typename T>
-void launch_coup_cols(int64_t n_tn, int npc, const int32_t* t_nodes, const int64_t* t_ptr, const int32_t* t_col,
-                      const float* tval, float sgn, const double* Xe, int64_t ldxe, int nE, int N, T* W, int64_t ldw,
+void launch_coup_cols(int64_t n_tn, int bpc, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
+                      const float* tile, float sgn, const double* Xe, int64_t ldxe, int nE, int N, T* W, int64_t ldw,
                       cudaStream_t st);
 void launch_cheb_combine_f4(int64_t nrows, int ld, const double* rowscale, const float* X, const float* Yc,
-                            const float* Yp, float* Yn, double alpha, double c, double beta, cudaStream_t st);
+                            const float* Yp, float* Yn, const double* coef, cudaStream_t st);
 // out[node_r] += sgn * sum_q val[q] * Xe[col[q]]   (rows = nodes that meet a support)
 template <typename T>
 void launch_spmm_nodes(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
@@ -75,11 +80,12 @@ void launch_spmm_segments(int64_t nseg, const int64_t* seg_start, const int64_t*
 void launch_seg_reduce(int nrows, const int64_t* row_seg_ptr, const double* part, double sgn,
                        const double* base, int64_t ldb, double alpha_base, double* out, int64_t ldo, int N,
                        cudaStream_t st);
-// Chebyshev combine: Ynew = alpha (x - c Ycur) + beta Yprev, x = scale_row * Xsrc
+// Chebyshev combine: Ynew = alpha (x - c Ycur) + beta Yprev, x = scale_row * Xsrc, with
+// coef = {alpha, c, beta} in device memory
 template <typename T>
 void launch_cheb_combine(int64_t nrows, const double* rowscale, const T* Xsrc, int64_t ldx, const T* Ycur,
-                         int64_t ldc, const T* Yprev, int64_t ldp, T* Ynew, int64_t ldn, double alpha, double c,
-                         double beta, int N, cudaStream_t st);
+                         int64_t ldc, const T* Yprev, int64_t ldp, T* Ynew, int64_t ldn, const double* coef, int N,
+                         cudaStream_t st);
 template <typename T>
 void launch_row_scale(int64_t nrows, const double* rowscale, const T* X, int64_t ldx, T* Y, int64_t ldy, int N,
                       cudaStream_t st);
@@ -95,9 +101,11 @@ void launch_zero_rows_f32(int64_t nrows, float* X, int64_t ldx, int N, cudaStrea
 // ---- tcgen05 cell products (efe_cell_tc3.cu) ----
 int64_t tc3_image_elems(int64_t n_cell);
 void launch_build_asplit(const double* Hcc, int64_t n_cell, float* A1, float* A2, cudaStream_t st);
+// tile: column tile width (64, 96 or 160; 0 = default 160)
 int launch_cell_tc3(const float* A1, const float* A2, const int32_t* cells, int64_t ncells, const MeshDev& m,
                     const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
-                    cudaStream_t st);
+                    cudaStream_t st, int tile = 0);
+const int* tc3_tiles(int* count);
 
 // ---- FP64-grade products on the BF16 tensor cores (efe_oz.cu) ----
 int64_t oz_hexp_elems(int64_t n_cell);
@@ -109,6 +117,11 @@ int launch_oz_cell(const double* Hcc, const int* hexp, const int32_t* cells, int
                    cudaStream_t st);
 int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, const double* B, int64_t ldb,
                    const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st);
+// C (Na x N) = A^T B, A: K x Na, B: K x N (K large); aexp / bexp per column (launch_oz_colexp)
+int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const int* aexp, const double* B,
+                   int64_t ldb, const int* bexp, double* C, int64_t ldc, bool sym, double* work, int64_t work_elems,
+                   int2* pairs_dev, int n_sm, int* err, cudaStream_t st);
+int oz_gram_max_pairs(int Na, int N);
 
 // ---- dense FP64 ----
 // C[M x Nc] = alpha * A[M x K] B[K x Nc] + beta * C   (row-major, lda/ldb/ldc)

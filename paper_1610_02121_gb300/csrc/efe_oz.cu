@@ -18,13 +18,20 @@
 // Modes:
 //   CELL  W(cell nodes) += H^cc_e Y_e for the cells of one parity colour
 //         (Sec. V, last paragraph; cells of a colour share no node);
-//   ROWS  C = A B for a tall A (rows x K, K <= 144) and a small B (K x N).
+//   ROWS  C = A B for a tall A (rows x K, K <= 144) and a small B (K x N);
+//   GRAM  C = A^T B for tall A, B (K x Na, K x N, K large): items are (tile
+//         pair, K segment); each segment is formed in 256-row groups (exact
+//         FP32 sums for t <= 5) drained into FP64 partial tiles, which a
+//         fixed-order reduction adds up.
 //
 // Warp roles (512 threads): warp 0 issues the MMAs (one elected lane),
 // warps 1-11 slice operands into the shared-memory stage ring (3 stages),
 // warps 12-15 combine the accumulators and write the result.  All waits are
 // bounded (about one second); on timeout the CTA records an error and leaves.
 #include <stdint.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "efe_kernels.h"
 
@@ -131,7 +138,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 struct OzArgs {
-  int mode;                 // 0: CELL, 1: ROWS
+  int mode;                 // 0: CELL, 1: ROWS, 2: GRAM
   // CELL
   const double* H;          // n_cell x 125 x 125
   const int* hexp;          // n_cell x 128 row exponents
@@ -153,7 +160,44 @@ struct OzArgs {
   int64_t ldo;
   int N, ntiles;
   int* err;
+  // GRAM: C = A^T B with A (Kbig x Na, lda), B (Kbig x N, ldb); aexp / fexp per
+  // column of A / B; work items = (tile pair, K segment of seg_len rows);
+  // FP64 partial tiles to part[segment][Na][N]
+  int64_t Kbig, seg_len;
+  int Na, nseg, npairs;
+  const int2* pairs;        // (M tile, N tile) of every item pair
+  double* part;
 };
+
+// work item of a CTA: cell / row block / tile pair and its K range
+struct OzItem {
+  int64_t ia, e, m0, kb;
+  int c0, ncol, nmma, seg;
+};
+
+__device__ __forceinline__ OzItem oz_item(const OzArgs& g, int64_t item) {
+  OzItem it;
+  if (g.mode == 2) {
+    const int64_t pr = item / g.nseg;
+    it.seg = (int)(item % g.nseg);
+    const int2 tp = g.pairs[pr];
+    it.ia = pr;
+    it.e = 0;
+    it.m0 = (int64_t)tp.x * OZ_M;
+    it.c0 = tp.y * OZ_TW;
+    it.kb = (int64_t)it.seg * g.seg_len;
+  } else {
+    it.ia = item / g.ntiles;
+    it.c0 = (int)(item % g.ntiles) * OZ_TW;
+    it.e = (g.mode == 0) ? g.cells[it.ia] : 0;
+    it.m0 = it.ia * OZ_M;
+    it.kb = 0;
+    it.seg = 0;
+  }
+  it.ncol = min(OZ_TW, g.N - it.c0);
+  it.nmma = ((it.ncol + 15) / 16) * 16;
+  return it;
+}
 
 __device__ __forceinline__ int64_t oz_cell_node(const MeshDev& m, int64_t e, int k) {
   const int i = (int)(e % m.nc[0]), j = (int)((e / m.nc[0]) % m.nc[1]), kk = (int)(e / ((int64_t)m.nc[0] * m.nc[1]));
@@ -195,21 +239,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
   const int64_t nA = (g.mode == 0) ? g.ncells : (g.arows + OZ_M - 1) / OZ_M;
-  const int64_t nitems = nA * g.ntiles;
+  const int64_t nitems = (g.mode == 2) ? (int64_t)g.npairs * g.nseg : nA * g.ntiles;
   const int64_t my = nitems > blockIdx.x ? (nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  const int nch = (g.K + OZ_KC - 1) / OZ_KC;
+  // chunks of 16 K per item; the accumulators are drained every gsz chunks
+  // (GRAM: every 256 rows, where the FP32 sums of t <= 5 are still exact)
+  const int nch = (g.mode == 2) ? (int)(g.seg_len / OZ_KC) : (g.K + OZ_KC - 1) / OZ_KC;
+  const int gsz = (g.mode == 2) ? 16 : nch;
+  const int ngrp = nch / gsz;
 
   if (warp == 0) {
     // ---------------------------------------------------------------- MMA issuer
     for (int64_t t = 0; t < my && !*abort_flag; ++t) {
       const int64_t item = blockIdx.x + t * gridDim.x;
-      const int c0 = (int)(item % g.ntiles) * OZ_TW;
-      const int ncol = min(OZ_TW, g.N - c0);
-      const int nmma = ((ncol + 15) / 16) * 16;
+      const OzItem it = oz_item(g, item);
+      const int nmma = it.nmma;
       bool ok = true;
-      if (t >= 1) ok = bar_wait(acce, (uint32_t)((t - 1) & 1));
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       for (int kc = 0; kc < nch && ok; ++kc) {
+        const int64_t gc = t * ngrp + kc / gsz;   // accumulator group counter
+        if (kc % gsz == 0) {
+          if (gc >= 1) ok = bar_wait(acce, (uint32_t)((gc - 1) & 1));
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (!ok) break;
+        }
         const int64_t ch = t * nch + kc;
         const int s = (int)(ch % OZ_STAGES);
         ok = bar_wait(conv + s, (uint32_t)((ch / OZ_STAGES) & 1));
@@ -227,14 +278,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
             for (int i = 1; i < tt; ++i) {
               const int j = tt - i;
               if (i > OZ_S || j > OZ_S) continue;
-              const uint32_t acc = (kc > 0 || !first[a]) ? 1u : 0u;
+              const uint32_t acc = (kc % gsz > 0 || !first[a]) ? 1u : 0u;
               first[a] = false;
               mma_bf16(tmem + (uint32_t)(a * OZ_TW), sdesc(sA + (uint32_t)(i - 1) * OzL::ASL),
                        sdesc(sB + (uint32_t)(j - 1) * OzL::BSL), id, acc);
             }
           }
           mma_commit(empty + s);
-          if (kc == nch - 1) mma_commit(accf);
+          if (kc % gsz == gsz - 1) mma_commit(accf);
         }
         __syncwarp();
       }
@@ -247,12 +298,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
     // ---------------------------------------------------------------- slicers
     const int ct = tid - OZ_CONV_W0 * 32;
     for (int64_t t = 0; t < my && !*abort_flag; ++t) {
-      const int64_t item = blockIdx.x + t * gridDim.x;
-      const int64_t ia = item / g.ntiles;
-      const int c0 = (int)(item % g.ntiles) * OZ_TW;
-      const int ncol = min(OZ_TW, g.N - c0);
-      const int nmma = ((ncol + 15) / 16) * 16;
-      const int64_t e = (g.mode == 0) ? g.cells[ia] : 0;
+      const OzItem it = oz_item(g, blockIdx.x + t * gridDim.x);
+      const int64_t ia = it.ia, e = it.e;
+      const int c0 = it.c0, ncol = it.ncol, nmma = it.nmma;
       bool ok = true;
       for (int kc = 0; kc < nch; ++kc) {
         const int64_t ch = t * nch + kc;
@@ -271,7 +319,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
           const int row = w >> 1, oct = w & 1;        // row of A, or column n of the product
           double x[8];
           int E = -2000;
-          if (isA) {
+          if (g.mode == 2) {
+            const int64_t k0 = it.kb + kc * OZ_KC + oct * 8;
+            if (isA) {
+              const int64_t col = it.m0 + row;
+              if (col < g.Na) E = g.aexp[col];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) x[q] = (col < g.Na && k0 + q < g.Kbig) ? g.A[(k0 + q) * g.lda + col] : 0.0;
+            } else {
+              if (row < ncol) E = g.fexp[c0 + row];
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                x[q] = (row < ncol && k0 + q < g.Kbig) ? g.B[(k0 + q) * g.ldb + c0 + row] : 0.0;
+            }
+          } else if (isA) {
             if (g.mode == 0) {
               E = g.hexp[e * OZ_M + row];
 #pragma unroll
@@ -351,72 +412,81 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
     const int quarter = warp & 3;
     const int r = quarter * 32 + lane;
     for (int64_t t = 0; t < my && !*abort_flag; ++t) {
-      const int64_t item = blockIdx.x + t * gridDim.x;
-      const int64_t ia = item / g.ntiles;
-      const int c0 = (int)(item % g.ntiles) * OZ_TW;
-      const int ncol = min(OZ_TW, g.N - c0);
-      if (!bar_wait(accf, (uint32_t)(t & 1))) {
-        *abort_flag = 1;
-        atomicExch(g.err, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const OzItem it = oz_item(g, blockIdx.x + t * gridDim.x);
+      const int c0 = it.c0, ncol = it.ncol;
       bool live;
       int Er;
       double* orow;
       if (g.mode == 0) {
-        const int64_t e = g.cells[ia];
         live = r < NL;
-        Er = g.hexp[e * OZ_M + r];
-        orow = live ? g.out + oz_cell_node(g.m, e, r) * g.ldo + c0 : nullptr;
-      } else {
-        const int64_t row = ia * OZ_M + r;
+        Er = g.hexp[it.e * OZ_M + r];
+        orow = live ? g.out + oz_cell_node(g.m, it.e, r) * g.ldo + c0 : nullptr;
+      } else if (g.mode == 1) {
+        const int64_t row = it.m0 + r;
         live = row < g.arows;
         Er = live ? g.aexp[row] : 0;
         orow = live ? g.out + row * g.ldo + c0 : nullptr;
+      } else {
+        const int64_t row = it.m0 + r;
+        live = row < g.Na;
+        Er = live ? g.aexp[row] : 0;
+        orow = live ? g.part + ((int64_t)it.seg * g.Na + row) * g.N + c0 : nullptr;
       }
-      for (int cb = 0; cb < ncol; cb += 8) {
-        uint32_t v[OZ_NACC][8];
+      bool stop = false;
+      for (int grp = 0; grp < ngrp; ++grp) {
+        const int64_t gc = t * ngrp + grp;
+        if (!bar_wait(accf, (uint32_t)(gc & 1))) {
+          *abort_flag = 1;
+          atomicExch(g.err, 1);
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // modes 0 and 2 add to what is there (mode 2 from its second group on)
+        const bool add = (g.mode == 0) || (g.mode == 2 && grp > 0);
+        for (int cb = 0; cb < ncol; cb += 8) {
+          uint32_t v[OZ_NACC][8];
 #pragma unroll
-        for (int a = 0; a < OZ_NACC; ++a)
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-              : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
-                "=r"(v[a][6]), "=r"(v[a][7])
-              : "r"(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * OZ_TW + cb))
-              : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (live) {
-          double cur[8];
-          if (g.mode == 0) {
+          for (int a = 0; a < OZ_NACC; ++a)
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
+                  "=r"(v[a][6]), "=r"(v[a][7])
+                : "r"(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * OZ_TW + cb))
+                : "memory");
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (live) {
+            double cur[8];
+            if (add) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) cur[q] = (cb + q < ncol) ? orow[cb + q] : 0.0;
-          }
+              for (int q = 0; q < 8; ++q) cur[q] = (cb + q < ncol) ? orow[cb + q] : 0.0;
+            }
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int n = cb + q;
-            if (n >= ncol) break;
-            float s1, e1, s2, e2, s3, e3;
-            two_sum(__uint_as_float(v[0][q]), __uint_as_float(v[1][q]), s1, e1);
-            two_sum(s1, __uint_as_float(v[2][q]), s2, e2);
-            two_sum(s2, __uint_as_float(v[3][q]), s3, e3);
-            const float lo = ((__uint_as_float(v[4][q]) + e3) + e2) + e1;
-            // exact power-of-two scale built from its bit pattern (normal range), ldexp otherwise
-            const int k2 = Er + g.fexp[c0 + n] - 14;
-            const double sc = (k2 > -1022 && k2 < 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52)
-                                                        : ldexp(1.0, k2);
-            const double val = ((double)s3 + (double)lo) * sc;
-            if (g.mode == 0) orow[n] = cur[q] + val;
-            else orow[n] = val;
+            for (int q = 0; q < 8; ++q) {
+              const int n = cb + q;
+              if (n >= ncol) break;
+              float s1, e1, s2, e2, s3, e3;
+              two_sum(__uint_as_float(v[0][q]), __uint_as_float(v[1][q]), s1, e1);
+              two_sum(s1, __uint_as_float(v[2][q]), s2, e2);
+              two_sum(s2, __uint_as_float(v[3][q]), s3, e3);
+              const float lo = ((__uint_as_float(v[4][q]) + e3) + e2) + e1;
+              // exact power-of-two scale built from its bit pattern (normal range), ldexp otherwise
+              const int k2 = Er + g.fexp[c0 + n] - 14;
+              const double sc = (k2 > -1022 && k2 < 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52)
+                                                          : ldexp(1.0, k2);
+              const double val = ((double)s3 + (double)lo) * sc;
+              orow[n] = add ? cur[q] + val : val;
+            }
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        bar_arrive(acce);
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      bar_arrive(acce);
+      if (stop) break;
     }
   }
   __syncthreads();
-  if (warp == 0 && my > 0 && *abort_flag) bar_wait(accf, (uint32_t)((my - 1) & 1));
+  if (warp == 0 && my > 0 && *abort_flag) bar_wait(accf, (uint32_t)((my * ngrp - 1) & 1));
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -469,7 +539,7 @@ __global__ void k_oz_hexp(const double* __restrict__ H, int64_t n_cell, int* __r
 
 int oz_launch(const OzArgs& a, int n_sm, cudaStream_t st) {
   const int64_t nA = (a.mode == 0) ? a.ncells : (a.arows + OZ_M - 1) / OZ_M;
-  const int64_t items = nA * a.ntiles;
+  const int64_t items = (a.mode == 2) ? (int64_t)a.npairs * a.nseg : nA * a.ntiles;
   if (items <= 0) return 0;
   const unsigned grid = (unsigned)(items < n_sm ? items : n_sm);
   cudaFuncSetAttribute(k_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OzL::TOTAL);
@@ -552,5 +622,84 @@ int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int*
   a.err = err;
   return oz_launch(a, n_sm, st);
 }
+
+// C (Na x N) = A^T B for tall A (K x Na) and B (K x N), FP64-grade: the K rows
+// are cut into segments (work items with the tile pairs), each segment's
+// product is formed in 256-row groups (exact FP32 accumulation) and summed in
+// FP64 into its partial tile; partials are then added in fixed order.  sym:
+// C is symmetric, only tiles that meet the upper triangle are formed and the
+// rest is mirrored.  aexp / bexp: launch_oz_colexp of A and B.  work: at least
+// oz_gram_work_elems doubles; pairs_dev: at least oz_gram_max_pairs int2.
+int64_t oz_gram_segments(int64_t K, int npairs, int n_sm) {
+  int64_t nseg = std::max<int64_t>(1, (2 * (int64_t)n_sm + npairs - 1) / npairs);
+  nseg = std::min<int64_t>(nseg, (K + 255) / 256);
+  return std::max<int64_t>(nseg, 1);
+}
+
+int oz_gram_pairs(int Na, int N, bool sym, int2* pairs_host) {
+  const int mt = (Na + OZ_M - 1) / OZ_M, nt = (N + OZ_TW - 1) / OZ_TW;
+  int np = 0;
+  for (int i = 0; i < mt; ++i)
+    for (int j = 0; j < nt; ++j) {
+      if (sym && i * OZ_M > j * OZ_TW + OZ_TW - 1) continue;   // tile entirely below the diagonal
+      if (pairs_host) pairs_host[np] = make_int2(i, j);
+      ++np;
+    }
+  return np;
+}
+
+namespace {
+__global__ void k_oz_gram_reduce(int nseg, int Na, int N, const double* __restrict__ part, int sym,
+                                 double* __restrict__ C, int64_t ldc) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)Na * N) return;
+  const int i = (int)(idx / N), j = (int)(idx % N);
+  const bool mirror = sym && i > j;
+  const int64_t src = mirror ? (int64_t)j * N + i : idx;
+  double s = 0.0;
+  for (int k = 0; k < nseg; ++k) s += part[(int64_t)k * Na * N + src];
+  C[(int64_t)i * ldc + j] = s;
+}
+}  // namespace
+
+int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const int* aexp, const double* B,
+                   int64_t ldb, const int* bexp, double* C, int64_t ldc, bool sym, double* work, int64_t work_elems,
+                   int2* pairs_dev, int n_sm, int* err, cudaStream_t st) {
+  if (K <= 0 || Na <= 0 || N <= 0) return 0;
+  if (sym && Na != N) return 1;
+  std::vector<int2> pairs(oz_gram_pairs(Na, N, sym, nullptr));
+  const int np = oz_gram_pairs(Na, N, sym, pairs.data());
+  int64_t nseg = oz_gram_segments(K, np, n_sm);
+  while (nseg > 1 && nseg * (int64_t)Na * N > work_elems) --nseg;
+  if (nseg * (int64_t)Na * N > work_elems) return 1;
+  const int64_t seg_len = ((K + nseg - 1) / nseg + 255) / 256 * 256;
+  nseg = (K + seg_len - 1) / seg_len;
+  if (cudaMemcpyAsync(pairs_dev, pairs.data(), sizeof(int2) * np, cudaMemcpyHostToDevice, st) != cudaSuccess) return 1;
+  OzArgs a{};
+  a.mode = 2;
+  a.A = A;
+  a.lda = lda;
+  a.B = B;
+  a.ldb = ldb;
+  a.aexp = aexp;
+  a.fexp = bexp;
+  a.Kbig = K;
+  a.seg_len = seg_len;
+  a.Na = Na;
+  a.N = N;
+  a.nseg = (int)nseg;
+  a.npairs = np;
+  a.pairs = pairs_dev;
+  a.part = work;
+  a.ntiles = (N + OZ_TW - 1) / OZ_TW;
+  a.err = err;
+  if (oz_launch(a, n_sm, st)) return 1;
+  k_oz_gram_reduce<<<(unsigned)(((int64_t)Na * N + 255) / 256), 256, 0, st>>>((int)nseg, Na, N, work, sym ? 1 : 0, C,
+                                                                             ldc);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return 0;
+}
+
+int oz_gram_max_pairs(int Na, int N) { return oz_gram_pairs(Na, N, false, nullptr); }
 
 }  // namespace efe

@@ -48,7 +48,7 @@ def desc_params(offset=None, scale=None):
 
 
 def scf_to_convergence(G, X, rho_in, n_electrons, m, tol_e=1e-6, tol_rho=1e-4, max_it=100, precision="fp64",
-                       fp64_tail=0, **scf_kw):
+                       fp64_tail=0, passes=1, **scf_kw):
     """Run efe_scf_step until |dE| < tol_e and |rho_out - rho_in| < tol_rho.
     Returns (last result, iterations, rho_out)."""
     import torch
@@ -56,7 +56,7 @@ def scf_to_convergence(G, X, rho_in, n_electrons, m, tol_e=1e-6, tol_rho=1e-4, m
     G.scf_init(n_electrons, **scf_kw)
     e_prev, res = None, None
     for it in range(1, max_it + 1):
-        res = G.scf_step(X, rho_in, rho_out, m, precision=precision, fp64_tail=fp64_tail)
+        res = G.scf_step(X, rho_in, rho_out, m, passes=passes, precision=precision, fp64_tail=fp64_tail)
         if e_prev is not None and abs(res["total"] - e_prev) < tol_e and res["drho"] < tol_rho:
             return res, it, rho_out
         e_prev = res["total"]

@@ -118,7 +118,10 @@ def test_learned_start_gain():
     cluster from SAD and from the learned density: both reach the same energy
     (within 1e-5 Ha/atom) and the learned start needs no more SCF iterations."""
     from paper_1610_02121_gb300 import learned as LR
-    m = 12
+    m, passes = 40, 3
+    kw = dict(tol_e=1e-6, tol_rho=1e-5, max_it=120, passes=passes, beta=0.3, n_hist=8)
+    # training densities: 60 SCF iterations (converged or close to it, |rho_out - rho_in| < 1e-3)
+    kw_train = dict(kw, max_it=60)
     train = [W.random_cluster(4, [6, 8], seed=s, h_min=1.2, h_max=4.0, pad=7.0) for s in (11, 12, 13)]
     rows = []
     model = LR.DensityModel(seed=1)
@@ -129,7 +132,8 @@ def test_learned_start_gain():
         N = int(ne / 2) + 10
         X = to_dev(W.initial_block(s, N, seed=1))
         rs = G.sad_density([W.sad_shells(z) for z in s["Z"]], ne)
-        res, its, rho = LR.scf_to_convergence(G, X, rs.clone(), ne, m)
+        res, its, rho = LR.scf_to_convergence(G, X, rs.clone(), ne, m, **kw_train)
+        assert res["drho"] < 1e-3
         D = G.descriptors(LR.desc_params(), precision="fp32")
         raw.append((G, rho, rs, D))
     model.set_standardisation(torch.cat([d for (_, _, _, d) in raw])[::97])
@@ -145,9 +149,12 @@ def test_learned_start_gain():
     ne = float(np.sum(s["Z"]))
     N = int(ne / 2) + 10
     rs = G.sad_density([W.sad_shells(z) for z in s["Z"]], ne)
-    r_sad, it_sad, _ = LR.scf_to_convergence(G, to_dev(W.initial_block(s, N, seed=1)), rs.clone(), ne, m)
+    r_sad, it_sad, _ = LR.scf_to_convergence(G, to_dev(W.initial_block(s, N, seed=1)), rs.clone(), ne, m, **kw)
     r_ml, it_ml, _ = LR.scf_to_convergence(G, to_dev(W.initial_block(s, N, seed=1)), model.start_density(G, rs, ne),
-                                           ne, m)
+                                           ne, m, **kw)
+    print(f"SCF iterations: SAD start {it_sad}, learned start {it_ml}; energies {r_sad['total']:.8f} "
+          f"{r_ml['total']:.8f}; final losses {losses[0]:.4g} -> {losses[-1]:.4g}")
+    assert it_sad < kw["max_it"] and it_ml < kw["max_it"]
     n_atoms = len(s["Z"])
     assert abs(r_sad["total"] - r_ml["total"]) < 1e-5 * n_atoms
     assert it_ml <= it_sad, (it_ml, it_sad)

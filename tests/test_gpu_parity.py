@@ -255,3 +255,25 @@ def test_fp64_tensor_engine_converges(tiny_pair):
         np.testing.assert_allclose(eps[:nconv], ref[:nconv], atol=1e-8)
     finally:
         G.set_fp64_engine("dfma")
+
+
+@pytest.mark.parametrize("which,N", [("tiny", 150), ("hydrogen", 8), ("hydrogen", 40)])
+def test_fp64_tensor_engine_gram(tiny_pair, which, N):
+    """Cholesky-QR and Rayleigh-Ritz with the tensor-core A^T B (K split into
+    segments of 256-row exact groups, FP64 partial tiles, symmetric tiles only
+    above the diagonal) give the DFMA path's Ritz values."""
+    if which == "tiny":
+        G = tiny_pair[1]
+        s = tiny_pair[0].system
+    else:
+        s = W.hydrogen(cells=6, half=10.0, tau=1e-8, max_depth=6)
+        G = gpu_system(s)
+    X = to_dev(W.random_block(s, N, seed=91))
+    G.set_fp64_engine("dfma")
+    e_ref, r_ref = G.rayleigh_ritz(X.clone())
+    G.set_fp64_engine("tensor")
+    try:
+        e, r = G.rayleigh_ritz(X.clone())
+    finally:
+        G.set_fp64_engine("dfma")
+    np.testing.assert_allclose(e, e_ref, rtol=1e-10, atol=1e-10 * np.abs(e_ref).max())
