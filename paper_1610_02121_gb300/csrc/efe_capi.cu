@@ -55,6 +55,8 @@ struct efe_handle {
   int n_sm = 148;
   int fp64_engine = 0;      // 0: FP64 DFMA products; 1: FP64-grade products on the BF16 tensor cores
   int* hexp = nullptr;      // per-cell row exponents of H^cc_e (tensor-core FP64 products)
+  unsigned char* oz_aimg = nullptr;  // pre-sliced BF16 digit images of H^cc_e (made on first use)
+  bool oz_aimg_valid = false;
   int* oz_fexp = nullptr;   // per-column exponents (N)
   int* oz_bexp = nullptr;   // per-column exponents of small right-hand matrices (N)
   int* oz_aexp = nullptr;   // per-row exponents of tall left-hand matrices (rows)
@@ -298,12 +300,17 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
                    bool tc = false) {
   if constexpr (sizeof(T) == 8) {
     if (h->fp64_engine == 1 && N > 8) {
+      if (!h->oz_aimg_valid) {
+        if (!h->oz_aimg) TRY(dalloc(h, &h->oz_aimg, h->n_cell * oz_cell_image_bytes()));
+        launch_oz_preslice(h->Hcc, h->hexp, h->n_cell, h->oz_aimg, st);
+        h->oz_aimg_valid = true;
+      }
       launch_oz_colexp((const double*)Y, ldy, h->n_nodes, N, h->oz_fexp, st);
       for (int c = 0; c < 8; ++c) {
         const int64_t nc = h->colour_off[c + 1] - h->colour_off[c];
         if (nc == 0) continue;
         launch_oz_cell(h->Hcc, h->hexp, h->colour_cells + h->colour_off[c], nc, h->mesh, (const double*)Y, ldy,
-                       h->oz_fexp, (double*)Wc, ldw, N, h->n_sm, h->info + 4, st);
+                       h->oz_fexp, (double*)Wc, ldw, N, h->n_sm, h->info + 4, st, h->oz_aimg);
       }
       CKL();
       return EFE_OK;
@@ -1099,6 +1106,7 @@ int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
   launch_build_asplit(h->Hcc, h->n_cell, h->As1, h->As2, st);
   launch_oz_hexp(h->Hcc, h->n_cell, h->hexp, st);
   CKL();
+  h->oz_aimg_valid = false;   // the digit images follow H^cc_e (remade on first use)
   h->potential_set = true;
   return EFE_OK;
 }

@@ -408,11 +408,13 @@ __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, int bpc, const 
     const int64_t r0 = bb * CPB;
     const int nb = (int)min((int64_t)CPB, n_tn - r0);
     const int64_t s0 = slot_off[bb], s1 = slot_off[bb + 1];
-    // thread t owns output tile (4 nodes x 4 columns); results summed over the slot passes
+    // thread t owns output tiles (4 nodes x 4 columns) t and t + bd of each group of
+    // 2 bd tiles; results summed over the slot passes
     const int ntile = (CPB / 4) * ncb;
-    float r[2][4][4] = {};
     __syncthreads();
     if (tid < nb) sg[tid] = t_nodes[r0 + tid];
+    for (int tg = 0; tg < ntile; tg += 2 * bd) {
+    float r[2][4][4] = {};
     for (int64_t sp = s0; sp < s1; sp += CPF) {
       const int nf = (int)min((int64_t)CPF, s1 - sp);
       __syncthreads();
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, int bpc, const 
       if (tid < nf) sf[tid] = slots[sp + tid];
       __syncthreads();
       for (int k = 0; k < 2; ++k) {
-        const int t = tid + k * bd;
+        const int t = tg + tid + k * bd;
         if (t >= ntile) break;
         const int ub = t / ncb, cb = t % ncb;
         for (int sl = 0; sl < nf; ++sl) {
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, int bpc, const 
       }
     }
     for (int k = 0; k < 2; ++k) {
-      const int t = tid + k * bd;
+      const int t = tg + tid + k * bd;
       if (t >= ntile) break;
       const int ub = t / ncb, cb = t % ncb;
 #pragma unroll
@@ -450,6 +452,7 @@ __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, int bpc, const 
         for (int j = 0; j < 4; ++j)
           if (cb * 4 + j < N) wr[j] = (T)((float)wr[j] + sgn * r[k][i][j]);
       }
+    }
     }
   }
 }

@@ -112,9 +112,12 @@ int64_t oz_hexp_elems(int64_t n_cell);
 void launch_oz_hexp(const double* Hcc, int64_t n_cell, int* hexp, cudaStream_t st);
 void launch_oz_colexp(const double* Y, int64_t ldy, int64_t rows, int N, int* fexp, cudaStream_t st);
 void launch_oz_rowexp(const double* A, int64_t lda, int64_t rows, int K, int* aexp, cudaStream_t st);
+// Aimg: pre-sliced digit images of H^cc_e (launch_oz_preslice), or NULL to slice on the fly
 int launch_oz_cell(const double* Hcc, const int* hexp, const int32_t* cells, int64_t ncells, const MeshDev& m,
                    const double* Y, int64_t ldy, const int* fexp, double* W, int64_t ldw, int N, int n_sm, int* err,
-                   cudaStream_t st);
+                   cudaStream_t st, const unsigned char* Aimg = nullptr);
+int64_t oz_cell_image_bytes();
+void launch_oz_preslice(const double* Hcc, const int* hexp, int64_t n_cell, unsigned char* img, cudaStream_t st);
 int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, const double* B, int64_t ldb,
                    const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st);
 // C (Na x N) = A^T B, A: K x Na, B: K x N (K large); aexp / bexp per column (launch_oz_colexp)

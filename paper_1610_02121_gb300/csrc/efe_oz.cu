@@ -99,6 +99,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uin
       "l"(a), "l"(b), "r"(id), "r"(acc)
       : "memory");
 }
+__device__ __forceinline__ void bar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
                : "memory");
@@ -142,6 +154,7 @@ struct OzArgs {
   // CELL
   const double* H;          // n_cell x 125 x 125
   const int* hexp;          // n_cell x 128 row exponents
+  const unsigned char* Aimg;  // optional pre-sliced digit images of H^cc_e (oz_cell_image_bytes per cell)
   const int32_t* cells;
   int64_t ncells;
   MeshDev m;
@@ -218,6 +231,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   uint64_t* acce = conv + 7;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(conv + 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(conv + 9);
+  uint64_t* afull = conv + 10;                                  // [3] pre-sliced A chunks landed
+  const bool apre = (g.mode == 0) && g.Aimg != nullptr;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
                  "r"(OZ_TMEM_COLS)
@@ -228,6 +243,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
     for (int s = 0; s < OZ_STAGES; ++s) {
       bar_init(conv + s, OZ_CONV_T);
       bar_init(empty + s, 1);
+      bar_init(afull + s, 1);
     }
     bar_init(accf, 1);
     bar_init(acce, 128);
@@ -264,6 +280,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         const int64_t ch = t * nch + kc;
         const int s = (int)(ch % OZ_STAGES);
         ok = bar_wait(conv + s, (uint32_t)((ch / OZ_STAGES) & 1));
+        if (ok && apre) ok = bar_wait(afull + s, (uint32_t)((ch / OZ_STAGES) & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) break;
         if (lane == 0) {
@@ -311,9 +328,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         }
         unsigned char* SA = sm + s * OzL::STAGE;
         unsigned char* SB = SA + OZ_S * OzL::ASL;
+        if (apre && ct == 0) {
+          // the cell's pre-sliced chunk: seven 4 KB slices, one bulk copy
+          bar_expect_tx(afull + s, OZ_S * OzL::ASL);
+          bulk_g2s(SA, g.Aimg + ((e * (int64_t)nch + kc) * OZ_S) * OzL::ASL, OZ_S * OzL::ASL, afull + s);
+        }
         // one thread per (row, 8-wide K octet): eight loads in flight, then seven
-        // 16-byte slice stores (one core-matrix row each)
-        for (int v = ct; v < (OZ_M + nmma) * 2; v += OZ_CONV_T) {
+        // 16-byte slice stores (one core-matrix row each); with pre-sliced cells
+        // only the vector block (the B tasks) is sliced here
+        for (int v = ct + (apre ? OZ_M * 2 : 0); v < (OZ_M + nmma) * 2; v += OZ_CONV_T) {
           const bool isA = v < OZ_M * 2;
           const int w = isA ? v : v - OZ_M * 2;
           const int row = w >> 1, oct = w & 1;        // row of A, or column n of the product
@@ -407,6 +430,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         break;
       }
     }
+    if (apre && ct == 0 && *abort_flag && my > 0) {
+      // let the last bulk copy of this thread land before the CTA can leave
+      const int64_t cl = my * nch - 1;
+      bar_wait(afull + (int)(cl % OZ_STAGES), (uint32_t)((cl / OZ_STAGES) & 1));
+    }
   } else {
     // ---------------------------------------------------------------- epilogue
     const int quarter = warp & 3;
@@ -495,6 +523,50 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   }
 }
 
+// Digit images of every H^cc_e: per cell, per 16-wide K chunk, the seven 4 KB
+// BF16 slices in the shared-memory layout of the MMA operand (row exponents hexp).
+__global__ void k_oz_preslice(const double* __restrict__ H, const int* __restrict__ hexp, int64_t n_cell,
+                              unsigned char* __restrict__ img) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // (cell, row, K octet)
+  const int nch = (NL + OZ_KC - 1) / OZ_KC;
+  if (t >= n_cell * OZ_M * nch * 2) return;
+  const int oct = (int)(t % 2);
+  const int kc = (int)((t / 2) % nch);
+  const int row = (int)((t / (2 * nch)) % OZ_M);
+  const int64_t e = t / (2 * nch * OZ_M);
+  const int E = hexp[e * OZ_M + row];
+  uint32_t pk[OZ_S][4];
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pk[i][q] = 0u;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int k = kc * OZ_KC + oct * 8 + q;
+    const double x = (row < NL && k < NL) ? H[e * (int64_t)(NL * NL) + row * NL + k] : 0.0;
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    const uint32_t sgn = (uint32_t)((bits >> 48) & 0x8000);
+    unsigned long long qq = 0;
+    const int rs = 1026 + E - ex;
+    if (ex != 0 && rs >= 0 && rs < 64) qq = ((unsigned long long)(bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> rs;
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) {
+      const uint32_t d = (uint32_t)(qq >> (42 - 7 * i)) & 127u;
+      uint32_t h16 = 0;
+      if (d) {
+        const int p = 31 - __clz(d);
+        h16 = sgn | ((uint32_t)(p + 127 - 7 * i) << 7) | ((d << (7 - p)) & 0x7Fu);
+      }
+      pk[i][q >> 1] |= h16 << (16 * (q & 1));
+    }
+  }
+  unsigned char* base = img + ((e * nch + kc) * OZ_S) * (int64_t)OzL::ASL + bo(row, oct * 8);
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i)
+    *reinterpret_cast<uint4*>(base + (int64_t)i * OzL::ASL) = make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+}
+
 // per-row scale exponents of an FP64 matrix (one warp per row)
 __global__ void k_oz_rowexp(const double* __restrict__ A, int64_t lda, int64_t rows, int K, int* __restrict__ eout) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -576,14 +648,24 @@ void launch_oz_rowexp(const double* A, int64_t lda, int64_t rows, int K, int* ae
 
 // W(nodes of the colour's cells) += H^cc_e Y_e, FP64-grade through the BF16 tensor cores.
 // fexp: per-column exponents of Y (launch_oz_colexp).
+int64_t oz_cell_image_bytes() { return (int64_t)((NL + OZ_KC - 1) / OZ_KC) * OZ_S * OzL::ASL; }
+
+void launch_oz_preslice(const double* Hcc, const int* hexp, int64_t n_cell, unsigned char* img, cudaStream_t st) {
+  const int64_t n = n_cell * OZ_M * ((NL + OZ_KC - 1) / OZ_KC) * 2;
+  if (n <= 0) return;
+  k_oz_preslice<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Hcc, hexp, n_cell, img);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 int launch_oz_cell(const double* Hcc, const int* hexp, const int32_t* cells, int64_t ncells, const MeshDev& m,
                    const double* Y, int64_t ldy, const int* fexp, double* W, int64_t ldw, int N, int n_sm, int* err,
-                   cudaStream_t st) {
+                   cudaStream_t st, const unsigned char* Aimg) {
   if (ncells <= 0 || N <= 0) return 0;
   OzArgs a{};
   a.mode = 0;
   a.H = Hcc;
   a.hexp = hexp;
+  a.Aimg = Aimg;
   a.cells = cells;
   a.ncells = ncells;
   a.m = m;
