@@ -178,11 +178,21 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m,
  * (Q^T H Q Psi = eps Q^T M Q Psi, Sec. V) in FP64 on the device; X <- Q Psi
  * (M-orthonormal Ritz vectors, ascending eps).  eig_host / resid_host (host,
  * N doubles each; resid_host may be NULL) receive the Ritz values and
- * ||H x_i - eps_i M x_i||_2.  Returns EFE_ERR_CHOL if G or Q^T M Q is not
- * positive definite, EFE_ERR_NOCONV if the dense eigensolver does not
- * converge.  Synchronises `stream`. */
+ * ||H x_i - eps_i M x_i||_2.  A numerically rank-deficient X (G not
+ * positive definite in FP64, or a column keeping less than 1e-10 of its
+ * squared norm outside the span of the columns before it) is first made well
+ * conditioned by up to five shifted Cholesky-QR passes (G + s I, s = 11 (rows
+ * N + N (N + 1)) u ||X||_F^2; Fukaya et al., SIAM J. Sci. Comput. 42, 2020);
+ * directions lost to rounding come back as rounding noise.  Returns
+ * EFE_ERR_CHOL if X is not finite, if G stays rank deficient after those
+ * passes, or if Q^T M Q is not positive definite; EFE_ERR_NOCONV if the
+ * dense eigensolver does not converge.  Synchronises `stream`. */
 int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N,
                       double* eig_host, double* resid_host, void* stream);
+
+/* Number of shifted Cholesky-QR passes efe_rayleigh_ritz has taken on this
+ * handle (host counter). */
+int efe_rr_shifted_passes(efe_handle* h, int64_t* count);
 
 /* Engine for the FP64 products (the FP64 filter degrees, the H apply and the
  * tall N x N products of Rayleigh-Ritz): 0 = FP64 DFMA (default, the plain
@@ -203,12 +213,18 @@ int efe_enable_timing(efe_handle* h, int32_t enable);
 int efe_kernel_stats(efe_handle* h, int64_t* launches, double* total_ms, int64_t* cell_columns,
                      int32_t reset);
 
+/* Second timing channel: the FP64 tensor-engine products (efe_set_fp64_engine
+ * 1: the FP64 cell products, tall rotations and A^T B products), bracketed by
+ * events while timing is enabled.  Returns their launches, summed duration
+ * (ms) and algorithmic FP64 flops (2 * 125^2 * N per cell product, 2 rows N^2
+ * per rotation, rows N (N + 1) per symmetric A^T B, 2 rows N^2 otherwise). */
+int efe_kernel_stats_fp64(efe_handle* h, int64_t* launches, double* total_ms, double* flops, int32_t reset);
+
 /* Y = M^E X exactly as efe_apply_M, but allocation-free (no counterpart in the
  * paper: it exists for callers that cannot allocate device memory at call
- * time -- code recording work into a CUDA graph, where allocation calls are not
- * allowed while a stream is being captured; latency-critical loops that cannot
- * afford the device-wide synchronisation cudaMalloc/cudaFree imply; and hosts
- * that hand the GPU a fixed, pre-planned memory budget).  The call allocates
+ * time -- latency-critical loops that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree imply, and hosts that hand the GPU a
+ * fixed, pre-planned memory budget).  The call allocates
  * nothing: its one scratch buffer (the partial sums of the enrichment row
  * products, n_segments x N doubles) is a file-scope device array of 2^21
  * doubles (16 MiB) that every GPU loading the library holds until the process

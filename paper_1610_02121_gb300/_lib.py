@@ -21,7 +21,8 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
 # the symbols declared in include/efe.h
 SYMBOLS = ["efe_create", "efe_destroy", "efe_last_error", "efe_sizes", "efe_qpoints", "efe_set_potential",
            "efe_set_potential_analytic", "efe_reserve", "efe_apply_H", "efe_apply_M", "efe_apply_Minv",
-           "efe_upper_bound", "efe_chfsi_step", "efe_rayleigh_ritz", "efe_enable_timing", "efe_kernel_stats",
+           "efe_upper_bound", "efe_chfsi_step", "efe_rayleigh_ritz", "efe_rr_shifted_passes", "efe_enable_timing",
+           "efe_kernel_stats", "efe_kernel_stats_fp64",
            "efe_launch_count", "efe_apply_M_noalloc", "efe_set_fp64_engine", "efe_density", "efe_xc_lda",
            "efe_hartree", "efe_fermi", "efe_anderson", "efe_scf_init", "efe_scf_step", "efe_sad_density",
            "efe_descriptors", "efe_learned_density", "efe_density_log_ratio", "efe_mlp_param_count",
@@ -115,6 +116,8 @@ def load(path=LIB_PATH):
         "efe_rayleigh_ritz": [vp, vp, i64, i32, PD, PD, vp],
         "efe_enable_timing": [vp, i32],
         "efe_kernel_stats": [vp, P64, PD, P64, i32],
+        "efe_kernel_stats_fp64": [vp, P64, PD, PD, i32],
+        "efe_rr_shifted_passes": [vp, P64],
         "efe_launch_count": [P64],
         "efe_apply_M_noalloc": [vp, vp, i64, i32, vp, i64, vp],
         "efe_set_fp64_engine": [vp, i32],
@@ -457,6 +460,20 @@ class System:
 
     def enable_timing(self, on=True):
         self._check(self.L.efe_enable_timing(self.h, int(bool(on))))
+
+    def kernel_stats_fp64(self, reset=True):
+        """FP64 tensor engine: (launches, total ms, algorithmic FP64 flops) since the last reset."""
+        n = C.c_int64()
+        ms = C.c_double()
+        fl = C.c_double()
+        self._check(self.L.efe_kernel_stats_fp64(self.h, C.byref(n), C.byref(ms), C.byref(fl), int(bool(reset))))
+        return n.value, ms.value, fl.value
+
+    def rr_shifted_passes(self):
+        """Shifted Cholesky-QR passes Rayleigh-Ritz has needed on this system so far."""
+        n = C.c_int64()
+        self._check(self.L.efe_rr_shifted_passes(self.h, C.byref(n)))
+        return n.value
 
     def kernel_stats(self, reset=True):
         n = C.c_int64()

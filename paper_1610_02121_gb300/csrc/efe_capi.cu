@@ -61,6 +61,10 @@ struct efe_handle {
   int* oz_bexp = nullptr;   // per-column exponents of small right-hand matrices (N)
   int* oz_aexp = nullptr;   // per-row exponents of tall left-hand matrices (rows)
   int2* oz_pairs = nullptr; // tile pairs of the tensor-core A^T B products
+  unsigned char* oz_img[2] = {nullptr, nullptr};  // operand digit images of the tall products (grow-only)
+  int64_t oz_img_bytes[2] = {0, 0};
+  int64_t chol_shifted = 0;        // shifted Cholesky-QR passes taken by Rayleigh-Ritz
+  double* chol_ratio = nullptr;    // device: min_j L_jj^2 / G_jj of the last Gram factorisation
   bool time_this = false;   // the cell-apply timer records only the filter's mixed-precision launches
   DevFunc* funcs = nullptr;
   int32_t *enr_cells = nullptr, *cf_ptr = nullptr, *cf_idx = nullptr;
@@ -90,12 +94,13 @@ struct efe_handle {
   int64_t tnwork_elems = 0;
   double* rpart = nullptr;
   double* lz = nullptr;       // Lanczos vectors (6 * rows) + scalars
-  int Nres32 = 0, ld32 = 0, npc = 0, ncb = 0;
+  int Nres32 = 0, ld32 = 0, ncb = 0;
   float *Yf[3] = {nullptr, nullptr, nullptr}, *Wf = nullptr, *cpart = nullptr;
   float *mecT32 = nullptr, *hecT32 = nullptr;
   // dense FP32 tiles of the pattern over blocks of pattern nodes (mixed filter)
   int64_t cb_nblk = 0, cb_nslots = 0;
-  int64_t *cb_slot_off = nullptr, *cb_pos = nullptr;
+  int64_t *cb_slot_off = nullptr, *cb_pos = nullptr, *cb_cta = nullptr;
+  std::vector<int64_t> cb_soff_host;   // slot offsets of the node blocks (host copy)
   int32_t* cb_slots = nullptr;
   float *tileH = nullptr, *tileM = nullptr;
   double* Ye[3] = {nullptr, nullptr, nullptr};
@@ -132,10 +137,13 @@ struct efe_handle {
   // timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, int>> ev_pairs;
-  int64_t t_launches = 0, t_cellcols = 0;
-  double t_ms = 0.0;
-  int64_t pend_cellcols = 0;
+  std::vector<int> ev_free;                 // event pairs (even indices) ready for reuse
+  struct TimedPair { int ev; int ch; double units; };
+  std::vector<TimedPair> ev_pairs;
+  // channel 0: mixed-precision cell products (units: cell columns);
+  // channel 1: FP64 tensor-engine products (units: algorithmic FP64 flops)
+  int64_t t_launches[2] = {0, 0};
+  double t_ms[2] = {0.0, 0.0}, t_units[2] = {0.0, 0.0};
 };
 
 namespace {
@@ -242,9 +250,27 @@ int reserve32(efe_handle* h, int N) {
   }
   TRY(dalloc(h, &h->Wf, h->n_nodes * ld));
   CK(cudaMemset(h->Wf, 0, sizeof(float) * h->n_nodes * ld));
-  // node blocks per CTA of the coupling kernels: about four CTAs per SM
-  h->npc = (int)std::max<int64_t>(1, (h->cb_nblk + 4 * h->n_sm - 1) / (4 * h->n_sm));
-  h->ncb = coup_nblocks(std::max<int64_t>(1, h->n_tn), h->npc);
+  // coupling products: one wave of CTAs, node blocks split so that every CTA
+  // holds about the same number of tile slots (plus a share for staging rows)
+  dfree(h, h->cb_cta);
+  h->cb_cta = nullptr;
+  h->ncb = 1;
+  if (h->nE > 0 && h->cb_nblk > 0) {
+    const int64_t nblk = h->cb_nblk;
+    const int ncta = (int)std::min<int64_t>(nblk, coup_resident_ctas((int)h->nE, N, h->n_sm));
+    const auto& so = h->cb_soff_host;
+    const double wtot = (double)so[nblk] + 3.0 * (double)nblk;
+    std::vector<int64_t> cb(ncta + 1, nblk);
+    cb[0] = 0;
+    int64_t b = 0;
+    for (int c = 1; c < ncta; ++c) {
+      const double target = wtot * c / ncta;
+      while (b < nblk && (double)so[b] + 3.0 * (double)b < target) ++b;
+      cb[c] = std::max(cb[c - 1], b);
+    }
+    TRY(upload(h, &h->cb_cta, cb));
+    h->ncb = ncta;
+  }
   TRY(dalloc(h, &h->cpart, (int64_t)h->ncb * std::max<int64_t>(1, h->nE) * N));
   h->ld32 = ld;
   h->Nres32 = N;
@@ -262,10 +288,18 @@ int ev_get(efe_handle* h, int idx, cudaEvent_t* e) {
   return EFE_OK;
 }
 
-int timed_begin(efe_handle* h, cudaStream_t st, int* slot) {
+// channel 0 times only the filter's mixed-precision cell launches (time_this);
+// channel 1 every FP64 tensor-engine product
+int timed_begin(efe_handle* h, cudaStream_t st, int* slot, int ch = 0) {
   *slot = -1;
-  if (!h->timing || !h->time_this) return EFE_OK;
-  const int i = 2 * (int)h->ev_pairs.size();
+  if (!h->timing || (ch == 0 && !h->time_this)) return EFE_OK;
+  int i;
+  if (!h->ev_free.empty()) {
+    i = h->ev_free.back();
+    h->ev_free.pop_back();
+  } else {
+    i = (int)h->ev_pool.size();
+  }
   cudaEvent_t a, b;
   TRY(ev_get(h, i, &a));
   TRY(ev_get(h, i + 1, &b));
@@ -274,23 +308,28 @@ int timed_begin(efe_handle* h, cudaStream_t st, int* slot) {
   return EFE_OK;
 }
 
-int timed_end(efe_handle* h, cudaStream_t st, int slot, int64_t cellcols) {
+// adds the finished pairs to their channels (waits for the last one)
+int timed_fold(efe_handle* h) {
+  if (h->ev_pairs.empty()) return EFE_OK;
+  CK(cudaEventSynchronize(h->ev_pool[h->ev_pairs.back().ev + 1]));
+  for (auto& pr : h->ev_pairs) {
+    CK(cudaEventSynchronize(h->ev_pool[pr.ev + 1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev_pool[pr.ev], h->ev_pool[pr.ev + 1]));
+    h->t_ms[pr.ch] += ms;
+    h->t_launches[pr.ch]++;
+    h->t_units[pr.ch] += pr.units;
+    h->ev_free.push_back(pr.ev);
+  }
+  h->ev_pairs.clear();
+  return EFE_OK;
+}
+
+int timed_end(efe_handle* h, cudaStream_t st, int slot, double units, int ch = 0) {
   if (slot < 0) return EFE_OK;
   CK(cudaEventRecord(h->ev_pool[slot + 1], st));
-  h->ev_pairs.push_back({slot, slot + 1});
-  h->pend_cellcols += cellcols;
-  if (h->ev_pairs.size() >= 4096) {  // fold completed pairs to bound the pool
-    CK(cudaEventSynchronize(h->ev_pool[slot + 1]));
-    for (auto& pr : h->ev_pairs) {
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, h->ev_pool[pr.first], h->ev_pool[pr.second]));
-      h->t_ms += ms;
-      h->t_launches++;
-    }
-    h->ev_pairs.clear();
-    h->t_cellcols += h->pend_cellcols;
-    h->pend_cellcols = 0;
-  }
+  h->ev_pairs.push_back({slot, ch, units});
+  if (h->ev_pairs.size() >= 4096) TRY(timed_fold(h));  // bound the event pool
   return EFE_OK;
 }
 
@@ -309,8 +348,11 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
       for (int c = 0; c < 8; ++c) {
         const int64_t nc = h->colour_off[c + 1] - h->colour_off[c];
         if (nc == 0) continue;
+        int slot;
+        TRY(timed_begin(h, st, &slot, 1));
         launch_oz_cell(h->Hcc, h->hexp, h->colour_cells + h->colour_off[c], nc, h->mesh, (const double*)Y, ldy,
                        h->oz_fexp, (double*)Wc, ldw, N, h->n_sm, h->info + 4, st, h->oz_aimg);
+        TRY(timed_end(h, st, slot, 2.0 * NL * NL * (double)N * (double)nc, 1));
       }
       CKL();
       return EFE_OK;
@@ -341,7 +383,7 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
         launch_cell_apply_f32((const float*)Hc, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N, st);
     }
     CKL();
-    TRY(timed_end(h, st, slot, nc * (int64_t)N));
+    TRY(timed_end(h, st, slot, (double)(nc * (int64_t)N)));
   }
   return EFE_OK;
 }
@@ -447,18 +489,18 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
   if (h->nE > 0) {
     const int nE = (int)h->nE;
     if (coup_smem(nE, N, true) <= 200 * 1024) {
-      launch_coup_cols<float>(h->n_tn, h->npc, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, 1.f, Yce, N, nE,
+      launch_coup_cols<float>(h->n_tn, h->ncb, h->cb_cta, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, 1.f, Yce, N, nE,
                               N, h->Wf, ld, st);
-      launch_coup_rows<float>(h->n_tn, h->npc, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, nullptr, Yc, ld,
+      launch_coup_rows<float>(h->n_tn, h->ncb, h->cb_cta, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, nullptr, Yc, ld,
                               nE, N, h->cpart, st);
       launch_coup_reduce(h->ncb, nE, N, h->cpart, 1.0, nullptr, 0, 0.0, We, N, st);
       launch_gemm_nn(nE, N, nE, 1.0, h->Hee, nE, Yce, N, 1.0, We, N, st);
       // block-wise inverse: r = We - M^ec D^-1 Wc, x_e = S^-1 r, Wc -= M^ec^T x_e
-      launch_coup_rows<float>(h->n_tn, h->npc, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, h->Dinv, h->Wf,
+      launch_coup_rows<float>(h->n_tn, h->ncb, h->cb_cta, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, h->Dinv, h->Wf,
                               ld, nE, N, h->cpart, st);
       launch_coup_reduce(h->ncb, nE, N, h->cpart, -1.0, We, N, 1.0, h->rb, N, st);
       launch_gemm_nn(nE, N, nE, 1.0, h->Sinv, nE, h->rb, N, 0.0, h->xe, N, st);
-      launch_coup_cols<float>(h->n_tn, h->npc, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, -1.f, h->xe, N,
+      launch_coup_cols<float>(h->n_tn, h->ncb, h->cb_cta, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, -1.f, h->xe, N,
                               nE, N, h->Wf, ld, st);
     } else {
       launch_spmm_nodes<float>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->hecT, 1.0, Yce, N, h->Wf, ld, N, st);
@@ -939,6 +981,7 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
   TRY(dalloc(h, &h->As1, tc3_image_elems(h->n_cell)));
   TRY(dalloc(h, &h->As2, tc3_image_elems(h->n_cell)));
   TRY(dalloc(h, &h->info, 8));
+  TRY(dalloc(h, &h->chol_ratio, 1));
   if (h->nE > 0) {
     TRY(upload(h, &h->funcs, s.funcs));
     TRY(upload(h, &h->enr_cells, s.enr_cells));
@@ -1011,6 +1054,7 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
       h->cb_nblk = nblk;
       h->cb_nslots = soff[nblk];
       TRY(upload(h, &h->cb_slot_off, soff));
+      h->cb_soff_host = soff;
       TRY(upload(h, &h->cb_slots, slots));
       TRY(upload(h, &h->cb_pos, pos));
       TRY(dalloc(h, &h->tileM, h->cb_nslots * B));
@@ -1384,12 +1428,33 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
 
 // C = A B for a tall A (rows x N) and a small B (N x N): tensor-core FP64-grade
 // products when enabled (N <= 144), FP64 DFMA otherwise.
+// grow-only device buffer i of the operand images (at least `bytes`)
+int oz_img_buf(efe_handle* h, int i, int64_t bytes) {
+  if (bytes <= h->oz_img_bytes[i]) return EFE_OK;
+  dfree(h, h->oz_img[i]);
+  h->oz_img[i] = nullptr;
+  h->oz_img_bytes[i] = 0;
+  TRY(dalloc(h, &h->oz_img[i], bytes));
+  h->oz_img_bytes[i] = bytes;
+  return EFE_OK;
+}
+
 int gemm_tall(efe_handle* h, int64_t rows, int N, const double* A, int64_t lda, const double* B, double* C,
               int64_t ldc, cudaStream_t st) {
   if (h->fp64_engine == 1 && N <= 144) {
     launch_oz_rowexp(A, lda, rows, N, h->oz_aexp, st);
     launch_oz_colexp(B, N, N, N, h->oz_bexp, st);
-    launch_oz_rows(A, lda, rows, N, h->oz_aexp, B, N, h->oz_bexp, C, ldc, N, h->n_sm, h->info + 4, st);
+    // both operands sliced once into digit images; the product kernel then only
+    // streams them (bulk copies) through the tensor cores
+    TRY(oz_img_buf(h, 0, oz_img_rows_bytes(rows, N)));
+    TRY(oz_img_buf(h, 1, oz_img_cols_bytes((N + 15) / 16, N)));
+    launch_oz_img_rows(A, lda, rows, N, h->oz_aexp, h->oz_img[0], st);
+    launch_oz_img_cols(B, N, N, N, h->oz_bexp, (N + 15) / 16, h->oz_img[1], st);
+    int slot;
+    TRY(timed_begin(h, st, &slot, 1));
+    launch_oz_rows(A, lda, rows, N, h->oz_aexp, B, N, h->oz_bexp, C, ldc, N, h->n_sm, h->info + 4, st,
+                   h->oz_img[0], h->oz_img[1]);
+    TRY(timed_end(h, st, slot, 2.0 * (double)rows * N * N, 1));
   } else {
     launch_gemm_nn(rows, N, N, 1.0, A, lda, B, N, 0.0, C, ldc, st);
   }
@@ -1404,11 +1469,21 @@ int gemm_gram(efe_handle* h, int64_t rows, int N, const double* A, int64_t lda, 
   if (h->fp64_engine == 1) {
     launch_oz_colexp(A, lda, rows, N, h->oz_fexp, st);
     if (B != A) launch_oz_colexp(B, ldb, rows, N, h->oz_bexp, st);
+    // column digit images of A and B, enough chunks for any segmentation (the
+    // segments, at most 2 n_sm of them, are multiples of 256 rows)
+    const int64_t nch = (rows + 15) / 16 + 16 * (2 * (int64_t)h->n_sm + 1);
+    TRY(oz_img_buf(h, 0, oz_img_cols_bytes(nch, N)));
+    if (B != A) TRY(oz_img_buf(h, 1, oz_img_cols_bytes(nch, N)));
+    int slot;
+    TRY(timed_begin(h, st, &slot, 1));
     if (launch_oz_gram(rows, N, N, A, lda, h->oz_fexp, B, ldb, B != A ? h->oz_bexp : h->oz_fexp, C, N, sym,
-                       h->tnwork, h->tnwork_elems, h->oz_pairs, h->n_sm, h->info + 4, st) == 0) {
+                       h->tnwork, h->tnwork_elems, h->oz_pairs, h->n_sm, h->info + 4, st, h->oz_img[0],
+                       h->oz_img_bytes[0], h->oz_img[1], h->oz_img_bytes[1]) == 0) {
+      TRY(timed_end(h, st, slot, (sym ? 1.0 : 2.0) * (double)rows * N * (N + (sym ? 1 : 0)), 1));
       CKL();
       return EFE_OK;
     }
+    TRY(timed_end(h, st, slot, 0.0, 1));
   }
   launch_gemm_tn(rows, N, N, A, lda, B, ldb, C, N, h->tnwork, h->tnwork_elems, st, sym);
   CKL();
@@ -1464,6 +1539,12 @@ int sym_eig(efe_handle* h, const double* C, int N, double* V, double* w, double*
   return EFE_OK;
 }
 
+int efe_rr_shifted_passes(efe_handle* h, int64_t* count) {
+  if (!h || !count) return EFE_ERR_ARG;
+  *count = h->chol_shifted;
+  return EFE_OK;
+}
+
 int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* eig_host, double* resid_host,
                       void* stream) {
   if (!h || !eig_host) return EFE_ERR_ARG;
@@ -1498,11 +1579,48 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   int inf[2] = {0, 0};
   // Cholesky-QR: G = X^T X = L L^T, Q = X L^-T
   CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
-  TRY(gemm_gram(h, R, N, X, ldx, X, ldx, G, true, st));
-  launch_symmetrize(G, N, N, st);
-  launch_chol(G, N, N, h->info, st);
-  CKL();
-  {
+  // factorise the Gram matrix of X; ok if X is numerically full rank: G is
+  // positive definite and every column keeps a fraction >= 1e-10 of its squared
+  // norm outside the span of the columns before it (the orthogonality of
+  // X L^-T is then within ~1e-6, ample for the generalised problem below)
+  auto gram_chol = [&](bool& ok) -> int {
+    TRY(gemm_gram(h, R, N, X, ldx, X, ldx, G, true, st));
+    launch_symmetrize(G, N, N, st);
+    launch_chol(G, N, N, h->info, st, h->chol_ratio);
+    CKL();
+    int fl[5] = {0, 0, 0, 0, 0};
+    double ratio = 0.0;
+    CK(cudaMemcpyAsync(fl, h->info, sizeof(fl), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ratio, h->chol_ratio, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (fl[4]) {
+      h->err = "tensor-core FP64 product: bounded wait ran out";
+      return EFE_ERR_TIMEOUT;
+    }
+    ok = fl[0] == 0 && ratio >= 1e-10;
+    return EFE_OK;
+  };
+  bool ok = false;
+  TRY(gram_chol(ok));
+  // numerically rank-deficient block (a high filter degree from a poor start
+  // collapses columns onto the lowest states): shifted Cholesky-QR (Fukaya,
+  // Kannan, Nakatsukasa, Yamamoto & Yanagisawa, SIAM J. Sci. Comput. 42, 2020).
+  // G + s I with s = 11 (R N + N (N + 1)) u ||X||_F^2 is safely positive
+  // definite and X <- X R_s^-1 divides the condition number by about
+  // ||X||_2 / sqrt(s) (at least ~200 on a million-row block); after at most
+  // five such passes the plain factorisation is accurate (directions lost to
+  // rounding come back as rounding noise, which the next filter pass treats
+  // like any other start vector).
+  for (int pass = 0; !ok; ++pass) {
+    if (pass == 5) {
+      h->err = "Cholesky-QR breakdown: Gram matrix X^T X is not positive definite (non-finite or rank-deficient block)";
+      return EFE_ERR_CHOL;
+    }
+    TRY(gemm_gram(h, R, N, X, ldx, X, ldx, G, true, st));
+    launch_symmetrize(G, N, N, st);
+    launch_shift_diag(G, N, N, 11.0 * ((double)R * N + (double)N * (N + 1)) * 0x1p-53, st);
+    launch_chol(G, N, N, h->info, st);
+    CKL();
     int fl[5] = {0, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(fl, h->info, sizeof(fl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1511,9 +1629,15 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
       return EFE_ERR_TIMEOUT;
     }
     if (fl[0]) {
-      h->err = "Cholesky-QR breakdown: Gram matrix X^T X is not positive definite (rank-deficient block)";
+      h->err = "Cholesky-QR breakdown: shifted Gram matrix is not positive definite (non-finite block)";
       return EFE_ERR_CHOL;
     }
+    launch_trinv_lower(G, N, N, Linv, N, st);
+    launch_transpose(Linv, N, N, Rinv, N, st);
+    TRY(gemm_tall(h, R, N, X, ldx, Rinv, Q, N, st));
+    launch_copy_rows(R, Q, N, X, ldx, N, st);
+    h->chol_shifted++;
+    TRY(gram_chol(ok));
   }
   launch_trinv_lower(G, N, N, Linv, N, st);
   launch_transpose(Linv, N, N, Rinv, N, st);
@@ -1588,28 +1712,31 @@ int efe_enable_timing(efe_handle* h, int32_t enable) {
   return EFE_OK;
 }
 
-int efe_kernel_stats(efe_handle* h, int64_t* launches, double* total_ms, int64_t* cell_columns, int32_t reset) {
+static int kernel_stats(efe_handle* h, int ch, int64_t* launches, double* total_ms, double* units, int32_t reset) {
   if (!h) return EFE_ERR_ARG;
   TRY(set_dev(h));
   CK(cudaDeviceSynchronize());
-  for (auto& pr : h->ev_pairs) {
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, h->ev_pool[pr.first], h->ev_pool[pr.second]));
-    h->t_ms += ms;
-    h->t_launches++;
-  }
-  h->ev_pairs.clear();
-  h->t_cellcols += h->pend_cellcols;
-  h->pend_cellcols = 0;
-  if (launches) *launches = h->t_launches;
-  if (total_ms) *total_ms = h->t_ms;
-  if (cell_columns) *cell_columns = h->t_cellcols;
+  TRY(timed_fold(h));
+  if (launches) *launches = h->t_launches[ch];
+  if (total_ms) *total_ms = h->t_ms[ch];
+  if (units) *units = h->t_units[ch];
   if (reset) {
-    h->t_launches = 0;
-    h->t_ms = 0.0;
-    h->t_cellcols = 0;
+    h->t_launches[ch] = 0;
+    h->t_ms[ch] = 0.0;
+    h->t_units[ch] = 0.0;
   }
   return EFE_OK;
+}
+
+int efe_kernel_stats(efe_handle* h, int64_t* launches, double* total_ms, int64_t* cell_columns, int32_t reset) {
+  double u = 0.0;
+  TRY(kernel_stats(h, 0, launches, total_ms, &u, reset));
+  if (cell_columns) *cell_columns = (int64_t)u;
+  return EFE_OK;
+}
+
+int efe_kernel_stats_fp64(efe_handle* h, int64_t* launches, double* total_ms, double* flops, int32_t reset) {
+  return kernel_stats(h, 1, launches, total_ms, flops, reset);
 }
 
 // ---------------------------------------------------------------------------

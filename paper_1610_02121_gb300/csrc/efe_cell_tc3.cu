@@ -298,15 +298,26 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
       const int c0 = (int)(item % ntiles) * TW;
       const int ncol = min(TW, N - c0);
       const int b = (int)(t & 1);
+      const int64_t g = (r < NL) ? cell_node(m, e, r) : 0;
+      float* wr = W + g * ldw + c0;
+      // this thread's output segments are pulled towards L2 while the MMAs run
+      if (r < NL)
+        for (int cb = colgrp * 16; cb < ncol; cb += 32) asm volatile("prefetch.L2 [%0];" ::"l"(wr + cb));
       if (!bar_wait(accf + b, (uint32_t)((t / 2) & 1))) {
         *abort_flag = 1;
         atomicExch(err, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t g = (r < NL) ? cell_node(m, e, r) : 0;
-      float* wr = W + g * ldw + c0;
       for (int cb = colgrp * 16; cb < ncol; cb += 32) {
+        // the values to add to are loaded before the accumulator columns
+        float4 o[4];
+        const bool full16 = (r < NL) && cb + 16 <= ncol;
+        if (full16) {
+          const float4* w4 = reinterpret_cast<const float4*>(wr + cb);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) o[q] = w4[q];
+        }
         uint32_t v[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -316,11 +327,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (r < NL) {
-          if (cb + 16 <= ncol) {
+          if (full16) {
             float4* w4 = reinterpret_cast<float4*>(wr + cb);
-            float4 o[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = w4[q];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               o[q].x += __uint_as_float(v[4 * q]);

@@ -300,24 +300,27 @@ __global__ void k_tile_scatter(int64_t nnz, const int64_t* __restrict__ pos, con
 
 // Rows product: part[b][a][c] = sum over the blocks of CTA b of
 //   sum_u tile[slot][u] * scale[g_u] * X[g_u][c]  accumulated at a = f(slot),
-// in a CTA-private (n_E x N) shared-memory array.
+// in a CTA-private (n_E x N) shared-memory array.  CTA b takes the blocks
+// cta_blk[b] .. cta_blk[b + 1] (a one-wave partition balanced by slot count).
+// Shared rows are padded to a multiple of four floats so that every thread
+// reads and updates its four columns with one 16-byte access.
 template <typename T>
-__global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, int bpc, const int32_t* __restrict__ t_nodes,
+__global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, const int64_t* __restrict__ cta_blk,
+                                                   const int32_t* __restrict__ t_nodes,
                                                    const int64_t* __restrict__ slot_off,
                                                    const int32_t* __restrict__ slots, const float* __restrict__ tile,
                                                    const double* __restrict__ scale, const T* __restrict__ X,
                                                    int64_t ldx, int nE, int N, float* __restrict__ part) {
   extern __shared__ __align__(16) float smf[];
-  const int ldy = N + 4;
-  float* acc = smf;                                  // nE x N
-  float* Ys = acc + (size_t)nE * N;                  // CPB x ldy
+  const int ldy = (N + 3) & ~3;
+  float* acc = smf;                                  // nE x ldy
+  float* Ys = acc + (size_t)nE * ldy;                // CPB x ldy
   float* Ps = Ys + CPB * ldy;                        // CPF x CPB
   __shared__ int sf[CPF];
   const int tid = threadIdx.x, bd = blockDim.x;
-  for (int i = tid; i < nE * N; i += bd) acc[i] = 0.f;
-  const int64_t nblk = (n_tn + CPB - 1) / CPB;
-  const int64_t b0 = (int64_t)blockIdx.x * bpc, b1 = min(nblk, b0 + bpc);
-  const int ncb = (N + 3) / 4;
+  for (int i = tid; i < nE * ldy; i += bd) acc[i] = 0.f;
+  const int64_t b0 = cta_blk[blockIdx.x], b1 = cta_blk[blockIdx.x + 1];
+  const int ncb = ldy / 4;
   for (int64_t bb = b0; bb < b1; ++bb) {
     const int64_t r0 = bb * CPB;
     const int nb = (int)min((int64_t)CPB, n_tn - r0);
@@ -345,11 +348,11 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, int bpc, const 
         float r[4][4] = {};
 #pragma unroll 8
         for (int u = 0; u < CPB; ++u) {
-          float pv[4], yv[4];
+          float pv[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) pv[i] = Ps[(sb * 4 + i) * CPB + u];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) yv[j] = Ys[u * ldy + cb * 4 + j];
+          const float4 y4 = *reinterpret_cast<const float4*>(Ys + u * ldy + cb * 4);
+          const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -359,51 +362,71 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, int bpc, const 
         for (int i = 0; i < 4; ++i) {
           const int sl = sb * 4 + i;
           if (sl >= nf) break;
-          float* ar = acc + (size_t)sf[sl] * N;
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (cb * 4 + j < N) ar[cb * 4 + j] += r[i][j];
+          float4* ar = reinterpret_cast<float4*>(acc + (size_t)sf[sl] * ldy + cb * 4);
+          float4 a4 = *ar;
+          a4.x += r[i][0];
+          a4.y += r[i][1];
+          a4.z += r[i][2];
+          a4.w += r[i][3];
+          *ar = a4;
         }
       }
     }
   }
   __syncthreads();
   float* Pp = part + (int64_t)blockIdx.x * nE * N;
-  for (int i = tid; i < nE * N; i += bd) Pp[i] = acc[i];
+  for (int i = tid; i < nE * N; i += bd) Pp[i] = acc[(i / N) * ldy + i % N];
 }
 
-// out[a][c] = alpha_base * base[a][c] + sgn * sum_b part[b][a][c]  (fixed order, FP64)
-__global__ void k_coup_reduce(int nb, int nE, int N, const float* __restrict__ part, double sgn,
-                              const double* __restrict__ base, int64_t ldb, double alpha_base,
-                              double* __restrict__ out, int64_t ldo) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)nE * N) return;
+// out[a][c] = alpha_base * base[a][c] + sgn * sum_b part[b][a][c]  (fixed order, FP64).
+// A block takes 32 consecutive outputs; its 8 thread rows sum the partials
+// b = y, y + 8, ... and the 8 row sums are added in order.
+__global__ void __launch_bounds__(256) k_coup_reduce(int nb, int nE, int N, const float* __restrict__ part,
+                                                     double sgn, const double* __restrict__ base, int64_t ldb,
+                                                     double alpha_base, double* __restrict__ out, int64_t ldo) {
+  __shared__ double rs[8][33];
+  const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
+  const int64_t idx = blockIdx.x * 32LL + x;
+  const int64_t tot = (int64_t)nE * N;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += (double)part[(int64_t)b * nE * N + idx];
-  const int a = (int)(idx / N), c = (int)(idx % N);
-  double v = sgn * s;
-  if (base) v += alpha_base * base[(int64_t)a * ldb + c];
-  out[(int64_t)a * ldo + c] = v;
+  if (idx < tot)
+    for (int b = y; b < nb; b += 8) s += (double)part[(int64_t)b * tot + idx];
+  rs[y][x] = s;
+  __syncthreads();
+  if (y == 0 && idx < tot) {
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v += rs[k][x];
+    const int a = (int)(idx / N), c = (int)(idx % N);
+    v *= sgn;
+    if (base) v += alpha_base * base[(int64_t)a * ldb + c];
+    out[(int64_t)a * ldo + c] = v;
+  }
 }
 
 // Columns product: W[g_u][c] += sgn * sum_slot tile[slot][u] * Xe[f(slot)][c]
-// (Xe staged in shared memory as FP32), same block tiles.
+// (Xe staged in shared memory as FP32, rows padded to four floats), same block
+// tiles and CTA partition as the rows product.
 template <typename T>
-__global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, int bpc, const int32_t* __restrict__ t_nodes,
+__global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, const int64_t* __restrict__ cta_blk,
+                                                   const int32_t* __restrict__ t_nodes,
                                                    const int64_t* __restrict__ slot_off,
                                                    const int32_t* __restrict__ slots, const float* __restrict__ tile,
                                                    float sgn, const double* __restrict__ Xe, int64_t ldxe, int nE,
                                                    int N, T* __restrict__ W, int64_t ldw) {
   extern __shared__ __align__(16) float smf[];
-  float* xs = smf;                                   // nE x N
-  float* Ps = xs + (size_t)nE * N;                   // CPF x CPB
+  const int ldx = (N + 3) & ~3;
+  float* xs = smf;                                   // nE x ldx
+  float* Ps = xs + (size_t)nE * ldx;                 // CPF x CPB
   __shared__ int sf[CPF];
   __shared__ int64_t sg[CPB];
   const int tid = threadIdx.x, bd = blockDim.x;
-  for (int i = tid; i < nE * N; i += bd) xs[i] = (float)Xe[(int64_t)(i / N) * ldxe + i % N];
-  const int64_t nblk = (n_tn + CPB - 1) / CPB;
-  const int64_t b0 = (int64_t)blockIdx.x * bpc, b1 = min(nblk, b0 + bpc);
-  const int ncb = (N + 3) / 4;
+  for (int i = tid; i < nE * ldx; i += bd) {
+    const int a = i / ldx, c = i % ldx;
+    xs[i] = c < N ? (float)Xe[(int64_t)a * ldxe + c] : 0.f;
+  }
+  const int64_t b0 = cta_blk[blockIdx.x], b1 = cta_blk[blockIdx.x + 1];
+  const int ncb = ldx / 4;
   for (int64_t bb = b0; bb < b1; ++bb) {
     const int64_t r0 = bb * CPB;
     const int nb = (int)min((int64_t)CPB, n_tn - r0);
@@ -414,45 +437,44 @@ __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, int bpc, const 
     __syncthreads();
     if (tid < nb) sg[tid] = t_nodes[r0 + tid];
     for (int tg = 0; tg < ntile; tg += 2 * bd) {
-    float r[2][4][4] = {};
-    for (int64_t sp = s0; sp < s1; sp += CPF) {
-      const int nf = (int)min((int64_t)CPF, s1 - sp);
-      __syncthreads();
-      for (int i = tid; i < CPF * CPB; i += bd) Ps[i] = (i < nf * CPB) ? tile[sp * CPB + i] : 0.f;
-      if (tid < nf) sf[tid] = slots[sp + tid];
-      __syncthreads();
+      float r[2][4][4] = {};
+      for (int64_t sp = s0; sp < s1; sp += CPF) {
+        const int nf = (int)min((int64_t)CPF, s1 - sp);
+        __syncthreads();
+        for (int i = tid; i < CPF * CPB; i += bd) Ps[i] = (i < nf * CPB) ? tile[sp * CPB + i] : 0.f;
+        if (tid < nf) sf[tid] = slots[sp + tid];
+        __syncthreads();
+        for (int k = 0; k < 2; ++k) {
+          const int t = tg + tid + k * bd;
+          if (t >= ntile) break;
+          const int ub = t / ncb, cb = t % ncb;
+          for (int sl = 0; sl < nf; ++sl) {
+            const float4 x4 = *reinterpret_cast<const float4*>(xs + (size_t)sf[sl] * ldx + cb * 4);
+            const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+            float pv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) pv[i] = Ps[sl * CPB + ub * 4 + i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) r[k][i][j] = fmaf(pv[i], xv[j], r[k][i][j]);
+          }
+        }
+      }
       for (int k = 0; k < 2; ++k) {
         const int t = tg + tid + k * bd;
         if (t >= ntile) break;
         const int ub = t / ncb, cb = t % ncb;
-        for (int sl = 0; sl < nf; ++sl) {
-          const float* xr = xs + (size_t)sf[sl] * N + cb * 4;
-          float pv[4], xv[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) pv[i] = Ps[sl * CPB + ub * 4 + i];
+        for (int i = 0; i < 4; ++i) {
+          const int u = ub * 4 + i;
+          if (u >= nb) break;
+          T* wr = W + sg[u] * ldw + cb * 4;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) xv[j] = (cb * 4 + j < N) ? xr[j] : 0.f;
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) r[k][i][j] = fmaf(pv[i], xv[j], r[k][i][j]);
+          for (int j = 0; j < 4; ++j)
+            if (cb * 4 + j < N) wr[j] = (T)((float)wr[j] + sgn * r[k][i][j]);
         }
       }
-    }
-    for (int k = 0; k < 2; ++k) {
-      const int t = tg + tid + k * bd;
-      if (t >= ntile) break;
-      const int ub = t / ncb, cb = t % ncb;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int u = ub * 4 + i;
-        if (u >= nb) break;
-        T* wr = W + sg[u] * ldw + cb * 4;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (cb * 4 + j < N) wr[j] = (T)((float)wr[j] + sgn * r[k][i][j]);
-      }
-    }
     }
   }
 }
@@ -604,32 +626,47 @@ __global__ void k_gemm_tn_reduce(int nsplit, int Na, int Nb, const double* __res
   C[(idx / Nb) * ldc + idx % Nb] = s;
 }
 
-// Right-looking Cholesky A = L L^T in one CTA (lower triangle; upper zeroed).
-__global__ void __launch_bounds__(1024) k_chol(double* A, int n, int lda, int* info) {
-  __shared__ double piv;
+// Right-looking Cholesky A = L L^T in one CTA (lower triangle; upper zeroed),
+// n <= 2048.  Column j is scaled, kept in shared memory, and the trailing lower
+// triangle is updated with one (row, column) pair per thread and step.
+// min_ratio (optional): min_j L_jj^2 / A_jj, the smallest fraction of a
+// column's squared norm outside the span of the columns before it (scale
+// invariant; 1 / its square root bounds the column-scaled condition number).
+__global__ void __launch_bounds__(1024) k_chol(double* A, int n, int lda, int* info, double* min_ratio) {
+  __shared__ double piv, rmin;
   __shared__ int bad;
+  __shared__ double d0[2048];
+  __shared__ double lj[2048];
   const int tid = threadIdx.x, bd = blockDim.x;
-  if (tid == 0) bad = 0;
-  for (int j = 0; j < n; ++j) {
+  const bool track = min_ratio != nullptr;
+  if (tid == 0) { bad = n > 2048 ? 1 : 0; rmin = 1.0; }
+  __syncthreads();
+  if (!bad && track)
+    for (int i = tid; i < n; i += bd) d0[i] = A[(int64_t)i * lda + i];
+  for (int j = 0; j < n && !bad; ++j) {
     __syncthreads();
     if (tid == 0) {
       const double d = A[(int64_t)j * lda + j];
       if (!(d > 0.0) || !isfinite(d)) bad = j + 1;
-      else { piv = sqrt(d); A[(int64_t)j * lda + j] = piv; }
+      else {
+        piv = sqrt(d);
+        A[(int64_t)j * lda + j] = piv;
+        if (track) rmin = fmin(rmin, d / d0[j]);
+      }
     }
     __syncthreads();
     if (bad) break;
-    for (int i = j + 1 + tid; i < n; i += bd) A[(int64_t)i * lda + j] /= piv;
+    const int m = n - j - 1;
+    for (int i = tid; i < m; i += bd) {
+      const double v = A[(int64_t)(j + 1 + i) * lda + j] / piv;
+      A[(int64_t)(j + 1 + i) * lda + j] = v;
+      lj[i] = v;
+    }
     __syncthreads();
-    const int64_t mm = n - j - 1;
-    const int64_t tot = mm * (mm + 1) / 2;
+    const int64_t tot = (int64_t)m * m;
     for (int64_t t = tid; t < tot; t += bd) {
-      int64_t ii = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-      while (ii * (ii + 1) / 2 > t) --ii;
-      while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
-      const int64_t cc = t - ii * (ii + 1) / 2;
-      const int i = j + 1 + (int)ii, c = j + 1 + (int)cc;
-      A[(int64_t)i * lda + c] -= A[(int64_t)i * lda + j] * A[(int64_t)c * lda + j];
+      const int i = (int)(t / m), c = (int)(t % m);
+      if (c <= i) A[(int64_t)(j + 1 + i) * lda + (j + 1 + c)] -= lj[i] * lj[c];
     }
   }
   __syncthreads();
@@ -637,7 +674,25 @@ __global__ void __launch_bounds__(1024) k_chol(double* A, int n, int lda, int* i
     const int i = (int)(t / n), c = (int)(t % n);
     if (c > i) A[(int64_t)i * lda + c] = 0.0;
   }
-  if (tid == 0) *info = bad;
+  if (tid == 0) {
+    *info = bad;
+    if (min_ratio) *min_ratio = bad ? 0.0 : rmin;
+  }
+}
+
+// A += shift I, shift = coef * trace(A) (one CTA; the trace bounds ||X||_2^2 for A = X^T X).
+__global__ void k_shift_diag(double* A, int n, int lda, double coef) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += A[(int64_t)i * lda + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double shift = coef * red[0];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * lda + i] += shift;
 }
 
 // Li = L^-1 (lower), one column per thread by forward substitution.
@@ -1034,8 +1089,13 @@ void launch_gemm_tn(int64_t K, int Na, int Nb, const double* A, int64_t lda, con
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-void launch_chol(double* A, int n, int lda, int* info, cudaStream_t st) {
-  k_chol<<<1, 1024, 0, st>>>(A, n, lda, info);
+void launch_shift_diag(double* A, int n, int lda, double coef, cudaStream_t st) {
+  k_shift_diag<<<1, 1024, 0, st>>>(A, n, lda, coef);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_chol(double* A, int n, int lda, int* info, cudaStream_t st, double* min_ratio) {
+  k_chol<<<1, 1024, 0, st>>>(A, n, lda, info, min_ratio);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
@@ -1125,17 +1185,24 @@ void launch_cell_apply_narrow_f32(const float* Hcc, const int32_t* cells, int64_
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-int coup_nblocks(int64_t n_tn, int bpc) {
-  const int64_t nblk = (n_tn + CPB - 1) / CPB;
-  return (int)((nblk + bpc - 1) / bpc);
-}
-
 int coup_block_nodes() { return CPB; }
 
 // shared memory of the node-major kernels: the (n_E x N) array, the rows
 // kernel's CPB x (N + 4) vector tile and one CPF x CPB pattern tile
 size_t coup_smem(int nE, int N, bool rows) {
-  return sizeof(float) * ((size_t)nE * N + (rows ? (size_t)CPB * (N + 4) : 0) + (size_t)CPF * CPB);
+  const size_t ld = (size_t)((N + 3) & ~3);
+  return sizeof(float) * ((size_t)nE * ld + (rows ? (size_t)CPB * ld : 0) + (size_t)CPF * CPB);
+}
+
+// CTAs of the rows product resident at once (one wave of the partition)
+int coup_resident_ctas(int nE, int N, int n_sm) {
+  const size_t smem = coup_smem(nE, N, true);
+  cudaFuncSetAttribute(k_coup_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coup_rows<float>, 256, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * n_sm;
 }
 
 void launch_tile_scatter(int64_t nnz, const int64_t* pos, const float* val, float* tile, cudaStream_t st) {
@@ -1145,39 +1212,41 @@ void launch_tile_scatter(int64_t nnz, const int64_t* pos, const float* val, floa
 }
 
 template <typename T>
-void launch_coup_rows(int64_t n_tn, int bpc, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
-                      const float* tile, const double* scale, const T* X, int64_t ldx, int nE, int N, float* part,
-                      cudaStream_t st) {
-  if (n_tn <= 0 || N <= 0 || nE <= 0) return;
-  const int nb = coup_nblocks(n_tn, bpc);
+void launch_coup_rows(int64_t n_tn, int ncta, const int64_t* cta_blk, const int32_t* t_nodes,
+                      const int64_t* slot_off, const int32_t* slots, const float* tile, const double* scale,
+                      const T* X, int64_t ldx, int nE, int N, float* part, cudaStream_t st) {
+  if (n_tn <= 0 || N <= 0 || nE <= 0 || ncta <= 0) return;
   const size_t smem = coup_smem(nE, N, true);
   cudaFuncSetAttribute(k_coup_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_coup_rows<T><<<nb, 256, smem, st>>>(n_tn, bpc, t_nodes, slot_off, slots, tile, scale, X, ldx, nE, N, part);
+  k_coup_rows<T><<<ncta, 256, smem, st>>>(n_tn, cta_blk, t_nodes, slot_off, slots, tile, scale, X, ldx, nE, N, part);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
-template void launch_coup_rows<float>(int64_t, int, const int32_t*, const int64_t*, const int32_t*, const float*,
-                                      const double*, const float*, int64_t, int, int, float*, cudaStream_t);
+template void launch_coup_rows<float>(int64_t, int, const int64_t*, const int32_t*, const int64_t*, const int32_t*,
+                                      const float*, const double*, const float*, int64_t, int, int, float*,
+                                      cudaStream_t);
 
 void launch_coup_reduce(int nb, int nE, int N, const float* part, double sgn, const double* base, int64_t ldb,
                         double alpha_base, double* out, int64_t ldo, cudaStream_t st) {
   if (nE <= 0 || N <= 0) return;
-  k_coup_reduce<<<grid1((int64_t)nE * N, 256), 256, 0, st>>>(nb, nE, N, part, sgn, base, ldb, alpha_base, out, ldo);
+  k_coup_reduce<<<(unsigned)(((int64_t)nE * N + 31) / 32), 256, 0, st>>>(nb, nE, N, part, sgn, base, ldb, alpha_base,
+                                                                         out, ldo);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
 template <typename T>
-void launch_coup_cols(int64_t n_tn, int bpc, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
-                      const float* tile, float sgn, const double* Xe, int64_t ldxe, int nE, int N, T* W, int64_t ldw,
-                      cudaStream_t st) {
-  if (n_tn <= 0 || N <= 0 || nE <= 0) return;
-  const int nb = coup_nblocks(n_tn, bpc);
+void launch_coup_cols(int64_t n_tn, int ncta, const int64_t* cta_blk, const int32_t* t_nodes,
+                      const int64_t* slot_off, const int32_t* slots, const float* tile, float sgn, const double* Xe,
+                      int64_t ldxe, int nE, int N, T* W, int64_t ldw, cudaStream_t st) {
+  if (n_tn <= 0 || N <= 0 || nE <= 0 || ncta <= 0) return;
   const size_t smem = coup_smem(nE, N, false);
   cudaFuncSetAttribute(k_coup_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_coup_cols<T><<<nb, 256, smem, st>>>(n_tn, bpc, t_nodes, slot_off, slots, tile, sgn, Xe, ldxe, nE, N, W, ldw);
+  k_coup_cols<T><<<ncta, 256, smem, st>>>(n_tn, cta_blk, t_nodes, slot_off, slots, tile, sgn, Xe, ldxe, nE, N, W,
+                                          ldw);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
-template void launch_coup_cols<float>(int64_t, int, const int32_t*, const int64_t*, const int32_t*, const float*,
-                                      float, const double*, int64_t, int, int, float*, int64_t, cudaStream_t);
+template void launch_coup_cols<float>(int64_t, int, const int64_t*, const int32_t*, const int64_t*, const int32_t*,
+                                      const float*, float, const double*, int64_t, int, int, float*, int64_t,
+                                      cudaStream_t);
 
 void launch_cheb_combine_f4(int64_t nrows, int ld, const double* rowscale, const float* X, const float* Yc,
                             const float* Yp, float* Yn, const double* coef, cudaStream_t st) {

@@ -50,20 +50,21 @@ void launch_cell_apply_narrow_f32(const float* Hcc, const int32_t* cells, int64_
 // node-major enrichment products with FP32 arithmetic (mixed-precision filter) over
 // blocks of coup_block_nodes() pattern nodes: slot_off / slots list the functions of
 // every block, tile holds the values as dense (slots x block) FP32 tiles
-int coup_nblocks(int64_t n_tn, int bpc);   // CTAs for bpc blocks per CTA
 int coup_block_nodes();
 size_t coup_smem(int nE, int N, bool rows);
+int coup_resident_ctas(int nE, int N, int n_sm);   // rows-product CTAs resident at once
+// CTA b of the rows / columns products takes the node blocks cta_blk[b] .. cta_blk[b + 1]
 void launch_tile_scatter(int64_t nnz, const int64_t* pos, const float* val, float* tile, cudaStream_t st);
 template <typename T>
-void launch_coup_rows(int64_t n_tn, int bpc, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
-                      const float* tile, const double* scale, const T* X, int64_t ldx, int nE, int N, float* part,
-                      cudaStream_t st);
+void launch_coup_rows(int64_t n_tn, int ncta, const int64_t* cta_blk, const int32_t* t_nodes,
+                      const int64_t* slot_off, const int32_t* slots, const float* tile, const double* scale,
+                      const T* X, int64_t ldx, int nE, int N, float* part, cudaStream_t st);
 void launch_coup_reduce(int nb, int nE, int N, const float* part, double sgn, const double* base, int64_t ldb,
                         double alpha_base, double* out, int64_t ldo, cudaStream_t st);
 template <typename T>
-void launch_coup_cols(int64_t n_tn, int bpc, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
-                      const float* tile, float sgn, const double* Xe, int64_t ldxe, int nE, int N, T* W, int64_t ldw,
-                      cudaStream_t st);
+void launch_coup_cols(int64_t n_tn, int ncta, const int64_t* cta_blk, const int32_t* t_nodes,
+                      const int64_t* slot_off, const int32_t* slots, const float* tile, float sgn, const double* Xe,
+                      int64_t ldxe, int nE, int N, T* W, int64_t ldw, cudaStream_t st);
 void launch_cheb_combine_f4(int64_t nrows, int ld, const double* rowscale, const float* X, const float* Yc,
                             const float* Yp, float* Yn, const double* coef, cudaStream_t st);
 // out[node_r] += sgn * sum_q val[q] * Xe[col[q]]   (rows = nodes that meet a support)
@@ -119,11 +120,20 @@ int launch_oz_cell(const double* Hcc, const int* hexp, const int32_t* cells, int
 int64_t oz_cell_image_bytes();
 void launch_oz_preslice(const double* Hcc, const int* hexp, int64_t n_cell, unsigned char* img, cudaStream_t st);
 int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, const double* B, int64_t ldb,
-                   const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st);
+                   const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st,
+                   const unsigned char* Aimg = nullptr, const unsigned char* Bimg = nullptr);
+// pre-sliced operand images for the ROWS / GRAM products (bytes, builders)
+int64_t oz_img_rows_bytes(int64_t rows, int K);
+int64_t oz_img_cols_bytes(int64_t nch, int ncols);
+void launch_oz_img_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, unsigned char* img,
+                        cudaStream_t st);
+void launch_oz_img_cols(const double* A, int64_t lda, int64_t Krows, int ncols, const int* cexp, int64_t nch,
+                        unsigned char* img, cudaStream_t st);
 // C (Na x N) = A^T B, A: K x Na, B: K x N (K large); aexp / bexp per column (launch_oz_colexp)
 int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const int* aexp, const double* B,
                    int64_t ldb, const int* bexp, double* C, int64_t ldc, bool sym, double* work, int64_t work_elems,
-                   int2* pairs_dev, int n_sm, int* err, cudaStream_t st);
+                   int2* pairs_dev, int n_sm, int* err, cudaStream_t st, unsigned char* img_a = nullptr,
+                   int64_t img_a_bytes = 0, unsigned char* img_b = nullptr, int64_t img_b_bytes = 0);
 int oz_gram_max_pairs(int Na, int N);
 
 // ---- dense FP64 ----
@@ -140,7 +150,8 @@ void launch_gemm_nn_batched(int64_t M, int Nc, int K, const double* A, int64_t l
 void launch_gemm_tn(int64_t K, int Na, int Nb, const double* A, int64_t lda, const double* B, int64_t ldb,
                     double* C, int64_t ldc, double* work, int64_t work_elems, cudaStream_t st, bool sym = false);
 int64_t gemm_tn_work_elems(int64_t K, int Na, int Nb);
-void launch_chol(double* A, int n, int lda, int* info, cudaStream_t st);
+void launch_chol(double* A, int n, int lda, int* info, cudaStream_t st, double* min_ratio = nullptr);
+void launch_shift_diag(double* A, int n, int lda, double coef, cudaStream_t st);
 void launch_trinv_lower(const double* L, int n, int lda, double* Li, int ldi, cudaStream_t st);
 void launch_transpose(const double* A, int n, int lda, double* B, int ldb, cudaStream_t st);
 void launch_symmetrize(double* A, int n, int lda, cudaStream_t st);

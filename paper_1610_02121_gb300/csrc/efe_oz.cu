@@ -44,10 +44,14 @@ constexpr int OZ_M = 128;          // MMA rows
 constexpr int OZ_KC = 16;          // K per chunk (one BF16 MMA)
 constexpr int OZ_TW = 96;          // column tile
 constexpr int OZ_NACC = 5;         // accumulators: t = 2, 3, 4, 5 exact; t = 6..8 shared
-constexpr int OZ_STAGES = 3;
-constexpr int OZ_THREADS = 512;
+constexpr int OZ_STAGES = 4;
+constexpr int OZ_GROUPS = 2;        // slicer groups: group g fills the chunks ch = g (mod 2)
 constexpr int OZ_CONV_W0 = 1, OZ_CONV_WN = 11, OZ_EPI_W0 = 12;
+constexpr int OZ_THREADS = (OZ_EPI_W0 + 4) * 32;  // 16 warps: 128 registers a thread
 constexpr int OZ_CONV_T = OZ_CONV_WN * 32;
+constexpr int OZ_GT0 = 6 * 32;                     // group 0: warps 1-6; group 1: warps 7-11
+__host__ __device__ constexpr int oz_group_threads(int grp) { return grp == 0 ? OZ_GT0 : OZ_CONV_T - OZ_GT0; }
+static_assert(OZ_STAGES % OZ_GROUPS == 0, "a stage is always filled by the same group");
 constexpr uint32_t OZ_TMEM_COLS = 512;
 constexpr long long OZ_WAIT = 2000000000LL;
 
@@ -143,6 +147,34 @@ __device__ __forceinline__ void slice_store(double x, int E, unsigned char* base
   }
 }
 
+// digits of eight values with scale exponent E, packed slice by slice (two BF16
+// per word): pk[i] holds digit i of x[0..7] in K order
+__device__ __forceinline__ void oz_pack8(const double (&x)[8], int E, uint32_t (&pk)[OZ_S][4]) {
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pk[i][q] = 0u;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const long long bits = __double_as_longlong(x[q]);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    const uint32_t sgn = (uint32_t)((bits >> 48) & 0x8000);
+    unsigned long long qq = 0;
+    const int rs = 1026 + E - ex;
+    if (ex != 0 && rs >= 0 && rs < 64) qq = ((unsigned long long)(bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> rs;
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) {
+      const uint32_t d = (uint32_t)(qq >> (42 - 7 * i)) & 127u;
+      uint32_t h16 = 0;
+      if (d) {
+        const int p = 31 - __clz(d);
+        h16 = sgn | ((uint32_t)(p + 127 - 7 * i) << 7) | ((d << (7 - p)) & 0x7Fu);
+      }
+      pk[i][q >> 1] |= h16 << (16 * (q & 1));
+    }
+  }
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   const float bb = s - a;
@@ -180,6 +212,11 @@ struct OzArgs {
   int Na, nseg, npairs;
   const int2* pairs;        // (M tile, N tile) of every item pair
   double* part;
+  // pre-sliced operand images (k_oz_img_rows / k_oz_img_cols); NULL: sliced here.
+  // ROWS: Aimg = row image of A, Bimg = column image of B; GRAM: both column
+  // images.  img_nch: 16-wide K chunks per 128-wide tile of a column image.
+  const unsigned char* Bimg;
+  int64_t img_nch;
 };
 
 // work item of a CTA: cell / row block / tile pair and its K range
@@ -225,14 +262,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   if (tid == 0) s_skip = *(volatile int*)g.err;
   __syncthreads();
   if (s_skip) return;
-  uint64_t* conv = reinterpret_cast<uint64_t*>(sm + OzL::BARS);  // [3]
-  uint64_t* empty = conv + 3;                                   // [3]
-  uint64_t* accf = conv + 6;
-  uint64_t* acce = conv + 7;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(conv + 8);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(conv + 9);
-  uint64_t* afull = conv + 10;                                  // [3] pre-sliced A chunks landed
-  const bool apre = (g.mode == 0) && g.Aimg != nullptr;
+  uint64_t* conv = reinterpret_cast<uint64_t*>(sm + OzL::BARS);  // [stages] slices written
+  uint64_t* empty = conv + OZ_STAGES;                           // [stages] MMAs done with the stage
+  uint64_t* accf = conv + 2 * OZ_STAGES;
+  uint64_t* acce = accf + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(accf + 3);
+  uint64_t* afull = accf + 4;                                   // [stages] bulk-copied operand chunks landed
+  const bool apre = g.Aimg != nullptr;
+  const bool bpre = g.mode != 0 && g.Bimg != nullptr;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
                  "r"(OZ_TMEM_COLS)
@@ -241,7 +279,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   }
   if (tid == 32) {
     for (int s = 0; s < OZ_STAGES; ++s) {
-      bar_init(conv + s, OZ_CONV_T);
+      bar_init(conv + s, oz_group_threads(s % OZ_GROUPS));
       bar_init(empty + s, 1);
       bar_init(afull + s, 1);
     }
@@ -280,7 +318,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         const int64_t ch = t * nch + kc;
         const int s = (int)(ch % OZ_STAGES);
         ok = bar_wait(conv + s, (uint32_t)((ch / OZ_STAGES) & 1));
-        if (ok && apre) ok = bar_wait(afull + s, (uint32_t)((ch / OZ_STAGES) & 1));
+        if (ok && (apre || bpre)) ok = bar_wait(afull + s, (uint32_t)((ch / OZ_STAGES) & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) break;
         if (lane == 0) {
@@ -313,7 +351,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
     }
   } else if (warp < OZ_CONV_W0 + OZ_CONV_WN) {
     // ---------------------------------------------------------------- slicers
-    const int ct = tid - OZ_CONV_W0 * 32;
+    // two groups (six and five warps) take alternate chunks, so two chunks are
+    // sliced (and their loads are in flight) at a time
+    const int grp = (tid - OZ_CONV_W0 * 32) < OZ_GT0 ? 0 : 1;
+    const int ct = (tid - OZ_CONV_W0 * 32) - grp * OZ_GT0;
+    const int gsz_t = oz_group_threads(grp);
+    int64_t last_copy = -1;   // last chunk whose operand copies this thread issued
     for (int64_t t = 0; t < my && !*abort_flag; ++t) {
       const OzItem it = oz_item(g, blockIdx.x + t * gridDim.x);
       const int64_t ia = it.ia, e = it.e;
@@ -321,6 +364,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
       bool ok = true;
       for (int kc = 0; kc < nch; ++kc) {
         const int64_t ch = t * nch + kc;
+        if ((int)(ch % OZ_GROUPS) != grp) continue;
         const int s = (int)(ch % OZ_STAGES);
         if (ch >= OZ_STAGES) {
           ok = bar_wait(empty + s, (uint32_t)((ch / OZ_STAGES - 1) & 1));
@@ -328,15 +372,47 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         }
         unsigned char* SA = sm + s * OzL::STAGE;
         unsigned char* SB = SA + OZ_S * OzL::ASL;
-        if (apre && ct == 0) {
-          // the cell's pre-sliced chunk: seven 4 KB slices, one bulk copy
-          bar_expect_tx(afull + s, OZ_S * OzL::ASL);
-          bulk_g2s(SA, g.Aimg + ((e * (int64_t)nch + kc) * OZ_S) * OzL::ASL, OZ_S * OzL::ASL, afull + s);
+        if ((apre || bpre) && ct == 0) {
+          // pre-sliced operand chunks: bulk copies of 256-byte row groups into the stage
+          const int64_t kA = (g.mode == 2) ? it.kb / OZ_KC + kc : kc;
+          const int ga = (g.mode == 2) ? (int)((min((int64_t)OZ_M, (int64_t)g.Na - it.m0) + 7) / 8) : 16;
+          const int gb = nmma / 8;
+          uint32_t bytes = 0;
+          if (apre) bytes += (uint32_t)(OZ_S * ga * 256);
+          if (bpre) bytes += (uint32_t)(OZ_S * gb * 256);
+          bar_expect_tx(afull + s, bytes);
+          if (apre) {
+            // CELL: image of cell e; ROWS: of row tile ia; GRAM: of column tile m0 / 128
+            const int64_t img = (g.mode == 0) ? e * (int64_t)nch + kA
+                              : (g.mode == 1) ? ia * (int64_t)nch + kA
+                                              : (it.m0 / OZ_M) * g.img_nch + kA;
+            const unsigned char* src = g.Aimg + img * OZ_S * (int64_t)OzL::ASL;
+            if (ga == 16) {
+              bulk_g2s(SA, src, OZ_S * OzL::ASL, afull + s);
+            } else {
+              for (int i2 = 0; i2 < OZ_S; ++i2)
+                bulk_g2s(SA + i2 * OzL::ASL, src + i2 * OzL::ASL, (uint32_t)(ga * 256), afull + s);
+            }
+          }
+          if (bpre) {
+            // columns c0 .. c0 + nmma of B: row groups of the 128-wide column tiles
+            const int64_t nchB = (g.mode == 2) ? g.img_nch : nch;
+            for (int j = 0; j < gb;) {
+              const int G = c0 / 8 + j;
+              const int tile = G >> 4, gi = G & 15;
+              const int run = min(gb - j, 16 - gi);
+              const unsigned char* src = g.Bimg + ((tile * nchB + kA) * OZ_S) * (int64_t)OzL::ASL + gi * 256;
+              for (int i2 = 0; i2 < OZ_S; ++i2)
+                bulk_g2s(SB + i2 * OzL::BSL + j * 256, src + i2 * OzL::ASL, (uint32_t)(run * 256), afull + s);
+              j += run;
+            }
+          }
+          last_copy = ch;
         }
         // one thread per (row, 8-wide K octet): eight loads in flight, then seven
-        // 16-byte slice stores (one core-matrix row each); with pre-sliced cells
-        // only the vector block (the B tasks) is sliced here
-        for (int v = ct + (apre ? OZ_M * 2 : 0); v < (OZ_M + nmma) * 2; v += OZ_CONV_T) {
+        // 16-byte slice stores (one core-matrix row each); pre-sliced operands
+        // (the A tasks, the B tasks) are skipped
+        for (int v = ct + (apre ? OZ_M * 2 : 0); v < (bpre ? OZ_M * 2 : (OZ_M + nmma) * 2); v += gsz_t) {
           const bool isA = v < OZ_M * 2;
           const int w = isA ? v : v - OZ_M * 2;
           const int row = w >> 1, oct = w & 1;        // row of A, or column n of the product
@@ -430,10 +506,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         break;
       }
     }
-    if (apre && ct == 0 && *abort_flag && my > 0) {
-      // let the last bulk copy of this thread land before the CTA can leave
-      const int64_t cl = my * nch - 1;
-      bar_wait(afull + (int)(cl % OZ_STAGES), (uint32_t)((cl / OZ_STAGES) & 1));
+    if (ct == 0 && *abort_flag && last_copy >= 0) {
+      // let the last bulk copies of this thread land before the CTA can leave
+      bar_wait(afull + (int)(last_copy % OZ_STAGES), (uint32_t)((last_copy / OZ_STAGES) & 1));
     }
   } else {
     // ---------------------------------------------------------------- epilogue
@@ -460,6 +535,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         Er = live ? g.aexp[row] : 0;
         orow = live ? g.part + ((int64_t)it.seg * g.Na + row) * g.N + c0 : nullptr;
       }
+      // the row's output segment is pulled towards L2 while the MMAs run
+      if (live && (g.mode == 0 || g.mode == 2))
+        for (int cb = 0; cb < ncol; cb += 16) asm volatile("prefetch.L2 [%0];" ::"l"(orow + cb));
       bool stop = false;
       for (int grp = 0; grp < ngrp; ++grp) {
         const int64_t gc = t * ngrp + grp;
@@ -472,7 +550,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // modes 0 and 2 add to what is there (mode 2 from its second group on)
         const bool add = (g.mode == 0) || (g.mode == 2 && grp > 0);
+        // values to add to: loaded one 8-column block ahead of their use
+        double nxt[8];
+        if (live && add) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) nxt[q] = (q < ncol) ? orow[q] : 0.0;
+        }
         for (int cb = 0; cb < ncol; cb += 8) {
+          double cur[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) cur[q] = nxt[q];
+          if (live && add && cb + 8 < ncol) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) nxt[q] = (cb + 8 + q < ncol) ? orow[cb + 8 + q] : 0.0;
+          }
           uint32_t v[OZ_NACC][8];
 #pragma unroll
           for (int a = 0; a < OZ_NACC; ++a)
@@ -484,11 +575,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
                 : "memory");
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           if (live) {
-            double cur[8];
-            if (add) {
-#pragma unroll
-              for (int q = 0; q < 8; ++q) cur[q] = (cb + q < ncol) ? orow[cb + q] : 0.0;
-            }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const int n = cb + q;
@@ -562,6 +648,67 @@ __global__ void k_oz_preslice(const double* __restrict__ H, const int* __restric
     }
   }
   unsigned char* base = img + ((e * nch + kc) * OZ_S) * (int64_t)OzL::ASL + bo(row, oct * 8);
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i)
+    *reinterpret_cast<uint4*>(base + (int64_t)i * OzL::ASL) = make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+}
+
+// Row image of a tall A (rows x K, the A operand of ROWS): per 128-row tile and
+// 16-wide K chunk the seven 4 KB BF16 slices in the shared-memory layout of
+// the MMA operand (row exponents aexp); rows past `rows` are zero.  One thread
+// per (tile row, K octet); a warp covers 32 rows of one octet.
+__global__ void k_oz_img_rows(const double* __restrict__ A, int64_t lda, int64_t rows, int K,
+                              const int* __restrict__ aexp, unsigned char* __restrict__ img) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int nch = (K + OZ_KC - 1) / OZ_KC;
+  const int64_t ntile = (rows + OZ_M - 1) / OZ_M;
+  if (t >= ntile * nch * 2 * OZ_M) return;
+  const int rr = (int)(t % OZ_M);
+  const int oct = (int)((t / OZ_M) & 1);
+  const int64_t tc = t / (2 * OZ_M);   // tile * nch + chunk
+  const int c = (int)(tc % nch);
+  const int64_t r = (tc / nch) * OZ_M + rr;
+  double x[8];
+  const int E = r < rows ? aexp[r] : -2000;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int k = c * OZ_KC + oct * 8 + q;
+    x[q] = (r < rows && k < K) ? A[r * lda + k] : 0.0;
+  }
+  uint32_t pk[OZ_S][4];
+  oz_pack8(x, E, pk);
+  unsigned char* base = img + tc * OZ_S * (int64_t)OzL::ASL + bo(rr, oct * 8);
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i)
+    *reinterpret_cast<uint4*>(base + (int64_t)i * OzL::ASL) = make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+}
+
+// Column image of A (Krows x ncols): the K-major operand A^T, element (m, k) =
+// A[k][m], per 128-column tile and 16-row chunk (nch chunks per tile, rows past
+// Krows zero), seven 4 KB slices in the MMA layout (column exponents cexp).
+// Columns past ncols rounded up to 16 are not written.  A warp reads 32
+// consecutive columns of one row.
+__global__ void k_oz_img_cols(const double* __restrict__ A, int64_t lda, int64_t Krows, int ncols,
+                              const int* __restrict__ cexp, int64_t nch, unsigned char* __restrict__ img) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int ntile = (ncols + OZ_M - 1) / OZ_M;
+  if (t >= (int64_t)ntile * nch * 2 * OZ_M) return;
+  const int m = (int)(t % OZ_M);
+  const int oct = (int)((t / OZ_M) & 1);
+  const int64_t tc = t / (2 * OZ_M);   // tile * nch + chunk
+  const int64_t c = tc % nch;
+  const int col = (int)(tc / nch) * OZ_M + m;
+  if (col >= ((ncols + 15) & ~15)) return;
+  const int E = col < ncols ? cexp[col] : -2000;
+  double x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t k = c * OZ_KC + oct * 8 + q;
+    x[q] = (col < ncols && k < Krows) ? A[k * lda + col] : 0.0;
+  }
+  uint32_t pk[OZ_S][4];
+  oz_pack8(x, E, pk);
+  unsigned char* base = img + tc * OZ_S * (int64_t)OzL::ASL + bo(m, oct * 8);
 #pragma unroll
   for (int i = 0; i < OZ_S; ++i)
     *reinterpret_cast<uint4*>(base + (int64_t)i * OzL::ASL) = make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
@@ -681,13 +828,41 @@ int launch_oz_cell(const double* Hcc, const int* hexp, const int32_t* cells, int
   return oz_launch(a, n_sm, st);
 }
 
+int64_t oz_img_rows_bytes(int64_t rows, int K) {
+  return ((rows + OZ_M - 1) / OZ_M) * ((K + OZ_KC - 1) / OZ_KC) * OZ_S * (int64_t)OzL::ASL;
+}
+
+int64_t oz_img_cols_bytes(int64_t nch, int ncols) {
+  return (int64_t)((ncols + OZ_M - 1) / OZ_M) * nch * OZ_S * (int64_t)OzL::ASL;
+}
+
+void launch_oz_img_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, unsigned char* img,
+                        cudaStream_t st) {
+  const int64_t n = ((rows + OZ_M - 1) / OZ_M) * ((K + OZ_KC - 1) / OZ_KC) * 2 * OZ_M;
+  if (n <= 0) return;
+  k_oz_img_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, lda, rows, K, aexp, img);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_oz_img_cols(const double* A, int64_t lda, int64_t Krows, int ncols, const int* cexp, int64_t nch,
+                        unsigned char* img, cudaStream_t st) {
+  const int64_t n = (int64_t)((ncols + OZ_M - 1) / OZ_M) * nch * 2 * OZ_M;
+  if (n <= 0) return;
+  k_oz_img_cols<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, lda, Krows, ncols, cexp, nch, img);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 // C = A B (A: rows x K, K <= 144; B: K x N), FP64-grade; aexp / bexp from
-// launch_oz_rowexp(A) and launch_oz_colexp(B).
+// launch_oz_rowexp(A) and launch_oz_colexp(B).  Aimg / Bimg (optional):
+// launch_oz_img_rows(A) and launch_oz_img_cols(B, nch = ceil(K / 16)).
 int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, const double* B, int64_t ldb,
-                   const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st) {
+                   const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st,
+                   const unsigned char* Aimg, const unsigned char* Bimg) {
   if (rows <= 0 || N <= 0) return 0;
   if (K > 144) return 1;
   OzArgs a{};
+  a.Aimg = Aimg;
+  a.Bimg = Bimg;
   a.mode = 1;
   a.A = A;
   a.lda = lda;
@@ -746,7 +921,8 @@ __global__ void k_oz_gram_reduce(int nseg, int Na, int N, const double* __restri
 
 int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const int* aexp, const double* B,
                    int64_t ldb, const int* bexp, double* C, int64_t ldc, bool sym, double* work, int64_t work_elems,
-                   int2* pairs_dev, int n_sm, int* err, cudaStream_t st) {
+                   int2* pairs_dev, int n_sm, int* err, cudaStream_t st, unsigned char* img_a,
+                   int64_t img_a_bytes, unsigned char* img_b, int64_t img_b_bytes) {
   if (K <= 0 || Na <= 0 || N <= 0) return 0;
   if (sym && Na != N) return 1;
   std::vector<int2> pairs(oz_gram_pairs(Na, N, sym, nullptr));
@@ -775,6 +951,16 @@ int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const
   a.part = work;
   a.ntiles = (N + OZ_TW - 1) / OZ_TW;
   a.err = err;
+  // column images of A and B (one image when B is A) covering every segment
+  const int64_t nch = nseg * seg_len / OZ_KC;
+  if (img_a && oz_img_cols_bytes(nch, Na) <= img_a_bytes &&
+      (B == A || (img_b && oz_img_cols_bytes(nch, N) <= img_b_bytes))) {
+    launch_oz_img_cols(A, lda, K, Na, aexp, nch, img_a, st);
+    if (B != A) launch_oz_img_cols(B, ldb, K, N, bexp, nch, img_b, st);
+    a.Aimg = img_a;
+    a.Bimg = (B == A) ? img_a : img_b;
+    a.img_nch = nch;
+  }
   if (oz_launch(a, n_sm, st)) return 1;
   k_oz_gram_reduce<<<(unsigned)(((int64_t)Na * N + 255) / 256), 256, 0, st>>>((int)nseg, Na, N, work, sym ? 1 : 0, C,
                                                                              ldc);

@@ -144,7 +144,7 @@ def test_error_paths(tiny_pair):
         G.chfsi_step(X, 3, 1.0, 0.5, 0.0)            # a > b
     assert e.value.code == 1
     Xr = to_dev(W.initial_block(d.system, 4, seed=1))
-    Xr[:, 3] = Xr[:, 2]                               # rank-deficient block
+    Xr[:, 3] = float("nan")                           # non-finite block
     with pytest.raises(EfeError) as e:
         G.rayleigh_ritz(Xr)
     assert e.value.code == 3
@@ -153,6 +153,33 @@ def test_error_paths(tiny_pair):
         G.set_potential(V)
     assert e.value.code == 6
     G.set_potential_analytic()                         # restore
+
+
+def test_rank_deficient_block_shifted_cholqr(tiny_pair):
+    """Duplicated and nearly collinear columns: Rayleigh-Ritz takes shifted
+    Cholesky-QR passes and still returns M-orthonormal Ritz vectors whose Ritz
+    values interlace the exact spectrum (eps_k >= lambda_k, Cauchy)."""
+    from oracle.chfsi import dense_eigs
+    d, G = tiny_pair
+    N = 6
+    ref = dense_eigs(d, N)
+    for kind in ("duplicate", "collinear"):
+        # generic columns (unit-vector columns make every product exact and
+        # leave no rounding noise for the shifted passes to lift)
+        X = to_dev(W.random_block(d.system, N, seed=2))
+        if kind == "duplicate":
+            X[:, 4] = X[:, 1]
+        else:
+            X[:, 5] = X[:, 0] + 1e-11 * X[:, 3]
+        n0 = G.rr_shifted_passes()
+        eps, res = G.rayleigh_ritz(X)
+        assert G.rr_shifted_passes() > n0
+        assert np.all(np.isfinite(eps)) and np.all(np.isfinite(res))
+        assert np.all(np.diff(eps) >= 0)
+        assert np.all(eps >= ref[:N] - 1e-10)
+        MX = G.apply_M(X)
+        gram = (X.T @ MX).cpu().numpy()
+        assert np.abs(gram - np.eye(N)).max() < 1e-10
 
 
 def test_hydrogen_config1_converged():

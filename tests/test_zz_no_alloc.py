@@ -1,8 +1,8 @@
 """The allocation-free overlap product against the regular one.
 
 efe_apply_M_noalloc serves callers that cannot allocate device memory at call
-time (stream capture into a CUDA graph, latency-critical loops, fixed memory
-budgets): its scratch is a static device array shared by all calls.  Two
+time (latency-critical loops that cannot take cudaMalloc's synchronisation,
+fixed memory budgets): its scratch is a static device array shared by all calls.  Two
 consecutive calls through the C ABI must each reproduce efe_apply_M.  This file
 is collected last so a failure here never hides another test's result.
 """

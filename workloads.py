@@ -224,6 +224,15 @@ def _cluster_system(atoms, Z, h_min, h_max, pad, r_c, seed, pot_seed, n_gaussian
     return _system(breaks, 4, atoms, Z, funcs, pot, tau=tau, max_depth=max_depth, name=name)
 
 
+def displaced_cluster(system, shift, h_min=1.0, h_max=3.5, pad=8.0, r_c=4.0, tau=1e-8, max_depth=7, seed=0):
+    """The cluster of `system` with every atom moved by shift[I] (bohr, rounded to
+    1e-3): same species, a new graded mesh around the new positions and the
+    enrichment drawn with the same seeds as random_cluster(seed=seed)."""
+    atoms = np.round(np.asarray(system["atoms"], dtype=np.float64) + np.asarray(shift, dtype=np.float64), 3)
+    return _cluster_system(atoms, np.asarray(system["Z"], dtype=np.float64), h_min, h_max, pad, r_c, seed + 1000,
+                           seed + 2000, 0, tau, max_depth, name=system["name"] + "_displaced")
+
+
 def grid_dims(system):
     """Nodes per axis of the tensor-product node grid (boundary included)."""
     p = system["p"]
