@@ -391,6 +391,7 @@ def main():
     if roof_other is not None:
         line["roofline_other_kernel"] = roof_other
     line["kernel_ms_per_step"] = {"k_cell_tc3": k_ms / args.steps, "k_oz": oz_ms / args.steps}
+    line["shifted_cholqr_passes_total"] = G.rr_shifted_passes()
     if clocks:
         line["clocks"] = clocks
     # FP64 mode of the same step

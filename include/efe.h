@@ -179,7 +179,7 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m,
  * (M-orthonormal Ritz vectors, ascending eps).  eig_host / resid_host (host,
  * N doubles each; resid_host may be NULL) receive the Ritz values and
  * ||H x_i - eps_i M x_i||_2.  A numerically rank-deficient X (G not
- * positive definite in FP64, or a column keeping less than 1e-10 of its
+ * positive definite in FP64, or a column keeping less than 1e-14 of its
  * squared norm outside the span of the columns before it) is first made well
  * conditioned by up to five shifted Cholesky-QR passes (G + s I, s = 11 (rows
  * N + N (N + 1)) u ||X||_F^2; Fukaya et al., SIAM J. Sci. Comput. 42, 2020);

@@ -1580,9 +1580,11 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   // Cholesky-QR: G = X^T X = L L^T, Q = X L^-T
   CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
   // factorise the Gram matrix of X; ok if X is numerically full rank: G is
-  // positive definite and every column keeps a fraction >= 1e-10 of its squared
-  // norm outside the span of the columns before it (the orthogonality of
-  // X L^-T is then within ~1e-6, ample for the generalised problem below)
+  // positive definite and every column keeps a fraction >= 1e-14 of its squared
+  // norm outside the span of the columns before it (X L^-T is then orthogonal
+  // to ~1e-2, well conditioned enough for the generalised problem below; the
+  // filter's spread of amplifications over an all-electron spectrum routinely
+  // leaves blocks between 1e-14 and 1e-10)
   auto gram_chol = [&](bool& ok) -> int {
     TRY(gemm_gram(h, R, N, X, ldx, X, ldx, G, true, st));
     launch_symmetrize(G, N, N, st);
@@ -1597,7 +1599,7 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
       h->err = "tensor-core FP64 product: bounded wait ran out";
       return EFE_ERR_TIMEOUT;
     }
-    ok = fl[0] == 0 && ratio >= 1e-10;
+    ok = fl[0] == 0 && ratio >= 1e-14;
     return EFE_OK;
   };
   bool ok = false;
