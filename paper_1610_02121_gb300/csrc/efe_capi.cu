@@ -99,7 +99,8 @@ struct efe_handle {
   float *mecT32 = nullptr, *hecT32 = nullptr;
   // dense FP32 tiles of the pattern over blocks of pattern nodes (mixed filter)
   int64_t cb_nblk = 0, cb_nslots = 0;
-  int64_t *cb_slot_off = nullptr, *cb_pos = nullptr, *cb_cta = nullptr;
+  int64_t *cb_slot_off = nullptr, *cb_pos = nullptr, *cb_cta = nullptr, *cb_cta_cols = nullptr;
+  int ncb_cols = 1;                    // CTAs of the columns product
   std::vector<int64_t> cb_soff_host;   // slot offsets of the node blocks (host copy)
   int32_t* cb_slots = nullptr;
   float *tileH = nullptr, *tileM = nullptr;
@@ -250,14 +251,15 @@ int reserve32(efe_handle* h, int N) {
   }
   TRY(dalloc(h, &h->Wf, h->n_nodes * ld));
   CK(cudaMemset(h->Wf, 0, sizeof(float) * h->n_nodes * ld));
-  // coupling products: one wave of CTAs, node blocks split so that every CTA
-  // holds about the same number of tile slots (plus a share for staging rows)
-  dfree(h, h->cb_cta);
-  h->cb_cta = nullptr;
-  h->ncb = 1;
-  if (h->nE > 0 && h->cb_nblk > 0) {
+  // coupling products: one wave of CTAs each, node blocks split so that every
+  // CTA holds about the same number of tile slots (plus a share for staging rows)
+  auto partition = [&](bool rows, int64_t** dev, int* ncta_out) -> int {
+    dfree(h, *dev);
+    *dev = nullptr;
+    *ncta_out = 1;
+    if (h->nE <= 0 || h->cb_nblk <= 0) return EFE_OK;
     const int64_t nblk = h->cb_nblk;
-    const int ncta = (int)std::min<int64_t>(nblk, coup_resident_ctas((int)h->nE, N, h->n_sm));
+    const int ncta = (int)std::min<int64_t>(nblk, coup_resident_ctas((int)h->nE, N, h->n_sm, rows));
     const auto& so = h->cb_soff_host;
     const double wtot = (double)so[nblk] + 3.0 * (double)nblk;
     std::vector<int64_t> cb(ncta + 1, nblk);
@@ -268,9 +270,12 @@ int reserve32(efe_handle* h, int N) {
       while (b < nblk && (double)so[b] + 3.0 * (double)b < target) ++b;
       cb[c] = std::max(cb[c - 1], b);
     }
-    TRY(upload(h, &h->cb_cta, cb));
-    h->ncb = ncta;
-  }
+    TRY(upload(h, dev, cb));
+    *ncta_out = ncta;
+    return EFE_OK;
+  };
+  TRY(partition(true, &h->cb_cta, &h->ncb));
+  TRY(partition(false, &h->cb_cta_cols, &h->ncb_cols));
   TRY(dalloc(h, &h->cpart, (int64_t)h->ncb * std::max<int64_t>(1, h->nE) * N));
   h->ld32 = ld;
   h->Nres32 = N;
@@ -489,7 +494,7 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
   if (h->nE > 0) {
     const int nE = (int)h->nE;
     if (coup_smem(nE, N, true) <= 200 * 1024) {
-      launch_coup_cols<float>(h->n_tn, h->ncb, h->cb_cta, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, 1.f, Yce, N, nE,
+      launch_coup_cols<float>(h->n_tn, h->ncb_cols, h->cb_cta_cols, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, 1.f, Yce, N, nE,
                               N, h->Wf, ld, st);
       launch_coup_rows<float>(h->n_tn, h->ncb, h->cb_cta, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, nullptr, Yc, ld,
                               nE, N, h->cpart, st);
@@ -500,7 +505,7 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
                               ld, nE, N, h->cpart, st);
       launch_coup_reduce(h->ncb, nE, N, h->cpart, -1.0, We, N, 1.0, h->rb, N, st);
       launch_gemm_nn(nE, N, nE, 1.0, h->Sinv, nE, h->rb, N, 0.0, h->xe, N, st);
-      launch_coup_cols<float>(h->n_tn, h->ncb, h->cb_cta, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, -1.f, h->xe, N,
+      launch_coup_cols<float>(h->n_tn, h->ncb_cols, h->cb_cta_cols, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, -1.f, h->xe, N,
                               nE, N, h->Wf, ld, st);
     } else {
       launch_spmm_nodes<float>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->hecT, 1.0, Yce, N, h->Wf, ld, N, st);

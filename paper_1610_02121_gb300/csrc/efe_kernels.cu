@@ -178,6 +178,75 @@ __global__ void k_spmm_segments(const int64_t* __restrict__ seg_start, const int
   }
 }
 
+// Narrow blocks (N <= 4: the Lanczos vector): the lanes of a warp split the
+// entries of a row / segment instead of the columns, and the lane partials are
+// added by a fixed shuffle tree (reproducible).
+constexpr int SPMM_NARROW = 4;
+
+template <typename T>
+__global__ void k_spmm_nodes_narrow(int64_t nrows, const int32_t* __restrict__ rnode, const int64_t* __restrict__ ptr,
+                                    const int32_t* __restrict__ col, const double* __restrict__ val, double sgn,
+                                    const double* __restrict__ Xe, int64_t ldxe, T* __restrict__ out, int64_t ldo,
+                                    int N) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  const int64_t q0 = ptr[w], q1 = ptr[w + 1];
+  double s[SPMM_NARROW] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t q = q0 + lane; q < q1; q += 32) {
+    const double v = val[q];
+    const double* xr = Xe + (int64_t)col[q] * ldxe;
+#pragma unroll
+    for (int c = 0; c < SPMM_NARROW; ++c)
+      if (c < N) s[c] = fma(v, xr[c], s[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < SPMM_NARROW; ++c)
+    for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o);
+  if (lane == 0) {
+    const int64_t g = rnode[w];
+#pragma unroll
+    for (int c = 0; c < SPMM_NARROW; ++c)
+      if (c < N) {
+        T* o = out + g * ldo + c;
+        *o = (T)((double)(*o) + sgn * s[c]);
+      }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_spmm_segments_narrow(const int64_t* __restrict__ seg_start,
+                                                              const int64_t* __restrict__ seg_end,
+                                                              const int32_t* __restrict__ col,
+                                                              const double* __restrict__ val,
+                                                              const double* __restrict__ scale,
+                                                              const T* __restrict__ Xc, int64_t ldx,
+                                                              double* __restrict__ part, int N) {
+  __shared__ double red[8][SPMM_NARROW];
+  const int64_t seg = blockIdx.x;
+  const int64_t q0 = seg_start[seg], q1 = seg_end[seg];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  double s[SPMM_NARROW] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    const int64_t g = col[q];
+    const double v = scale ? val[q] * scale[g] : val[q];
+#pragma unroll
+    for (int c = 0; c < SPMM_NARROW; ++c)
+      if (c < N) s[c] = fma(v, (double)Xc[g * ldx + c], s[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < SPMM_NARROW; ++c) {
+    for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o);
+    if (lane == 0) red[wp][c] = s[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k][threadIdx.x];
+    part[seg * N + threadIdx.x] = t;
+  }
+}
+
 __global__ void k_seg_reduce(int nrows, const int64_t* __restrict__ row_seg_ptr, const double* __restrict__ part,
                              double sgn, const double* __restrict__ base, int64_t ldb, double alpha_base,
                              double* __restrict__ out, int64_t ldo, int N) {
@@ -315,7 +384,7 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, const int64_t* 
   const int ldy = (N + 3) & ~3;
   float* acc = smf;                                  // nE x ldy
   float* Ys = acc + (size_t)nE * ldy;                // CPB x ldy
-  float* Ps = Ys + CPB * ldy;                        // CPF x CPB
+  float* Ps = Ys + CPB * ldy;                        // CPB x (CPF + 4): node-major slice of the tile
   __shared__ int sf[CPF];
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int i = tid; i < nE * ldy; i += bd) acc[i] = 0.f;
@@ -339,7 +408,10 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, const int64_t* 
     for (int64_t sp = s0; sp < s1; sp += CPF) {
       const int nf = (int)min((int64_t)CPF, s1 - sp);
       __syncthreads();
-      for (int i = tid; i < CPF * CPB; i += bd) Ps[i] = (i < nf * CPB) ? tile[sp * CPB + i] : 0.f;
+      for (int i = tid; i < CPF * CPB; i += bd) {
+        const int sl = i / CPB, u = i % CPB;
+        Ps[u * (CPF + 4) + sl] = (i < nf * CPB) ? tile[sp * CPB + i] : 0.f;
+      }
       if (tid < nf) sf[tid] = slots[sp + tid];
       __syncthreads();
       const int nsb = (nf + 3) / 4;
@@ -348,9 +420,8 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, const int64_t* 
         float r[4][4] = {};
 #pragma unroll 8
         for (int u = 0; u < CPB; ++u) {
-          float pv[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) pv[i] = Ps[(sb * 4 + i) * CPB + u];
+          const float4 p4 = *reinterpret_cast<const float4*>(Ps + u * (CPF + 4) + sb * 4);
+          const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
           const float4 y4 = *reinterpret_cast<const float4*>(Ys + u * ldy + cb * 4);
           const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
@@ -451,9 +522,8 @@ __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, const int64_t* 
           for (int sl = 0; sl < nf; ++sl) {
             const float4 x4 = *reinterpret_cast<const float4*>(xs + (size_t)sf[sl] * ldx + cb * 4);
             const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
-            float pv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) pv[i] = Ps[sl * CPB + ub * 4 + i];
+            const float4 p4 = *reinterpret_cast<const float4*>(Ps + sl * CPB + ub * 4);
+            const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -965,7 +1035,11 @@ void launch_spmm_nodes(int64_t nrows, const int32_t* rnode, const int64_t* ptr, 
                        const double* val, double sgn, const double* Xe, int64_t ldxe, T* out, int64_t ldo, int N,
                        cudaStream_t st) {
   if (nrows <= 0 || N <= 0) return;
-  k_spmm_nodes<T><<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out, ldo, N);
+  if (N <= SPMM_NARROW)
+    k_spmm_nodes_narrow<T><<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out,
+                                                                   ldo, N);
+  else
+    k_spmm_nodes<T><<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out, ldo, N);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 template void launch_spmm_nodes<double>(int64_t, const int32_t*, const int64_t*, const int32_t*, const double*,
@@ -978,8 +1052,12 @@ void launch_spmm_segments(int64_t nseg, const int64_t* seg_start, const int64_t*
                           const double* val, const double* scale, const T* Xc, int64_t ldx, double* part, int N,
                           cudaStream_t st) {
   if (nseg <= 0 || N <= 0) return;
-  const int t = N >= 128 ? 128 : ((N + 31) / 32) * 32;
-  k_spmm_segments<T><<<(unsigned)nseg, t, 0, st>>>(seg_start, seg_end, col, val, scale, Xc, ldx, part, N);
+  if (N <= SPMM_NARROW) {
+    k_spmm_segments_narrow<T><<<(unsigned)nseg, 256, 0, st>>>(seg_start, seg_end, col, val, scale, Xc, ldx, part, N);
+  } else {
+    const int t = N >= 128 ? 128 : ((N + 31) / 32) * 32;
+    k_spmm_segments<T><<<(unsigned)nseg, t, 0, st>>>(seg_start, seg_end, col, val, scale, Xc, ldx, part, N);
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 template void launch_spmm_segments<double>(int64_t, const int64_t*, const int64_t*, const int32_t*, const double*,
@@ -1191,17 +1269,22 @@ int coup_block_nodes() { return CPB; }
 // kernel's CPB x (N + 4) vector tile and one CPF x CPB pattern tile
 size_t coup_smem(int nE, int N, bool rows) {
   const size_t ld = (size_t)((N + 3) & ~3);
-  return sizeof(float) * ((size_t)nE * ld + (rows ? (size_t)CPB * ld : 0) + (size_t)CPF * CPB);
+  return sizeof(float) * ((size_t)nE * ld + (rows ? (size_t)CPB * ld + (size_t)CPB * (CPF + 4) : (size_t)CPF * CPB));
 }
 
-// CTAs of the rows product resident at once (one wave of the partition)
-int coup_resident_ctas(int nE, int N, int n_sm) {
-  const size_t smem = coup_smem(nE, N, true);
-  cudaFuncSetAttribute(k_coup_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// CTAs of the rows (or columns) product resident at once (one wave of its partition)
+int coup_resident_ctas(int nE, int N, int n_sm, bool rows) {
+  const size_t smem = coup_smem(nE, N, rows);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coup_rows<float>, 256, smem) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
+  cudaError_t e;
+  if (rows) {
+    cudaFuncSetAttribute(k_coup_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coup_rows<float>, 256, smem);
+  } else {
+    cudaFuncSetAttribute(k_coup_cols<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coup_cols<float>, 256, smem);
+  }
+  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
   return per_sm * n_sm;
 }
 

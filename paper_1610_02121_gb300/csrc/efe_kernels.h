@@ -52,7 +52,7 @@ void launch_cell_apply_narrow_f32(const float* Hcc, const int32_t* cells, int64_
 // every block, tile holds the values as dense (slots x block) FP32 tiles
 int coup_block_nodes();
 size_t coup_smem(int nE, int N, bool rows);
-int coup_resident_ctas(int nE, int N, int n_sm);   // rows-product CTAs resident at once
+int coup_resident_ctas(int nE, int N, int n_sm, bool rows);   // CTAs of one product resident at once
 // CTA b of the rows / columns products takes the node blocks cta_blk[b] .. cta_blk[b + 1]
 void launch_tile_scatter(int64_t nnz, const int64_t* pos, const float* val, float* tile, cudaStream_t st);
 template <typename T>

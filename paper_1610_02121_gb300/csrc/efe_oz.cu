@@ -60,7 +60,8 @@ struct OzL {
   static constexpr uint32_t BSL = OZ_TW * OZ_KC * 2;       // one B slice, 3 KB
   static constexpr uint32_t STAGE = OZ_S * (ASL + BSL);    // 49 KB
   static constexpr uint32_t BARS = OZ_STAGES * STAGE;
-  static constexpr size_t TOTAL = (size_t)BARS + 256;
+  static constexpr uint32_t STG = BARS + 256;                // epilogue staging: up to 12 warps x 32 rows x 9 doubles
+  static constexpr size_t TOTAL = (size_t)STG + 12 * 32 * 9 * 8;
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -175,6 +176,20 @@ __device__ __forceinline__ void oz_pack8(const double (&x)[8], int E, uint32_t (
   }
 }
 
+// x * 2^k in FP64, built from the bit pattern of x (exact; no FP64 arithmetic).
+// Every accumulator value and error term here is zero or at least 2^-42 in
+// magnitude (the smallest digit-product unit), so x is never subnormal;
+// results outside the normal FP64 range take ldexp.
+__device__ __forceinline__ double f32_scaled(float x, int k) {
+  const uint32_t b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xFFu);
+  if (e == 0) return 0.0;
+  const int E = e - 127 + 1023 + k;
+  if (E < 1 || E > 2046) return ldexp((double)x, k);
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | ((unsigned long long)E << 52) |
+                                          ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   const float bb = s - a;
@@ -271,6 +286,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   uint64_t* afull = accf + 4;                                   // [stages] bulk-copied operand chunks landed
   const bool apre = g.Aimg != nullptr;
   const bool bpre = g.mode != 0 && g.Bimg != nullptr;
+  // both operands pre-sliced: nothing to slice, so one thread issues the copies
+  // and warps 4-15 share the epilogue (three warps per TMEM lane quarter)
+  const bool img_only = apre && bpre;
+  const int n_epi = img_only ? 12 : 4;
+  const int epi_w0 = img_only ? 4 : OZ_EPI_W0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
                  "r"(OZ_TMEM_COLS)
@@ -279,12 +299,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   }
   if (tid == 32) {
     for (int s = 0; s < OZ_STAGES; ++s) {
-      bar_init(conv + s, oz_group_threads(s % OZ_GROUPS));
+      bar_init(conv + s, img_only ? 1 : oz_group_threads(s % OZ_GROUPS));
       bar_init(empty + s, 1);
       bar_init(afull + s, 1);
     }
     bar_init(accf, 1);
-    bar_init(acce, 128);
+    bar_init(acce, n_epi * 32);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -349,13 +369,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         break;
       }
     }
-  } else if (warp < OZ_CONV_W0 + OZ_CONV_WN) {
+  } else if (img_only ? (warp == OZ_CONV_W0 && lane == 0) : (warp < OZ_CONV_W0 + OZ_CONV_WN)) {
     // ---------------------------------------------------------------- slicers
     // two groups (six and five warps) take alternate chunks, so two chunks are
-    // sliced (and their loads are in flight) at a time
-    const int grp = (tid - OZ_CONV_W0 * 32) < OZ_GT0 ? 0 : 1;
-    const int ct = (tid - OZ_CONV_W0 * 32) - grp * OZ_GT0;
-    const int gsz_t = oz_group_threads(grp);
+    // sliced (and their loads are in flight) at a time; with both operands
+    // pre-sliced a single thread takes every chunk
+    const int grp = img_only ? 0 : ((tid - OZ_CONV_W0 * 32) < OZ_GT0 ? 0 : 1);
+    const int ct = img_only ? 0 : (tid - OZ_CONV_W0 * 32) - grp * OZ_GT0;
+    const int gsz_t = img_only ? 1 : oz_group_threads(grp);
     int64_t last_copy = -1;   // last chunk whose operand copies this thread issued
     for (int64_t t = 0; t < my && !*abort_flag; ++t) {
       const OzItem it = oz_item(g, blockIdx.x + t * gridDim.x);
@@ -364,7 +385,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
       bool ok = true;
       for (int kc = 0; kc < nch; ++kc) {
         const int64_t ch = t * nch + kc;
-        if ((int)(ch % OZ_GROUPS) != grp) continue;
+        if (!img_only && (int)(ch % OZ_GROUPS) != grp) continue;
         const int s = (int)(ch % OZ_STAGES);
         if (ch >= OZ_STAGES) {
           ok = bar_wait(empty + s, (uint32_t)((ch / OZ_STAGES - 1) & 1));
@@ -510,10 +531,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
       // let the last bulk copies of this thread land before the CTA can leave
       bar_wait(afull + (int)(last_copy % OZ_STAGES), (uint32_t)((last_copy / OZ_STAGES) & 1));
     }
-  } else {
+  } else if (warp >= epi_w0) {
     // ---------------------------------------------------------------- epilogue
-    const int quarter = warp & 3;
+    // each thread owns one accumulator row (its TMEM lane); an 8-column block of
+    // results goes through a per-warp shared tile so that the global loads and
+    // stores run along the rows (8 consecutive values per row, 4 rows per
+    // instruction) instead of one row per lane
+    const int quarter = warp & 3;   // the TMEM lane quarter this warp may read
     const int r = quarter * 32 + lane;
+    const int ew = warp - epi_w0, part = ew >> 2, nparts = n_epi >> 2;   // column blocks part, part + nparts, ...
+    double* stg = reinterpret_cast<double*>(sm + OzL::STG) + ew * (32 * 9);
     for (int64_t t = 0; t < my && !*abort_flag; ++t) {
       const OzItem it = oz_item(g, blockIdx.x + t * gridDim.x);
       const int c0 = it.c0, ncol = it.ncol;
@@ -537,7 +564,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
       }
       // the row's output segment is pulled towards L2 while the MMAs run
       if (live && (g.mode == 0 || g.mode == 2))
-        for (int cb = 0; cb < ncol; cb += 16) asm volatile("prefetch.L2 [%0];" ::"l"(orow + cb));
+        for (int cb = 8 * part; cb < ncol; cb += 8 * nparts) asm volatile("prefetch.L2 [%0];" ::"l"(orow + cb));
       bool stop = false;
       for (int grp = 0; grp < ngrp; ++grp) {
         const int64_t gc = t * ngrp + grp;
@@ -550,19 +577,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // modes 0 and 2 add to what is there (mode 2 from its second group on)
         const bool add = (g.mode == 0) || (g.mode == 2 && grp > 0);
-        // values to add to: loaded one 8-column block ahead of their use
+        // with twelve epilogue warps the results go out through a per-warp shared
+        // tile (rows written 8 values at a time, 4 rows per instruction); with four,
+        // each thread writes its own row and loads the values it adds to one
+        // 8-column block ahead (fewer instructions, which bound that case)
+        const unsigned long long orow_u = (unsigned long long)orow;
         double nxt[8];
-        if (live && add) {
+        if (!img_only && live && add) {
 #pragma unroll
           for (int q = 0; q < 8; ++q) nxt[q] = (q < ncol) ? orow[q] : 0.0;
         }
-        for (int cb = 0; cb < ncol; cb += 8) {
+        for (int cb = 8 * part; cb < ncol; cb += 8 * nparts) {
           double cur[8];
+          if (!img_only) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) cur[q] = nxt[q];
-          if (live && add && cb + 8 < ncol) {
+            for (int q = 0; q < 8; ++q) cur[q] = nxt[q];
+            if (live && add && cb + 8 < ncol) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) nxt[q] = (cb + 8 + q < ncol) ? orow[cb + 8 + q] : 0.0;
+              for (int q = 0; q < 8; ++q) nxt[q] = (cb + 8 + q < ncol) ? orow[cb + 8 + q] : 0.0;
+            }
           }
           uint32_t v[OZ_NACC][8];
 #pragma unroll
@@ -574,23 +607,43 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
                 : "r"(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * OZ_TW + cb))
                 : "memory");
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (live) {
+          double val[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int n = cb + q;
-              if (n >= ncol) break;
+          for (int q = 0; q < 8; ++q) {
+            const int n = cb + q;
+            val[q] = 0.0;
+            if (live && n < ncol) {
               float s1, e1, s2, e2, s3, e3;
               two_sum(__uint_as_float(v[0][q]), __uint_as_float(v[1][q]), s1, e1);
               two_sum(s1, __uint_as_float(v[2][q]), s2, e2);
               two_sum(s2, __uint_as_float(v[3][q]), s3, e3);
               const float lo = ((__uint_as_float(v[4][q]) + e3) + e2) + e1;
-              // exact power-of-two scale built from its bit pattern (normal range), ldexp otherwise
+              // (s3 + lo) 2^k2: both parts scaled exactly by their bit patterns, one FP64
+              // add (the FP64 pipe is the scarce one in this epilogue)
               const int k2 = Er + g.fexp[c0 + n] - 14;
-              const double sc = (k2 > -1022 && k2 < 1023) ? __longlong_as_double((long long)(k2 + 1023) << 52)
-                                                          : ldexp(1.0, k2);
-              const double val = ((double)s3 + (double)lo) * sc;
-              orow[n] = add ? cur[q] + val : val;
+              val[q] = f32_scaled(s3, k2) + f32_scaled(lo, k2);
             }
+          }
+          if (img_only) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) stg[lane * 9 + q] = val[q];
+            __syncwarp();
+            // row rr = 4 j + lane / 8 of this warp, column cb + lane % 8
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int rr = 4 * j + (lane >> 3), cq = lane & 7;
+              double* rp = (double*)__shfl_sync(0xffffffffu, orow_u, rr);
+              const int lv = __shfl_sync(0xffffffffu, (int)live, rr);
+              if (lv && cb + cq < ncol) {
+                const double x = stg[rr * 9 + cq];
+                rp[cb + cq] = add ? rp[cb + cq] + x : x;
+              }
+            }
+            __syncwarp();
+          } else if (live) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if (cb + q < ncol) orow[cb + q] = add ? cur[q] + val[q] : val[q];
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
