@@ -178,41 +178,10 @@ __global__ void k_spmm_segments(const int64_t* __restrict__ seg_start, const int
   }
 }
 
-// Narrow blocks (N <= 4: the Lanczos vector): the lanes of a warp split the
-// entries of a row / segment instead of the columns, and the lane partials are
-// added by a fixed shuffle tree (reproducible).
+// Narrow blocks (N <= 4: the Lanczos vector): the threads of a block split the
+// entries of a segment instead of the columns, and the partials are added by a
+// fixed shuffle tree and a fixed-order sum over the warps (reproducible).
 constexpr int SPMM_NARROW = 4;
-
-template <typename T>
-__global__ void k_spmm_nodes_narrow(int64_t nrows, const int32_t* __restrict__ rnode, const int64_t* __restrict__ ptr,
-                                    const int32_t* __restrict__ col, const double* __restrict__ val, double sgn,
-                                    const double* __restrict__ Xe, int64_t ldxe, T* __restrict__ out, int64_t ldo,
-                                    int N) {
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-  const int lane = threadIdx.x & 31;
-  if (w >= nrows) return;
-  const int64_t q0 = ptr[w], q1 = ptr[w + 1];
-  double s[SPMM_NARROW] = {0.0, 0.0, 0.0, 0.0};
-  for (int64_t q = q0 + lane; q < q1; q += 32) {
-    const double v = val[q];
-    const double* xr = Xe + (int64_t)col[q] * ldxe;
-#pragma unroll
-    for (int c = 0; c < SPMM_NARROW; ++c)
-      if (c < N) s[c] = fma(v, xr[c], s[c]);
-  }
-#pragma unroll
-  for (int c = 0; c < SPMM_NARROW; ++c)
-    for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o);
-  if (lane == 0) {
-    const int64_t g = rnode[w];
-#pragma unroll
-    for (int c = 0; c < SPMM_NARROW; ++c)
-      if (c < N) {
-        T* o = out + g * ldo + c;
-        *o = (T)((double)(*o) + sgn * s[c]);
-      }
-  }
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_spmm_segments_narrow(const int64_t* __restrict__ seg_start,
@@ -328,24 +297,41 @@ __global__ void __launch_bounds__(256) k_cell_apply_narrow(const T* __restrict__
   }
   __syncthreads();
   const T* He = Hcc + e * (int64_t)(NL * NL);
-  for (int r = warp; r < NL; r += 8) {
-    T acc[NMAX];
+  // four rows per warp at a time: sixteen independent loads in flight per lane,
+  // and lane i writes row r0 + i
+  for (int r0 = warp * 4; r0 < NL; r0 += 32) {
+    T acc[4][NMAX];
 #pragma unroll
-    for (int cc = 0; cc < NMAX; ++cc) acc[cc] = T(0);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int cc = 0; cc < NMAX; ++cc) acc[i][cc] = T(0);
     for (int kk = lane; kk < NL; kk += 32) {
-      const T h = He[r * NL + kk];
+      T h[4];
 #pragma unroll
-      for (int cc = 0; cc < NMAX; ++cc) acc[cc] = fma(h, ys[kk][cc], acc[cc]);
+      for (int i = 0; i < 4; ++i) h[i] = (r0 + i < NL) ? He[(r0 + i) * NL + kk] : T(0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int cc = 0; cc < NMAX; ++cc) acc[i][cc] = fma(h[i], ys[kk][cc], acc[i][cc]);
     }
+    T mine[NMAX];
 #pragma unroll
-    for (int cc = 0; cc < NMAX; ++cc)
+    for (int cc = 0; cc < NMAX; ++cc) mine[cc] = T(0);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[cc] += __shfl_down_sync(0xffffffffu, acc[cc], o);
-    if (lane == 0) {
-      T* wr = W + gnode[r] * ldw;
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int cc = 0; cc < NMAX; ++cc) {
+        T v = acc[i][cc];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        v = __shfl_sync(0xffffffffu, v, 0);
+        if (lane == i) mine[cc] = v;
+      }
+    if (lane < 4 && r0 + lane < NL) {
+      T* wr = W + gnode[r0 + lane] * ldw;
 #pragma unroll
       for (int cc = 0; cc < NMAX; ++cc)
-        if (cc < N) wr[cc] += acc[cc];
+        if (cc < N) wr[cc] += mine[cc];
     }
   }
 }
@@ -384,7 +370,7 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, const int64_t* 
   const int ldy = (N + 3) & ~3;
   float* acc = smf;                                  // nE x ldy
   float* Ys = acc + (size_t)nE * ldy;                // CPB x ldy
-  float* Ps = Ys + CPB * ldy;                        // CPB x (CPF + 4): node-major slice of the tile
+  float* Ps = Ys + CPB * ldy;                        // CPF x CPB
   __shared__ int sf[CPF];
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int i = tid; i < nE * ldy; i += bd) acc[i] = 0.f;
@@ -408,10 +394,7 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, const int64_t* 
     for (int64_t sp = s0; sp < s1; sp += CPF) {
       const int nf = (int)min((int64_t)CPF, s1 - sp);
       __syncthreads();
-      for (int i = tid; i < CPF * CPB; i += bd) {
-        const int sl = i / CPB, u = i % CPB;
-        Ps[u * (CPF + 4) + sl] = (i < nf * CPB) ? tile[sp * CPB + i] : 0.f;
-      }
+      for (int i = tid; i < CPF * CPB; i += bd) Ps[i] = (i < nf * CPB) ? tile[sp * CPB + i] : 0.f;
       if (tid < nf) sf[tid] = slots[sp + tid];
       __syncthreads();
       const int nsb = (nf + 3) / 4;
@@ -420,8 +403,9 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, const int64_t* 
         float r[4][4] = {};
 #pragma unroll 8
         for (int u = 0; u < CPB; ++u) {
-          const float4 p4 = *reinterpret_cast<const float4*>(Ps + u * (CPF + 4) + sb * 4);
-          const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+          float pv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) pv[i] = Ps[(sb * 4 + i) * CPB + u];
           const float4 y4 = *reinterpret_cast<const float4*>(Ys + u * ldy + cb * 4);
           const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
@@ -540,9 +524,20 @@ __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, const int64_t* 
           const int u = ub * 4 + i;
           if (u >= nb) break;
           T* wr = W + sg[u] * ldw + cb * 4;
+          if (sizeof(T) == 4 && (ldw & 3) == 0 && ((uintptr_t)W & 15) == 0 && cb * 4 + 4 <= ldw) {
+            // padded FP32 rows: one 16-byte update (columns past N add zero)
+            float4* w4 = reinterpret_cast<float4*>(wr);
+            float4 o = *w4;
+            o.x += sgn * r[k][i][0];
+            o.y += sgn * r[k][i][1];
+            o.z += sgn * r[k][i][2];
+            o.w += sgn * r[k][i][3];
+            *w4 = o;
+          } else {
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (cb * 4 + j < N) wr[j] = (T)((float)wr[j] + sgn * r[k][i][j]);
+            for (int j = 0; j < 4; ++j)
+              if (cb * 4 + j < N) wr[j] = (T)((float)wr[j] + sgn * r[k][i][j]);
+          }
         }
       }
     }
@@ -1035,11 +1030,7 @@ void launch_spmm_nodes(int64_t nrows, const int32_t* rnode, const int64_t* ptr, 
                        const double* val, double sgn, const double* Xe, int64_t ldxe, T* out, int64_t ldo, int N,
                        cudaStream_t st) {
   if (nrows <= 0 || N <= 0) return;
-  if (N <= SPMM_NARROW)
-    k_spmm_nodes_narrow<T><<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out,
-                                                                   ldo, N);
-  else
-    k_spmm_nodes<T><<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out, ldo, N);
+  k_spmm_nodes<T><<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out, ldo, N);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 template void launch_spmm_nodes<double>(int64_t, const int32_t*, const int64_t*, const int32_t*, const double*,
@@ -1269,7 +1260,7 @@ int coup_block_nodes() { return CPB; }
 // kernel's CPB x (N + 4) vector tile and one CPF x CPB pattern tile
 size_t coup_smem(int nE, int N, bool rows) {
   const size_t ld = (size_t)((N + 3) & ~3);
-  return sizeof(float) * ((size_t)nE * ld + (rows ? (size_t)CPB * ld + (size_t)CPB * (CPF + 4) : (size_t)CPF * CPB));
+  return sizeof(float) * ((size_t)nE * ld + (rows ? (size_t)CPB * ld : 0) + (size_t)CPF * CPB);
 }
 
 // CTAs of the rows (or columns) product resident at once (one wave of its partition)
