@@ -365,8 +365,14 @@ def main():
     if oz_launch > 0 and oz_ms > 0:
         bf16_peak, bf16_src = peaks_bf16()
         oz_tf = oz_flops / (oz_ms * 1e-3) / 1e12
+        # DRAM traffic per launch: ncu dram bytes of every k_oz launch of one si16s step (CELL 0.89 GB,
+        # symmetric Gram 2.50 GB, A^T B Gram 3.80 GB, rotation 2.73 GB), weighted by the step's mix
+        # (24 / 1 / 2 / 4 launches) and scaled to si16 by the rows and cells processed (x 2.72)
+        oz_traffic = 3.72e9 if (args.workload == "si16" and N == 135 and m == 40) else None
         roof_oz = {"bound": "tensor", "achieved": 28.0 * oz_tf, "peak": bf16_peak, "unit": "TFLOP/s",
-                   "frac": 28.0 * oz_tf / bf16_peak, "traffic": None, "kernel": "k_oz (FP64-grade products)",
+                   "frac": 28.0 * oz_tf / bf16_peak, "traffic": oz_traffic,
+                   "traffic_source": "ncu dram bytes per mode on si16s, step mix, scaled x2.72 to si16",
+                   "kernel": "k_oz (FP64-grade products)",
                    "launches": oz_launch, "avg_launch_ms": oz_ms / oz_launch, "fp64_grade_tflops": oz_tf,
                    "vs_fp64_dgemm_peak": oz_tf / 1.05,
                    "note": "achieved = 28 BF16 digit products per FP64 product x algorithmic FP64 flops / time",

@@ -380,15 +380,33 @@ __global__ void __launch_bounds__(256) k_coup_rows(int64_t n_tn, const int64_t* 
     const int64_t r0 = bb * CPB;
     const int nb = (int)min((int64_t)CPB, n_tn - r0);
     __syncthreads();
-    for (int i = tid; i < CPB * ldy; i += bd) {
-      const int u = i / ldy, c = i % ldy;
-      float v = 0.f;
-      if (u < nb && c < N) {
-        const int64_t g = t_nodes[r0 + u];
-        v = (float)X[g * ldx + c];
-        if (scale) v *= (float)scale[g];
+    if (sizeof(T) == 4 && (ldx & 3) == 0 && ((uintptr_t)X & 15) == 0 && ldy <= ldx) {
+      // padded FP32 rows: four columns per 16-byte load (columns past N are zero)
+      const int q4 = ldy / 4;
+      for (int i = tid; i < CPB * q4; i += bd) {
+        const int u = i / q4, c4 = i % q4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (u < nb) {
+          const int64_t g = t_nodes[r0 + u];
+          v = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(X) + g * ldx + 4 * c4);
+          if (scale) {
+            const float sc = (float)scale[g];
+            v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
+          }
+        }
+        *reinterpret_cast<float4*>(Ys + u * ldy + 4 * c4) = v;
       }
-      Ys[i] = v;
+    } else {
+      for (int i = tid; i < CPB * ldy; i += bd) {
+        const int u = i / ldy, c = i % ldy;
+        float v = 0.f;
+        if (u < nb && c < N) {
+          const int64_t g = t_nodes[r0 + u];
+          v = (float)X[g * ldx + c];
+          if (scale) v *= (float)scale[g];
+        }
+        Ys[i] = v;
+      }
     }
     const int64_t s0 = slot_off[bb], s1 = slot_off[bb + 1];
     for (int64_t sp = s0; sp < s1; sp += CPF) {
