@@ -24,10 +24,13 @@
 //         FP32 sums for t <= 5) drained into FP64 partial tiles, which a
 //         fixed-order reduction adds up.
 //
-// Warp roles (512 threads): warp 0 issues the MMAs (one elected lane),
-// warps 1-11 slice operands into the shared-memory stage ring (3 stages),
-// warps 12-15 combine the accumulators and write the result.  All waits are
-// bounded (about one second); on timeout the CTA records an error and leaves.
+// Warp roles (512 threads): warp 0 issues the MMAs (one elected lane); while
+// an operand is sliced here (CELL's vector block), warps 1-7 slice into the
+// shared-memory stage ring (4 stages, two groups taking alternate chunks) and
+// warps 8-15 combine the accumulators and write the result; when both operands
+// are pre-sliced images (ROWS, GRAM) one thread issues the bulk copies and
+// warps 4-15 share the epilogue.  All waits are bounded (about one second); on
+// timeout the CTA records an error and leaves.
 #include <stdint.h>
 
 #include <algorithm>
@@ -46,10 +49,10 @@ constexpr int OZ_TW = 96;          // column tile
 constexpr int OZ_NACC = 5;         // accumulators: t = 2, 3, 4, 5 exact; t = 6..8 shared
 constexpr int OZ_STAGES = 4;
 constexpr int OZ_GROUPS = 2;        // slicer groups: group g fills the chunks ch = g (mod 2)
-constexpr int OZ_CONV_W0 = 1, OZ_CONV_WN = 11, OZ_EPI_W0 = 12;
-constexpr int OZ_THREADS = (OZ_EPI_W0 + 4) * 32;  // 16 warps: 128 registers a thread
+constexpr int OZ_CONV_W0 = 1, OZ_CONV_WN = 7, OZ_EPI_W0 = 8;   // slicing: warps 1-7 slice, 8-15 epilogue
+constexpr int OZ_THREADS = 16 * 32;                // 16 warps: 128 registers a thread
 constexpr int OZ_CONV_T = OZ_CONV_WN * 32;
-constexpr int OZ_GT0 = 6 * 32;                     // group 0: warps 1-6; group 1: warps 7-11
+constexpr int OZ_GT0 = 4 * 32;                     // group 0: warps 1-4; group 1: warps 5-7
 __host__ __device__ constexpr int oz_group_threads(int grp) { return grp == 0 ? OZ_GT0 : OZ_CONV_T - OZ_GT0; }
 static_assert(OZ_STAGES % OZ_GROUPS == 0, "a stage is always filled by the same group");
 constexpr uint32_t OZ_TMEM_COLS = 512;
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   // both operands pre-sliced: nothing to slice, so one thread issues the copies
   // and warps 4-15 share the epilogue (three warps per TMEM lane quarter)
   const bool img_only = apre && bpre;
-  const int n_epi = img_only ? 12 : 4;
+  const int n_epi = img_only ? 12 : 8;
   const int epi_w0 = img_only ? 4 : OZ_EPI_W0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
     }
   } else if (img_only ? (warp == OZ_CONV_W0 && lane == 0) : (warp < OZ_CONV_W0 + OZ_CONV_WN)) {
     // ---------------------------------------------------------------- slicers
-    // two groups (six and five warps) take alternate chunks, so two chunks are
+    // two groups (four and three warps) take alternate chunks, so two chunks are
     // sliced (and their loads are in flight) at a time; with both operands
     // pre-sliced a single thread takes every chunk
     const int grp = img_only ? 0 : ((tid - OZ_CONV_W0 * 32) < OZ_GT0 ? 0 : 1);
@@ -585,16 +588,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         double nxt[8];
         if (!img_only && live && add) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) nxt[q] = (q < ncol) ? orow[q] : 0.0;
+          for (int q = 0; q < 8; ++q) nxt[q] = (8 * part + q < ncol) ? orow[8 * part + q] : 0.0;
         }
         for (int cb = 8 * part; cb < ncol; cb += 8 * nparts) {
           double cur[8];
           if (!img_only) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) cur[q] = nxt[q];
-            if (live && add && cb + 8 < ncol) {
+            const int cn = cb + 8 * nparts;
+            if (live && add && cn < ncol) {
 #pragma unroll
-              for (int q = 0; q < 8; ++q) nxt[q] = (cb + 8 + q < ncol) ? orow[cb + 8 + q] : 0.0;
+              for (int q = 0; q < 8; ++q) nxt[q] = (cn + q < ncol) ? orow[cn + q] : 0.0;
             }
           }
           uint32_t v[OZ_NACC][8];
