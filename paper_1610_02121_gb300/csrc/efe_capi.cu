@@ -49,7 +49,7 @@ struct efe_handle {
   double *D = nullptr, *Dinv = nullptr, *mask = nullptr, *Dm = nullptr;
   double* Hcc = nullptr;
   float* Hcc32 = nullptr;
-  float *As1 = nullptr, *As2 = nullptr;  // TF32 split images of H^cc_e (chunk-major)
+  float* Aimg32 = nullptr;  // FP32 images of H^cc_e in the tensor-core layout (chunk-major)
   int tc_mode = 0;          // 1: TF32 tcgen05 cell products, 2: 3-term split TF32 (FP32-grade)
   int tc_tile = 0, tc_tile_N = 0;  // autotuned column tile of the tensor-core cell kernel for N
   int n_sm = 148;
@@ -376,7 +376,7 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
         launch_cell_apply_f64((const double*)Hc, cl, nc, h->mesh, (const double*)Y, ldy, (double*)Wc, ldw, N, st);
     } else {
       if (tc) {
-        if (launch_cell_tc3(h->As1, h->As2, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N,
+        if (launch_cell_tc3(h->Aimg32, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N,
                             h->tc_mode == 2, h->n_sm, h->info + 4, st, h->tc_tile_N == N ? h->tc_tile : 0)) {
           h->err = "tensor-core cell kernel needs 16-byte aligned rows";
           return EFE_ERR_ARG;
@@ -983,8 +983,7 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
   TRY(dalloc(h, &h->Hcc32, h->n_cell * NL * NL));
   TRY(dalloc(h, &h->hexp, oz_hexp_elems(h->n_cell)));
   TRY(dalloc(h, &h->oz_aexp, h->rows));
-  TRY(dalloc(h, &h->As1, tc3_image_elems(h->n_cell)));
-  TRY(dalloc(h, &h->As2, tc3_image_elems(h->n_cell)));
+  TRY(dalloc(h, &h->Aimg32, tc3_image_elems(h->n_cell)));
   TRY(dalloc(h, &h->info, 8));
   TRY(dalloc(h, &h->chol_ratio, 1));
   if (h->nE > 0) {
@@ -1152,7 +1151,7 @@ int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
     CKL();
   }
   launch_to_f32(h->Hcc, h->Hcc32, h->n_cell * NL * NL, st);
-  launch_build_asplit(h->Hcc, h->n_cell, h->As1, h->As2, st);
+  launch_build_aimg(h->Hcc, h->n_cell, h->Aimg32, st);
   launch_oz_hexp(h->Hcc, h->n_cell, h->hexp, st);
   CKL();
   h->oz_aimg_valid = false;   // the digit images follow H^cc_e (remade on first use)
@@ -2264,7 +2263,7 @@ int efe_autotune(efe_handle* h, int32_t N, int32_t precision, int32_t* tile_out,
       for (int c = 0; c < 8; ++c) {
         const int64_t nc = h->colour_off[c + 1] - h->colour_off[c];
         if (nc == 0) continue;
-        if (launch_cell_tc3(h->As1, h->As2, h->colour_cells + h->colour_off[c], nc, h->mesh, h->Yf[0], h->ld32, h->Wf,
+        if (launch_cell_tc3(h->Aimg32, h->colour_cells + h->colour_off[c], nc, h->mesh, h->Yf[0], h->ld32, h->Wf,
                             h->ld32, N, precision == EFE_PREC_TF32X3, h->n_sm, h->info + 4, st, tiles[i])) {
           h->err = "tensor-core cell kernel needs 16-byte aligned rows";
           return EFE_ERR_ARG;

@@ -6,16 +6,17 @@
 // per cell and column tile, FP32 accumulation in tensor memory.
 //
 // Roles of the 16 warps of a persistent CTA:
-//   warp 0      producer: per chunk one bulk copy of each pre-split A image
-//               (H^cc_e = A1 + A2, TF32 parts, 16 KB each, already in the
-//               core-matrix layout) and one bulk copy per node row of Y into
-//               a raw staging buffer, all completing on mbarrier `full`;
+//   warp 0      producer: per chunk one bulk copy of the cell's FP32 image
+//               (H^cc_e, 16 KB, already in the core-matrix layout) and one
+//               bulk copy per node row of Y into a raw staging buffer, all
+//               completing on mbarrier `full`;
 //   warp 1      MMA issuer: 4 (one pass) or 12 (3-term split: A1 B1 + A1 B2 +
 //               A2 B1) tcgen05.mma per chunk into one of two TMEM
 //               accumulators, commits to `empty` (stage reusable) and, after
 //               the last chunk, to `acc_full`;
-//   warps 2-7   converters: raw rows -> K-major core-matrix B1 (and B2 = the
-//               TF32 remainder), arrive on `conv`;
+//   warps 2-7   converters: the A chunk in place -> A1 = TF32(A) (and A2 =
+//               the TF32 remainder), raw rows -> K-major core-matrix B1 (and
+//               B2), arrive on `conv`;
 //   warps 8-15  epilogue: tcgen05.ld of the accumulator rows, read-modify-write
 //               scatter into W, arrive on `acc_empty`.
 // Two stages ring the chunks.  Every wait is bounded (about one second); on
@@ -123,7 +124,7 @@ __device__ __forceinline__ uint32_t cmo(int row, int k) {
 }
 
 template <bool SPLIT, int TW>
-__global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restrict__ A1g, const float* __restrict__ A2g,
+__global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restrict__ Ag,
                                                             const int32_t* __restrict__ cells, int64_t ncells,
                                                             MeshDev m, const float* __restrict__ Y, int64_t ldy,
                                                             float* __restrict__ W, int64_t ldw, int N, int ntiles,
@@ -186,13 +187,9 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
         }
         unsigned char* S = sm + s * T3Layout<TW>::STAGE;
         const int nrows = min(T3_KC, NL - kc * T3_KC);
-        if (lane == 0)
-          bar_expect_tx(full + s, (SPLIT ? 2u : 1u) * T3Layout<TW>::A + (uint32_t)nrows * row_bytes);
+        if (lane == 0) bar_expect_tx(full + s, T3Layout<TW>::A + (uint32_t)nrows * row_bytes);
         __syncwarp();
-        if (lane == 0) {
-          bulk_g2s(S, A1g + (e * T3_NCH + kc) * (T3_M * T3_KC), T3Layout<TW>::A, full + s);
-          if (SPLIT) bulk_g2s(S + T3Layout<TW>::A, A2g + (e * T3_NCH + kc) * (T3_M * T3_KC), T3Layout<TW>::A, full + s);
-        }
+        if (lane == 0) bulk_g2s(S, Ag + (e * T3_NCH + kc) * (T3_M * T3_KC), T3Layout<TW>::A, full + s);
         if (lane < nrows) {
           const int64_t g = cell_node(m, e, kc * T3_KC + lane);
           bulk_g2s(S + 2 * T3Layout<TW>::A + 2 * T3Layout<TW>::B + (uint32_t)lane * (TW * 4), Y + g * ldy + c0, row_bytes,
@@ -261,6 +258,22 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
         unsigned char* B1 = S + 2 * T3Layout<TW>::A;
         unsigned char* B2 = B1 + T3Layout<TW>::B;
         const int nrows = min(T3_KC, NL - kc * T3_KC);
+        {
+          // the A chunk in place: A1 = TF32(A), A2 = TF32(A - A1) (elementwise, any layout)
+          float4* a1 = reinterpret_cast<float4*>(S);
+          float4* a2 = reinterpret_cast<float4*>(S + T3Layout<TW>::A);
+          for (int v = ct; v < (int)(T3Layout<TW>::A / 16); v += T3_CONV_WARPS * 32) {
+            const float4 x = a1[v];
+            float4 h4;
+            h4.x = tf32r(x.x); h4.y = tf32r(x.y); h4.z = tf32r(x.z); h4.w = tf32r(x.w);
+            a1[v] = h4;
+            if (SPLIT) {
+              float4 l4;
+              l4.x = tf32r(x.x - h4.x); l4.y = tf32r(x.y - h4.y); l4.z = tf32r(x.z - h4.z); l4.w = tf32r(x.w - h4.w);
+              a2[v] = l4;
+            }
+          }
+        }
         for (int v = ct; v < nmma * 8; v += T3_CONV_WARPS * 32) {
           const int n = v % nmma, kq = v / nmma;
           float y[4];
@@ -368,30 +381,26 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
 // TF32 split images of H^cc_e, chunk-major: [cell][chunk][row group][1 KB], each
 // chunk a contiguous 16 KB image of the K-major core-matrix layout.
 // A1 = tf32(h), A2 = tf32(h - A1) (h in FP64).
-__global__ void k_build_asplit(const double* __restrict__ Hcc, int64_t n_cell, float* __restrict__ A1,
-                               float* __restrict__ A2) {
+__global__ void k_build_aimg(const double* __restrict__ Hcc, int64_t n_cell, float* __restrict__ A) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n_cell * T3_M * T3_K) return;
   const int64_t e = idx / (T3_M * T3_K);
   const int rk = (int)(idx % (T3_M * T3_K));
   const int r = rk / T3_K, k = rk % T3_K;
   const double h = (r < NL && k < NL) ? Hcc[e * (int64_t)(NL * NL) + r * NL + k] : 0.0;
-  const float hi = tf32r((float)h);
-  const float lo = tf32r((float)(h - (double)hi));
   const int kc = k / T3_KC, kl = k % T3_KC;
   const int64_t off = (e * T3_NCH + kc) * (T3_M * T3_KC) + (cmo(r, kl) + (uint32_t)(kl & 3) * 4u) / 4;
-  A1[off] = hi;
-  A2[off] = lo;
+  A[off] = (float)h;
 }
 
 }  // namespace
 
 int64_t tc3_image_elems(int64_t n_cell) { return n_cell * T3_M * T3_K; }
 
-void launch_build_asplit(const double* Hcc, int64_t n_cell, float* A1, float* A2, cudaStream_t st) {
+void launch_build_aimg(const double* Hcc, int64_t n_cell, float* A, cudaStream_t st) {
   const int64_t n = n_cell * T3_M * T3_K;
   if (n <= 0) return;
-  k_build_asplit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Hcc, n_cell, A1, A2);
+  k_build_aimg<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Hcc, n_cell, A);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
@@ -399,7 +408,7 @@ void launch_build_asplit(const double* Hcc, int64_t n_cell, float* A1, float* A2
 // elements and rows 16-byte aligned (the bulk copies need 16-byte sizes and addresses).
 namespace {
 template <int TW>
-void tc3_launch(const float* A1, const float* A2, const int32_t* cells, int64_t ncells, const MeshDev& m,
+void tc3_launch(const float* A, const int32_t* cells, int64_t ncells, const MeshDev& m,
                 const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
                 cudaStream_t st) {
   const int ntiles = (N + TW - 1) / TW;
@@ -408,10 +417,10 @@ void tc3_launch(const float* A1, const float* A2, const int32_t* cells, int64_t 
   const size_t smem = T3Layout<TW>::TOTAL;
   if (split) {
     cudaFuncSetAttribute(k_cell_tc3<true, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cell_tc3<true, TW><<<grid, T3_THREADS, smem, st>>>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err);
+    k_cell_tc3<true, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err);
   } else {
     cudaFuncSetAttribute(k_cell_tc3<false, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cell_tc3<false, TW><<<grid, T3_THREADS, smem, st>>>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err);
+    k_cell_tc3<false, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err);
   }
 }
 }  // namespace
@@ -422,17 +431,17 @@ const int* tc3_tiles(int* count) {
   return tiles;
 }
 
-int launch_cell_tc3(const float* A1, const float* A2, const int32_t* cells, int64_t ncells, const MeshDev& m,
+int launch_cell_tc3(const float* A, const int32_t* cells, int64_t ncells, const MeshDev& m,
                     const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
                     cudaStream_t st, int tile) {
   if (ncells <= 0 || N <= 0) return 0;
   if ((ldy & 3) || (ldw & 3)) return 1;
   if (tile == 64)
-    tc3_launch<64>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
+    tc3_launch<64>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
   else if (tile == 96)
-    tc3_launch<96>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
+    tc3_launch<96>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
   else if (tile == 160 || tile == 0)
-    tc3_launch<160>(A1, A2, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
+    tc3_launch<160>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
   else
     return 1;
   g_launches.fetch_add(1, std::memory_order_relaxed);

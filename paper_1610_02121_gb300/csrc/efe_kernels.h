@@ -101,9 +101,10 @@ void launch_zero_rows_f32(int64_t nrows, float* X, int64_t ldx, int N, cudaStrea
 
 // ---- tcgen05 cell products (efe_cell_tc3.cu) ----
 int64_t tc3_image_elems(int64_t n_cell);
-void launch_build_asplit(const double* Hcc, int64_t n_cell, float* A1, float* A2, cudaStream_t st);
+// FP32 image of every H^cc_e in the MMA's core-matrix layout (split into TF32 parts in the kernel)
+void launch_build_aimg(const double* Hcc, int64_t n_cell, float* A, cudaStream_t st);
 // tile: column tile width (64, 96 or 160; 0 = default 160)
-int launch_cell_tc3(const float* A1, const float* A2, const int32_t* cells, int64_t ncells, const MeshDev& m,
+int launch_cell_tc3(const float* A, const int32_t* cells, int64_t ncells, const MeshDev& m,
                     const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
                     cudaStream_t st, int tile = 0);
 const int* tc3_tiles(int* count);
