@@ -352,9 +352,9 @@ def main():
     else:
         achieved = alg_bytes / (k_ms * 1e-3) / 1e9
         # DRAM traffic of one launch from the ncu capture of this kernel on the si16s mesh
-        # (327 MB for 1,053 cells at N = 135: 310 KB per cell), scaled by the cells per launch
+        # (249 MB for 1,053 cells at N = 135: 237 KB per cell), scaled by the cells per launch
         cells_per_launch = cellcols / float(max(n_launch, 1) * N)
-        traffic = 310.4e3 * cells_per_launch if (prec == "tf32x3" and N == 135) else None
+        traffic = 236.7e3 * cells_per_launch if (prec == "tf32x3" and N == 135) else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": traffic, "traffic_source": "ncu dram bytes of the si16s capture, scaled by cells per launch",
                 "algorithmic_bytes_per_launch": alg_bytes / max(n_launch, 1),
@@ -365,10 +365,10 @@ def main():
     if oz_launch > 0 and oz_ms > 0:
         bf16_peak, bf16_src = peaks_bf16()
         oz_tf = oz_flops / (oz_ms * 1e-3) / 1e12
-        # DRAM traffic per launch: ncu dram bytes of every k_oz launch of one si16s step (CELL 0.89 GB,
-        # symmetric Gram 2.50 GB, A^T B Gram 3.80 GB, rotation 2.73 GB), weighted by the step's mix
+        # DRAM traffic per launch: ncu dram bytes of every k_oz launch of one si16s step (CELL 0.90 GB,
+        # symmetric Gram 2.48 GB, A^T B Gram 3.79 GB, rotation 2.73 GB), weighted by the step's mix
         # (24 / 1 / 2 / 4 launches) and scaled to si16 by the rows and cells processed (x 2.72)
-        oz_traffic = 3.72e9 if (args.workload == "si16" and N == 135 and m == 40) else None
+        oz_traffic = 3.73e9 if (args.workload == "si16" and N == 135 and m == 40) else None
         roof_oz = {"bound": "tensor", "achieved": 28.0 * oz_tf, "peak": bf16_peak, "unit": "TFLOP/s",
                    "frac": 28.0 * oz_tf / bf16_peak, "traffic": oz_traffic,
                    "traffic_source": "ncu dram bytes per mode on si16s, step mix, scaled x2.72 to si16",
