@@ -183,6 +183,33 @@ __global__ void k_spmm_segments(const int64_t* __restrict__ seg_start, const int
 // fixed shuffle tree and a fixed-order sum over the warps (reproducible).
 constexpr int SPMM_NARROW = 4;
 
+// one row per thread (N <= 4): the rows' few entries are walked by consecutive
+// threads instead of one lane of a warp per row
+template <typename T>
+__global__ void k_spmm_nodes_rowthread(int64_t nrows, const int32_t* __restrict__ rnode,
+                                       const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                       const double* __restrict__ val, double sgn, const double* __restrict__ Xe,
+                                       int64_t ldxe, T* __restrict__ out, int64_t ldo, int N) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w >= nrows) return;
+  const int64_t q0 = ptr[w], q1 = ptr[w + 1];
+  double s[SPMM_NARROW] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t q = q0; q < q1; ++q) {
+    const double v = val[q];
+    const double* xr = Xe + (int64_t)col[q] * ldxe;
+#pragma unroll
+    for (int c = 0; c < SPMM_NARROW; ++c)
+      if (c < N) s[c] = fma(v, xr[c], s[c]);
+  }
+  const int64_t g = rnode[w];
+#pragma unroll
+  for (int c = 0; c < SPMM_NARROW; ++c)
+    if (c < N) {
+      T* o = out + g * ldo + c;
+      *o = (T)((double)(*o) + sgn * s[c]);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_spmm_segments_narrow(const int64_t* __restrict__ seg_start,
                                                               const int64_t* __restrict__ seg_end,
@@ -1048,7 +1075,11 @@ void launch_spmm_nodes(int64_t nrows, const int32_t* rnode, const int64_t* ptr, 
                        const double* val, double sgn, const double* Xe, int64_t ldxe, T* out, int64_t ldo, int N,
                        cudaStream_t st) {
   if (nrows <= 0 || N <= 0) return;
-  k_spmm_nodes<T><<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out, ldo, N);
+  if (N <= SPMM_NARROW)
+    k_spmm_nodes_rowthread<T><<<grid1(nrows, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out,
+                                                                 ldo, N);
+  else
+    k_spmm_nodes<T><<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out, ldo, N);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 template void launch_spmm_nodes<double>(int64_t, const int32_t*, const int64_t*, const int32_t*, const double*,
