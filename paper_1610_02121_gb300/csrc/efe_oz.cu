@@ -23,6 +23,10 @@
 //         pair, K segment); each segment is formed in 256-row groups (exact
 //         FP32 sums for t <= 5) drained into FP64 partial tiles, which a
 //         fixed-order reduction adds up.
+// Pre-sliced operands arrive in the stages by bulk asynchronous copies: the
+// cell matrices' digit images (k_oz_preslice, once per potential) in CELL, and
+// both operands' images (k_oz_img_rows / k_oz_img_cols, once per product) in
+// ROWS and GRAM; only CELL's vector block is sliced inside the kernel.
 //
 // Warp roles (512 threads): warp 0 issues the MMAs (one elected lane); while
 // an operand is sliced here (CELL's vector block), warps 1-7 slice into the
