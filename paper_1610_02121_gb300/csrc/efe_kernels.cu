@@ -672,6 +672,35 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int64_t M, int Nc, int K, doubl
   }
 }
 
+// Small products (fewer 48 x 48 tiles than SMs: the n_E x N coupling solves and
+// the N x N Rayleigh-Ritz products): one output per thread in 16 x 16 tiles, so
+// that several times more SMs share the FP64 work.  Same summation order (k
+// ascending, one fused multiply-add each) as k_gemm_nn, hence the same bits.
+__global__ void __launch_bounds__(256) k_gemm_nn_small(int64_t M, int Nc, int K, double alpha,
+                                                       const double* __restrict__ A, int64_t lda,
+                                                       const double* __restrict__ B, int64_t ldb, double beta,
+                                                       double* __restrict__ C, int64_t ldc) {
+  __shared__ double As[16][17];
+  __shared__ double Bs[16][17];
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const int64_t r = (int64_t)blockIdx.x * 16 + ty;
+  const int c = blockIdx.y * 16 + tx;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    As[ty][tx] = (r < M && k0 + tx < K) ? A[r * lda + k0 + tx] : 0.0;
+    Bs[ty][tx] = (k0 + ty < K && c < Nc) ? B[(int64_t)(k0 + ty) * ldb + c] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
+    __syncthreads();
+  }
+  if (r < M && c < Nc) {
+    double v = alpha * acc;
+    if (beta != 0.0) v += beta * C[r * ldc + c];
+    C[r * ldc + c] = v;
+  }
+}
+
 constexpr int64_t TN_KC = 8192;
 
 __global__ void __launch_bounds__(256) k_gemm_tn_part(int64_t K, int Na, int Nb, const double* __restrict__ A,
@@ -1175,7 +1204,12 @@ void launch_gemm_nn(int64_t M, int Nc, int K, double alpha, const double* A, int
                     int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st) {
   if (M <= 0 || Nc <= 0) return;
   dim3 g((unsigned)((M + GT - 1) / GT), (unsigned)((Nc + GT - 1) / GT));
-  k_gemm_nn<<<g, 256, 0, st>>>(M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, 0, 0);
+  if ((int64_t)g.x * g.y < 148) {
+    dim3 gs((unsigned)((M + 15) / 16), (unsigned)((Nc + 15) / 16));
+    k_gemm_nn_small<<<gs, 256, 0, st>>>(M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  } else {
+    k_gemm_nn<<<g, 256, 0, st>>>(M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc, 0, 0, 0);
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
