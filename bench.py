@@ -104,21 +104,20 @@ def peaks_bf16():
 
 
 def clocks_start(dev):
+    """Sample SM clocks, power and throttle reasons every 200 ms (nvidia-smi) while
+    the timed region runs; the samples are parsed in memory."""
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                 else os.devnull, "w")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
                               "-i", str(dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        return p, f
+        return p
     except Exception:
-        return None, None
+        return None
 
 
-def clocks_stop(h):
-    p, f = h
+def clocks_stop(p):
     if p is None:
         return None
     p.terminate()
@@ -127,9 +126,6 @@ def clocks_stop(h):
     except Exception:
         p.kill()
         out, _ = p.communicate()
-    if f is not None:
-        f.write(out)
-        f.close()
     sm, mx, reasons = [], [], set()
     names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
     for line in out.strip().splitlines():
@@ -306,7 +302,7 @@ def main():
             G.kernel_stats(reset=True)
             G.kernel_stats_fp64(reset=True)
         l0 = P.launch_count()
-        clk = clocks_start(local) if timing else (None, None)
+        clk = clocks_start(local) if timing else None
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)

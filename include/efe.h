@@ -145,16 +145,19 @@ int efe_set_potential_analytic(efe_handle* h, const efe_potential_desc* pot, voi
 int efe_reserve(efe_handle* h, int32_t N);
 
 /* Y = H^E X (Eq. H2x2): matrix-free cell products of H^cc plus the
- * enrichment coupling, boundary rows zeroed.  X, Y in X layout (FP64 device). */
+ * enrichment coupling, boundary rows zeroed.  X, Y in X layout (FP64 device).
+ * X and Y must not overlap (EFE_ERR_ARG): Y is written while X is read. */
 int efe_apply_H(efe_handle* h, const double* X, int64_t ldx, int32_t N,
                 double* Y, int64_t ldy, void* stream);
 
-/* Y = M^E X (Eq. M2x2) with the GLL-diagonal M^cc. */
+/* Y = M^E X (Eq. M2x2) with the GLL-diagonal M^cc.  X and Y must not
+ * overlap (EFE_ERR_ARG). */
 int efe_apply_M(efe_handle* h, const double* X, int64_t ldx, int32_t N,
                 double* Y, int64_t ldy, void* stream);
 
 /* Y = (M^E)^-1 X by the block-wise (Banachiewicz) formula of Sec. IV.D,
- * applied matrix-free: x_e = S^-1 (W_e - M^ec D^-1 W_c), x_c = D^-1 (W_c - M^ec^T x_e). */
+ * applied matrix-free: x_e = S^-1 (W_e - M^ec D^-1 W_c), x_c = D^-1 (W_c - M^ec^T x_e).
+ * X is copied to the workspace first, so Y may be X. */
 int efe_apply_Minv(efe_handle* h, const double* X, int64_t ldx, int32_t N,
                    double* Y, int64_t ldy, void* stream);
 
@@ -176,9 +179,11 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m,
 
 /* Cholesky-QR (G = X^T X = R^T R, Q = X R^-1) and Rayleigh-Ritz
  * (Q^T H Q Psi = eps Q^T M Q Psi, Sec. V) in FP64 on the device; X <- Q Psi
- * (M-orthonormal Ritz vectors, ascending eps).  eig_host / resid_host (host,
- * N doubles each; resid_host may be NULL) receive the Ritz values and
- * ||H x_i - eps_i M x_i||_2.  A numerically rank-deficient X (G not
+ * (M-orthonormal Ritz vectors, ascending eps), N <= 4096.  eig_host / resid_host
+ * (host, N doubles each; resid_host may be NULL, which skips the residual
+ * work) receive the Ritz values and ||H x_i - eps_i M x_i||_2.  Large blocks
+ * (a third R x N FP64 block above 16 GiB) form H Q, M Q and the residuals in
+ * two column panels inside the workspace.  A numerically rank-deficient X (G not
  * positive definite in FP64, or a column keeping less than 1e-14 of its
  * squared norm outside the span of the columns before it) is first made well
  * conditioned by up to five shifted Cholesky-QR passes (G + s I, s = 11 (rows
@@ -202,6 +207,23 @@ int efe_rr_shifted_passes(efe_handle* h, int64_t* count);
  * 2^-48 of sum |a||b|).  Applies to N > 8 cell products and to N <= 144 tall
  * products; other cases keep DFMA.  Host setting, no device work. */
 int efe_set_fp64_engine(efe_handle* h, int32_t engine);
+
+/* Test and tuning controls (no counterpart in the paper).  Host settings, no
+ * device work; EFE_ERR_ARG for an unknown option or a value out of range.
+ * Every default (0) picks by size; the settings exist so that the tests can
+ * drive each code path on small inputs. */
+#define EFE_OPT_GRID_CAP 1       /* the persistent tensor-core kernels (tcgen05 cell kernel, FP64 engine) run at most
+                                    this many CTAs, so each CTA walks several work items (0: one CTA per SM);
+                                    results do not depend on it */
+#define EFE_OPT_IMAGE_ROWS 2     /* FP64 engine: rows per panel of the operand digit images of the tall products
+                                    (0: panels whose images fit 8 GiB) */
+#define EFE_OPT_RR_PANELS 3      /* 1: Rayleigh-Ritz forms H Q and M Q in two column panels (and the residuals by
+                                    fresh H and M applies) whatever the size; 0: only when a third R x N FP64 block
+                                    would exceed 16 GiB.  Takes effect at the next workspace reservation */
+#define EFE_OPT_DENSE_BLOCKED 4  /* 1: the blocked multi-CTA dense N x N kernels (Cholesky, triangular inverse,
+                                    block Jacobi eigensolver) whatever the size; 0: for N > 512 (Cholesky:
+                                    N > 2048) */
+int efe_set_option(efe_handle* h, int32_t option, int64_t value);
 
 /* Kernel timing: when enabled, the library brackets every launch of its
  * classical cell-apply kernel (any precision) with CUDA events on the
@@ -229,13 +251,15 @@ int efe_kernel_stats_fp64(efe_handle* h, int64_t* launches, double* total_ms, do
  * products, n_segments x N doubles) is a file-scope device array of 2^21
  * doubles (16 MiB) that every GPU loading the library holds until the process
  * exits; the handle's own operator storage was allocated by efe_create.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Sizes needing more than 2^21 scratch doubles return
- * EFE_ERR_ARG.  All calls share the array and it keeps the last call's
- * contents (every entry a call reads is written by that call first), so calls
- * that overlap on the GPU -- on different streams or from different threads --
- * race and must be serialised by the caller.  Arguments as efe_apply_M. */
+ * efe_create maps the library's device module and looks up the array's device
+ * address (cudaGetSymbolAddress) with the handle's device current, so this call
+ * itself loads nothing and looks nothing up.  Sizes needing more than 2^21
+ * scratch doubles return EFE_ERR_ARG before any device work.  All calls share
+ * the array and it keeps the last call's contents (every entry a call reads is
+ * written by that call first), so calls that overlap on the GPU -- on
+ * different streams or from different threads -- race and must be serialised
+ * by the caller.  X and Y must not overlap (EFE_ERR_ARG).  Arguments as
+ * efe_apply_M. */
 int efe_apply_M_noalloc(efe_handle* h, const double* X, int64_t ldx, int32_t N,
                         double* Y, int64_t ldy, void* stream);
 
@@ -412,7 +436,11 @@ int efe_mlp_forward(const efe_mlp_shape* s, const void* params, const void* X, i
 /* grads = d(sum_i dy_i y_i)/d params for the X, work of the last forward call */
 int efe_mlp_backward(const efe_mlp_shape* s, const void* params, const void* X, int64_t n, const void* work,
                      const void* dy, void* grads, void* scratch, int32_t precision, void* stream);
-/* loss = sum c (yh - y)^2 / sum c (host), dy = d loss / d yh (device) */
+/* loss = sum c (yh - y)^2 / sum c (host), dy = d loss / d yh (device).  The two
+ * sums go through a small file-scope device array shared by every call in the
+ * process (per device), and the call synchronises `stream` to read them:
+ * concurrent efe_wmse calls on one device race on that array and must be
+ * serialised by the caller. */
 int efe_wmse(const void* yh, const void* y, const void* c, int64_t n, void* dy, double* loss, int32_t precision,
              void* stream);
 /* one Adam step (Kingma & Ba) on n parameters with moments m, v; t counts from 1 */

@@ -23,7 +23,7 @@ SYMBOLS = ["efe_create", "efe_destroy", "efe_last_error", "efe_sizes", "efe_qpoi
            "efe_set_potential_analytic", "efe_reserve", "efe_apply_H", "efe_apply_M", "efe_apply_Minv",
            "efe_upper_bound", "efe_chfsi_step", "efe_rayleigh_ritz", "efe_rr_shifted_passes", "efe_enable_timing",
            "efe_kernel_stats", "efe_kernel_stats_fp64",
-           "efe_launch_count", "efe_apply_M_noalloc", "efe_set_fp64_engine", "efe_density", "efe_xc_lda",
+           "efe_launch_count", "efe_apply_M_noalloc", "efe_set_fp64_engine", "efe_set_option", "efe_density", "efe_xc_lda",
            "efe_hartree", "efe_fermi", "efe_anderson", "efe_scf_init", "efe_scf_step", "efe_sad_density",
            "efe_descriptors", "efe_learned_density", "efe_density_log_ratio", "efe_mlp_param_count",
            "efe_mlp_work_elems", "efe_mlp_scratch_elems", "efe_mlp_forward", "efe_mlp_backward", "efe_wmse",
@@ -121,6 +121,7 @@ def load(path=LIB_PATH):
         "efe_launch_count": [P64],
         "efe_apply_M_noalloc": [vp, vp, i64, i32, vp, i64, vp],
         "efe_set_fp64_engine": [vp, i32],
+        "efe_set_option": [vp, i32, i64],
         "efe_density": [vp, vp, i64, i32, vp, vp, i32, vp],
         "efe_xc_lda": [vp, vp, vp, vp, vp],
         "efe_hartree": [vp, vp, vp, vp, dbl, i32, C.POINTER(C.c_int32), vp],
@@ -180,6 +181,31 @@ def fermi(eps, n_electrons, kT):
     if rc != EFE_OK:
         raise EfeError(rc, "efe_fermi: not enough states for the electron count")
     return occ, mu.value
+
+
+def check_block(X, rows, like=None):
+    """Validate a vector block before its pointer goes to the library: a 2-D FP64
+    tensor with ``rows`` rows, unit column stride and leading dimension >= N, on
+    a CUDA device; with ``like``, also the same shape as that block.  Raises
+    ValueError (shape, dtype, strides) or TypeError (not a tensor) before any
+    device work, so that a wrong block never reaches a kernel."""
+    if not hasattr(X, "dim") or not hasattr(X, "dtype"):
+        raise TypeError("vector block must be a torch tensor")
+    if X.dim() != 2:
+        raise ValueError(f"vector block must be 2-D, got {X.dim()}-D")
+    if str(X.dtype) != "torch.float64":
+        raise ValueError(f"vector block must be float64, got {X.dtype}")
+    if X.shape[0] != rows:
+        raise ValueError(f"vector block has {X.shape[0]} rows, the system has {rows} (nodes + enrichment)")
+    if X.shape[1] < 1:
+        raise ValueError("vector block has no columns")
+    if X.stride(1) != 1 or X.stride(0) < X.shape[1]:
+        raise ValueError("vector block needs unit column stride and leading dimension >= N")
+    if like is not None and tuple(X.shape) != tuple(like.shape):
+        raise ValueError(f"output block shape {tuple(X.shape)} differs from input {tuple(like.shape)}")
+    if not X.is_cuda:
+        raise ValueError("vector block must live on a CUDA device")
+    return C.c_void_p(X.data_ptr()), X.stride(0), X.shape[1]
 
 
 def _dptr(a):
@@ -265,10 +291,8 @@ class System:
         except Exception:
             pass
 
-    @staticmethod
-    def _block(X):
-        assert X.is_cuda and X.dtype.is_floating_point and X.dim() == 2 and X.stride(1) == 1
-        return C.c_void_p(X.data_ptr()), X.stride(0), X.shape[1]
+    def _block(self, X, like=None):
+        return check_block(X, self.rows, like)
 
     # -- API -------------------------------------------------------------------
     def qpoints(self):
@@ -295,7 +319,7 @@ class System:
         px, ldx, N = self._block(X)
         if Y is None:
             Y = self._torch.empty_like(X)
-        py, ldy, _ = self._block(Y)
+        py, ldy, _ = self._block(Y, like=X)
         self._check(fn(self.h, px, ldx, N, py, ldy, self._stream()))
         return Y
 
@@ -452,6 +476,19 @@ class System:
         ms = np.zeros(3)
         self._check(self.L.efe_autotune(self.h, int(N), PREC[precision], C.byref(t), _dptr(ms)))
         return t.value, ms
+
+    OPTIONS = {"grid_cap": 1, "image_rows": 2, "rr_panels": 3, "dense_blocked": 4}
+
+    def set_option(self, name, value):
+        """Test/tuning control of the library (EFE_OPT_*): grid_cap (CTAs of the
+        persistent tensor-core kernels), image_rows (FP64-engine image panel rows),
+        rr_panels (1: panelled Rayleigh-Ritz), dense_blocked (1: multi-CTA dense
+        kernels); 0 restores the size-based default."""
+        self._check(self.L.efe_set_option(self.h, self.OPTIONS[name], int(value)))
+
+    def set_grid_cap(self, max_ctas):
+        """Cap the persistent tensor-core kernels at max_ctas CTAs (0: one per SM)."""
+        self.set_option("grid_cap", max_ctas)
 
     def set_fp64_engine(self, engine):
         """0: FP64 DFMA products; 1 (or "tensor"): FP64-grade products on the BF16 tensor cores."""

@@ -55,7 +55,7 @@ def build(verbose=False, force=False):
     cuda_inc = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "include")
     for f in cpp:
         obj = os.path.join(BUILD, f + ".o")
-        jobs.append(["g++", "-O3", "-std=c++17", "-fopenmp", "-fPIC", "-I" + cuda_inc,
+        jobs.append(["g++", "-O3", "-fno-math-errno", "-std=c++17", "-fopenmp", "-fPIC", "-I" + cuda_inc,
                      "-c", os.path.join(CSRC, f), "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=max(2, len(jobs))) as ex:
         outs = list(ex.map(_run, jobs))

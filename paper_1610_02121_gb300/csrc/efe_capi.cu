@@ -53,6 +53,11 @@ struct efe_handle {
   int tc_mode = 0;          // 1: TF32 tcgen05 cell products, 2: 3-term split TF32 (FP32-grade)
   int tc_tile = 0, tc_tile_N = 0;  // autotuned column tile of the tensor-core cell kernel for N
   int n_sm = 148;
+  int grid_cap = 0;         // test/tuning cap on the persistent tensor-core grids (0: one CTA per SM)
+  int64_t opt_image_rows = 0;   // rows per operand-image panel of the FP64 engine's tall products (0: by budget)
+  int opt_rr_panels = 0;        // 1: Rayleigh-Ritz in column panels whatever the size
+  int opt_dense_blocked = 0;    // 1: blocked multi-CTA dense N x N kernels whatever the size
+  double* noalloc_part = nullptr;  // device address of the static scratch of efe_apply_M_noalloc
   int fp64_engine = 0;      // 0: FP64 DFMA products; 1: FP64-grade products on the BF16 tensor cores
   int* hexp = nullptr;      // per-cell row exponents of H^cc_e (tensor-core FP64 products)
   unsigned char* oz_aimg = nullptr;  // pre-sliced BF16 digit images of H^cc_e (made on first use)
@@ -95,7 +100,16 @@ struct efe_handle {
   double* rpart = nullptr;
   double* lz = nullptr;       // Lanczos vectors (6 * rows) + scalars
   int Nres32 = 0, ld32 = 0, ncb = 0;
-  float *Yf[3] = {nullptr, nullptr, nullptr}, *Wf = nullptr, *cpart = nullptr;
+  // FP32 classical blocks of the mixed degrees: two recurrence slots (each
+  // degree overwrites Y_{k-2} in place) and the cell-product output; when the
+  // rows need no padding they live inside the FP64 workspace (slots in W, the
+  // output in B1), which the mixed degrees do not use
+  float *Yf[2] = {nullptr, nullptr}, *Wf = nullptr, *cpart = nullptr;
+  bool f32_alias = false;
+  double* We = nullptr;       // n_E x N FP64 coupling rows of the mixed degrees
+  void* dsc = nullptr;        // scratch of the blocked dense N x N kernels (grow-only)
+  int64_t dsc_bytes = 0;
+  bool whole_rr = true;       // Rayleigh-Ritz holds H Q and M Q whole (B2 exists); else column panels in W
   float *mecT32 = nullptr, *hecT32 = nullptr;
   // dense FP32 tiles of the pattern over blocks of pattern nodes (mixed filter)
   int64_t cb_nblk = 0, cb_nslots = 0;
@@ -104,7 +118,7 @@ struct efe_handle {
   std::vector<int64_t> cb_soff_host;   // slot offsets of the node blocks (host copy)
   int32_t* cb_slots = nullptr;
   float *tileH = nullptr, *tileM = nullptr;
-  double* Ye[3] = {nullptr, nullptr, nullptr};
+  double* Ye[2] = {nullptr, nullptr};
   // Chebyshev coefficients {alpha, c, beta} per degree: pinned host staging and device copy
   double* coefh = nullptr;
   double* coefd = nullptr;
@@ -210,20 +224,57 @@ int set_dev(efe_handle* h) {
 
 inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
 
+// CTAs of the persistent tensor-core kernels (cell kernel, FP64 engine): one per
+// SM unless a cap is set (EFE_OPT_GRID_CAP)
+inline int tc_grid(const efe_handle* h) {
+  return (h->grid_cap > 0 && h->grid_cap < h->n_sm) ? h->grid_cap : h->n_sm;
+}
+
+// Byte size above which Rayleigh-Ritz no longer keeps H Q and M Q as whole
+// blocks (a third FP64 block) but forms them in two column panels inside W.
+constexpr int64_t WHOLE_RR_MAX_BYTES = 16ll << 30;
+
+// FP32 blocks of the mixed degrees (see efe_handle): dropped before the FP64
+// workspace they may live in is reallocated
+void free32(efe_handle* h) {
+  if (!h->f32_alias) {
+    for (int i = 0; i < 2; ++i) dfree(h, h->Yf[i]);
+    dfree(h, h->Wf);
+  }
+  for (int i = 0; i < 2; ++i) {
+    dfree(h, h->Ye[i]);
+    h->Yf[i] = nullptr;
+    h->Ye[i] = nullptr;
+  }
+  dfree(h, h->cpart);
+  dfree(h, h->We);
+  h->Wf = nullptr;
+  h->cpart = nullptr;
+  h->We = nullptr;
+  h->f32_alias = false;
+  h->Nres32 = 0;
+}
+
 int reserve(efe_handle* h, int N) {
   if (N <= h->Nres) return EFE_OK;
+  free32(h);
   for (void* p : {(void*)h->B1, (void*)h->B2, (void*)h->W, (void*)h->xe, (void*)h->rb, (void*)h->part,
                   (void*)h->small, (void*)h->tnwork, (void*)h->rpart})
     dfree(h, p);
+  h->B2 = nullptr;
   const int64_t R = h->rows;
+  h->whole_rr = (int64_t)sizeof(double) * R * N <= WHOLE_RR_MAX_BYTES && !h->opt_rr_panels;
   TRY(dalloc(h, &h->B1, R * N));
-  TRY(dalloc(h, &h->B2, R * N));
-  TRY(dalloc(h, &h->W, R * N));
+  // W: in panel mode it holds two R x ceil(N/2) panels side by side
+  TRY(dalloc(h, &h->W, R * (N + (h->whole_rr ? 0 : 1))));
+  if (h->whole_rr) TRY(dalloc(h, &h->B2, R * N));
   TRY(dalloc(h, &h->xe, std::max<int64_t>(1, h->nE) * N));
   TRY(dalloc(h, &h->rb, std::max<int64_t>(1, h->nE) * N));
   TRY(dalloc(h, &h->part, std::max<int64_t>(1, h->nseg) * N));
   TRY(dalloc(h, &h->small, 24 * (int64_t)N * N + 8 * (int64_t)N));
-  h->tnwork_elems = gemm_tn_work_elems(R, N, N);
+  // split-K partials of the DFMA A^T B products and the segment partials of the
+  // tensor-core ones (both fit their split counts to this size)
+  h->tnwork_elems = std::max<int64_t>(gemm_tn_work_elems(R, N, N), 4 * (int64_t)N * N);
   TRY(dalloc(h, &h->tnwork, h->tnwork_elems));
   TRY(dalloc(h, &h->rpart, ((R + 2047) / 2048 + 1) * (int64_t)N));
   dfree(h, h->oz_fexp);
@@ -238,19 +289,29 @@ int reserve(efe_handle* h, int N) {
 
 int reserve32(efe_handle* h, int N) {
   if (N <= h->Nres32) return EFE_OK;
-  for (int i = 0; i < 3; ++i) { dfree(h, h->Yf[i]); dfree(h, h->Ye[i]); }
-  dfree(h, h->Wf);
-  dfree(h, h->cpart);
+  TRY(reserve(h, std::max(N, h->Nres)));
+  free32(h);
   // classical rows padded to a multiple of 8 elements: 16-byte aligned rows for
-  // vector loads and TMA boxes; the padding columns are zero and stay zero
+  // vector loads and bulk copies; the padding columns are zero and stay zero
   const int ld = (N + 7) / 8 * 8;
-  for (int i = 0; i < 3; ++i) {
-    TRY(dalloc(h, &h->Yf[i], h->n_nodes * ld));
-    CK(cudaMemset(h->Yf[i], 0, sizeof(float) * h->n_nodes * ld));
-    TRY(dalloc(h, &h->Ye[i], std::max<int64_t>(1, h->nE) * N));
+  const int64_t n32 = h->n_nodes * ld;
+  if (ld == N) {
+    // no padding to keep at zero: the two slots share W (R x N doubles hold
+    // 2 n_nodes x N floats), the cell-product output lives in B1
+    h->Yf[0] = reinterpret_cast<float*>(h->W);
+    h->Yf[1] = h->Yf[0] + n32;
+    h->Wf = reinterpret_cast<float*>(h->B1);
+    h->f32_alias = true;
+  } else {
+    for (int i = 0; i < 2; ++i) {
+      TRY(dalloc(h, &h->Yf[i], n32));
+      CK(cudaMemset(h->Yf[i], 0, sizeof(float) * n32));
+    }
+    TRY(dalloc(h, &h->Wf, n32));
+    CK(cudaMemset(h->Wf, 0, sizeof(float) * n32));
   }
-  TRY(dalloc(h, &h->Wf, h->n_nodes * ld));
-  CK(cudaMemset(h->Wf, 0, sizeof(float) * h->n_nodes * ld));
+  for (int i = 0; i < 2; ++i) TRY(dalloc(h, &h->Ye[i], std::max<int64_t>(1, h->nE) * N));
+  TRY(dalloc(h, &h->We, std::max<int64_t>(1, h->nE) * N));
   // coupling products: one wave of CTAs each, node blocks split so that every
   // CTA holds about the same number of tile slots (plus a share for staging rows)
   auto partition = [&](bool rows, int64_t** dev, int* ncta_out) -> int {
@@ -356,7 +417,7 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
         int slot;
         TRY(timed_begin(h, st, &slot, 1));
         launch_oz_cell(h->Hcc, h->hexp, h->colour_cells + h->colour_off[c], nc, h->mesh, (const double*)Y, ldy,
-                       h->oz_fexp, (double*)Wc, ldw, N, h->n_sm, h->info + 4, st, h->oz_aimg);
+                       h->oz_fexp, (double*)Wc, ldw, N, tc_grid(h), h->info + 4, st, h->oz_aimg);
         TRY(timed_end(h, st, slot, 2.0 * NL * NL * (double)N * (double)nc, 1));
       }
       CKL();
@@ -377,7 +438,7 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
     } else {
       if (tc) {
         if (launch_cell_tc3(h->Aimg32, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N,
-                            h->tc_mode == 2, h->n_sm, h->info + 4, st, h->tc_tile_N == N ? h->tc_tile : 0)) {
+                            h->tc_mode == 2, tc_grid(h), h->info + 4, st, h->tc_tile_N == N ? h->tc_tile : 0)) {
           h->err = "tensor-core cell kernel needs 16-byte aligned rows";
           return EFE_ERR_ARG;
         }
@@ -486,7 +547,7 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
                double* Yne, const double* coef, int N, cudaStream_t st) {
   const int64_t nn = h->n_nodes;
   const int ld = h->ld32;
-  double* We = h->W;  // nE x N FP64 scratch
+  double* We = h->We;  // nE x N FP64 scratch (W may hold the FP32 slots)
   CK(cudaMemsetAsync(h->Wf, 0, sizeof(float) * nn * ld, st));
   h->time_this = true;
   TRY(cell_apply_all<float>(h, h->Hcc32, Yc, ld, h->Wf, ld, N, st, h->tc_mode != 0));
@@ -900,6 +961,10 @@ int anderson_apply(efe_handle* h, const HistDev& hs, double beta, double* out, c
   return EFE_OK;
 }
 
+// device address of the allocation-free entry point's static scratch (defined
+// with that entry point below)
+int noalloc_scratch(efe_handle* h, int dev, double** out);
+
 }  // namespace
 
 extern "C" {
@@ -917,6 +982,10 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev));
     h->n_sm = nsm > 0 ? nsm : 148;
   }
+  // map this library's device module and look up the static scratch of
+  // efe_apply_M_noalloc now, so that the entry point itself never loads a
+  // module or allocates
+  TRY(noalloc_scratch(h, h->dev, &h->noalloc_part));
   Setup s;
   int rc;
   try {
@@ -1202,10 +1271,24 @@ static int check_block(efe_handle* h, const void* X, int64_t ldx, int N) {
   return EFE_OK;
 }
 
+// The products below write Y while they still read X: the two blocks (rows x N
+// with their leading dimensions) must not share any byte.
+static int check_disjoint(efe_handle* h, const double* X, int64_t ldx, const double* Y, int64_t ldy, int N) {
+  const uintptr_t x0 = (uintptr_t)X, y0 = (uintptr_t)Y;
+  const uintptr_t x1 = x0 + sizeof(double) * (uintptr_t)((h->rows - 1) * ldx + N);
+  const uintptr_t y1 = y0 + sizeof(double) * (uintptr_t)((h->rows - 1) * ldy + N);
+  if (x0 < y1 && y0 < x1) {
+    h->err = "X and Y overlap (in-place products are not supported)";
+    return EFE_ERR_ARG;
+  }
+  return EFE_OK;
+}
+
 int efe_apply_H(efe_handle* h, const double* X, int64_t ldx, int32_t N, double* Y, int64_t ldy, void* stream) {
   if (!h) return EFE_ERR_ARG;
   TRY(check_block(h, X, ldx, N));
   TRY(check_block(h, Y, ldy, N));
+  TRY(check_disjoint(h, X, ldx, Y, ldy, N));
   TRY(set_dev(h));
   TRY(reserve(h, N));
   return apply_H_impl(h, X, ldx, N, Y, ldy, S(stream));
@@ -1215,6 +1298,7 @@ int efe_apply_M(efe_handle* h, const double* X, int64_t ldx, int32_t N, double* 
   if (!h) return EFE_ERR_ARG;
   TRY(check_block(h, X, ldx, N));
   TRY(check_block(h, Y, ldy, N));
+  TRY(check_disjoint(h, X, ldx, Y, ldy, N));
   TRY(set_dev(h));
   TRY(reserve(h, N));
   return apply_M_impl(h, X, ldx, N, Y, ldy, S(stream));
@@ -1364,38 +1448,39 @@ static int chfsi_enqueue(efe_handle* h, double* X, int64_t ldx, int32_t N, int32
   const int64_t nn = h->n_nodes;
   h->tc_mode = (precision == EFE_PREC_TF32) ? 1 : (precision == EFE_PREC_TF32X3 ? 2 : 0);
   CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
-  // FP64 buffers: slot 0 = X (user, ldx), 1 = B1, 2 = B2 (ld = N)
-  double* buf[3] = {X, h->B1, h->B2};
-  int64_t ld[3] = {ldx, N, N};
+  // Two slots per precision: degree k writes Y_k over Y_{k-2} (the combine is
+  // elementwise), degree 1 into the free slot.  FP64 slots: 0 = X (user, ldx),
+  // 1 = B1 (ld N).
+  double* buf[2] = {X, h->B1};
+  int64_t ld[2] = {ldx, N};
   int prev = -1, cur = 0;
   int k = 1;
   if (n_low > 0) {
-    // load Y_0 into the low-precision buffers
+    // load Y_0 into FP32 slot 0
     launch_f64_to_f32_rows(nn, X, ldx, h->Yf[0], h->ld32, N, st);
     if (h->nE > 0) launch_copy_rows(h->nE, X + nn * ldx, ldx, h->Ye[0], N, N, st);
     CKL();
     int p32 = -1, c32 = 0;
     for (; k <= n_low; ++k) {
-      const int nx = (c32 + 1) % 3 == p32 ? (c32 + 2) % 3 : (c32 + 1) % 3;
+      const int nx = 1 - c32;
       TRY(degree_f32(h, h->Yf[c32], h->Ye[c32], p32 >= 0 ? h->Yf[p32] : nullptr, p32 >= 0 ? h->Ye[p32] : nullptr,
                      h->Yf[nx], h->Ye[nx], h->coefd + 3 * (k - 1), N, st));
       p32 = c32;
       c32 = nx;
     }
-    // hand the last two degrees to FP64 storage: prev -> B1, cur -> B2
-    launch_f32_to_f64_rows(nn, h->Yf[c32], h->ld32, h->B2, N, N, st);
-    if (h->nE > 0) launch_copy_rows(h->nE, h->Ye[c32], N, h->B2 + nn * N, N, N, st);
-    cur = 2;
-    if (p32 >= 0) {
-      launch_f32_to_f64_rows(nn, h->Yf[p32], h->ld32, h->B1, N, N, st);
-      if (h->nE > 0) launch_copy_rows(h->nE, h->Ye[p32], N, h->B1 + nn * N, N, N, st);
-      prev = 1;
-    }
+    // hand the last two degrees to FP64 storage: current -> X (free since Y_0
+    // was loaded), previous -> B1 (the FP32 slots may live in W and B1 holds
+    // only the dead cell-product output)
+    launch_f32_to_f64_rows(nn, h->Yf[c32], h->ld32, X, ldx, N, st);
+    if (h->nE > 0) launch_copy_rows(h->nE, h->Ye[c32], N, X + nn * ldx, ldx, N, st);
+    cur = 0;
+    launch_f32_to_f64_rows(nn, h->Yf[p32], h->ld32, h->B1, N, N, st);
+    if (h->nE > 0) launch_copy_rows(h->nE, h->Ye[p32], N, h->B1 + nn * N, N, N, st);
+    prev = 1;
     CKL();
   }
   for (; k <= m; ++k) {
-    int nx = 0;
-    while (nx == cur || nx == prev) ++nx;
+    const int nx = prev >= 0 ? prev : 1 - cur;
     TRY(degree_f64(h, buf[cur], ld[cur], prev >= 0 ? buf[prev] : nullptr, prev >= 0 ? ld[prev] : 0, buf[nx], ld[nx],
                    h->coefd + 3 * (k - 1), N, st));
     prev = cur;
@@ -1430,8 +1515,6 @@ int efe_chfsi_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, 
   return EFE_OK;
 }
 
-// C = A B for a tall A (rows x N) and a small B (N x N): tensor-core FP64-grade
-// products when enabled (N <= 144), FP64 DFMA otherwise.
 // grow-only device buffer i of the operand images (at least `bytes`)
 int oz_img_buf(efe_handle* h, int i, int64_t bytes) {
   if (bytes <= h->oz_img_bytes[i]) return EFE_OK;
@@ -1443,53 +1526,130 @@ int oz_img_buf(efe_handle* h, int i, int64_t bytes) {
   return EFE_OK;
 }
 
-int gemm_tall(efe_handle* h, int64_t rows, int N, const double* A, int64_t lda, const double* B, double* C,
+// Device bytes the digit images of one tall product may take: the operands are
+// sliced in row panels of at most this size (14 bytes per FP64 value).
+constexpr int64_t OZ_IMAGE_BUDGET = 8ll << 30;
+
+// rows per image panel: `unit`-row multiples whose image (bytes_per_row each)
+// fits the budget, or the test override
+int64_t image_panel_rows(const efe_handle* h, int64_t rows, int64_t bytes_per_row, int64_t unit) {
+  int64_t pr = h->opt_image_rows > 0 ? h->opt_image_rows : OZ_IMAGE_BUDGET / std::max<int64_t>(1, bytes_per_row);
+  pr = std::max<int64_t>(unit, pr / unit * unit);
+  return std::min(pr, (rows + unit - 1) / unit * unit);
+}
+
+// C = A B for a tall A (rows x K) and a small B (K x Nc, ld Nc): FP64-grade
+// tensor-core products when enabled (A sliced in row panels whose digit image
+// fits the budget; K in exact groups of 144 inside the kernel), FP64 DFMA
+// otherwise.
+int gemm_tall(efe_handle* h, int64_t rows, int K, int Nc, const double* A, int64_t lda, const double* B, double* C,
               int64_t ldc, cudaStream_t st) {
-  if (h->fp64_engine == 1 && N <= 144) {
-    launch_oz_rowexp(A, lda, rows, N, h->oz_aexp, st);
-    launch_oz_colexp(B, N, N, N, h->oz_bexp, st);
-    // both operands sliced once into digit images; the product kernel then only
-    // streams them (bulk copies) through the tensor cores
-    TRY(oz_img_buf(h, 0, oz_img_rows_bytes(rows, N)));
-    TRY(oz_img_buf(h, 1, oz_img_cols_bytes((N + 15) / 16, N)));
-    launch_oz_img_rows(A, lda, rows, N, h->oz_aexp, h->oz_img[0], st);
-    launch_oz_img_cols(B, N, N, N, h->oz_bexp, (N + 15) / 16, h->oz_img[1], st);
-    int slot;
-    TRY(timed_begin(h, st, &slot, 1));
-    launch_oz_rows(A, lda, rows, N, h->oz_aexp, B, N, h->oz_bexp, C, ldc, N, h->n_sm, h->info + 4, st,
-                   h->oz_img[0], h->oz_img[1]);
-    TRY(timed_end(h, st, slot, 2.0 * (double)rows * N * N, 1));
+  if (h->fp64_engine == 1) {
+    launch_oz_rowexp(A, lda, rows, K, h->oz_aexp, st);
+    launch_oz_colexp(B, Nc, K, Nc, h->oz_bexp, st);
+    const int64_t nchk = (K + 15) / 16;
+    TRY(oz_img_buf(h, 1, oz_img_cols_bytes(nchk, Nc)));
+    launch_oz_img_cols(B, Nc, K, Nc, h->oz_bexp, nchk, h->oz_img[1], st);
+    const int64_t pr = image_panel_rows(h, rows, oz_img_rows_bytes(128, K) / 128, 128);
+    TRY(oz_img_buf(h, 0, oz_img_rows_bytes(pr, K)));
+    for (int64_t r0 = 0; r0 < rows; r0 += pr) {
+      const int64_t n = std::min(pr, rows - r0);
+      // both operands sliced once into digit images; the product kernel then only
+      // streams them (bulk copies) through the tensor cores
+      launch_oz_img_rows(A + r0 * lda, lda, n, K, h->oz_aexp + r0, h->oz_img[0], st);
+      int slot;
+      TRY(timed_begin(h, st, &slot, 1));
+      launch_oz_rows(A + r0 * lda, lda, n, K, h->oz_aexp + r0, B, Nc, h->oz_bexp, C + r0 * ldc, ldc, Nc, tc_grid(h),
+                     h->info + 4, st, h->oz_img[0], h->oz_img[1]);
+      TRY(timed_end(h, st, slot, 2.0 * (double)n * K * Nc, 1));
+    }
   } else {
-    launch_gemm_nn(rows, N, N, 1.0, A, lda, B, N, 0.0, C, ldc, st);
+    launch_gemm_nn(rows, Nc, K, 1.0, A, lda, B, Nc, 0.0, C, ldc, st);
   }
   CKL();
   return EFE_OK;
 }
 
-// C (N x N) = A^T B for tall A, B (rows x N): FP64 DFMA split-K, or with the
-// tensor-core FP64 engine the sliced A^T B (exponents per column over all rows).
-int gemm_gram(efe_handle* h, int64_t rows, int N, const double* A, int64_t lda, const double* B, int64_t ldb,
-              double* C, bool sym, cudaStream_t st) {
+// C (Na x Nb, ldc) = A^T B for tall A (rows x Na), B (rows x Nb): FP64 DFMA
+// split-K, or with the tensor-core FP64 engine the sliced A^T B (exponents per
+// column over all rows; the rows in panels whose column images fit the budget,
+// each panel's product added to C).  sym: C is symmetric (Na = Nb): only the
+// tiles that meet the upper triangle are formed, the rest mirrored.
+int gemm_gram(efe_handle* h, int64_t rows, int Na, int Nb, const double* A, int64_t lda, const double* B,
+              int64_t ldb, double* C, int64_t ldc, bool sym, cudaStream_t st) {
   if (h->fp64_engine == 1) {
-    launch_oz_colexp(A, lda, rows, N, h->oz_fexp, st);
-    if (B != A) launch_oz_colexp(B, ldb, rows, N, h->oz_bexp, st);
-    // column digit images of A and B, enough chunks for any segmentation (the
-    // segments, at most 2 n_sm of them, are multiples of 256 rows)
-    const int64_t nch = (rows + 15) / 16 + 16 * (2 * (int64_t)h->n_sm + 1);
-    TRY(oz_img_buf(h, 0, oz_img_cols_bytes(nch, N)));
-    if (B != A) TRY(oz_img_buf(h, 1, oz_img_cols_bytes(nch, N)));
-    int slot;
-    TRY(timed_begin(h, st, &slot, 1));
-    if (launch_oz_gram(rows, N, N, A, lda, h->oz_fexp, B, ldb, B != A ? h->oz_bexp : h->oz_fexp, C, N, sym,
-                       h->tnwork, h->tnwork_elems, h->oz_pairs, h->n_sm, h->info + 4, st, h->oz_img[0],
-                       h->oz_img_bytes[0], h->oz_img[1], h->oz_img_bytes[1]) == 0) {
-      TRY(timed_end(h, st, slot, (sym ? 1.0 : 2.0) * (double)rows * N * (N + (sym ? 1 : 0)), 1));
+    launch_oz_colexp(A, lda, rows, Na, h->oz_fexp, st);
+    if (B != A) launch_oz_colexp(B, ldb, rows, Nb, h->oz_bexp, st);
+    const int* bexp = B != A ? h->oz_bexp : h->oz_fexp;
+    // column digit images: per 16 rows, 28 KB per 128 columns of each operand
+    const int64_t per16 = oz_img_cols_bytes(1, Na) + (B != A ? oz_img_cols_bytes(1, Nb) : 0);
+    const int64_t kp = image_panel_rows(h, rows, (per16 + 15) / 16, 256);
+    // image chunks of a panel: enough for any segmentation (the segments, at
+    // most 2 n_sm of them, are multiples of 256 rows)
+    const int64_t nch = (std::min(kp, rows) + 15) / 16 + 16 * (2 * (int64_t)tc_grid(h) + 1);
+    TRY(oz_img_buf(h, 0, oz_img_cols_bytes(nch, Na)));
+    if (B != A) TRY(oz_img_buf(h, 1, oz_img_cols_bytes(nch, Nb)));
+    bool ok = true;
+    for (int64_t k0 = 0; k0 < rows && ok; k0 += kp) {
+      const int64_t kn = std::min(kp, rows - k0);
+      int slot;
+      TRY(timed_begin(h, st, &slot, 1));
+      ok = launch_oz_gram(kn, Na, Nb, A + k0 * lda, lda, h->oz_fexp, B + k0 * ldb, ldb, bexp, C, ldc, sym, h->tnwork,
+                          h->tnwork_elems, h->oz_pairs, tc_grid(h), h->info + 4, st, h->oz_img[0],
+                          h->oz_img_bytes[0], h->oz_img[1], h->oz_img_bytes[1], k0 > 0) == 0;
+      TRY(timed_end(h, st, slot, ok ? (sym ? 1.0 : 2.0) * (double)kn * Na * (Nb + (sym ? 1 : 0)) : 0.0, 1));
+    }
+    if (ok) {
       CKL();
       return EFE_OK;
     }
-    TRY(timed_end(h, st, slot, 0.0, 1));
   }
-  launch_gemm_tn(rows, N, N, A, lda, B, ldb, C, N, h->tnwork, h->tnwork_elems, st, sym);
+  launch_gemm_tn(rows, Na, Nb, A, lda, B, ldb, C, ldc, h->tnwork, h->tnwork_elems, st, sym);
+  CKL();
+  return EFE_OK;
+}
+
+// Largest block of vectors Rayleigh-Ritz takes (its dense N x N work).
+constexpr int RR_MAX_N = 4096;
+
+// grow-only scratch of the blocked dense kernels
+int dense_scratch(efe_handle* h, int64_t bytes) {
+  if (bytes <= h->dsc_bytes) return EFE_OK;
+  dfree(h, h->dsc);
+  h->dsc = nullptr;
+  h->dsc_bytes = 0;
+  unsigned char* p = nullptr;
+  TRY(dalloc(h, &p, bytes));
+  h->dsc = p;
+  h->dsc_bytes = bytes;
+  return EFE_OK;
+}
+
+// the one-CTA dense kernels up to these sizes, the blocked multi-CTA ones above
+constexpr int CHOL_ONE_CTA_MAX = 2048;
+constexpr int DENSE_SMALL_MAX = 512;
+
+// A = L L^T in place (lower, n x n, ld n); *info: 0 or j + 1 of the first breakdown
+int chol_lower(efe_handle* h, double* A, int n, cudaStream_t st, double* min_ratio, int* info = nullptr) {
+  if (!info) info = h->info;
+  if (n <= CHOL_ONE_CTA_MAX && !h->opt_dense_blocked) {
+    launch_chol(A, n, n, info, st, min_ratio);
+  } else {
+    TRY(dense_scratch(h, (int64_t)sizeof(double) * chol_blocked_scratch(n)));
+    launch_chol_blocked(A, n, n, info, min_ratio, (double*)h->dsc, st);
+  }
+  CKL();
+  return EFE_OK;
+}
+
+// Li = L^-1 (lower, n x n, ld n)
+int trinv_lower(efe_handle* h, const double* L, int n, double* Li, cudaStream_t st) {
+  if (n <= DENSE_SMALL_MAX && !h->opt_dense_blocked) {
+    launch_trinv_lower(L, n, n, Li, n, st);
+  } else {
+    TRY(dense_scratch(h, (int64_t)sizeof(double) * ((int64_t)n * n / 4 + 64 * (int64_t)n)));
+    launch_trinv_blocked(L, n, n, Li, n, (double*)h->dsc, st);
+  }
   CKL();
   return EFE_OK;
 }
@@ -1501,7 +1661,10 @@ int gemm_gram(efe_handle* h, int64_t rows, int N, const double* A, int64_t lda, 
 // nearly diagonal and FP64 Jacobi finishes it in two or three sweeps
 // (quadratic convergence); V = Q V'.  Falls back to FP64 Jacobi from scratch
 // if the FP32 stage fails.  Scratch: 9 N x N blocks at E.
+int sym_eig_blocked(efe_handle* h, const double* C, int N, double* V, double* w, double* E, cudaStream_t st);
+
 int sym_eig(efe_handle* h, const double* C, int N, double* V, double* w, double* E, cudaStream_t st) {
+  if (N > DENSE_SMALL_MAX || h->opt_dense_blocked) return sym_eig_blocked(h, C, N, V, w, E, st);
   const int64_t NN = (int64_t)N * N;
   float* C32 = reinterpret_cast<float*>(E);
   float* V32 = C32 + NN;
@@ -1543,6 +1706,67 @@ int sym_eig(efe_handle* h, const double* C, int N, double* V, double* w, double*
   return EFE_OK;
 }
 
+// The same two stages for large N on many SMs: block Jacobi in FP32 to an
+// off-diagonal size ~1e-6, the FP32 vectors made orthonormal in FP64 (blocked
+// Cholesky and triangular inverse), then FP64 block Jacobi on the nearly
+// diagonal Q^T C Q (two or three sweeps).
+int sym_eig_blocked(efe_handle* h, const double* C, int N, double* V, double* w, double* E, cudaStream_t st) {
+  const int64_t NN = (int64_t)N * N;
+  float* V32 = reinterpret_cast<float*>(E);
+  float* w32 = V32 + NN;
+  double* Q0 = E + NN;
+  double* G = Q0 + NN;
+  double* Li = G + NN;
+  double* LiT = Li + NN;
+  double* Q = LiT + NN;
+  double* T1 = Q + NN;
+  double* C2 = T1 + NN;
+  double* V2 = C2 + NN;
+  CK(cudaMemsetAsync(h->info + 1, 0, 2 * sizeof(int), st));
+  TRY(dense_scratch(h, block_jacobi_scratch_bytes(N, (int)sizeof(double))));
+  double ratio = 0.0;
+  const int r32 = block_jacobi<float>(C, N, N, V32, N, w32, 40, 1e-12, h->dsc, st, &ratio);
+  if (r32 < 0) {
+    h->err = "block Jacobi (FP32 stage): CUDA error";
+    return EFE_ERR_CUDA;
+  }
+  bool refine = true;
+  if (r32 == 0) {
+    launch_f32_to_f64_rows(N, V32, N, Q0, N, N, st);
+    launch_gemm_tn(N, N, N, Q0, N, Q0, N, G, N, h->tnwork, h->tnwork_elems, st, true);
+    launch_symmetrize(G, N, N, st);
+    TRY(chol_lower(h, G, N, st, nullptr, h->info + 2));
+    int inf = 0;
+    CK(cudaMemcpyAsync(&inf, h->info + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    refine = inf == 0;
+  }
+  const double* C64 = C;
+  if (refine && r32 == 0) {
+    TRY(trinv_lower(h, G, N, Li, st));
+    launch_transpose(Li, N, N, LiT, N, st);
+    launch_gemm_nn(N, N, N, 1.0, Q0, N, LiT, N, 0.0, Q, N, st);
+    launch_gemm_tn(N, N, N, Q, N, C, N, T1, N, h->tnwork, h->tnwork_elems, st, false);
+    launch_gemm_nn(N, N, N, 1.0, T1, N, Q, N, 0.0, C2, N, st);
+    launch_symmetrize(C2, N, N, st);
+    C64 = C2;
+  }
+  // FP64 stage: on the nearly diagonal C2, or on C itself if the FP32 stage failed
+  const int r64 = block_jacobi<double>(C64, N, N, C64 == C ? V : V2, N, w, C64 == C ? 60 : 20, 1e-28, h->dsc, st,
+                                       &ratio);
+  if (r64 < 0) {
+    h->err = "block Jacobi (FP64 stage): CUDA error";
+    return EFE_ERR_CUDA;
+  }
+  if (r64 == 1 && ratio > 1e-20) {
+    h->err = "block Jacobi eigensolver did not converge";
+    return EFE_ERR_NOCONV;
+  }
+  if (C64 != C) launch_gemm_nn(N, N, N, 1.0, Q, N, V2, N, 0.0, V, N, st);
+  CKL();
+  return EFE_OK;
+}
+
 int efe_rr_shifted_passes(efe_handle* h, int64_t* count) {
   if (!h || !count) return EFE_ERR_ARG;
   *count = h->chol_shifted;
@@ -1553,8 +1777,8 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
                       void* stream) {
   if (!h || !eig_host) return EFE_ERR_ARG;
   TRY(check_block(h, X, ldx, N));
-  if (N > 2048) {
-    h->err = "N > 2048 not supported by the one-CTA dense eigensolver";
+  if (N > RR_MAX_N) {
+    h->err = "N above the dense eigensolver's limit (" + std::to_string(RR_MAX_N) + ")";
     return EFE_ERR_ARG;
   }
   TRY(set_dev(h));
@@ -1579,7 +1803,7 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   double* eps = wv + N;
   double* res = eps + N;
   double* E0 = res + N + 5 * (int64_t)N;   // eigensolver scratch: 9 blocks
-  double *Q = h->B1, *HQ = h->B2, *MQ = h->W;
+  double* Q = h->B1;
   int inf[2] = {0, 0};
   // Cholesky-QR: G = X^T X = L L^T, Q = X L^-T
   CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
@@ -1590,10 +1814,9 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   // filter's spread of amplifications over an all-electron spectrum routinely
   // leaves blocks between 1e-14 and 1e-10)
   auto gram_chol = [&](bool& ok) -> int {
-    TRY(gemm_gram(h, R, N, X, ldx, X, ldx, G, true, st));
+    TRY(gemm_gram(h, R, N, N, X, ldx, X, ldx, G, N, true, st));
     launch_symmetrize(G, N, N, st);
-    launch_chol(G, N, N, h->info, st, h->chol_ratio);
-    CKL();
+    TRY(chol_lower(h, G, N, st, h->chol_ratio));
     int fl[5] = {0, 0, 0, 0, 0};
     double ratio = 0.0;
     CK(cudaMemcpyAsync(fl, h->info, sizeof(fl), cudaMemcpyDeviceToHost, st));
@@ -1622,11 +1845,10 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
       h->err = "Cholesky-QR breakdown: Gram matrix X^T X is not positive definite (non-finite or rank-deficient block)";
       return EFE_ERR_CHOL;
     }
-    TRY(gemm_gram(h, R, N, X, ldx, X, ldx, G, true, st));
+    TRY(gemm_gram(h, R, N, N, X, ldx, X, ldx, G, N, true, st));
     launch_symmetrize(G, N, N, st);
     launch_shift_diag(G, N, N, 11.0 * ((double)R * N + (double)N * (N + 1)) * 0x1p-53, st);
-    launch_chol(G, N, N, h->info, st);
-    CKL();
+    TRY(chol_lower(h, G, N, st, nullptr));
     int fl[5] = {0, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(fl, h->info, sizeof(fl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1638,26 +1860,45 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
       h->err = "Cholesky-QR breakdown: shifted Gram matrix is not positive definite (non-finite block)";
       return EFE_ERR_CHOL;
     }
-    launch_trinv_lower(G, N, N, Linv, N, st);
+    TRY(trinv_lower(h, G, N, Linv, st));
     launch_transpose(Linv, N, N, Rinv, N, st);
-    TRY(gemm_tall(h, R, N, X, ldx, Rinv, Q, N, st));
+    TRY(gemm_tall(h, R, N, N, X, ldx, Rinv, Q, N, st));
     launch_copy_rows(R, Q, N, X, ldx, N, st);
     h->chol_shifted++;
     TRY(gram_chol(ok));
   }
-  launch_trinv_lower(G, N, N, Linv, N, st);
+  TRY(trinv_lower(h, G, N, Linv, st));
   launch_transpose(Linv, N, N, Rinv, N, st);
-  TRY(gemm_tall(h, R, N, X, ldx, Rinv, Q, N, st));
-  // projections
-  TRY(apply_H_impl(h, Q, N, N, HQ, N, st));
-  TRY(apply_M_impl(h, Q, N, N, MQ, N, st));
-  TRY(gemm_gram(h, R, N, Q, N, HQ, N, Hp, true, st));
-  TRY(gemm_gram(h, R, N, Q, N, MQ, N, Mp, true, st));
-  launch_symmetrize(Hp, N, N, st);
-  launch_symmetrize(Mp, N, N, st);
+  TRY(gemm_tall(h, R, N, N, X, ldx, Rinv, Q, N, st));
+  // projections H_p = Q^T H Q, M_p = Q^T M Q
+  const bool whole = h->whole_rr && h->B2 != nullptr;
+  if (whole) {
+    double *HQ = h->B2, *MQ = h->W;
+    TRY(apply_H_impl(h, Q, N, N, HQ, N, st));
+    TRY(apply_M_impl(h, Q, N, N, MQ, N, st));
+    TRY(gemm_gram(h, R, N, N, Q, N, HQ, N, Hp, N, true, st));
+    TRY(gemm_gram(h, R, N, N, Q, N, MQ, N, Mp, N, true, st));
+    launch_symmetrize(Hp, N, N, st);
+    launch_symmetrize(Mp, N, N, st);
+  } else {
+    // two column panels [0, n1) and [n1, N): H Q_p and M Q_p side by side in W;
+    // the panel's block column of H_p up to its last row (the upper triangle and
+    // the diagonal block), then the lower triangle mirrored
+    const int n1 = N / 2;
+    for (int pnl = 0; pnl < 2; ++pnl) {
+      const int c0 = pnl == 0 ? 0 : n1, c1 = pnl == 0 ? n1 : N, w = c1 - c0;
+      if (w <= 0) continue;
+      double *HQp = h->W, *MQp = h->W + R * w;
+      TRY(apply_H_impl(h, Q + c0, N, w, HQp, w, st));
+      TRY(apply_M_impl(h, Q + c0, N, w, MQp, w, st));
+      TRY(gemm_gram(h, R, c1, w, Q, N, HQp, w, Hp + c0, N, false, st));
+      TRY(gemm_gram(h, R, c1, w, Q, N, MQp, w, Mp + c0, N, false, st));
+    }
+    launch_mirror_upper(Hp, N, N, st);
+    launch_mirror_upper(Mp, N, N, st);
+  }
   CK(cudaMemcpyAsync(Lm, Mp, sizeof(double) * NN, cudaMemcpyDeviceToDevice, st));
-  launch_chol(Lm, N, N, h->info, st);
-  CKL();
+  TRY(chol_lower(h, Lm, N, st, nullptr));
   CK(cudaMemcpyAsync(inf, h->info, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (inf[0]) {
@@ -1665,7 +1906,7 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
     return EFE_ERR_CHOL;
   }
   // C = Lm^-1 Hp Lm^-T, eig(C) = (eps, Z), Psi = Lm^-T Z
-  launch_trinv_lower(Lm, N, N, Lminv, N, st);
+  TRY(trinv_lower(h, Lm, N, Lminv, st));
   launch_transpose(Lminv, N, N, LminvT, N, st);
   launch_gemm_nn(N, N, N, 1.0, Lminv, N, Hp, N, 0.0, T1, N, st);
   launch_gemm_nn(N, N, N, 1.0, T1, N, LminvT, N, 0.0, C, N, st);
@@ -1674,11 +1915,27 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   launch_sort_eig(wv, Vj, N, N, eps, Z, N, st);
   launch_gemm_nn(N, N, N, 1.0, LminvT, N, Z, N, 0.0, Psi, N, st);
   // rotation and residuals
-  TRY(gemm_tall(h, R, N, Q, N, Psi, X, ldx, st));
-  TRY(gemm_tall(h, R, N, HQ, N, Psi, Q, N, st));     // HX
-  TRY(gemm_tall(h, R, N, MQ, N, Psi, HQ, N, st));    // MX
-  launch_resid_norms(R, Q, N, HQ, N, eps, N, h->rpart, res, st);
-  CKL();
+  TRY(gemm_tall(h, R, N, N, Q, N, Psi, X, ldx, st));
+  if (resid_host) {
+    if (whole) {
+      TRY(gemm_tall(h, R, N, N, h->B2, N, Psi, Q, N, st));     // H X = (H Q) Psi
+      TRY(gemm_tall(h, R, N, N, h->W, N, Psi, h->B2, N, st));  // M X = (M Q) Psi
+      launch_resid_norms(R, Q, N, h->B2, N, eps, N, h->rpart, res, st);
+    } else {
+      // H X and M X of each panel of the rotated block, applied afresh (an H
+      // apply costs far less than rotating H Q at large N)
+      const int n1 = N / 2;
+      for (int pnl = 0; pnl < 2; ++pnl) {
+        const int c0 = pnl == 0 ? 0 : n1, c1 = pnl == 0 ? n1 : N, w = c1 - c0;
+        if (w <= 0) continue;
+        double *HXp = h->W, *MXp = h->W + R * w;
+        TRY(apply_H_impl(h, X + c0, ldx, w, HXp, w, st));
+        TRY(apply_M_impl(h, X + c0, ldx, w, MXp, w, st));
+        launch_resid_norms(R, HXp, w, MXp, w, eps + c0, w, h->rpart, res + c0, st);
+      }
+    }
+    CKL();
+  }
   CK(cudaMemcpyAsync(inf + 1, h->info + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(eig_host, eps, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
   if (resid_host) CK(cudaMemcpyAsync(resid_host, res, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
@@ -1689,7 +1946,7 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
     return EFE_ERR_TIMEOUT;
   }
   if (inf[1]) {
-    h->err = "Jacobi eigensolver did not converge";
+    h->err = "dense eigensolver did not converge";
     return EFE_ERR_NOCONV;
   }
   for (int i = 0; i < N; ++i)
@@ -1704,6 +1961,33 @@ int efe_set_fp64_engine(efe_handle* h, int32_t engine) {
   if (!h || (engine != 0 && engine != 1)) return EFE_ERR_ARG;
   h->fp64_engine = engine;
   return EFE_OK;
+}
+
+int efe_set_option(efe_handle* h, int32_t option, int64_t value) {
+  if (!h || value < 0) return EFE_ERR_ARG;
+  switch (option) {
+    case EFE_OPT_GRID_CAP:
+      if (value > (1 << 20)) return EFE_ERR_ARG;
+      h->grid_cap = (int)value;
+      return EFE_OK;
+    case EFE_OPT_IMAGE_ROWS:
+      h->opt_image_rows = value;
+      return EFE_OK;
+    case EFE_OPT_RR_PANELS:
+      if (value > 1) return EFE_ERR_ARG;
+      if (h->opt_rr_panels != (int)value) {
+        h->opt_rr_panels = (int)value;
+        h->Nres = 0;   // the workspace layout changes at the next reservation
+      }
+      return EFE_OK;
+    case EFE_OPT_DENSE_BLOCKED:
+      if (value > 1) return EFE_ERR_ARG;
+      h->opt_dense_blocked = (int)value;
+      return EFE_OK;
+    default:
+      h->err = "unknown option";
+      return EFE_ERR_ARG;
+  }
 }
 
 int efe_launch_count(int64_t* total) {
@@ -1951,9 +2235,12 @@ static __device__ __align__(256) double g_noalloc_scratch[EFE_NOALLOC_SCRATCH_DO
 namespace {
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[256] = {nullptr};
+}  // namespace
 
+namespace {
 // Device address of the scratch array on `dev` (which must be current).  Looked
-// up once per device; host code may not use the array's name as an address.
+// up once per device (by efe_create); host code may not use the array's name as
+// an address.
 int noalloc_scratch(efe_handle* h, int dev, double** out) {
   if (dev < 0 || dev >= 256) {
     h->err = "device ordinal out of range for the allocation-free scratch table";
@@ -1979,13 +2266,14 @@ extern "C" int efe_apply_M_noalloc(efe_handle* h, const double* X, int64_t ldx, 
   if (!h) return EFE_ERR_ARG;
   TRY(check_block(h, X, ldx, N));
   TRY(check_block(h, Y, ldy, N));
+  TRY(check_disjoint(h, X, ldx, Y, ldy, N));
   if (h->nE > 0 && h->nseg * (int64_t)N > EFE_NOALLOC_SCRATCH_DOUBLES) {
     h->err = "efe_apply_M_noalloc: segments x N exceeds the static scratch of 2^21 doubles";
     return EFE_ERR_ARG;
   }
   TRY(set_dev(h));
-  double* part = nullptr;
-  TRY(noalloc_scratch(h, h->dev, &part));
+  // looked up by efe_create (with this handle's device current)
+  double* part = h->noalloc_part;
   cudaStream_t st = S(stream);
   const int64_t nn = h->n_nodes;
   launch_row_scale<double>(nn, h->Dm, X, ldx, Y, ldy, N, st);
@@ -2264,7 +2552,7 @@ int efe_autotune(efe_handle* h, int32_t N, int32_t precision, int32_t* tile_out,
         const int64_t nc = h->colour_off[c + 1] - h->colour_off[c];
         if (nc == 0) continue;
         if (launch_cell_tc3(h->Aimg32, h->colour_cells + h->colour_off[c], nc, h->mesh, h->Yf[0], h->ld32, h->Wf,
-                            h->ld32, N, precision == EFE_PREC_TF32X3, h->n_sm, h->info + 4, st, tiles[i])) {
+                            h->ld32, N, precision == EFE_PREC_TF32X3, tc_grid(h), h->info + 4, st, tiles[i])) {
           h->err = "tensor-core cell kernel needs 16-byte aligned rows";
           return EFE_ERR_ARG;
         }

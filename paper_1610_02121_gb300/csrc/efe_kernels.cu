@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "efe_func.h"
@@ -18,6 +19,27 @@
 namespace efe {
 
 std::atomic<int64_t> g_launches{0};
+
+namespace {
+// SM count of the current device, looked up once per device ordinal
+std::atomic<int> g_sm_count[64];
+int current_sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 148;
+  }
+  int n = g_sm_count[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 148;
+    }
+    g_sm_count[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+}  // namespace
 
 namespace {
 
@@ -259,9 +281,11 @@ __global__ void k_seg_reduce(int nrows, const int64_t* __restrict__ row_seg_ptr,
 // coef = {alpha, c, beta} of this degree, read from device memory (so a captured
 // graph of the filter stays valid when the filter bounds change)
 template <typename T>
+// Yn may be Yp (the recurrence writes Y_k over Y_{k-2}; each element is read
+// before it is written by the same thread), so those two are not restrict.
 __global__ void k_cheb_combine(int64_t nrows, const double* __restrict__ rowscale, const T* __restrict__ X,
-                               int64_t ldx, const T* __restrict__ Yc, int64_t ldc, const T* __restrict__ Yp,
-                               int64_t ldp, T* __restrict__ Yn, int64_t ldn, const double* __restrict__ coef, int N) {
+                               int64_t ldx, const T* __restrict__ Yc, int64_t ldc, const T* Yp,
+                               int64_t ldp, T* Yn, int64_t ldn, const double* __restrict__ coef, int N) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= nrows * N) return;
   const double alpha = coef[0], cc = coef[1], beta = coef[2];
@@ -590,9 +614,10 @@ __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, const int64_t* 
 }
 
 // Chebyshev combine on 16-byte aligned FP32 rows (ld multiple of 4): four columns per thread.
+// as k_cheb_combine: Yn may be Yp
 __global__ void k_cheb_combine_f4(int64_t nrows, int ld4, const double* __restrict__ rowscale,
                                   const float4* __restrict__ X, const float4* __restrict__ Yc,
-                                  const float4* __restrict__ Yp, float4* __restrict__ Yn,
+                                  const float4* Yp, float4* Yn,
                                   const double* __restrict__ coef) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= nrows * ld4) return;
@@ -703,16 +728,17 @@ __global__ void __launch_bounds__(256) k_gemm_nn_small(int64_t M, int Nc, int K,
 
 constexpr int64_t TN_KC = 8192;
 
-__global__ void __launch_bounds__(256) k_gemm_tn_part(int64_t K, int Na, int Nb, const double* __restrict__ A,
-                                                      int64_t lda, const double* __restrict__ B, int64_t ldb,
+__global__ void __launch_bounds__(256) k_gemm_tn_part(int64_t K, int64_t kc, int Na, int Nb,
+                                                      const double* __restrict__ A, int64_t lda,
+                                                      const double* __restrict__ B, int64_t ldb,
                                                       double* __restrict__ part, int sym) {
   // symmetric products: only tiles on or above the diagonal are formed
   if (sym && blockIdx.x > blockIdx.y) return;
   __shared__ double As[16][GT + 1];
   __shared__ double Bs[16][GT + 1];
   const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
-  const int64_t kb = (int64_t)blockIdx.z * TN_KC;
-  const int64_t ke = min(K, kb + TN_KC);
+  const int64_t kb = (int64_t)blockIdx.z * kc;
+  const int64_t ke = min(K, kb + kc);
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
   double acc[3][3] = {};
   for (int64_t k0 = kb; k0 < ke; k0 += 16) {
@@ -861,6 +887,13 @@ __global__ void k_symmetrize(double* A, int n, int lda) {
   const double v = 0.5 * (A[(int64_t)i * lda + j] + A[(int64_t)j * lda + i]);
   A[(int64_t)i * lda + j] = v;
   A[(int64_t)j * lda + i] = v;
+}
+
+__global__ void k_mirror_upper(double* A, int n, int lda) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  if (i > j) A[(int64_t)i * lda + j] = A[(int64_t)j * lda + i];
 }
 
 // Parallel cyclic Jacobi (round-robin pairing) for a symmetric n x n matrix in
@@ -1204,7 +1237,8 @@ void launch_gemm_nn(int64_t M, int Nc, int K, double alpha, const double* A, int
                     int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st) {
   if (M <= 0 || Nc <= 0) return;
   dim3 g((unsigned)((M + GT - 1) / GT), (unsigned)((Nc + GT - 1) / GT));
-  if ((int64_t)g.x * g.y < 148) {
+  // fewer 48 x 48 output tiles than SMs: one output per thread in 16 x 16 tiles
+  if ((int64_t)g.x * g.y < current_sm_count()) {
     dim3 gs((unsigned)((M + 15) / 16), (unsigned)((Nc + 15) / 16));
     k_gemm_nn_small<<<gs, 256, 0, st>>>(M, Nc, K, alpha, A, lda, B, ldb, beta, C, ldc);
   } else {
@@ -1222,20 +1256,27 @@ void launch_gemm_nn_batched(int64_t M, int Nc, int K, const double* A, int64_t l
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-int64_t gemm_tn_work_elems(int64_t K, int Na, int Nb) {
-  const int64_t nsplit = (K + TN_KC - 1) / TN_KC;
-  return (nsplit < 1 ? 1 : nsplit) * (int64_t)Na * Nb;
+// K splits of an A^T B product: enough for about four CTAs per SM over the
+// output tiles, none shorter than TN_KC rows
+int64_t gemm_tn_splits(int64_t K, int Na, int Nb) {
+  const int64_t tiles = (int64_t)((Na + GT - 1) / GT) * ((Nb + GT - 1) / GT);
+  const int64_t want = (4 * (int64_t)current_sm_count() + tiles - 1) / tiles;
+  const int64_t most = (K + TN_KC - 1) / TN_KC;
+  return std::max<int64_t>(1, std::min(want, most));
 }
+
+int64_t gemm_tn_work_elems(int64_t K, int Na, int Nb) { return gemm_tn_splits(K, Na, Nb) * (int64_t)Na * Nb; }
 
 void launch_gemm_tn(int64_t K, int Na, int Nb, const double* A, int64_t lda, const double* B, int64_t ldb,
                     double* C, int64_t ldc, double* work, int64_t work_elems, cudaStream_t st, bool sym) {
   if (Na <= 0 || Nb <= 0) return;
-  int64_t nsplit = (K + TN_KC - 1) / TN_KC;
-  if (nsplit < 1) nsplit = 1;
-  (void)work_elems;
+  int64_t nsplit = gemm_tn_splits(K, Na, Nb);
+  nsplit = std::max<int64_t>(1, std::min(nsplit, work_elems / ((int64_t)Na * Nb)));
+  const int64_t kc = ((K + nsplit - 1) / nsplit + 15) / 16 * 16;
+  nsplit = std::max<int64_t>(1, (K + kc - 1) / kc);
   dim3 g((unsigned)((Na + GT - 1) / GT), (unsigned)((Nb + GT - 1) / GT), (unsigned)nsplit);
   const int sy = (sym && Na == Nb) ? 1 : 0;
-  k_gemm_tn_part<<<g, 256, 0, st>>>(K, Na, Nb, A, lda, B, ldb, work, sy);
+  k_gemm_tn_part<<<g, 256, 0, st>>>(K, kc, Na, Nb, A, lda, B, ldb, work, sy);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   k_gemm_tn_reduce<<<grid1((int64_t)Na * Nb, 256), 256, 0, st>>>((int)nsplit, Na, Nb, work, C, ldc, sy);
   g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -1258,6 +1299,11 @@ void launch_trinv_lower(const double* L, int n, int lda, double* Li, int ldi, cu
 
 void launch_transpose(const double* A, int n, int lda, double* B, int ldb, cudaStream_t st) {
   k_transpose<<<grid1((int64_t)n * n, 256), 256, 0, st>>>(A, n, lda, B, ldb);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_mirror_upper(double* A, int n, int lda, cudaStream_t st) {
+  k_mirror_upper<<<grid1((int64_t)n * n, 256), 256, 0, st>>>(A, n, lda);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 

@@ -130,11 +130,13 @@ void launch_oz_img_rows(const double* A, int64_t lda, int64_t rows, int K, const
                         cudaStream_t st);
 void launch_oz_img_cols(const double* A, int64_t lda, int64_t Krows, int ncols, const int* cexp, int64_t nch,
                         unsigned char* img, cudaStream_t st);
-// C (Na x N) = A^T B, A: K x Na, B: K x N (K large); aexp / bexp per column (launch_oz_colexp)
+// C (Na x N) = A^T B (+ C when accumulate), A: K x Na, B: K x N (K large); aexp / bexp per
+// column (launch_oz_colexp)
 int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const int* aexp, const double* B,
                    int64_t ldb, const int* bexp, double* C, int64_t ldc, bool sym, double* work, int64_t work_elems,
                    int2* pairs_dev, int n_sm, int* err, cudaStream_t st, unsigned char* img_a = nullptr,
-                   int64_t img_a_bytes = 0, unsigned char* img_b = nullptr, int64_t img_b_bytes = 0);
+                   int64_t img_a_bytes = 0, unsigned char* img_b = nullptr, int64_t img_b_bytes = 0,
+                   bool accumulate = false);
 int oz_gram_max_pairs(int Na, int N);
 
 // ---- dense FP64 ----
@@ -156,6 +158,23 @@ void launch_shift_diag(double* A, int n, int lda, double coef, cudaStream_t st);
 void launch_trinv_lower(const double* L, int n, int lda, double* Li, int ldi, cudaStream_t st);
 void launch_transpose(const double* A, int n, int lda, double* B, int ldb, cudaStream_t st);
 void launch_symmetrize(double* A, int n, int lda, cudaStream_t st);
+// A[i][j] = A[j][i] for i > j (the strict lower triangle from the upper one)
+void launch_mirror_upper(double* A, int n, int lda, cudaStream_t st);
+
+// ---- dense N x N kernels for large N (efe_dense.cu) ----
+// blocked Cholesky A = L L^T in place (lower; upper zeroed); info: 0 or j + 1 of the
+// first breakdown; min_ratio (optional): min_j L_jj^2 / A_jj; scratch: chol_blocked_scratch(n) doubles
+void launch_chol_blocked(double* A, int n, int lda, int* info, double* min_ratio, double* scratch, cudaStream_t st);
+int64_t chol_blocked_scratch(int n);
+// Li = L^-1 by 2 x 2 block recursion; scratch: n * n / 4 + 64 n doubles
+void launch_trinv_blocked(const double* L, int n, int lda, double* Li, int ldi, double* scratch, cudaStream_t st);
+// symmetric C = V diag(w) V^T by multi-CTA block Jacobi in precision T (float or double);
+// 0: converged (off-diagonal square sum <= tol2 x total), 1: sweeps ran out, -1: CUDA error;
+// ratio_out (optional): the last off / total ratio.  scratch: block_jacobi_scratch_bytes(n, sizeof(T))
+template <typename T>
+int block_jacobi(const double* C, int n, int ldc, T* V, int ldv, T* w, int max_sweeps, double tol2, void* scratch,
+                 cudaStream_t st, double* ratio_out);
+int64_t block_jacobi_scratch_bytes(int n, int elem);
 void launch_jacobi(double* A, int n, int lda, double* V, int ldv, double* w, int max_sweeps, int* info,
                    cudaStream_t st);
 // FP32 cyclic Jacobi to a relative off-diagonal size of 1e-6 (pre-diagonalisation)

@@ -7,7 +7,7 @@
 // is stored in BF16 as d_i 2^-7(i-1) (exact: 7 significant bits).  The product
 // sum_k a_i b_j of digit slices has weight 2^-7(i+j-2); for a fixed t = i + j
 // every partial sum is an integer multiple of 2^-7(t-2) below 2^24 of that
-// unit (K <= 144, at most four pairs), so the FP32 tensor-core accumulators
+// unit (K <= 144 per accumulation group, at most four pairs), so the FP32 tensor-core accumulators
 // for t = 2, 3, 4, 5 are exact.  The pairs with t = 6..8 share a fifth
 // accumulator (their FP32 rounding is below 2^-52 of the result); pairs with
 // t > 8 fall below the 49-bit truncation and are dropped.  The epilogue adds
@@ -18,7 +18,8 @@
 // Modes:
 //   CELL  W(cell nodes) += H^cc_e Y_e for the cells of one parity colour
 //         (Sec. V, last paragraph; cells of a colour share no node);
-//   ROWS  C = A B for a tall A (rows x K, K <= 144) and a small B (K x N);
+//   ROWS  C = A B for a tall A (rows x K) and a small B (K x N); K is taken in
+//         groups of 144 (exact FP32 sums), each group's FP64 value added to C;
 //   GRAM  C = A^T B for tall A, B (K x Na, K x N, K large): items are (tile
 //         pair, K segment); each segment is formed in 256-row groups (exact
 //         FP32 sums for t <= 5) drained into FP64 partial tiles, which a
@@ -51,6 +52,7 @@ constexpr int OZ_M = 128;          // MMA rows
 constexpr int OZ_KC = 16;          // K per chunk (one BF16 MMA)
 constexpr int OZ_TW = 96;          // column tile
 constexpr int OZ_NACC = 5;         // accumulators: t = 2, 3, 4, 5 exact; t = 6..8 shared
+constexpr int OZ_ROWS_KG = 9;      // ROWS: 16-wide K chunks per exact accumulation group (K <= 144)
 constexpr int OZ_STAGES = 4;
 constexpr int OZ_GROUPS = 2;        // slicer groups: group g fills the chunks ch = g (mod 2)
 constexpr int OZ_CONV_W0 = 1, OZ_CONV_WN = 7, OZ_EPI_W0 = 8;   // slicing: warps 1-7 slice, 8-15 epilogue
@@ -323,10 +325,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   const int64_t nitems = (g.mode == 2) ? (int64_t)g.npairs * g.nseg : nA * g.ntiles;
   const int64_t my = nitems > blockIdx.x ? (nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   // chunks of 16 K per item; the accumulators are drained every gsz chunks
-  // (GRAM: every 256 rows, where the FP32 sums of t <= 5 are still exact)
+  // (GRAM: every 256 rows, ROWS: every 144 K -- where the FP32 sums of t <= 5
+  // are still exact -- and CELL once, K = 125); later groups add to the result
   const int nch = (g.mode == 2) ? (int)(g.seg_len / OZ_KC) : (g.K + OZ_KC - 1) / OZ_KC;
-  const int gsz = (g.mode == 2) ? 16 : nch;
-  const int ngrp = nch / gsz;
+  const int gsz = (g.mode == 2) ? 16 : (g.mode == 1 ? min(nch, OZ_ROWS_KG) : nch);
+  const int ngrp = (nch + gsz - 1) / gsz;
 
   if (warp == 0) {
     // ---------------------------------------------------------------- MMA issuer
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
             }
           }
           mma_commit(empty + s);
-          if (kc % gsz == gsz - 1) mma_commit(accf);
+          if (kc % gsz == gsz - 1 || kc == nch - 1) mma_commit(accf);
         }
         __syncwarp();
       }
@@ -582,8 +585,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // modes 0 and 2 add to what is there (mode 2 from its second group on)
-        const bool add = (g.mode == 0) || (g.mode == 2 && grp > 0);
+        // CELL adds to what is there, GRAM and ROWS from their second group on
+        const bool add = (g.mode == 0) || grp > 0;
         // with twelve epilogue warps the results go out through a per-warp shared
         // tile (rows written 8 values at a time, 4 rows per instruction); with four,
         // each thread writes its own row and loads the values it adds to one
@@ -913,14 +916,13 @@ void launch_oz_img_cols(const double* A, int64_t lda, int64_t Krows, int ncols, 
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-// C = A B (A: rows x K, K <= 144; B: K x N), FP64-grade; aexp / bexp from
+// C = A B (A: rows x K; B: K x N), FP64-grade; aexp / bexp from
 // launch_oz_rowexp(A) and launch_oz_colexp(B).  Aimg / Bimg (optional):
 // launch_oz_img_rows(A) and launch_oz_img_cols(B, nch = ceil(K / 16)).
 int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, const double* B, int64_t ldb,
                    const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st,
                    const unsigned char* Aimg, const unsigned char* Bimg) {
-  if (rows <= 0 || N <= 0) return 0;
-  if (K > 144) return 1;
+  if (rows <= 0 || N <= 0 || K <= 0) return 0;
   OzArgs a{};
   a.Aimg = Aimg;
   a.Bimg = Bimg;
@@ -967,14 +969,14 @@ int oz_gram_pairs(int Na, int N, bool sym, int2* pairs_host) {
 }
 
 namespace {
-__global__ void k_oz_gram_reduce(int nseg, int Na, int N, const double* __restrict__ part, int sym,
+__global__ void k_oz_gram_reduce(int nseg, int Na, int N, const double* __restrict__ part, int sym, int accumulate,
                                  double* __restrict__ C, int64_t ldc) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= (int64_t)Na * N) return;
   const int i = (int)(idx / N), j = (int)(idx % N);
   const bool mirror = sym && i > j;
   const int64_t src = mirror ? (int64_t)j * N + i : idx;
-  double s = 0.0;
+  double s = accumulate ? C[(int64_t)i * ldc + j] : 0.0;
   for (int k = 0; k < nseg; ++k) s += part[(int64_t)k * Na * N + src];
   C[(int64_t)i * ldc + j] = s;
 }
@@ -983,7 +985,7 @@ __global__ void k_oz_gram_reduce(int nseg, int Na, int N, const double* __restri
 int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const int* aexp, const double* B,
                    int64_t ldb, const int* bexp, double* C, int64_t ldc, bool sym, double* work, int64_t work_elems,
                    int2* pairs_dev, int n_sm, int* err, cudaStream_t st, unsigned char* img_a,
-                   int64_t img_a_bytes, unsigned char* img_b, int64_t img_b_bytes) {
+                   int64_t img_a_bytes, unsigned char* img_b, int64_t img_b_bytes, bool accumulate) {
   if (K <= 0 || Na <= 0 || N <= 0) return 0;
   if (sym && Na != N) return 1;
   std::vector<int2> pairs(oz_gram_pairs(Na, N, sym, nullptr));
@@ -1023,8 +1025,8 @@ int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const
     a.img_nch = nch;
   }
   if (oz_launch(a, n_sm, st)) return 1;
-  k_oz_gram_reduce<<<(unsigned)(((int64_t)Na * N + 255) / 256), 256, 0, st>>>((int)nseg, Na, N, work, sym ? 1 : 0, C,
-                                                                             ldc);
+  k_oz_gram_reduce<<<(unsigned)(((int64_t)Na * N + 255) / 256), 256, 0, st>>>((int)nseg, Na, N, work, sym ? 1 : 0,
+                                                                             accumulate ? 1 : 0, C, ldc);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return 0;
 }

@@ -127,24 +127,37 @@ void trial_integrals(const TrialCtx& c, const double* pts, size_t np, double I[3
   I[0] = I[1] = I[2] = 0.0;
   const Setup& s = *c.s;
   const int na = (int)s.atom_Z.size();
-  for (size_t q = 0; q < np; ++q) {
-    const double* p = pts + 4 * q;
-    double f3 = 0.0, f4 = 0.0;
-    for (int i = 0; i < c.k; ++i) {
-      double v, g[3];
-      eval_func(s.funcs[c.fl[i]], p[0], p[1], p[2], &v, g);
-      f3 += v * v;
-      f4 += g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  constexpr int L = 8;   // points per pass of the nuclear sum (independent lanes, each in atom order)
+  for (size_t q0 = 0; q0 < np; q0 += L) {
+    const int nl = (int)std::min<size_t>(L, np - q0);
+    double px[L], py[L], pz[L], vn[L];
+    for (int t = 0; t < L; ++t) {
+      const double* p = pts + 4 * (q0 + std::min(t, nl - 1));
+      px[t] = p[0];
+      py[t] = p[1];
+      pz[t] = p[2];
+      vn[t] = 0.0;
     }
-    double vn = 0.0;
     for (int a = 0; a < na; ++a) {
-      double dx = p[0] - s.atom_xyz[3 * a], dy = p[1] - s.atom_xyz[3 * a + 1],
-             dz = p[2] - s.atom_xyz[3 * a + 2];
-      vn += s.atom_Z[a] / sqrt(dx * dx + dy * dy + dz * dz);
+      const double ax = s.atom_xyz[3 * a], ay = s.atom_xyz[3 * a + 1], az = s.atom_xyz[3 * a + 2], Za = s.atom_Z[a];
+      for (int t = 0; t < L; ++t) {
+        const double dx = px[t] - ax, dy = py[t] - ay, dz = pz[t] - az;
+        vn[t] += Za / sqrt(dx * dx + dy * dy + dz * dz);
+      }
     }
-    I[0] += p[3] * f3;
-    I[1] += p[3] * f4;
-    I[2] += p[3] * vn * f3;
+    for (int t = 0; t < nl; ++t) {
+      const double* p = pts + 4 * (q0 + t);
+      double f3 = 0.0, f4 = 0.0;
+      for (int i = 0; i < c.k; ++i) {
+        double v, g[3];
+        eval_func(s.funcs[c.fl[i]], p[0], p[1], p[2], &v, g);
+        f3 += v * v;
+        f4 += g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+      }
+      I[0] += p[3] * f3;
+      I[1] += p[3] * f4;
+      I[2] += p[3] * vn[t] * f3;
+    }
   }
 }
 
@@ -156,8 +169,10 @@ void push_box(const Box& b, std::vector<double>& boxes) {
   for (int d = 0; d < 3; ++d) boxes.push_back(b.hi[d]);
 }
 
+// Ip_known: the trial integrals over this box's own points when the caller
+// already formed them (a child's integrals of its parent's test), else NULL.
 void adaptive(const TrialCtx& c, const Box& b, int depth, int max_depth, double tau,
-              std::vector<double>& out, std::vector<double>& boxes) {
+              std::vector<double>& out, std::vector<double>& boxes, const double* Ip_known = nullptr) {
   std::vector<double> parent;
   gauss_box(b, c.n, c.gx, c.gw, parent);
   if (depth >= max_depth) {
@@ -166,11 +181,16 @@ void adaptive(const TrialCtx& c, const Box& b, int depth, int max_depth, double 
     return;
   }
   double Ip[3];
-  trial_integrals(c, parent.data(), parent.size() / 4, Ip);
+  if (Ip_known) {
+    for (int d = 0; d < 3; ++d) Ip[d] = Ip_known[d];
+  } else {
+    trial_integrals(c, parent.data(), parent.size() / 4, Ip);
+  }
   double mid[3];
   for (int d = 0; d < 3; ++d) mid[d] = 0.5 * (b.lo[d] + b.hi[d]);
   Box kids[8];
   double Ic[3] = {0.0, 0.0, 0.0};
+  double Ik_all[8][3];
   for (int k = 0; k < 8; ++k) {
     int bit[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
     for (int d = 0; d < 3; ++d) {
@@ -179,7 +199,7 @@ void adaptive(const TrialCtx& c, const Box& b, int depth, int max_depth, double 
     }
     std::vector<double> cp;
     gauss_box(kids[k], c.n, c.gx, c.gw, cp);
-    double Ik[3];
+    double* Ik = Ik_all[k];
     trial_integrals(c, cp.data(), cp.size() / 4, Ik);
     for (int d = 0; d < 3; ++d) Ic[d] += Ik[d];
   }
@@ -190,7 +210,7 @@ void adaptive(const TrialCtx& c, const Box& b, int depth, int max_depth, double 
     push_box(b, boxes);
     return;
   }
-  for (int k = 0; k < 8; ++k) adaptive(c, kids[k], depth + 1, max_depth, tau, out, boxes);
+  for (int k = 0; k < 8; ++k) adaptive(c, kids[k], depth + 1, max_depth, tau, out, boxes, Ik_all[k]);
 }
 
 }  // namespace

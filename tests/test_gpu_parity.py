@@ -304,3 +304,191 @@ def test_fp64_tensor_engine_gram(tiny_pair, which, N):
     finally:
         G.set_fp64_engine("dfma")
     np.testing.assert_allclose(e, e_ref, rtol=1e-10, atol=1e-10 * np.abs(e_ref).max())
+
+
+# --- persistent tensor-core kernels with several work items per CTA --------------
+# The tcgen05 kernels are persistent (one CTA per SM walks the work items).  On
+# the small meshes above every CTA gets one item; with the grid capped, each CTA
+# walks many items, so the double TMEM accumulator alternation, the mbarrier
+# phase flips across items and the stage ring wrap-around all run under the
+# oracle comparison.
+
+@pytest.fixture(scope="module")
+def mid_pair():
+    from oracle.operators import Discretisation
+    s = W.tiny(seed=11, cells=(4, 4, 4), max_depth=3)   # 64 cells, 8 per parity colour
+    return Discretisation(s), gpu_system(s)
+
+
+def _mid_bounds(d, X):
+    from oracle.chfsi import cholqr, lanczos_upper_bound, rayleigh_ritz
+    Q, _ = cholqr(X)
+    eps, _, _ = rayleigh_ritz(d.apply_H_assembled, d.apply_M_assembled, Q)
+    b = lanczos_upper_bound(d.apply_Htilde, d.apply_M_assembled, W.lanczos_start(d.system), 10)
+    return eps.max(), 1.05 * b, eps.min()
+
+
+@pytest.mark.parametrize("prec,tols", [("tf32", [(1, 6e-3), (7, 4e-2)]), ("tf32x3", [(1, 1e-5), (7, 5e-5)])])
+def test_tensor_core_cells_many_items_per_cta(mid_pair, prec, tols):
+    """k_cell_tc3 capped at 2 CTAs: N = 300 is two 160-column tiles, so each CTA
+    walks 8 (cell, tile) items per colour launch; the capped and uncapped
+    launches agree bit for bit (the items are independent and the scatter order
+    per colour is fixed).  Against the oracle: the 3-term split keeps the
+    one-item bounds; one TF32 pass errs by about 2 u_tf32 = 2^-10 times the
+    cancellation factor max(|H||Y|) / max|H Y| of the cell products, which is larger on this
+    mesh (its cells are twice the size of the 2x3x2 case's): 3.3e-3 measured
+    for one degree, bounds 6e-3 and 4e-2."""
+    from oracle.chfsi import chebyshev_filter_scaled
+    d, G = mid_pair
+    N = 300
+    X = W.random_block(d.system, N, seed=77)
+    a, b, a0 = _mid_bounds(d, W.initial_block(d.system, 20, seed=1))
+    for m, tol in tols:
+        ref = chebyshev_filter_scaled(d.apply_Htilde, X, m, a, b, a0)
+        G.set_grid_cap(2)
+        try:
+            Xd = to_dev(X)
+            G.chfsi_step(Xd, m, a, b, a0, precision=prec, fp64_tail=0)
+        finally:
+            G.set_grid_cap(0)
+        err = rel_err(Xd, ref)
+        assert err < tol, (m, err)
+        Xu = to_dev(X)
+        G.chfsi_step(Xu, m, a, b, a0, precision=prec, fp64_tail=0)
+        assert torch.equal(Xd, Xu)
+
+
+def test_fp64_engine_many_items_per_cta(mid_pair):
+    """k_oz on one CTA: CELL mode (N = 135: 8 cells x 2 column tiles per colour),
+    ROWS (the Rayleigh-Ritz rotations: 39 row tiles x 2 column tiles) and GRAM
+    (the Gram and projection products: 3 tile pairs, 20 groups of 256 rows each)
+    all walk many items on that one CTA.  H apply and a degree-7 FP64 filter
+    against the oracle, Ritz values against the oracle's Cholesky-QR + RR."""
+    from oracle.chfsi import chebyshev_filter_scaled, cholqr, rayleigh_ritz
+    d, G = mid_pair
+    N = 135
+    X = W.random_block(d.system, N, seed=78)
+    a, b, a0 = _mid_bounds(d, W.initial_block(d.system, 20, seed=1))
+    ref_f = chebyshev_filter_scaled(d.apply_Htilde, X, 7, a, b, a0)
+    Q, _ = cholqr(X)
+    eps_ref, _, _ = rayleigh_ritz(d.apply_H_assembled, d.apply_M_assembled, Q)
+    G.set_fp64_engine("tensor")
+    G.set_grid_cap(1)
+    try:
+        assert rel_err(G.apply_H(to_dev(X)), d.apply_H_assembled(X)) < 1e-10
+        Xd = to_dev(X)
+        G.chfsi_step(Xd, 7, a, b, a0, precision="fp64")
+        assert rel_err(Xd, ref_f) < 1e-8
+        eps, _ = G.rayleigh_ritz(to_dev(X))
+    finally:
+        G.set_grid_cap(0)
+        G.set_fp64_engine("dfma")
+    np.testing.assert_allclose(eps, eps_ref, atol=1e-9, rtol=1e-10)
+
+
+def test_in_place_products_rejected(tiny_pair):
+    import ctypes as C
+    d, G = tiny_pair
+    X = to_dev(W.random_block(d.system, 4, seed=5))
+    keep = X.clone()
+    for fn in (G.L.efe_apply_H, G.L.efe_apply_M):
+        rc = fn(G.h, C.c_void_p(X.data_ptr()), X.stride(0), 4, C.c_void_p(X.data_ptr()), X.stride(0), G._stream())
+        assert rc == 1
+    # overlapping by one column
+    big = to_dev(np.zeros((X.shape[0], 9)))
+    rc = G.L.efe_apply_M(G.h, C.c_void_p(big.data_ptr()), 9, 5, C.c_void_p(big[:, 4:].data_ptr()), 9, G._stream())
+    assert rc == 1
+    torch.cuda.synchronize()
+    assert torch.equal(X, keep)
+    # (M^E)^-1 works on a copy: in place is allowed
+    Y = G.apply_Minv(X, X.clone())
+    Z = X.clone()
+    G.apply_Minv(Z, Z)
+    assert torch.equal(Y, Z)
+
+
+# --- the large-N code paths (280-atom cluster, N ~ 2200), driven on small inputs --------
+# Rayleigh-Ritz in column panels, the FP64 engine's tall products with K > 144
+# (several exact accumulation groups) and with operand images in row panels,
+# the blocked multi-CTA Cholesky / triangular inverse / block Jacobi
+# eigensolver, and the FP32 recurrence slots living inside the FP64 workspace
+# (N a multiple of 8) -- each forced through EFE_OPT_* on the tiny mesh and
+# compared with the oracle.
+
+def _rr_ref(d, X):
+    from oracle.chfsi import cholqr, rayleigh_ritz
+    Q, _ = cholqr(X)
+    return rayleigh_ritz(d.apply_H_assembled, d.apply_M_assembled, Q)
+
+
+@pytest.mark.parametrize("engine", ["dfma", "tensor"])
+@pytest.mark.parametrize("N", [40, 150])
+def test_rayleigh_ritz_panels_and_blocked_dense(tiny_pair, engine, N):
+    """Forced: two column panels, blocked dense kernels, and (tensor engine)
+    image panels of 256 rows, so the Gram products accumulate over K panels and
+    the rotations run in row panels; N = 150 > 144 takes two K groups in the
+    tall products.  Ritz values, residuals and M-orthonormality against the
+    oracle's Cholesky-QR + Rayleigh-Ritz."""
+    d, G = tiny_pair
+    X = W.initial_block(d.system, N, seed=4)
+    eps_ref, _, res_ref = _rr_ref(d, X)
+    G.set_fp64_engine(engine)
+    G.set_option("rr_panels", 1)
+    G.set_option("dense_blocked", 1)
+    G.set_option("image_rows", 256)
+    try:
+        Xd = to_dev(X)
+        eps, res = G.rayleigh_ritz(Xd)
+        MX = G.apply_M(Xd)
+    finally:
+        G.set_option("image_rows", 0)
+        G.set_option("dense_blocked", 0)
+        G.set_option("rr_panels", 0)
+        G.set_fp64_engine("dfma")
+    np.testing.assert_allclose(eps, eps_ref, atol=1e-9, rtol=1e-10)
+    np.testing.assert_allclose(res, res_ref, atol=1e-8, rtol=1e-6)
+    gram = (Xd.T @ MX).cpu().numpy()
+    np.testing.assert_allclose(gram, np.eye(N), atol=1e-10)
+
+
+def test_tall_products_long_K_match_dfma(tiny_pair):
+    """The FP64 engine's tall product with K = N = 300 (three exact groups of
+    144, 144 and 12) and 256-row image panels gives the DFMA path's Ritz values
+    and vectors to FP64 rounding."""
+    d, G = tiny_pair
+    N = 300
+    X = to_dev(W.random_block(d.system, N, seed=93))
+    G.set_fp64_engine("dfma")
+    Xa = X.clone()
+    e_ref, _ = G.rayleigh_ritz(Xa)
+    G.set_fp64_engine("tensor")
+    G.set_option("image_rows", 256)
+    try:
+        Xb = X.clone()
+        e, _ = G.rayleigh_ritz(Xb)
+    finally:
+        G.set_option("image_rows", 0)
+        G.set_fp64_engine("dfma")
+    np.testing.assert_allclose(e, e_ref, rtol=1e-10, atol=1e-10 * np.abs(e_ref).max())
+    eps_ref, _, _ = _rr_ref(d, W.random_block(d.system, N, seed=93))
+    np.testing.assert_allclose(e, eps_ref, rtol=1e-9, atol=1e-9 * np.abs(eps_ref).max())
+
+
+@pytest.mark.parametrize("prec,N,tail,tol", [("tf32x3", 64, 2, 5e-5), ("fp32", 16, 0, 2e-5), ("tf32x3", 304, 0, 5e-5)])
+def test_mixed_filter_slots_inside_fp64_workspace(tiny_pair, prec, N, tol, tail):
+    """N a multiple of 8: the FP32 recurrence slots and the cell-product output
+    live inside the FP64 workspace (no padding columns); a degree-7 filter
+    against the oracle at the mixed-mode tolerances, then a Rayleigh-Ritz call
+    (which overwrites that workspace) and the same filter again, bitwise equal."""
+    from oracle.chfsi import chebyshev_filter_scaled
+    d, G = tiny_pair
+    X = W.random_block(d.system, N, seed=70 + N)
+    a, b, a0 = _bounds(d, 10)
+    ref = chebyshev_filter_scaled(d.apply_Htilde, X, 7, a, b, a0)
+    Xd = to_dev(X)
+    G.chfsi_step(Xd, 7, a, b, a0, precision=prec, fp64_tail=tail)
+    assert rel_err(Xd, ref) < tol
+    G.rayleigh_ritz(to_dev(W.random_block(d.system, N, seed=1)))
+    Xe = to_dev(X)
+    G.chfsi_step(Xe, 7, a, b, a0, precision=prec, fp64_tail=tail)
+    assert torch.equal(Xd, Xe)
