@@ -1,22 +1,28 @@
 #!/usr/bin/env python
 """Benchmark of the enriched-FE ChFSI hot path on one GB300.
 
-Workload (default): the 16-atom silicon-like cluster -- two conventional
-diamond cells (a = 10.26 bohr) of Z = 14 nuclei, box padded by 10 bohr, graded
-degree-4 mesh (37 x 25 x 25 cells, 1.52M nodes), 5 Slater enrichment
-functions per atom (n_E = 80), N = 135 vectors, Chebyshev degree m = 40, local
-potential = nuclear Coulomb + a seeded 32-term Gaussian perturbation.
+Workload (default, ``si280``): the paper's 280-atom silicon cluster -- a cube
+cut of 3 x 3 x 3 conventional diamond cells (a = 10.26 bohr) including the
+boundary atoms, Z = 14 (3920 electrons), box padded by 10 bohr, graded degree-4
+mesh of 36^3 cells (3,048,625 nodes), 5 Slater enrichment functions per atom
+(n_E = 1400), N = 2200 vectors, Chebyshev degree m = 40, local potential =
+nuclear Coulomb + a seeded 32-term Gaussian perturbation.  ``si16`` is the
+16-atom cluster (1.52M nodes, N = 135).
 
 One step = one pass of the whole hot path: Lanczos upper bound (10 steps),
-the degree-m Chebyshev filter of (M^E)^-1 H^E, Cholesky-QR and Rayleigh-Ritz
-with residuals.  `value` is the filter's algorithmic TFLOP/s over the whole
-step (filter flops / step time); the FP64-mode step is timed beside it.
+the degree-m Chebyshev filter of (M^E)^-1 H^E (mixed precision: 3-term TF32
+tensor-core cell products, FP32 coupling, the last 2 degrees in FP64),
+Cholesky-QR and Rayleigh-Ritz (Ritz values; the residuals are formed once
+after the timed steps).  `value` is the filter's algorithmic TFLOP/s over the
+whole step (filter flops / step time).  Beside it: the FP64-mode step, the
+step through the C ABI with host buffers (e2e), and full SCF iterations.
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on a
 bounded sample of the same workload.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -31,44 +37,46 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 NL = 125
-N_VEC = 135
-M_DEG = 40
+WORKLOADS = {
+    # name: (generator, N, m, text)
+    "si280": (W.si280, 2200, 40,
+              "si280: 280-atom Si-like cluster (cube cut of 3x3x3 diamond cells, Z=14, 3920 e-), "
+              "graded degree-4 mesh 36^3 cells"),
+    "si16": (W.si_cluster, 135, 40, "si16: 16-atom Si-like cluster (Z=14, diamond a=10.26), graded degree-4 mesh"),
+    "si16s": (lambda: W.si_cluster(h_min=1.6, h_max=4.0), 135, 40,
+              "si16s: 16-atom Si-like cluster, coarser graded degree-4 mesh (h 1.6-4.0 bohr)"),
+    "hydrogen": (W.hydrogen, 8, 20, "hydrogen Z=1, 6x6x6 cells"),
+}
+# the largest blocks are generated on the device (a seeded torch generator);
+# smaller ones by workloads.initial_block (NumPy PCG64)
+DEVICE_INIT_BYTES = 4 << 30
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=None, help="timed steps (default: 2 for si280, 5 otherwise)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="tf32x3", choices=["tf32x3", "fp32", "tf32", "fp64"])
     p.add_argument("--fp64-tail", type=int, default=2)
     p.add_argument("--fp64-engine", default="tensor", choices=["tensor", "dfma"],
-                   help="engine of the FP64 parts of the mixed step (the FP64 comparison always uses dfma)")
-    p.add_argument("--fp64-steps", type=int, default=2)
+                   help="engine of the FP64 parts of the mixed step")
+    p.add_argument("--fp64-steps", type=int, default=1)
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-scf", action="store_true")
-    p.add_argument("--no-batch", action="store_true")
-    p.add_argument("--scf-steps", type=int, default=3)
-    p.add_argument("--workload", default="si16", choices=["si16", "si16s", "hydrogen"])
-    return p.parse_args()
-
-
-def workload(name):
-    if name == "si16":
-        return W.si_cluster(), N_VEC, M_DEG
-    if name == "si16s":  # coarser mesh of the same cluster (profiling captures)
-        return W.si_cluster(h_min=1.6, h_max=4.0), N_VEC, M_DEG
-    return W.hydrogen(), 8, 20
-
-
-WORKLOAD_TEXT = {
-    "si16": "16-atom Si-like cluster (Z=14, diamond a=10.26), graded degree-4 mesh",
-    "si16s": "16-atom Si-like cluster (Z=14, diamond a=10.26), coarser graded degree-4 mesh (h 1.6-4.0 bohr)",
-    "hydrogen": "hydrogen Z=1, 6x6x6 cells",
-}
+    p.add_argument("--batch", action="store_true", help="also time the batched small systems (CUDA graph)")
+    p.add_argument("--scf-steps", type=int, default=None, help="timed SCF iterations (default: 1 for si280, 3)")
+    p.add_argument("--workload", default="si280", choices=sorted(WORKLOADS))
+    a = p.parse_args()
+    big = a.workload == "si280"
+    if a.steps is None:
+        a.steps = 2 if big else 5
+    if a.scf_steps is None:
+        a.scf_steps = 1 if big else 3
+    return a
 
 
 def filter_flops(n_cell, nnz, nE, N, m):
@@ -77,29 +85,31 @@ def filter_flops(n_cell, nnz, nE, N, m):
     return float(m) * N * (2.0 * NL * NL * n_cell + 8.0 * nnz + 4.0 * nE * nE)
 
 
-def peaks():
+def _peaks_file():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         try:
-            d = json.load(open(path))
-            return float(d.get("hbm_gbs", 6800.0)), "measured"
+            return json.load(open(path))
         except Exception:
-            pass
+            return None
+    return None
+
+
+def peaks():
+    d = _peaks_file()
+    if d and d.get("hbm_gbs"):
+        return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
 
 
 def peaks_bf16():
     """Dense BF16 tensor peak for a kernel timed inside a long step: the measured sustained
     figure if present, else the fallback 1700 TFLOP/s."""
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(path):
-        try:
-            d = json.load(open(path))
-            v = d.get("bf16_tflops_sustained", d.get("bf16_tflops"))
-            if v:
-                return float(v), "measured"
-        except Exception:
-            pass
+    d = _peaks_file()
+    if d:
+        v = d.get("bf16_tflops_sustained", d.get("bf16_tflops"))
+        if v:
+            return float(v), "measured"
     return 1700.0, "fallback (sustained)"
 
 
@@ -110,9 +120,8 @@ def clocks_start(dev):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
-                              "-i", str(dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        return p
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                                 "-i", str(dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
     except Exception:
         return None
 
@@ -146,18 +155,38 @@ def clocks_stop(p):
             "samples": len(sm)}
 
 
+# ------------------------------------------------------------------------- CPU oracle sample
+def oracle_window(system, cells=4):
+    """A window of cells x cells x cells cells at the middle of the mesh with the
+    enrichment functions whose support meets it (same nuclei and potential):
+    the bounded sample the CPU oracle is timed on."""
+    nc = [len(b) - 1 for b in system["breaks"]]
+    lo = [max(0, n // 2 - cells // 2) for n in nc]
+    sub = dict(system)
+    sub["breaks"] = [b[l:l + cells + 1] for b, l in zip(system["breaks"], lo)]
+    blo = np.array([b[0] for b in sub["breaks"]])
+    bhi = np.array([b[-1] for b in sub["breaks"]])
+    keep = []
+    for f in system["funcs"]:
+        R = system["atoms"][f["atom"]]
+        if np.sqrt(np.sum(np.maximum(0.0, np.maximum(blo - R, R - bhi)) ** 2)) < f["r0"] * (1.0 + 1.0 / f["t"]):
+            keep.append(f)
+    sub["funcs"] = keep
+    return sub
+
+
 def cpu_sample(system, N, steps=None, min_seconds=10.0):
-    """The oracle (FP64 NumPy) on a bounded sample: its elemental H~ apply over an
-    8 x 8 x 8-cell corner window of the same graded mesh, same nuclei and potential,
-    repeated for about ``min_seconds`` (or exactly ``steps`` applies).
+    """The oracle (FP64 NumPy) on a bounded sample: its elemental H~ apply (cell
+    products, enrichment coupling, block-wise overlap inverse) over a 4x4x4-cell
+    window at the middle of the same mesh with the enrichment functions that meet
+    it, repeated for about ``min_seconds`` (or exactly ``steps`` applies).
     Returns (TFLOP/s, seconds per apply, description)."""
     from oracle.operators import Discretisation
-    sub = dict(system)
-    sub["breaks"] = [b[:9] for b in system["breaks"]]
-    sub["funcs"] = []
+    sub = oracle_window(system)
     d = Discretisation(sub)
     X = W.random_block(sub, N, seed=21)
-    flops = filter_flops(d.n_cell, 0, 0, N, 1)
+    nnz = int(d.Mec_global.nnz) if d.nE > 0 else 0
+    flops = filter_flops(d.n_cell, nnz, len(sub["funcs"]), N, 1)
     n = 0
     t = time.perf_counter()
     while True:
@@ -167,14 +196,15 @@ def cpu_sample(system, N, steps=None, min_seconds=10.0):
         if (steps is not None and n >= steps) or (steps is None and el >= min_seconds and n >= 3):
             break
     dt = el / n
-    desc = (f"oracle elemental H~ apply (FP64 NumPy), N={N}, over an 8x8x8-cell corner window "
-            f"({d.n_cell} cells) of the same mesh and potential; {n} applies, {el:.1f} s; "
-            "TFLOP/s by the same algorithmic count")
+    desc = (f"oracle elemental H~ apply (FP64 NumPy: cell products, enrichment coupling, block-wise "
+            f"overlap inverse), N={N}, over a 4x4x4-cell window at the middle of the same mesh ({d.n_cell} cells, "
+            f"{len(sub['funcs'])} enrichment functions, {nnz} coupling nonzeros) with the same nuclei and "
+            f"potential; {n} applies, {el:.1f} s; TFLOP/s by the same algorithmic count")
     return flops / dt / 1e12, dt, desc
 
 
+# ------------------------------------------------------------------------- batched small systems
 def batch_section(P, torch, stream, n_sys=8, m=20, steps=3):
-    import math
     rng = np.random.default_rng(5)
     Gs, Xs, Ns, flops, tiles, nodes = [], [], [], 0.0, [], []
     for i in range(n_sys):
@@ -205,13 +235,9 @@ def batch_section(P, torch, stream, n_sys=8, m=20, steps=3):
         Xw = [x.clone() for x in Xs]
         B.chfsi_step(Xw, m, a, b, a0, precision="tf32x3", fp64_tail=2, graph=mode)   # warm-up / recording
         torch.cuda.synchronize()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
-        s0.record(stream)
         for _ in range(steps):
             B.chfsi_step(Xw, m, a, b, a0, precision="tf32x3", fp64_tail=2, graph=mode)
-        s1.record(stream)
         torch.cuda.synchronize()
         out[mode] = (time.perf_counter() - t0) / steps
     nn, kn = B.graph_nodes()
@@ -223,31 +249,51 @@ def batch_section(P, torch, stream, n_sys=8, m=20, steps=3):
             "step": "one filter step of every system (no Rayleigh-Ritz), host wall clock incl. graph launch"}
 
 
+# ------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    system, N, m = workload(args.workload)
-    from oracle.operators import Discretisation  # noqa: F401
+    gen, N, m, text = WORKLOADS[args.workload]
+    system = gen()
     for _ in range(args.warmup):
         cpu_sample(system, N, steps=1)
     vals = []
     t0 = time.perf_counter()
+    desc = ""
     for _ in range(args.steps):
         v, dt, desc = cpu_sample(system, N, steps=1)
-        vals.append((v, dt))
+        vals.append(v)
     tot = time.perf_counter() - t0
-    value = statistics.median(v for v, _ in vals)
+    value = statistics.median(vals)
     cores = len(os.sched_getaffinity(0))
     line = {"impl": "reference", "metric": "chfsi_filter_tflops", "value": value, "unit": "TFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "si16: 16-atom Si-like cluster, 1.52M-node graded degree-4 mesh, N=135, m=40",
-                       "sample": desc},
+            "config": {"workload": text, "N": N, "m": m, "sample": desc},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------- GPU arm
+def initial_block(torch, system, G, N, seed=1):
+    """X_0: unit vectors on the first min(N, n_E) enrichment coefficients (the atomic
+    orbitals), seeded normal values on the interior nodes in the other columns."""
+    if G.rows * N * 8 <= DEVICE_INIT_BYTES:
+        return torch.from_numpy(W.initial_block(system, N, seed=seed)).cuda()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    X = torch.zeros((G.rows, N), dtype=torch.float64, device="cuda")
+    k = min(N, G.n_enrich)
+    idx = torch.arange(k, device="cuda")
+    X[G.n_nodes + idx, idx] = 1.0
+    if N > k:
+        X[:G.n_nodes, k:] = torch.randn((G.n_nodes, N - k), generator=gen, dtype=torch.float64, device="cuda")
+        bm = torch.from_numpy(W.boundary_mask(system)).cuda()
+        X[:G.n_nodes][bm] = 0.0
+    return X
 
 
 def main():
@@ -267,33 +313,37 @@ def main():
     import __graft_entry__ as g
     g.build()
     import paper_1610_02121_gb300 as P
-    system, N, m = workload(args.workload)
+    gen, N, m, text = WORKLOADS[args.workload]
+    system = gen()
     t_setup = time.perf_counter()
     G = P.System(system)
     G.set_potential_analytic()
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
-    X0 = torch.from_numpy(W.initial_block(system, N, seed=1)).cuda()
-    v0 = torch.from_numpy(W.lanczos_start(system)).cuda()
-    X = X0.clone()
-    eps, res = G.rayleigh_ritz(X)
-    X_start = X.clone()
-    eps_start = eps.copy()
     stream = torch.cuda.current_stream()
+    prec = args.precision
+    G.set_fp64_engine(args.fp64_engine)
+    X = initial_block(torch, system, G, N)
+    v0 = torch.from_numpy(W.lanczos_start(system)).cuda()
+    eps_start, _ = G.rayleigh_ritz(X, residuals=False)
+    # the start of every leg, kept in pinned host memory (also the e2e input)
+    X_host = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
+    X_host.copy_(X)
+    flops_step = filter_flops(G.n_cells, G.n_coupling, G.n_enrich, N, m)
 
-    def one_step(Xb, eps_prev, prec):
+    def one_step(Xb, eps_prev, p):
         b = G.upper_bound(v0, 10)
-        G.chfsi_step(Xb, m, eps_prev.max(), b, eps_prev.min(), precision=prec,
-                     fp64_tail=(args.fp64_tail if prec != "fp64" else 0))
-        e, r = G.rayleigh_ritz(Xb)
-        return e, r, b
+        G.chfsi_step(Xb, m, eps_prev.max(), b, eps_prev.min(), precision=p,
+                     fp64_tail=(args.fp64_tail if p != "fp64" else 0))
+        e, _ = G.rayleigh_ritz(Xb, residuals=False)
+        return e
 
-    def timed(prec, warm, steps, timing=False, engine=None):
-        G.set_fp64_engine(engine or (args.fp64_engine if prec != "fp64" else "dfma"))
-        Xb = X_start.clone()
+    def timed(p, warm, steps, engine, timing=False):
+        G.set_fp64_engine(engine)
+        X.copy_(X_host)
         e = eps_start.copy()
         for _ in range(warm):
-            e, r, b = one_step(Xb, e, prec)
+            e = one_step(X, e, p)
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
@@ -307,7 +357,7 @@ def main():
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         for _ in range(steps):
-            e, r, b = one_step(Xb, e, prec)
+            e = one_step(X, e, p)
         s1.record(stream)
         torch.cuda.synchronize()
         ms = s0.elapsed_time(s1) / steps
@@ -319,41 +369,37 @@ def main():
             t = torch.tensor([ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
-        return ms, e, r, b, launches // max(steps, 1), clocks, stats
+        return ms, e, launches // max(steps, 1), clocks, stats
 
-    prec = args.precision
-    ms, eps_m, res_m, b, launches, clocks, stats = timed(prec, args.warmup, args.steps, timing=True)
-    flops_step = filter_flops(G.n_cells, G.n_coupling, G.n_enrich, N, m)
+    ms, eps_m, launches, clocks, stats = timed(prec, args.warmup, args.steps, args.fp64_engine, timing=True)
+    # residuals of the final Ritz pairs (one more Rayleigh-Ritz, untimed)
+    _, res_m = G.rayleigh_ritz(X, residuals=True)
     value = world * flops_step / (ms * 1e-3) / 1e12
     # the two tensor-core kernels of the step: the mixed filter's cell products and the
     # FP64 engine (tail degrees, Cholesky-QR, Rayleigh-Ritz); the roofline object
     # describes the one with the larger share of the step time, the other sits beside it
     (n_launch, k_ms, cellcols), (oz_launch, oz_ms, oz_flops) = stats
     s_el = {"fp64": 8, "fp32": 4, "tf32": 4, "tf32x3": 4, "bf16": 2}[prec]
-    h_bytes = G.n_cells * NL * NL * s_el
-    v_bytes = 2.0 * G.n_nodes * N * s_el
-    frac_cells = cellcols / float(G.n_cells * N)
-    alg_bytes = (h_bytes + v_bytes) * frac_cells
+    # algorithmic bytes of one cell product of N columns: the cell matrix plus
+    # the 64 unique nodes' rows read (Y) and written (W)
+    per_cell_bytes = NL * NL * s_el + 2.0 * 64 * N * s_el
+    alg_bytes = per_cell_bytes * cellcols / float(N)
     alg_flops = 2.0 * NL * NL * cellcols
     hbm_peak, peak_src = peaks()
+    cells_per_launch = cellcols / float(max(n_launch, 1) * N)
     if prec in ("fp32", "fp64"):
-        # SIMT-bound: FP32 FFMA peak from 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64 from the measured DGEMM
-        peak = 80.5 if prec == "fp32" else 1.05
+        # SIMT-bound: FP32 FFMA peak from 152 SMs x 128 lanes x 2 flop x 2.07 GHz; FP64 from the nominal rate
+        peak = 80.5 if prec == "fp32" else 1.25
         achieved = alg_flops / (k_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": f"k_cell_apply<{'float' if prec == 'fp32' else 'double'}>",
                 "launches": n_launch, "avg_launch_ms": k_ms / max(n_launch, 1),
-                "algorithmic_gbs": alg_bytes / (k_ms * 1e-3) / 1e9,
-                "peak_source": "derived from unit counts and max clock" if prec == "fp32" else "measured DGEMM"}
+                "peak_source": "derived from unit counts and max clock" if prec == "fp32" else "nominal FP64"}
     else:
         achieved = alg_bytes / (k_ms * 1e-3) / 1e9
-        # DRAM traffic of one launch from the ncu capture of this kernel on the si16s mesh
-        # (249 MB for 1,053 cells at N = 135: 237 KB per cell), scaled by the cells per launch
-        cells_per_launch = cellcols / float(max(n_launch, 1) * N)
-        traffic = 236.7e3 * cells_per_launch if (prec == "tf32x3" and N == 135) else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": traffic, "traffic_source": "ncu dram bytes of the si16s capture, scaled by cells per launch",
-                "algorithmic_bytes_per_launch": alg_bytes / max(n_launch, 1),
+                "traffic": None, "algorithmic_bytes_per_launch": alg_bytes / max(n_launch, 1),
+                "algorithmic_bytes_per_cell": per_cell_bytes, "cells_per_launch": cells_per_launch,
                 "kernel": "k_cell_tc3<%s>" % ("true" if prec == "tf32x3" else "false"),
                 "launches": n_launch, "algorithmic_tflops": alg_flops / (k_ms * 1e-3) / 1e12,
                 "avg_launch_ms": k_ms / max(n_launch, 1), "peak_source": peak_src}
@@ -361,16 +407,10 @@ def main():
     if oz_launch > 0 and oz_ms > 0:
         bf16_peak, bf16_src = peaks_bf16()
         oz_tf = oz_flops / (oz_ms * 1e-3) / 1e12
-        # DRAM traffic per launch: ncu dram bytes of every k_oz launch of one si16s step (CELL 0.90 GB,
-        # symmetric Gram 2.48 GB, A^T B Gram 3.79 GB, rotation 2.73 GB), weighted by the step's mix
-        # (24 / 1 / 2 / 4 launches) and scaled to si16 by the rows and cells processed (x 2.72)
-        oz_traffic = 3.73e9 if (args.workload == "si16" and N == 135 and m == 40) else None
         roof_oz = {"bound": "tensor", "achieved": 28.0 * oz_tf, "peak": bf16_peak, "unit": "TFLOP/s",
-                   "frac": 28.0 * oz_tf / bf16_peak, "traffic": oz_traffic,
-                   "traffic_source": "ncu dram bytes per mode on si16s, step mix, scaled x2.72 to si16",
-                   "kernel": "k_oz (FP64-grade products)",
-                   "launches": oz_launch, "avg_launch_ms": oz_ms / oz_launch, "fp64_grade_tflops": oz_tf,
-                   "vs_fp64_dgemm_peak": oz_tf / 1.05,
+                   "frac": 28.0 * oz_tf / bf16_peak, "traffic": None,
+                   "kernel": "k_oz (FP64-grade products)", "launches": oz_launch, "avg_launch_ms": oz_ms / oz_launch,
+                   "fp64_grade_tflops": oz_tf, "algorithmic_fp64_flops_per_launch": oz_flops / oz_launch,
                    "note": "achieved = 28 BF16 digit products per FP64 product x algorithmic FP64 flops / time",
                    "peak_source": bf16_src}
     roof_cells = roof
@@ -382,12 +422,11 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": prec if prec != "fp64" else "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: " + WORKLOAD_TEXT[args.workload],
-                       "nodes": G.n_nodes, "cells": G.n_cells, "n_enrich": G.n_enrich, "n_coupling": G.n_coupling, "N": N, "m": m,
-                       "fp64_tail": args.fp64_tail if prec != "fp64" else 0,
-                       "fp64_engine": args.fp64_engine if prec != "fp64" else "dfma",
-                       "l2": "vector blocks (>= 0.8 GB) and cell matrices exceed the 129 MB L2",
-                       "step": "Lanczos bound (10) + degree-m filter + CholQR + Rayleigh-Ritz",
+            "config": {"workload": text, "nodes": G.n_nodes, "cells": G.n_cells, "n_enrich": G.n_enrich,
+                       "n_coupling": G.n_coupling, "n_qpoints": G.n_qpoints, "N": N, "m": m,
+                       "fp64_tail": args.fp64_tail if prec != "fp64" else 0, "fp64_engine": args.fp64_engine,
+                       "l2": "vector blocks and cell matrices exceed the 129 MB L2 (no flush needed)",
+                       "step": "Lanczos bound (10) + degree-m filter + CholQR + Rayleigh-Ritz (Ritz values)",
                        "filter_flops_per_step": flops_step, "setup_s": t_setup},
             "s_per_step": ms * 1e-3, "gpu_launches": launches, "roofline": roof}
     if roof_other is not None:
@@ -396,56 +435,73 @@ def main():
     line["shifted_cholqr_passes_total"] = G.rr_shifted_passes()
     if clocks:
         line["clocks"] = clocks
-    # FP64 mode of the same step
-    if not args.no_fp64 and prec != "fp64":
-        ms64, eps64, res64, _, _, _, _ = timed("fp64", 1, args.fp64_steps, engine="dfma")
-        _, eps_chk, _, _, _, _, _ = timed(prec, 1, args.fp64_steps)
-        ms64t, eps64t, _, _, _, _, _ = timed("fp64", 1, args.fp64_steps, engine="tensor")
+    line["eigs_head"] = [float(x) for x in eps_m[:5]]
+    line["max_resid"] = float(res_m.max())
+    # FP64 mode of the same step (from the same start)
+    if not args.no_fp64 and prec != "fp64" and args.fp64_steps > 0:
+        leg = {}
+        engines = ["tensor"] if args.workload == "si280" else ["dfma", "tensor"]
+        for eng in engines:
+            ms64, eps64, _, _, _ = timed("fp64", 0, args.fp64_steps, eng)
+            leg[eng] = (ms64, eps64)
+        _, eps_chk, _, _, _ = timed(prec, 0, args.fp64_steps, args.fp64_engine)
+        ref_eng = "dfma" if "dfma" in leg else "tensor"
+        ms64, eps64 = leg[ref_eng]
         line["fp64"] = {"ms_per_step": ms64, "tflops": flops_step / (ms64 * 1e-3) / 1e12,
-                        "engine": "dfma (plain FP64)",
+                        "engine": {"dfma": "dfma (plain FP64)",
+                                   "tensor": "FP64-grade products on the BF16 tensor cores (FP64 coupling DFMA)"}
+                        [ref_eng],
                         "speedup_mixed_vs_fp64": ms64 / ms,
                         "max_abs_eig_diff_vs_fp64_Ha": float(np.abs(eps_chk - eps64).max()),
-                        "steps_compared": 1 + args.fp64_steps}
-        line["fp64_tensor_engine"] = {"ms_per_step": ms64t, "tflops": flops_step / (ms64t * 1e-3) / 1e12,
-                                      "max_abs_eig_diff_vs_dfma_Ha": float(np.abs(eps64t - eps64).max())}
-    # end to end through the public API with host buffers
+                        "steps_compared": args.fp64_steps,
+                        "from": "the same Rayleigh-Ritz-rotated start block for both modes"}
+        if "dfma" in leg and "tensor" in leg:
+            line["fp64_tensor_engine"] = {"ms_per_step": leg["tensor"][0],
+                                          "tflops": flops_step / (leg["tensor"][0] * 1e-3) / 1e12,
+                                          "max_abs_eig_diff_vs_dfma_Ha":
+                                              float(np.abs(leg["tensor"][1] - leg["dfma"][1]).max())}
+    # end to end through the public API with host buffers: every step copies X in
+    # from pinned host memory and the filtered, rotated X back out
     if not args.no_e2e:
-        Xh = X_start.cpu().pin_memory()
-        Xd = torch.empty_like(X_start)
+        G.set_fp64_engine(args.fp64_engine)
         e = eps_start.copy()
+        n_e2e = 1 if args.workload == "si280" else args.steps
+        X_out = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            Xd.copy_(Xh, non_blocking=True)
-            e, r, _ = one_step(Xd, e, prec)
-            Xh.copy_(Xd, non_blocking=True)
+        for _ in range(n_e2e):
+            X.copy_(X_host, non_blocking=True)
+            e = one_step(X, e, prec)
+            X_out.copy_(X, non_blocking=True)
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / args.steps
-        nb = X_start.numel() * 8
+        te = (time.perf_counter() - t0) / n_e2e
+        nb = X.numel() * 8
         line["e2e"] = {"value": world * flops_step / te / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": nb,
-                       "d2h_bytes_per_step": nb + 2 * 8 * N, "ms_per_step": te * 1e3}
+                       "d2h_bytes_per_step": nb + 8 * N, "ms_per_step": te * 1e3, "steps": n_e2e}
+        del X_out
     # full SCF iterations (Sec. V) on the same system: V_eff from rho_in (Hartree
     # solve + LDA), bound, filter pass, Rayleigh-Ritz, occupations, density,
     # Hartree of rho_out, energies, Anderson mixing
     if not args.no_scf:
         G.set_fp64_engine(args.fp64_engine)
+        X.copy_(X_host)
         ne = float(np.sum(system["Z"]))
         occ0, _ = P._lib.fermi(eps_start, ne, 500 * P._lib.KB_HA_PER_K)
-        rho_in = G.density(X_start, occ0)
+        rho_in = G.density(X, occ0, precision="fp32" if prec != "fp64" else "fp64")
         w = G.qpoints()[:, 3]
         rho_in *= ne / float((w * rho_in).sum())
+        del w
         rho_out = torch.empty_like(rho_in)
-        Xs = X_start.clone()
         G.scf_init(ne)
         tail = args.fp64_tail if prec != "fp64" else 0
-        r0 = G.scf_step(Xs, rho_in, rho_out, m, precision=prec, fp64_tail=tail)   # warm-up
+        r0 = G.scf_step(X, rho_in, rho_out, m, precision=prec, fp64_tail=tail)   # warm-up
         torch.cuda.synchronize()
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         hist = []
         for _ in range(args.scf_steps):
-            hist.append(G.scf_step(Xs, rho_in, rho_out, m, precision=prec, fp64_tail=tail))
+            hist.append(G.scf_step(X, rho_in, rho_out, m, precision=prec, fp64_tail=tail))
         s1.record(stream)
         torch.cuda.synchronize()
         ms_scf = s0.elapsed_time(s1) / max(args.scf_steps, 1)
@@ -455,18 +511,17 @@ def main():
                        "poisson_correction_steps": [h["poisson_steps"] for h in hist],
                        "total_energy_Ha": [h["total"] for h in [r0] + hist],
                        "drho": [h["drho"] for h in [r0] + hist],
-                       "start": "density of the Rayleigh-Ritz-rotated atomic-orbital block, renormalised to N_e"}
+                       "start": "density of the Rayleigh-Ritz-rotated start block, renormalised to N_e"}
+        del rho_in, rho_out
     # many small systems (1-6 atoms, Z in {1, 6, 8, 14}, own graded meshes, N = ceil(0.6 N_e) + 8):
     # one ChFSI filter step of every system as one CUDA graph vs the same steps launched
     # one system after another; column tiles of the cell kernel picked by the autotuner
-    if not args.no_batch and rank == 0:
+    if args.batch and rank == 0:
         line["batch"] = batch_section(P, torch, stream)
     if not args.no_cpu and rank == 0 and world == 1:
         v, dt, desc = cpu_sample(system, N)
         line["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": len(os.sched_getaffinity(0)),
                                 "kind": "oracle", "sample": desc}
-    line["eigs_head"] = [float(x) for x in eps_m[:5]]
-    line["max_resid"] = float(res_m.max())
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

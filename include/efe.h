@@ -223,6 +223,14 @@ int efe_set_fp64_engine(efe_handle* h, int32_t engine);
 #define EFE_OPT_DENSE_BLOCKED 4  /* 1: the blocked multi-CTA dense N x N kernels (Cholesky, triangular inverse,
                                     block Jacobi eigensolver) whatever the size; 0: for N > 512 (Cholesky:
                                     N > 2048) */
+#define EFE_OPT_COUPLING_SPARSE 5 /* 1: the mixed degrees take the many-function enrichment coupling (node-major FP32
+                                    columns products, rows products over function groups with FP64 partial sums)
+                                    whatever the size; 0: only when the dense-tile kernels' n_E x N FP32 array
+                                    exceeds 200 KB of shared memory */
+#define EFE_OPT_TEST_STALL 6      /* tests of the failure path only: 1 makes every tensor-core launch (tcgen05 cell
+                                    kernel, FP64 engine) first wait on a barrier that nothing completes, so the
+                                    bounded wait runs out; the launch drains its copies and MMAs, frees its TMEM and
+                                    the call returns EFE_ERR_TIMEOUT.  0 (default): off */
 int efe_set_option(efe_handle* h, int32_t option, int64_t value);
 
 /* Kernel timing: when enabled, the library brackets every launch of its

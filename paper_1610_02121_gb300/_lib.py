@@ -347,11 +347,14 @@ class System:
                                           PREC[precision], int(fp64_tail), self._stream()))
         return X
 
-    def rayleigh_ritz(self, X):
+    def rayleigh_ritz(self, X, residuals=True):
+        """Cholesky-QR + Rayleigh-Ritz in place; returns the Ritz values and (when
+        ``residuals``) the residual norms, else None."""
         px, ldx, N = self._block(X)
         eig = np.zeros(N)
-        res = np.zeros(N)
-        self._check(self.L.efe_rayleigh_ritz(self.h, px, ldx, N, _dptr(eig), _dptr(res), self._stream()))
+        res = np.zeros(N) if residuals else None
+        self._check(self.L.efe_rayleigh_ritz(self.h, px, ldx, N, _dptr(eig), _dptr(res) if residuals else None,
+                                             self._stream()))
         return eig, res
 
     def solve(self, X, m, tol=1e-8, max_iter=200, precision="fp64", fp64_tail=0, v0=None, n_conv=None,
@@ -477,13 +480,15 @@ class System:
         self._check(self.L.efe_autotune(self.h, int(N), PREC[precision], C.byref(t), _dptr(ms)))
         return t.value, ms
 
-    OPTIONS = {"grid_cap": 1, "image_rows": 2, "rr_panels": 3, "dense_blocked": 4}
+    OPTIONS = {"grid_cap": 1, "image_rows": 2, "rr_panels": 3, "dense_blocked": 4, "coupling_sparse": 5,
+               "test_stall": 6}
 
     def set_option(self, name, value):
         """Test/tuning control of the library (EFE_OPT_*): grid_cap (CTAs of the
         persistent tensor-core kernels), image_rows (FP64-engine image panel rows),
         rr_panels (1: panelled Rayleigh-Ritz), dense_blocked (1: multi-CTA dense
-        kernels); 0 restores the size-based default."""
+        kernels), coupling_sparse (1: many-function mixed coupling); 0 restores
+        the size-based default."""
         self._check(self.L.efe_set_option(self.h, self.OPTIONS[name], int(value)))
 
     def set_grid_cap(self, max_ctas):

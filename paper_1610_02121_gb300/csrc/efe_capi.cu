@@ -111,6 +111,17 @@ struct efe_handle {
   int64_t dsc_bytes = 0;
   bool whole_rr = true;       // Rayleigh-Ritz holds H Q and M Q whole (B2 exists); else column panels in W
   float *mecT32 = nullptr, *hecT32 = nullptr;
+  // function groups sharing one support (the many-function mixed coupling):
+  // items (first function, functions, node range) and per function its items and slot
+  int n_gitems = 0;
+  int4* gitems = nullptr;
+  int32_t *f_it0 = nullptr, *f_it1 = nullptr, *f_slot = nullptr;
+  float *hec32 = nullptr, *mecD32 = nullptr;   // row-pattern FP32 values of H^ec and M^ec D^-1
+  int64_t* ec_rowptr = nullptr;               // start of each function's row in the row pattern
+  double* gpart = nullptr;                    // n_gitems x grp_kmax() x N partial sums
+  float* Xe32 = nullptr;                      // n_E x N FP32 copy of an enrichment block
+  int opt_coup_sparse = 0;                    // 1: grouped sparse coupling whatever the size
+  int opt_test_stall = 0;                     // tests: tensor-core launches take their abort path
   // dense FP32 tiles of the pattern over blocks of pattern nodes (mixed filter)
   int64_t cb_nblk = 0, cb_nslots = 0;
   int64_t *cb_slot_off = nullptr, *cb_pos = nullptr, *cb_cta = nullptr, *cb_cta_cols = nullptr;
@@ -160,6 +171,10 @@ struct efe_handle {
   int64_t t_launches[2] = {0, 0};
   double t_ms[2] = {0.0, 0.0}, t_units[2] = {0.0, 0.0};
 };
+
+// tall FP64 product (defined with the Rayleigh-Ritz kernels below)
+extern "C" int gemm_tall(efe_handle* h, int64_t rows, int K, int Nc, const double* A, int64_t lda, const double* B,
+                         double* C, int64_t ldc, cudaStream_t st);
 
 namespace {
 
@@ -230,6 +245,12 @@ inline int tc_grid(const efe_handle* h) {
   return (h->grid_cap > 0 && h->grid_cap < h->n_sm) ? h->grid_cap : h->n_sm;
 }
 
+// the mixed degrees' dense-tile coupling kernels keep an (n_E x N) FP32 array
+// in shared memory: used when it fits, the sparse kernels otherwise
+inline bool coup_tiles_fit(const efe_handle* h, int N) {
+  return !h->opt_coup_sparse && coup_smem((int)h->nE, N, true) <= 200 * 1024;
+}
+
 // Byte size above which Rayleigh-Ritz no longer keeps H Q and M Q as whole
 // blocks (a third FP64 block) but forms them in two column panels inside W.
 constexpr int64_t WHOLE_RR_MAX_BYTES = 16ll << 30;
@@ -248,9 +269,13 @@ void free32(efe_handle* h) {
   }
   dfree(h, h->cpart);
   dfree(h, h->We);
+  dfree(h, h->gpart);
+  dfree(h, h->Xe32);
   h->Wf = nullptr;
   h->cpart = nullptr;
   h->We = nullptr;
+  h->gpart = nullptr;
+  h->Xe32 = nullptr;
   h->f32_alias = false;
   h->Nres32 = 0;
 }
@@ -318,7 +343,9 @@ int reserve32(efe_handle* h, int N) {
     dfree(h, *dev);
     *dev = nullptr;
     *ncta_out = 1;
-    if (h->nE <= 0 || h->cb_nblk <= 0) return EFE_OK;
+    // the dense-tile coupling kernels serve only blocks whose (n_E x N) array
+    // fits in shared memory (the mixed degrees take the sparse kernels otherwise)
+    if (h->nE <= 0 || h->cb_nblk <= 0 || !coup_tiles_fit(h, N)) return EFE_OK;
     const int64_t nblk = h->cb_nblk;
     const int ncta = (int)std::min<int64_t>(nblk, coup_resident_ctas((int)h->nE, N, h->n_sm, rows));
     const auto& so = h->cb_soff_host;
@@ -337,7 +364,11 @@ int reserve32(efe_handle* h, int N) {
   };
   TRY(partition(true, &h->cb_cta, &h->ncb));
   TRY(partition(false, &h->cb_cta_cols, &h->ncb_cols));
-  TRY(dalloc(h, &h->cpart, (int64_t)h->ncb * std::max<int64_t>(1, h->nE) * N));
+  TRY(dalloc(h, &h->cpart, coup_tiles_fit(h, N) ? (int64_t)h->ncb * std::max<int64_t>(1, h->nE) * N : 1));
+  if (h->nE > 0 && !coup_tiles_fit(h, N)) {
+    TRY(dalloc(h, &h->gpart, (int64_t)std::max(1, h->n_gitems) * grp_kmax() * N));
+    TRY(dalloc(h, &h->Xe32, h->nE * N));
+  }
   h->ld32 = ld;
   h->Nres32 = N;
   return EFE_OK;
@@ -417,7 +448,7 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
         int slot;
         TRY(timed_begin(h, st, &slot, 1));
         launch_oz_cell(h->Hcc, h->hexp, h->colour_cells + h->colour_off[c], nc, h->mesh, (const double*)Y, ldy,
-                       h->oz_fexp, (double*)Wc, ldw, N, tc_grid(h), h->info + 4, st, h->oz_aimg);
+                       h->oz_fexp, (double*)Wc, ldw, N, tc_grid(h), h->info + 4, st, h->oz_aimg, h->opt_test_stall);
         TRY(timed_end(h, st, slot, 2.0 * NL * NL * (double)N * (double)nc, 1));
       }
       CKL();
@@ -438,7 +469,8 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
     } else {
       if (tc) {
         if (launch_cell_tc3(h->Aimg32, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N,
-                            h->tc_mode == 2, tc_grid(h), h->info + 4, st, h->tc_tile_N == N ? h->tc_tile : 0)) {
+                            h->tc_mode == 2, tc_grid(h), h->info + 4, st, h->tc_tile_N == N ? h->tc_tile : 0,
+                            h->opt_test_stall)) {
           h->err = "tensor-core cell kernel needs 16-byte aligned rows";
           return EFE_ERR_ARG;
         }
@@ -540,6 +572,17 @@ int degree_f64(efe_handle* h, const double* Yc, int64_t ldc, const double* Yp, i
   return EFE_OK;
 }
 
+// C (n_E x N, ld N) = A (n_E x n_E) B (n_E x N, ld N) in FP64: the FP64-grade
+// tensor-core product when that engine is on and the product is large, DFMA
+// otherwise
+int gemm_ee(efe_handle* h, const double* A, const double* B, double* C, int N, cudaStream_t st) {
+  const int nE = (int)h->nE;
+  if (h->fp64_engine == 1 && (double)nE * nE * N >= 1e9) return gemm_tall(h, nE, nE, N, A, nE, B, C, N, st);
+  launch_gemm_nn(nE, N, nE, 1.0, A, nE, B, N, 0.0, C, N, st);
+  CKL();
+  return EFE_OK;
+}
+
 // --- one filter degree with the classical block in FP32 (enrichment rows FP64) ---
 // Classical rows use the padded leading dimension ld32; the enrichment
 // coupling runs node-major with FP32 products and FP64 cross-block sums.
@@ -554,7 +597,7 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
   h->time_this = false;
   if (h->nE > 0) {
     const int nE = (int)h->nE;
-    if (coup_smem(nE, N, true) <= 200 * 1024) {
+    if (coup_tiles_fit(h, N)) {
       launch_coup_cols<float>(h->n_tn, h->ncb_cols, h->cb_cta_cols, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, 1.f, Yce, N, nE,
                               N, h->Wf, ld, st);
       launch_coup_rows<float>(h->n_tn, h->ncb, h->cb_cta, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, nullptr, Yc, ld,
@@ -569,12 +612,21 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
       launch_coup_cols<float>(h->n_tn, h->ncb_cols, h->cb_cta_cols, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, -1.f, h->xe, N,
                               nE, N, h->Wf, ld, st);
     } else {
-      launch_spmm_nodes<float>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->hecT, 1.0, Yce, N, h->Wf, ld, N, st);
-      launch_spmm_segments<float>(h->nseg, h->seg_start, h->seg_end, h->ec_col, h->hec, nullptr, Yc, ld, h->part, N,
-                                  st);
-      launch_seg_reduce(nE, h->row_seg_ptr, h->part, 1.0, nullptr, 0, 0.0, We, N, N, st);
-      launch_gemm_nn(nE, N, nE, 1.0, h->Hee, nE, Yce, N, 1.0, We, N, st);
-      TRY(minv_core<float>(h, h->Wf, ld, We, N, N, st));
+      // many enrichment functions: node-major FP32 columns products, grouped
+      // FP32 rows products with FP64 partial sums, FP64 n_E x n_E products
+      const int64_t nE64 = h->nE;
+      launch_f64_to_f32_rows(nE64, Yce, N, h->Xe32, N, N, st);
+      launch_spmm_nodes_f32(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->hecT32, 1.f, h->Xe32, N, h->Wf, ld, N, st);
+      TRY(gemm_ee(h, h->Hee, Yce, h->rb, N, st));                       // H^ee Y_e
+      launch_grp_rows(h->n_gitems, h->gitems, h->ec_rowptr, h->ec_col, h->hec32, Yc, ld, h->gpart, N, st);
+      launch_grp_reduce(nE, h->f_it0, h->f_it1, h->f_slot, h->gpart, N, 1.0, h->rb, N, 1.0, We, N, st);
+      // block-wise inverse: r = We - M^ec D^-1 Wc, x_e = S^-1 r, Wc -= M^ec^T x_e
+      launch_grp_rows(h->n_gitems, h->gitems, h->ec_rowptr, h->ec_col, h->mecD32, h->Wf, ld, h->gpart, N, st);
+      launch_grp_reduce(nE, h->f_it0, h->f_it1, h->f_slot, h->gpart, N, -1.0, We, N, 1.0, h->rb, N, st);
+      TRY(gemm_ee(h, h->Sinv, h->rb, h->xe, N, st));
+      launch_f64_to_f32_rows(nE64, h->xe, N, h->Xe32, N, N, st);
+      launch_spmm_nodes_f32(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->mecT32, -1.f, h->Xe32, N, h->Wf, ld, N, st);
+      CKL();
     }
   }
   launch_cheb_combine_f4(nn, ld, h->Dinv, h->Wf, Yc, Yp, Yn, coef, st);
@@ -1091,6 +1143,47 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
     TRY(upload(h, &h->seg_start, ss));
     TRY(upload(h, &h->seg_end, se));
     TRY(upload(h, &h->row_seg_ptr, rsp));
+    {
+      // function groups sharing one support: consecutive functions of one atom
+      // with one cutoff and identical row patterns (at most grp_kmax() each),
+      // cut into items of GRP_SEG nodes for the many-function mixed coupling
+      constexpr int GRP_SEG = 2048;
+      std::vector<int4> items;
+      std::vector<int32_t> it0(s.nE), it1(s.nE), slot(s.nE);
+      int a = 0;
+      while (a < s.nE) {
+        const int64_t len = s.ec_ptr[a + 1] - s.ec_ptr[a];
+        int kg = 1;
+        while (a + kg < s.nE && kg < grp_kmax()) {
+          const int b = a + kg;
+          const bool same = s.funcs[b].Rx == s.funcs[a].Rx && s.funcs[b].Ry == s.funcs[a].Ry &&
+                            s.funcs[b].Rz == s.funcs[a].Rz && s.funcs[b].r0 == s.funcs[a].r0 &&
+                            s.funcs[b].t == s.funcs[a].t && s.ec_ptr[b + 1] - s.ec_ptr[b] == len &&
+                            std::equal(s.ec_col.begin() + s.ec_ptr[a], s.ec_col.begin() + s.ec_ptr[a + 1],
+                                       s.ec_col.begin() + s.ec_ptr[b]);
+          if (!same) break;
+          ++kg;
+        }
+        const int first = (int)items.size();
+        for (int64_t j = 0; j < len; j += GRP_SEG)
+          items.push_back(make_int4(a, kg, (int)j, (int)std::min<int64_t>(len, j + GRP_SEG)));
+        for (int k = 0; k < kg; ++k) {
+          it0[a + k] = first;
+          it1[a + k] = (int)items.size();
+          slot[a + k] = k;
+        }
+        a += kg;
+      }
+      h->n_gitems = (int)items.size();
+      TRY(upload(h, &h->gitems, items));
+      TRY(upload(h, &h->f_it0, it0));
+      TRY(upload(h, &h->f_it1, it1));
+      TRY(upload(h, &h->f_slot, slot));
+      TRY(upload(h, &h->ec_rowptr, s.ec_ptr));
+      std::vector<float> md(s.ec_col.size());
+      for (size_t q = 0; q < md.size(); ++q) md[q] = (float)(s.mec_val[q] * s.Dinv[s.ec_col[q]]);
+      TRY(upload(h, &h->mecD32, md));
+    }
     h->n_tn = (int64_t)s.t_nodes.size();
     TRY(upload(h, &h->t_nodes, s.t_nodes));
     TRY(upload(h, &h->t_ptr, s.t_ptr));
@@ -1100,6 +1193,7 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
     TRY(dalloc(h, &h->hecT, h->nnz));
     TRY(dalloc(h, &h->mecT32, h->nnz));
     TRY(dalloc(h, &h->hecT32, h->nnz));
+    TRY(dalloc(h, &h->hec32, h->nnz));
     launch_permute(h->nnz, h->mec, h->t_perm, h->mecT, 0);
     launch_to_f32(h->mecT, h->mecT32, h->nnz, 0);
     CKL();
@@ -1214,6 +1308,7 @@ int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
     launch_gather_sum(h->nnz, h->hec_kin, h->ec_cptr, h->ec_cidx, h->Pblk, h->hec, st);
     launch_permute(h->nnz, h->hec, h->t_perm, h->hecT, st);
     launch_to_f32(h->hecT, h->hecT32, h->nnz, st);
+    launch_to_f32(h->hec, h->hec32, h->nnz, st);
     launch_tile_scatter(h->nnz, h->cb_pos, h->hecT32, h->tileH, st);
     launch_gather_sum(h->nE * h->nE, h->Hee_kin, h->ee_cptr, h->ee_cidx, h->Qblk, h->Hee, st);
     launch_symmetrize(h->Hee, (int)h->nE, (int)h->nE, st);
@@ -1560,7 +1655,7 @@ int gemm_tall(efe_handle* h, int64_t rows, int K, int Nc, const double* A, int64
       int slot;
       TRY(timed_begin(h, st, &slot, 1));
       launch_oz_rows(A + r0 * lda, lda, n, K, h->oz_aexp + r0, B, Nc, h->oz_bexp, C + r0 * ldc, ldc, Nc, tc_grid(h),
-                     h->info + 4, st, h->oz_img[0], h->oz_img[1]);
+                     h->info + 4, st, h->oz_img[0], h->oz_img[1], h->opt_test_stall);
       TRY(timed_end(h, st, slot, 2.0 * (double)n * K * Nc, 1));
     }
   } else {
@@ -1596,7 +1691,7 @@ int gemm_gram(efe_handle* h, int64_t rows, int Na, int Nb, const double* A, int6
       TRY(timed_begin(h, st, &slot, 1));
       ok = launch_oz_gram(kn, Na, Nb, A + k0 * lda, lda, h->oz_fexp, B + k0 * ldb, ldb, bexp, C, ldc, sym, h->tnwork,
                           h->tnwork_elems, h->oz_pairs, tc_grid(h), h->info + 4, st, h->oz_img[0],
-                          h->oz_img_bytes[0], h->oz_img[1], h->oz_img_bytes[1], k0 > 0) == 0;
+                          h->oz_img_bytes[0], h->oz_img[1], h->oz_img_bytes[1], k0 > 0, h->opt_test_stall) == 0;
       TRY(timed_end(h, st, slot, ok ? (sym ? 1.0 : 2.0) * (double)kn * Na * (Nb + (sym ? 1 : 0)) : 0.0, 1));
     }
     if (ok) {
@@ -1984,6 +2079,17 @@ int efe_set_option(efe_handle* h, int32_t option, int64_t value) {
       if (value > 1) return EFE_ERR_ARG;
       h->opt_dense_blocked = (int)value;
       return EFE_OK;
+    case EFE_OPT_TEST_STALL:
+      if (value > 1) return EFE_ERR_ARG;
+      h->opt_test_stall = (int)value;
+      return EFE_OK;
+    case EFE_OPT_COUPLING_SPARSE:
+      if (value > 1) return EFE_ERR_ARG;
+      if (h->opt_coup_sparse != (int)value) {
+        h->opt_coup_sparse = (int)value;
+        h->Nres32 = 0;   // the mixed workspace is remade at the next filter call
+      }
+      return EFE_OK;
     default:
       h->err = "unknown option";
       return EFE_ERR_ARG;
@@ -2147,9 +2253,10 @@ int efe_scf_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, in
   launch_veff(h->nq, rho_in, h->vext, h->vh_in, h->vxc_in, h->V, st);
   CKL();
   TRY(efe_set_potential(h, h->V, stream));
-  std::vector<double> ev(N), rv(N), fv(N);
+  std::vector<double> ev(N), fv(N);
+  // the SCF step uses only the Ritz values (no residuals)
   if ((int)h->ritz.size() != N) {
-    TRY(efe_rayleigh_ritz(h, X, ldx, N, ev.data(), rv.data(), stream));
+    TRY(efe_rayleigh_ritz(h, X, ldx, N, ev.data(), nullptr, stream));
     h->ritz = ev;
   }
   // Lanczos start: the last column of X
@@ -2161,7 +2268,7 @@ int efe_scf_step(efe_handle* h, double* X, int64_t ldx, int32_t N, int32_t m, in
     const double a = *std::max_element(h->ritz.begin(), h->ritz.end());
     const double a0 = *std::min_element(h->ritz.begin(), h->ritz.end());
     TRY(efe_chfsi_step(h, X, ldx, N, m, a, b, a0, precision, fp64_tail, stream));
-    TRY(efe_rayleigh_ritz(h, X, ldx, N, ev.data(), rv.data(), stream));
+    TRY(efe_rayleigh_ritz(h, X, ldx, N, ev.data(), nullptr, stream));
     h->ritz = ev;
   }
   double mu = 0.0;

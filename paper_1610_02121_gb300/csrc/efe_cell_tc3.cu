@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
                                                             const int32_t* __restrict__ cells, int64_t ncells,
                                                             MeshDev m, const float* __restrict__ Y, int64_t ldy,
                                                             float* __restrict__ W, int64_t ldw, int N, int ntiles,
-                                                            int* __restrict__ err) {
+                                                            int* __restrict__ err, int stall) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // an earlier launch already failed: leave at once (CTA-uniform decision)
@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
   uint64_t* acce = full + 8;                                          // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 10);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(full + 11);
+  uint64_t* never = full + 12;   // no thread ever arrives here (the test stall waits on it)
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
       bar_init(accf + b, 1);
       bar_init(acce + b, T3_EPI_WARPS * 32);
     }
+    bar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -169,6 +171,9 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
   const uint32_t tmem = *tslot;
   const int64_t nitems = ncells * ntiles;
   const int64_t my_items = nitems > blockIdx.x ? (nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  // the last chunk whose bulk copies this thread issued / whose MMAs it committed
+  // (drained before the TMEM is released if the CTA aborts)
+  int64_t last_copy = -1, last_mma = -1;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -195,11 +200,16 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
           bulk_g2s(S + 2 * T3Layout<TW>::A + 2 * T3Layout<TW>::B + (uint32_t)lane * (TW * 4), Y + g * ldy + c0, row_bytes,
                    full + s);
         }
+        last_copy = ch;
         __syncwarp();
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    if (stall && my_items > 0 && !bar_wait(never, 0u)) {
+      // test stall: a wait that nothing completes runs out like a real one
+      if (lane == 0) { *abort_flag = 1; atomicExch(err, 1); }
+    }
     for (int64_t t = 0; t < my_items && !*abort_flag; ++t) {
       const int64_t item = blockIdx.x + t * gridDim.x;
       const int c0 = (int)(item % ntiles) * TW;
@@ -232,6 +242,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
           mma_commit(empty + s);
           if (kc == T3_NCH - 1) mma_commit(accf + b);
         }
+        last_mma = ch;
         __syncwarp();
       }
       if (!ok) {
@@ -361,14 +372,19 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
       bar_arrive(acce + b);
     }
   }
-  // all roles done: wait for any MMA still in flight before releasing TMEM
+  // all roles done.  After an abort, drain before the TMEM and the shared memory
+  // are released: every bulk copy issued into the stage ring lands (at most
+  // T3_STAGES chunks are in flight: the producer waits for a stage to empty
+  // before refilling it), and the last MMA commit (it covers every MMA this CTA
+  // issued) arrives; each drain wait is bounded like the pipeline's own.
   __syncthreads();
-  if (warp == 1 && my_items > 0) {
-    // the last accumulator commit covers every MMA this CTA issued
-    const int64_t tl = my_items - 1;
-    if (*abort_flag) {
-      bar_wait(accf + (int)(tl & 1), (uint32_t)((tl / 2) & 1));
+  if (*abort_flag) {
+    if (warp == 0 && lane == 0 && last_copy >= 0) {
+      for (int64_t ch = last_copy - T3_STAGES + 1; ch <= last_copy; ++ch)
+        if (ch >= 0) bar_wait(full + (int)(ch % T3_STAGES), (uint32_t)((ch / T3_STAGES) & 1));
     }
+    if (warp == 1 && lane == 0 && last_mma >= 0)
+      bar_wait(empty + (int)(last_mma % T3_STAGES), (uint32_t)((last_mma / T3_STAGES) & 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -410,17 +426,18 @@ namespace {
 template <int TW>
 void tc3_launch(const float* A, const int32_t* cells, int64_t ncells, const MeshDev& m,
                 const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
-                cudaStream_t st) {
+                cudaStream_t st, int stall) {
   const int ntiles = (N + TW - 1) / TW;
   const int64_t items = ncells * ntiles;
   const unsigned grid = (unsigned)(items < n_sm ? items : n_sm);
   const size_t smem = T3Layout<TW>::TOTAL;
   if (split) {
     cudaFuncSetAttribute(k_cell_tc3<true, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cell_tc3<true, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err);
+    k_cell_tc3<true, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err, stall);
   } else {
     cudaFuncSetAttribute(k_cell_tc3<false, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cell_tc3<false, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err);
+    k_cell_tc3<false, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err,
+                                                          stall);
   }
 }
 }  // namespace
@@ -433,15 +450,15 @@ const int* tc3_tiles(int* count) {
 
 int launch_cell_tc3(const float* A, const int32_t* cells, int64_t ncells, const MeshDev& m,
                     const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
-                    cudaStream_t st, int tile) {
+                    cudaStream_t st, int tile, int stall) {
   if (ncells <= 0 || N <= 0) return 0;
   if ((ldy & 3) || (ldw & 3)) return 1;
   if (tile == 64)
-    tc3_launch<64>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
+    tc3_launch<64>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st, stall);
   else if (tile == 96)
-    tc3_launch<96>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
+    tc3_launch<96>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st, stall);
   else if (tile == 160 || tile == 0)
-    tc3_launch<160>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st);
+    tc3_launch<160>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st, stall);
   else
     return 1;
   g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -200,6 +200,98 @@ __global__ void k_spmm_segments(const int64_t* __restrict__ seg_start, const int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision enrichment coupling for many enrichment functions (the
+// (n_E x N) array of the dense-tile kernels no longer fits in shared memory):
+// FP32 products, FP64 sums across node chunks.
+//
+// Rows product W_e = C X_c over function groups: the functions of one atom
+// with one cutoff share a support, hence one node list, so a CTA reads each
+// node row of its column tile once for the whole group (k_g <= GRP_KMAX
+// functions).  Work item = (group, node range); FP32 sums over chunks of 64
+// nodes are added into FP64 per-item partials; a fixed-order reduction over
+// the items of a function finishes.
+constexpr int GRP_KMAX = 8;
+constexpr int GRP_CHUNK = 64;
+constexpr int GRP_CT = 128;   // columns per CTA (one per thread)
+
+__global__ void __launch_bounds__(GRP_CT) k_grp_rows(const int4* __restrict__ items, const int64_t* __restrict__ ec_ptr,
+                                                    const int32_t* __restrict__ ec_col, const float* __restrict__ coef,
+                                                    const float* __restrict__ Xc, int64_t ldx, double* __restrict__ part,
+                                                    int N) {
+  __shared__ int64_t nd[GRP_CHUNK];
+  __shared__ float cf[GRP_KMAX][GRP_CHUNK];
+  const int4 it = items[blockIdx.x];   // first function, functions, node positions [j0, j1)
+  const int f0 = it.x, kg = it.y, j0 = it.z, j1 = it.w;
+  const int c = blockIdx.y * GRP_CT + threadIdx.x;
+  const int64_t base = ec_ptr[f0];
+  double acc[GRP_KMAX];
+#pragma unroll
+  for (int k = 0; k < GRP_KMAX; ++k) acc[k] = 0.0;
+  for (int j = j0; j < j1; j += GRP_CHUNK) {
+    const int n = min(GRP_CHUNK, j1 - j);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += GRP_CT) nd[t] = ec_col[base + j + t];
+    for (int t = threadIdx.x; t < kg * GRP_CHUNK; t += GRP_CT) {
+      const int k = t / GRP_CHUNK, jj = t % GRP_CHUNK;
+      cf[k][jj] = jj < n ? coef[ec_ptr[f0 + k] + j + jj] : 0.f;
+    }
+    __syncthreads();
+    if (c < N) {
+      float s[GRP_KMAX];
+#pragma unroll
+      for (int k = 0; k < GRP_KMAX; ++k) s[k] = 0.f;
+#pragma unroll 8
+      for (int jj = 0; jj < n; ++jj) {
+        const float x = Xc[nd[jj] * ldx + c];
+#pragma unroll
+        for (int k = 0; k < GRP_KMAX; ++k)
+          if (k < kg) s[k] = fmaf(cf[k][jj], x, s[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < GRP_KMAX; ++k) acc[k] += (double)s[k];
+    }
+  }
+  if (c < N) {
+    double* o = part + (int64_t)blockIdx.x * GRP_KMAX * N + c;
+    for (int k = 0; k < kg; ++k) o[(int64_t)k * N] = acc[k];
+  }
+}
+
+// out[f][c] = sgn * sum over the items of f's group (fixed order) + alpha * base[f][c]
+__global__ void k_grp_reduce(int nE, const int32_t* __restrict__ f_it0, const int32_t* __restrict__ f_it1,
+                             const int32_t* __restrict__ f_slot, const double* __restrict__ part, int N, double sgn,
+                             const double* __restrict__ base, int64_t ldb, double alpha, double* __restrict__ out,
+                             int64_t ldo) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nE * N) return;
+  const int f = (int)(idx / N), c = (int)(idx % N);
+  double s = 0.0;
+  for (int it = f_it0[f]; it < f_it1[f]; ++it) s += part[((int64_t)it * GRP_KMAX + f_slot[f]) * N + c];
+  double v = sgn * s;
+  if (base) v += alpha * base[(int64_t)f * ldb + c];
+  out[(int64_t)f * ldo + c] = v;
+}
+
+// Columns product W_c[node] += sgn * sum_f C[f][node] X_e[f] (node-major, FP32
+// products and sums over the node's few functions; X_e in FP32, L2-resident).
+__global__ void k_spmm_nodes_f32(int64_t nrows, const int32_t* __restrict__ rnode, const int64_t* __restrict__ ptr,
+                                 const int32_t* __restrict__ col, const float* __restrict__ val, float sgn,
+                                 const float* __restrict__ Xe, int64_t ldxe, float* __restrict__ out, int64_t ldo,
+                                 int N) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  const int64_t g = rnode[w];
+  const int64_t q0 = ptr[w], q1 = ptr[w + 1];
+  for (int c = lane; c < N; c += 32) {
+    float s = 0.f;
+    for (int64_t q = q0; q < q1; ++q) s = fmaf(val[q], Xe[(int64_t)col[q] * ldxe + c], s);
+    float* o = out + g * ldo + c;
+    *o = fmaf(sgn, s, *o);
+  }
+}
+
 // Narrow blocks (N <= 4: the Lanczos vector): the threads of a block split the
 // entries of a segment instead of the columns, and the partials are added by a
 // fixed shuffle tree and a fixed-order sum over the warps (reproducible).
@@ -1450,6 +1542,33 @@ void launch_coup_cols(int64_t n_tn, int ncta, const int64_t* cta_blk, const int3
 template void launch_coup_cols<float>(int64_t, int, const int64_t*, const int32_t*, const int64_t*, const int32_t*,
                                       const float*, float, const double*, int64_t, int, int, float*, int64_t,
                                       cudaStream_t);
+
+int grp_kmax() { return GRP_KMAX; }
+
+void launch_grp_rows(int n_items, const int4* items, const int64_t* ec_ptr, const int32_t* ec_col, const float* coef,
+                     const float* Xc, int64_t ldx, double* part, int N, cudaStream_t st) {
+  if (n_items <= 0 || N <= 0) return;
+  dim3 g((unsigned)n_items, (unsigned)((N + GRP_CT - 1) / GRP_CT));
+  k_grp_rows<<<g, GRP_CT, 0, st>>>(items, ec_ptr, ec_col, coef, Xc, ldx, part, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_grp_reduce(int nE, const int32_t* f_it0, const int32_t* f_it1, const int32_t* f_slot, const double* part,
+                       int N, double sgn, const double* base, int64_t ldb, double alpha, double* out, int64_t ldo,
+                       cudaStream_t st) {
+  if (nE <= 0 || N <= 0) return;
+  k_grp_reduce<<<grid1((int64_t)nE * N, 256), 256, 0, st>>>(nE, f_it0, f_it1, f_slot, part, N, sgn, base, ldb, alpha,
+                                                          out, ldo);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_spmm_nodes_f32(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
+                           const float* val, float sgn, const float* Xe, int64_t ldxe, float* out, int64_t ldo, int N,
+                           cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_spmm_nodes_f32<<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe, ldxe, out, ldo, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 
 void launch_cheb_combine_f4(int64_t nrows, int ld, const double* rowscale, const float* X, const float* Yc,
                             const float* Yp, float* Yn, const double* coef, cudaStream_t st) {

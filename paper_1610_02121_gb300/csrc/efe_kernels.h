@@ -67,6 +67,20 @@ void launch_coup_cols(int64_t n_tn, int ncta, const int64_t* cta_blk, const int3
                       int64_t ldxe, int nE, int N, T* W, int64_t ldw, cudaStream_t st);
 void launch_cheb_combine_f4(int64_t nrows, int ld, const double* rowscale, const float* X, const float* Yc,
                             const float* Yp, float* Yn, const double* coef, cudaStream_t st);
+// mixed coupling for many enrichment functions (FP32 products, FP64 partial sums):
+// rows product over function groups (items: first function, functions, node
+// positions [j0, j1) of the group's shared row pattern); part: n_items x
+// grp_kmax() x N doubles; then a fixed-order reduction per function
+int grp_kmax();
+void launch_grp_rows(int n_items, const int4* items, const int64_t* ec_ptr, const int32_t* ec_col, const float* coef,
+                     const float* Xc, int64_t ldx, double* part, int N, cudaStream_t st);
+void launch_grp_reduce(int nE, const int32_t* f_it0, const int32_t* f_it1, const int32_t* f_slot, const double* part,
+                       int N, double sgn, const double* base, int64_t ldb, double alpha, double* out, int64_t ldo,
+                       cudaStream_t st);
+// columns product, node-major, FP32 (Xe: FP32 rows, ldxe)
+void launch_spmm_nodes_f32(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
+                           const float* val, float sgn, const float* Xe, int64_t ldxe, float* out, int64_t ldo, int N,
+                           cudaStream_t st);
 // out[node_r] += sgn * sum_q val[q] * Xe[col[q]]   (rows = nodes that meet a support)
 template <typename T>
 void launch_spmm_nodes(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
@@ -104,12 +118,17 @@ int64_t tc3_image_elems(int64_t n_cell);
 // FP32 image of every H^cc_e in the MMA's core-matrix layout (split into TF32 parts in the kernel)
 void launch_build_aimg(const double* Hcc, int64_t n_cell, float* A, cudaStream_t st);
 // tile: column tile width (64, 96 or 160; 0 = default 160)
+// stall (tests only): the MMA warp first waits on a barrier nothing completes, so the
+// bounded wait runs out and the launch takes its abort path
 int launch_cell_tc3(const float* A, const int32_t* cells, int64_t ncells, const MeshDev& m,
                     const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
-                    cudaStream_t st, int tile = 0);
+                    cudaStream_t st, int tile = 0, int stall = 0);
 const int* tc3_tiles(int* count);
 
 // ---- FP64-grade products on the BF16 tensor cores (efe_oz.cu) ----
+// stall (tests only, every launcher below): the MMA warp first waits on a
+// barrier nothing completes, so the bounded wait runs out and the launch takes
+// its abort path
 int64_t oz_hexp_elems(int64_t n_cell);
 void launch_oz_hexp(const double* Hcc, int64_t n_cell, int* hexp, cudaStream_t st);
 void launch_oz_colexp(const double* Y, int64_t ldy, int64_t rows, int N, int* fexp, cudaStream_t st);
@@ -117,12 +136,12 @@ void launch_oz_rowexp(const double* A, int64_t lda, int64_t rows, int K, int* ae
 // Aimg: pre-sliced digit images of H^cc_e (launch_oz_preslice), or NULL to slice on the fly
 int launch_oz_cell(const double* Hcc, const int* hexp, const int32_t* cells, int64_t ncells, const MeshDev& m,
                    const double* Y, int64_t ldy, const int* fexp, double* W, int64_t ldw, int N, int n_sm, int* err,
-                   cudaStream_t st, const unsigned char* Aimg = nullptr);
+                   cudaStream_t st, const unsigned char* Aimg = nullptr, int stall = 0);
 int64_t oz_cell_image_bytes();
 void launch_oz_preslice(const double* Hcc, const int* hexp, int64_t n_cell, unsigned char* img, cudaStream_t st);
 int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, const double* B, int64_t ldb,
                    const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st,
-                   const unsigned char* Aimg = nullptr, const unsigned char* Bimg = nullptr);
+                   const unsigned char* Aimg = nullptr, const unsigned char* Bimg = nullptr, int stall = 0);
 // pre-sliced operand images for the ROWS / GRAM products (bytes, builders)
 int64_t oz_img_rows_bytes(int64_t rows, int K);
 int64_t oz_img_cols_bytes(int64_t nch, int ncols);
@@ -136,7 +155,7 @@ int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const
                    int64_t ldb, const int* bexp, double* C, int64_t ldc, bool sym, double* work, int64_t work_elems,
                    int2* pairs_dev, int n_sm, int* err, cudaStream_t st, unsigned char* img_a = nullptr,
                    int64_t img_a_bytes = 0, unsigned char* img_b = nullptr, int64_t img_b_bytes = 0,
-                   bool accumulate = false);
+                   bool accumulate = false, int stall = 0);
 int oz_gram_max_pairs(int Na, int N);
 
 // ---- dense FP64 ----

@@ -241,6 +241,7 @@ struct OzArgs {
   // images.  img_nch: 16-wide K chunks per 128-wide tile of a column image.
   const unsigned char* Bimg;
   int64_t img_nch;
+  int stall;                // tests only: the MMA warp first waits on a barrier nothing completes
 };
 
 // work item of a CTA: cell / row block / tile pair and its K range
@@ -293,6 +294,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(accf + 3);
   uint64_t* afull = accf + 4;                                   // [stages] bulk-copied operand chunks landed
+  uint64_t* never = afull + OZ_STAGES;                          // no thread ever arrives here (test stall)
   const bool apre = g.Aimg != nullptr;
   const bool bpre = g.mode != 0 && g.Bimg != nullptr;
   // both operands pre-sliced: nothing to slice, so one thread issues the copies
@@ -314,6 +316,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
     }
     bar_init(accf, 1);
     bar_init(acce, n_epi * 32);
+    bar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -330,9 +333,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   const int nch = (g.mode == 2) ? (int)(g.seg_len / OZ_KC) : (g.K + OZ_KC - 1) / OZ_KC;
   const int gsz = (g.mode == 2) ? 16 : (g.mode == 1 ? min(nch, OZ_ROWS_KG) : nch);
   const int ngrp = (nch + gsz - 1) / gsz;
+  // the last chunk whose MMAs this thread committed / whose bulk copies it issued
+  // (drained before the TMEM and shared memory are released after an abort)
+  int64_t last_mma = -1, last_copy = -1;
 
   if (warp == 0) {
     // ---------------------------------------------------------------- MMA issuer
+    if (g.stall && my > 0 && !bar_wait(never, 0u)) {
+      // test stall: a wait that nothing completes runs out like a real one
+      if (lane == 0) { *abort_flag = 1; atomicExch(g.err, 1); }
+    }
     for (int64_t t = 0; t < my && !*abort_flag; ++t) {
       const int64_t item = blockIdx.x + t * gridDim.x;
       const OzItem it = oz_item(g, item);
@@ -372,6 +382,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
           mma_commit(empty + s);
           if (kc % gsz == gsz - 1 || kc == nch - 1) mma_commit(accf);
         }
+        last_mma = ch;
         __syncwarp();
       }
       if (!ok) {
@@ -387,7 +398,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
     const int grp = img_only ? 0 : ((tid - OZ_CONV_W0 * 32) < OZ_GT0 ? 0 : 1);
     const int ct = img_only ? 0 : (tid - OZ_CONV_W0 * 32) - grp * OZ_GT0;
     const int gsz_t = img_only ? 1 : oz_group_threads(grp);
-    int64_t last_copy = -1;   // last chunk whose operand copies this thread issued
     for (int64_t t = 0; t < my && !*abort_flag; ++t) {
       const OzItem it = oz_item(g, blockIdx.x + t * gridDim.x);
       const int64_t ia = it.ia, e = it.e;
@@ -537,10 +547,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         break;
       }
     }
-    if (ct == 0 && *abort_flag && last_copy >= 0) {
-      // let the last bulk copies of this thread land before the CTA can leave
-      bar_wait(afull + (int)(last_copy % OZ_STAGES), (uint32_t)((last_copy / OZ_STAGES) & 1));
-    }
   } else if (warp >= epi_w0) {
     // ---------------------------------------------------------------- epilogue
     // each thread owns one accumulator row (its TMEM lane); an 8-column block of
@@ -663,8 +669,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
       if (stop) break;
     }
   }
+  // all roles done.  After an abort, drain before the TMEM and the shared memory
+  // are released: every bulk copy still in flight into the stage ring lands (a
+  // copy thread issues into a stage only after its MMAs released it, so at most
+  // the last OZ_STAGES chunks of a thread are outstanding; stages filled by the
+  // other group are drained by that group's thread), and the last MMA commit --
+  // which covers every MMA this CTA issued -- arrives.  Each drain wait is
+  // bounded like the pipeline's own.
   __syncthreads();
-  if (warp == 0 && my > 0 && *abort_flag) bar_wait(accf, (uint32_t)((my * ngrp - 1) & 1));
+  if (*abort_flag) {
+    if (last_copy >= 0) {
+      for (int64_t ch = last_copy - OZ_STAGES + 1; ch <= last_copy; ++ch)
+        if (ch >= 0 && (img_only || (int)(ch % OZ_GROUPS) == (int)(last_copy % OZ_GROUPS)))
+          bar_wait(afull + (int)(ch % OZ_STAGES), (uint32_t)((ch / OZ_STAGES) & 1));
+    }
+    if (warp == 0 && lane == 0 && last_mma >= 0)
+      bar_wait(empty + (int)(last_mma % OZ_STAGES), (uint32_t)((last_mma / OZ_STAGES) & 1));
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -870,7 +891,7 @@ void launch_oz_preslice(const double* Hcc, const int* hexp, int64_t n_cell, unsi
 
 int launch_oz_cell(const double* Hcc, const int* hexp, const int32_t* cells, int64_t ncells, const MeshDev& m,
                    const double* Y, int64_t ldy, const int* fexp, double* W, int64_t ldw, int N, int n_sm, int* err,
-                   cudaStream_t st, const unsigned char* Aimg) {
+                   cudaStream_t st, const unsigned char* Aimg, int stall) {
   if (ncells <= 0 || N <= 0) return 0;
   OzArgs a{};
   a.mode = 0;
@@ -889,6 +910,7 @@ int launch_oz_cell(const double* Hcc, const int* hexp, const int32_t* cells, int
   a.N = N;
   a.ntiles = (N + OZ_TW - 1) / OZ_TW;
   a.err = err;
+  a.stall = stall;
   return oz_launch(a, n_sm, st);
 }
 
@@ -921,7 +943,7 @@ void launch_oz_img_cols(const double* A, int64_t lda, int64_t Krows, int ncols, 
 // launch_oz_img_rows(A) and launch_oz_img_cols(B, nch = ceil(K / 16)).
 int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int* aexp, const double* B, int64_t ldb,
                    const int* bexp, double* C, int64_t ldc, int N, int n_sm, int* err, cudaStream_t st,
-                   const unsigned char* Aimg, const unsigned char* Bimg) {
+                   const unsigned char* Aimg, const unsigned char* Bimg, int stall) {
   if (rows <= 0 || N <= 0 || K <= 0) return 0;
   OzArgs a{};
   a.Aimg = Aimg;
@@ -940,6 +962,7 @@ int launch_oz_rows(const double* A, int64_t lda, int64_t rows, int K, const int*
   a.N = N;
   a.ntiles = (N + OZ_TW - 1) / OZ_TW;
   a.err = err;
+  a.stall = stall;
   return oz_launch(a, n_sm, st);
 }
 
@@ -985,7 +1008,7 @@ __global__ void k_oz_gram_reduce(int nseg, int Na, int N, const double* __restri
 int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const int* aexp, const double* B,
                    int64_t ldb, const int* bexp, double* C, int64_t ldc, bool sym, double* work, int64_t work_elems,
                    int2* pairs_dev, int n_sm, int* err, cudaStream_t st, unsigned char* img_a,
-                   int64_t img_a_bytes, unsigned char* img_b, int64_t img_b_bytes, bool accumulate) {
+                   int64_t img_a_bytes, unsigned char* img_b, int64_t img_b_bytes, bool accumulate, int stall) {
   if (K <= 0 || Na <= 0 || N <= 0) return 0;
   if (sym && Na != N) return 1;
   std::vector<int2> pairs(oz_gram_pairs(Na, N, sym, nullptr));
@@ -1014,6 +1037,7 @@ int launch_oz_gram(int64_t K, int Na, int N, const double* A, int64_t lda, const
   a.part = work;
   a.ntiles = (N + OZ_TW - 1) / OZ_TW;
   a.err = err;
+  a.stall = stall;
   // column images of A and B (one image when B is A) covering every segment
   const int64_t nch = nseg * seg_len / OZ_KC;
   if (img_a && oz_img_cols_bytes(nch, Na) <= img_a_bytes &&

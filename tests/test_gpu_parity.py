@@ -492,3 +492,54 @@ def test_mixed_filter_slots_inside_fp64_workspace(tiny_pair, prec, N, tol, tail)
     Xe = to_dev(X)
     G.chfsi_step(Xe, 7, a, b, a0, precision=prec, fp64_tail=tail)
     assert torch.equal(Xd, Xe)
+
+
+@pytest.mark.parametrize("prec,N,tol", [("tf32x3", 24, 5e-5), ("tf32x3", 300, 5e-5), ("fp32", 12, 2e-5)])
+def test_mixed_filter_grouped_coupling(tiny_pair, prec, N, tol):
+    """The many-function enrichment coupling of the mixed degrees (node-major
+    FP32 columns products; rows products over the functions that share a
+    support, FP32 over 64-node chunks, FP64 across chunks and items), forced on
+    the tiny mesh: a degree-7 filter against the oracle at the mixed-mode
+    tolerances of the dense-tile path."""
+    from oracle.chfsi import chebyshev_filter_scaled
+    d, G = tiny_pair
+    X = W.random_block(d.system, N, seed=80 + N)
+    a, b, a0 = _bounds(d, 10)
+    ref = chebyshev_filter_scaled(d.apply_Htilde, X, 7, a, b, a0)
+    G.set_option("coupling_sparse", 1)
+    try:
+        Xd = to_dev(X)
+        G.chfsi_step(Xd, 7, a, b, a0, precision=prec, fp64_tail=0)
+    finally:
+        G.set_option("coupling_sparse", 0)
+    assert rel_err(Xd, ref) < tol
+
+
+@pytest.mark.parametrize("engine,prec", [("dfma", "tf32x3"), ("tensor", "fp64")])
+def test_bounded_wait_runs_out_then_recovers(tiny_pair, engine, prec):
+    """Failure path of the tensor-core kernels without a GPU fault: with the test
+    stall on, the MMA warp first waits on an mbarrier that nothing completes; the
+    bounded wait (about a second) runs out, the CTA drains its bulk copies and
+    MMAs, frees its TMEM, and the call returns EFE_ERR_TIMEOUT.  The next normal
+    call on the same handle succeeds and matches the oracle."""
+    from oracle.chfsi import chebyshev_filter_scaled
+    from paper_1610_02121_gb300 import EfeError
+    d, G = tiny_pair
+    N, m = 12, 3
+    X = W.initial_block(d.system, N, seed=2)
+    a, b, a0 = _bounds(d, N)
+    G.set_fp64_engine(engine)
+    try:
+        G.set_option("test_stall", 1)
+        try:
+            with pytest.raises(EfeError) as e:
+                G.chfsi_step(to_dev(X), m, a, b, a0, precision=prec, fp64_tail=0)
+            assert e.value.code == 5
+        finally:
+            G.set_option("test_stall", 0)
+        ref = chebyshev_filter_scaled(d.apply_Htilde, X, m, a, b, a0)
+        Xd = to_dev(X)
+        G.chfsi_step(Xd, m, a, b, a0, precision=prec, fp64_tail=0)
+        assert rel_err(Xd, ref) < (1e-5 if prec == "tf32x3" else 1e-8)
+    finally:
+        G.set_fp64_engine("dfma")

@@ -216,6 +216,16 @@ def si280(h_min=1.3, h_max=3.0, pad=10.0, r_c=4.0, seed=4, pot_seed=6, n_gaussia
                            name=f"si{len(atoms)}")
 
 
+def carbon_monoxide(h_min=1.0, h_max=3.0, pad=6.0, r_c=4.0, seed=12, tau=1e-7, max_depth=6):
+    """C-O pair (Z = 6, 8; bond 2.132 bohr along x, 14 electrons) on a graded
+    degree-4 mesh, Slater 1s/2s/2p enrichment (5 per atom, seeded exponents),
+    bare nuclear potential: the small multi-atom system whose converged SCF the
+    oracle provides for parity."""
+    atoms = np.array([[0.0, 0.0, 0.0], [2.132, 0.0, 0.0]])
+    return _cluster_system(atoms, np.array([6.0, 8.0]), h_min, h_max, pad, r_c, seed, seed + 1, 0, tau, max_depth,
+                           name="co")
+
+
 def _cluster_system(atoms, Z, h_min, h_max, pad, r_c, seed, pot_seed, n_gaussians, tau,
                     max_depth, name):
     rng = np.random.Generator(np.random.PCG64(seed))
