@@ -616,7 +616,8 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
       // FP32 rows products with FP64 partial sums, FP64 n_E x n_E products
       const int64_t nE64 = h->nE;
       launch_f64_to_f32_rows(nE64, Yce, N, h->Xe32, N, N, st);
-      launch_spmm_nodes_f32(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->hecT32, 1.f, h->Xe32, N, h->Wf, ld, N, st);
+      launch_coup_cols_chunk(h->n_tn, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, 1.f, h->Xe32, N, N, h->Wf, ld,
+                             st);
       TRY(gemm_ee(h, h->Hee, Yce, h->rb, N, st));                       // H^ee Y_e
       launch_grp_rows(h->n_gitems, h->gitems, h->ec_rowptr, h->ec_col, h->hec32, Yc, ld, h->gpart, N, st);
       launch_grp_reduce(nE, h->f_it0, h->f_it1, h->f_slot, h->gpart, N, 1.0, h->rb, N, 1.0, We, N, st);
@@ -625,7 +626,8 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
       launch_grp_reduce(nE, h->f_it0, h->f_it1, h->f_slot, h->gpart, N, -1.0, We, N, 1.0, h->rb, N, st);
       TRY(gemm_ee(h, h->Sinv, h->rb, h->xe, N, st));
       launch_f64_to_f32_rows(nE64, h->xe, N, h->Xe32, N, N, st);
-      launch_spmm_nodes_f32(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->mecT32, -1.f, h->Xe32, N, h->Wf, ld, N, st);
+      launch_coup_cols_chunk(h->n_tn, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, -1.f, h->Xe32, N, N, h->Wf,
+                             ld, st);
       CKL();
     }
   }
@@ -1147,7 +1149,7 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
       // function groups sharing one support: consecutive functions of one atom
       // with one cutoff and identical row patterns (at most grp_kmax() each),
       // cut into items of GRP_SEG nodes for the many-function mixed coupling
-      constexpr int GRP_SEG = 2048;
+      constexpr int GRP_SEG = 1024;
       std::vector<int4> items;
       std::vector<int32_t> it0(s.nE), it1(s.nE), slot(s.nE);
       int a = 0;
@@ -1637,14 +1639,37 @@ int64_t image_panel_rows(const efe_handle* h, int64_t rows, int64_t bytes_per_ro
 // tensor-core products when enabled (A sliced in row panels whose digit image
 // fits the budget; K in exact groups of 144 inside the kernel), FP64 DFMA
 // otherwise.
+int gemm_tall_ld(efe_handle* h, int64_t rows, int K, int Nc, const double* A, int64_t lda, const double* B,
+                 int64_t ldb, double* C, int64_t ldc, cudaStream_t st);
+
 int gemm_tall(efe_handle* h, int64_t rows, int K, int Nc, const double* A, int64_t lda, const double* B, double* C,
               int64_t ldc, cudaStream_t st) {
+  return gemm_tall_ld(h, rows, K, Nc, A, lda, B, Nc, C, ldc, st);
+}
+
+// C = A R for an upper-triangular R (N x N, ld N): column panels of C need only
+// the leading rows of R, so each panel is a tall product with K = its last
+// column + 1 (about 0.6 of the full product's work at N ~ 2000)
+int gemm_tall_upper(efe_handle* h, int64_t rows, int N, const double* A, int64_t lda, const double* R, double* C,
+                    int64_t ldc, cudaStream_t st) {
+  constexpr int CPW = 384;   // four 96-column tiles of the tensor-core product
+  if (N <= CPW) return gemm_tall(h, rows, N, N, A, lda, R, C, ldc, st);
+  for (int c0 = 0; c0 < N; c0 += CPW) {
+    const int c1 = std::min(N, c0 + CPW);
+    TRY(gemm_tall_ld(h, rows, c1, c1 - c0, A, lda, R + c0, N, C + c0, ldc, st));
+  }
+  return EFE_OK;
+}
+
+// C = A B, B: K x Nc with leading dimension ldb
+int gemm_tall_ld(efe_handle* h, int64_t rows, int K, int Nc, const double* A, int64_t lda, const double* B,
+                 int64_t ldb, double* C, int64_t ldc, cudaStream_t st) {
   if (h->fp64_engine == 1) {
     launch_oz_rowexp(A, lda, rows, K, h->oz_aexp, st);
-    launch_oz_colexp(B, Nc, K, Nc, h->oz_bexp, st);
+    launch_oz_colexp(B, ldb, K, Nc, h->oz_bexp, st);
     const int64_t nchk = (K + 15) / 16;
     TRY(oz_img_buf(h, 1, oz_img_cols_bytes(nchk, Nc)));
-    launch_oz_img_cols(B, Nc, K, Nc, h->oz_bexp, nchk, h->oz_img[1], st);
+    launch_oz_img_cols(B, ldb, K, Nc, h->oz_bexp, nchk, h->oz_img[1], st);
     const int64_t pr = image_panel_rows(h, rows, oz_img_rows_bytes(128, K) / 128, 128);
     TRY(oz_img_buf(h, 0, oz_img_rows_bytes(pr, K)));
     for (int64_t r0 = 0; r0 < rows; r0 += pr) {
@@ -1654,12 +1679,12 @@ int gemm_tall(efe_handle* h, int64_t rows, int K, int Nc, const double* A, int64
       launch_oz_img_rows(A + r0 * lda, lda, n, K, h->oz_aexp + r0, h->oz_img[0], st);
       int slot;
       TRY(timed_begin(h, st, &slot, 1));
-      launch_oz_rows(A + r0 * lda, lda, n, K, h->oz_aexp + r0, B, Nc, h->oz_bexp, C + r0 * ldc, ldc, Nc, tc_grid(h),
+      launch_oz_rows(A + r0 * lda, lda, n, K, h->oz_aexp + r0, B, ldb, h->oz_bexp, C + r0 * ldc, ldc, Nc, tc_grid(h),
                      h->info + 4, st, h->oz_img[0], h->oz_img[1], h->opt_test_stall);
       TRY(timed_end(h, st, slot, 2.0 * (double)n * K * Nc, 1));
     }
   } else {
-    launch_gemm_nn(rows, Nc, K, 1.0, A, lda, B, Nc, 0.0, C, ldc, st);
+    launch_gemm_nn(rows, Nc, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, st);
   }
   CKL();
   return EFE_OK;
@@ -1847,7 +1872,9 @@ int sym_eig_blocked(efe_handle* h, const double* C, int N, double* V, double* w,
     C64 = C2;
   }
   // FP64 stage: on the nearly diagonal C2, or on C itself if the FP32 stage failed
-  const int r64 = block_jacobi<double>(C64, N, N, C64 == C ? V : V2, N, w, C64 == C ? 60 : 20, 1e-28, h->dsc, st,
+  // off-diagonal Frobenius norm <= 1e-13 of the total: eigenvalue errors of
+  // order 1e-26 relative, far below FP64 rounding of the projected matrix
+  const int r64 = block_jacobi<double>(C64, N, N, C64 == C ? V : V2, N, w, C64 == C ? 60 : 20, 1e-26, h->dsc, st,
                                        &ratio);
   if (r64 < 0) {
     h->err = "block Jacobi (FP64 stage): CUDA error";
@@ -1957,14 +1984,14 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
     }
     TRY(trinv_lower(h, G, N, Linv, st));
     launch_transpose(Linv, N, N, Rinv, N, st);
-    TRY(gemm_tall(h, R, N, N, X, ldx, Rinv, Q, N, st));
+    TRY(gemm_tall_upper(h, R, N, X, ldx, Rinv, Q, N, st));
     launch_copy_rows(R, Q, N, X, ldx, N, st);
     h->chol_shifted++;
     TRY(gram_chol(ok));
   }
   TRY(trinv_lower(h, G, N, Linv, st));
   launch_transpose(Linv, N, N, Rinv, N, st);
-  TRY(gemm_tall(h, R, N, N, X, ldx, Rinv, Q, N, st));
+  TRY(gemm_tall_upper(h, R, N, X, ldx, Rinv, Q, N, st));
   // projections H_p = Q^T H Q, M_p = Q^T M Q
   const bool whole = h->whole_rr && h->B2 != nullptr;
   if (whole) {
@@ -1977,8 +2004,9 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
     launch_symmetrize(Mp, N, N, st);
   } else {
     // two column panels [0, n1) and [n1, N): H Q_p and M Q_p side by side in W;
-    // the panel's block column of H_p up to its last row (the upper triangle and
-    // the diagonal block), then the lower triangle mirrored
+    // the panel's block column of H_p above its diagonal block in full, the
+    // (symmetric) diagonal block by its upper tiles, then the lower triangle
+    // mirrored
     const int n1 = N / 2;
     for (int pnl = 0; pnl < 2; ++pnl) {
       const int c0 = pnl == 0 ? 0 : n1, c1 = pnl == 0 ? n1 : N, w = c1 - c0;
@@ -1986,8 +2014,12 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
       double *HQp = h->W, *MQp = h->W + R * w;
       TRY(apply_H_impl(h, Q + c0, N, w, HQp, w, st));
       TRY(apply_M_impl(h, Q + c0, N, w, MQp, w, st));
-      TRY(gemm_gram(h, R, c1, w, Q, N, HQp, w, Hp + c0, N, false, st));
-      TRY(gemm_gram(h, R, c1, w, Q, N, MQp, w, Mp + c0, N, false, st));
+      if (c0 > 0) {
+        TRY(gemm_gram(h, R, c0, w, Q, N, HQp, w, Hp + c0, N, false, st));
+        TRY(gemm_gram(h, R, c0, w, Q, N, MQp, w, Mp + c0, N, false, st));
+      }
+      TRY(gemm_gram(h, R, w, w, Q + c0, N, HQp, w, Hp + (int64_t)c0 * N + c0, N, true, st));
+      TRY(gemm_gram(h, R, w, w, Q + c0, N, MQp, w, Mp + (int64_t)c0 * N + c0, N, true, st));
     }
     launch_mirror_upper(Hp, N, N, st);
     launch_mirror_upper(Mp, N, N, st);

@@ -215,33 +215,37 @@ constexpr int GRP_KMAX = 8;
 constexpr int GRP_CHUNK = 64;
 constexpr int GRP_CT = 128;   // columns per CTA (one per thread)
 
-__global__ void __launch_bounds__(GRP_CT) k_grp_rows(const int4* __restrict__ items, const int64_t* __restrict__ ec_ptr,
+__global__ void __launch_bounds__(GRP_CT, 8) k_grp_rows(const int4* __restrict__ items, const int64_t* __restrict__ ec_ptr,
                                                     const int32_t* __restrict__ ec_col, const float* __restrict__ coef,
                                                     const float* __restrict__ Xc, int64_t ldx, double* __restrict__ part,
                                                     int N) {
   __shared__ int64_t nd[GRP_CHUNK];
   __shared__ float cf[GRP_KMAX][GRP_CHUNK];
+  __shared__ int64_t rowp[GRP_KMAX];
   const int4 it = items[blockIdx.x];   // first function, functions, node positions [j0, j1)
   const int f0 = it.x, kg = it.y, j0 = it.z, j1 = it.w;
   const int c = blockIdx.y * GRP_CT + threadIdx.x;
-  const int64_t base = ec_ptr[f0];
+  if (threadIdx.x < kg) rowp[threadIdx.x] = ec_ptr[f0 + threadIdx.x];
   double acc[GRP_KMAX];
 #pragma unroll
   for (int k = 0; k < GRP_KMAX; ++k) acc[k] = 0.0;
   for (int j = j0; j < j1; j += GRP_CHUNK) {
     const int n = min(GRP_CHUNK, j1 - j);
     __syncthreads();
-    for (int t = threadIdx.x; t < n; t += GRP_CT) nd[t] = ec_col[base + j + t];
-    for (int t = threadIdx.x; t < kg * GRP_CHUNK; t += GRP_CT) {
+    const int64_t base = rowp[0];
+    if (threadIdx.x < n) nd[threadIdx.x] = ec_col[base + j + threadIdx.x];
+#pragma unroll
+    for (int u = 0; u < GRP_KMAX * GRP_CHUNK / GRP_CT; ++u) {
+      const int t = threadIdx.x + u * GRP_CT;
       const int k = t / GRP_CHUNK, jj = t % GRP_CHUNK;
-      cf[k][jj] = jj < n ? coef[ec_ptr[f0 + k] + j + jj] : 0.f;
+      if (k < kg) cf[k][jj] = jj < n ? coef[rowp[k] + j + jj] : 0.f;
     }
     __syncthreads();
     if (c < N) {
       float s[GRP_KMAX];
 #pragma unroll
       for (int k = 0; k < GRP_KMAX; ++k) s[k] = 0.f;
-#pragma unroll 8
+#pragma unroll 16
       for (int jj = 0; jj < n; ++jj) {
         const float x = Xc[nd[jj] * ldx + c];
 #pragma unroll
@@ -254,7 +258,9 @@ __global__ void __launch_bounds__(GRP_CT) k_grp_rows(const int4* __restrict__ it
   }
   if (c < N) {
     double* o = part + (int64_t)blockIdx.x * GRP_KMAX * N + c;
-    for (int k = 0; k < kg; ++k) o[(int64_t)k * N] = acc[k];
+#pragma unroll
+    for (int k = 0; k < GRP_KMAX; ++k)
+      if (k < kg) o[(int64_t)k * N] = acc[k];
   }
 }
 
@@ -623,6 +629,66 @@ __global__ void __launch_bounds__(256) k_coup_reduce(int nb, int nE, int N, cons
 // Columns product: W[g_u][c] += sgn * sum_slot tile[slot][u] * Xe[f(slot)][c]
 // (Xe staged in shared memory as FP32, rows padded to four floats), same block
 // tiles and CTA partition as the rows product.
+// Columns product for many enrichment functions, over the node blocks of the
+// dense tiles: a CTA takes one block of CPB consecutive pattern nodes and one
+// chunk of GRP_CT columns, stages the block's (slots x CPB) tile and the X_e
+// rows of its slots (FP32) in shared memory -- each X_e row is read once per
+// block instead of once per node -- and adds sgn * tile^T X_e into the block's
+// W rows (FP32 products and sums over the block's functions).
+__global__ void __launch_bounds__(GRP_CT) k_coup_cols_chunk(int64_t n_tn, const int32_t* __restrict__ t_nodes,
+                                                           const int64_t* __restrict__ slot_off,
+                                                           const int32_t* __restrict__ slots,
+                                                           const float* __restrict__ tile, float sgn,
+                                                           const float* __restrict__ Xe, int64_t ldxe, int N,
+                                                           float* __restrict__ W, int64_t ldw) {
+  __shared__ __align__(16) float T[CPF][CPB];
+  __shared__ float Xs[CPF][GRP_CT];
+  __shared__ int64_t nd[CPB];
+  const int64_t b = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int c = blockIdx.y * GRP_CT + tid;
+  const int64_t r0 = b * CPB;
+  const int nb = (int)min((int64_t)CPB, n_tn - r0);
+  if (tid < nb) nd[tid] = t_nodes[r0 + tid];
+  float acc[CPB];
+#pragma unroll
+  for (int i = 0; i < CPB; ++i) acc[i] = 0.f;
+  const int64_t s0 = slot_off[b], s1 = slot_off[b + 1];
+  for (int64_t sp = s0; sp < s1; sp += CPF) {
+    const int nf = (int)min((int64_t)CPF, s1 - sp);
+    __syncthreads();
+    // independent loads, several in flight per thread
+#pragma unroll 4
+    for (int i = tid; i < nf * CPB; i += GRP_CT) T[i / CPB][i % CPB] = tile[sp * CPB + i];
+#pragma unroll 8
+    for (int k = 0; k < nf; ++k) Xs[k][tid] = c < N ? Xe[(int64_t)slots[sp + k] * ldxe + c] : 0.f;
+    __syncthreads();
+    for (int k = 0; k < nf; ++k) {
+      const float x = Xs[k][tid];
+      const float4* t4 = reinterpret_cast<const float4*>(T[k]);
+#pragma unroll
+      for (int i4 = 0; i4 < CPB / 4; ++i4) {
+        const float4 tv = t4[i4];
+        acc[4 * i4] = fmaf(tv.x, x, acc[4 * i4]);
+        acc[4 * i4 + 1] = fmaf(tv.y, x, acc[4 * i4 + 1]);
+        acc[4 * i4 + 2] = fmaf(tv.z, x, acc[4 * i4 + 2]);
+        acc[4 * i4 + 3] = fmaf(tv.w, x, acc[4 * i4 + 3]);
+      }
+    }
+  }
+  if (c < N) {
+    // all of the block's W values are loaded before any is stored (independent
+    // loads in flight together; the compiler cannot reorder loads past stores to
+    // rows it cannot prove distinct)
+    float wv[CPB];
+#pragma unroll
+    for (int i = 0; i < CPB; ++i) wv[i] = i < nb ? W[nd[i] * ldw + c] : 0.f;
+#pragma unroll
+    for (int i = 0; i < CPB; ++i)
+      if (i < nb) W[nd[i] * ldw + c] = fmaf(sgn, acc[i], wv[i]);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, const int64_t* __restrict__ cta_blk,
                                                    const int32_t* __restrict__ t_nodes,
@@ -1559,6 +1625,16 @@ void launch_grp_reduce(int nE, const int32_t* f_it0, const int32_t* f_it1, const
   if (nE <= 0 || N <= 0) return;
   k_grp_reduce<<<grid1((int64_t)nE * N, 256), 256, 0, st>>>(nE, f_it0, f_it1, f_slot, part, N, sgn, base, ldb, alpha,
                                                           out, ldo);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_coup_cols_chunk(int64_t n_tn, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
+                            const float* tile, float sgn, const float* Xe, int64_t ldxe, int N, float* W, int64_t ldw,
+                            cudaStream_t st) {
+  const int64_t nblk = (n_tn + CPB - 1) / CPB;
+  if (nblk <= 0 || N <= 0) return;
+  dim3 g((unsigned)nblk, (unsigned)((N + GRP_CT - 1) / GRP_CT));
+  k_coup_cols_chunk<<<g, GRP_CT, 0, st>>>(n_tn, t_nodes, slot_off, slots, tile, sgn, Xe, ldxe, N, W, ldw);
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 

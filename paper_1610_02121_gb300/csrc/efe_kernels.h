@@ -77,6 +77,10 @@ void launch_grp_rows(int n_items, const int4* items, const int64_t* ec_ptr, cons
 void launch_grp_reduce(int nE, const int32_t* f_it0, const int32_t* f_it1, const int32_t* f_slot, const double* part,
                        int N, double sgn, const double* base, int64_t ldb, double alpha, double* out, int64_t ldo,
                        cudaStream_t st);
+// columns product over the dense tiles' node blocks (X_e rows staged once per block), FP32
+void launch_coup_cols_chunk(int64_t n_tn, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
+                            const float* tile, float sgn, const float* Xe, int64_t ldxe, int N, float* W, int64_t ldw,
+                            cudaStream_t st);
 // columns product, node-major, FP32 (Xe: FP32 rows, ldxe)
 void launch_spmm_nodes_f32(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
                            const float* val, float sgn, const float* Xe, int64_t ldxe, float* out, int64_t ldo, int N,

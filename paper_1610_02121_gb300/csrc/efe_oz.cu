@@ -578,6 +578,92 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         Er = live ? g.aexp[row] : 0;
         orow = live ? g.part + ((int64_t)it.seg * g.Na + row) * g.N + c0 : nullptr;
       }
+      if (img_only) {
+        // Both operands pre-sliced (ROWS, GRAM): every K group's sum is added
+        // into FP32 (hi, lo) pairs held in registers (error-free two-sum, then a
+        // renormalisation: about 48 bits), so the TMEM accumulators are released
+        // as soon as they are read and the next group's MMAs run while this
+        // thread does its arithmetic; the FP64 result is formed and written once
+        // per item.  Twelve epilogue warps: at most four 8-column blocks a thread.
+        constexpr int MAXB = 4;
+        float hi[MAXB][8], lo[MAXB][8];
+        bool stop = false;
+        for (int grp = 0; grp < ngrp; ++grp) {
+          const int64_t gc = t * ngrp + grp;
+          if (!bar_wait(accf, (uint32_t)(gc & 1))) {
+            *abort_flag = 1;
+            atomicExch(g.err, 1);
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < MAXB; ++j) {
+            const int cb = 8 * part + 8 * nparts * j;
+            if (cb >= ncol) break;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {   // four columns at a time (fewer live registers)
+              uint32_t v[OZ_NACC][4];
+#pragma unroll
+              for (int a = 0; a < OZ_NACC; ++a)
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3])
+                             : "r"(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * OZ_TW + cb + 4 * hh))
+                             : "memory");
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                const int q = 4 * hh + qq;
+                float s1, e1, s2, e2, s3, e3;
+                two_sum(__uint_as_float(v[0][qq]), __uint_as_float(v[1][qq]), s1, e1);
+                two_sum(s1, __uint_as_float(v[2][qq]), s2, e2);
+                two_sum(s2, __uint_as_float(v[3][qq]), s3, e3);
+                const float lg = ((__uint_as_float(v[4][qq]) + e3) + e2) + e1;
+                if (grp == 0) {
+                  hi[j][q] = s3;
+                  lo[j][q] = lg;
+                } else {
+                  float sh, eh;
+                  two_sum(hi[j][q], s3, sh, eh);
+                  const float l = (lo[j][q] + lg) + eh;
+                  hi[j][q] = sh + l;
+                  lo[j][q] = l - (hi[j][q] - sh);
+                }
+              }
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          bar_arrive(acce);
+        }
+        if (stop) break;
+        const unsigned long long orow_u = (unsigned long long)orow;
+#pragma unroll
+        for (int j = 0; j < MAXB; ++j) {
+          const int cb = 8 * part + 8 * nparts * j;
+          if (cb >= ncol) break;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int n = cb + q;
+            double val = 0.0;
+            if (live && n < ncol) {
+              const int k2 = Er + g.fexp[c0 + n] - 14;
+              val = f32_scaled(hi[j][q], k2) + f32_scaled(lo[j][q], k2);
+            }
+            stg[lane * 9 + q] = val;
+          }
+          __syncwarp();
+          // row rr = 4 jj + lane / 8 of this warp, column cb + lane % 8
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int rr = 4 * jj + (lane >> 3), cq = lane & 7;
+            double* rp = (double*)__shfl_sync(0xffffffffu, orow_u, rr);
+            const int lv = __shfl_sync(0xffffffffu, (int)live, rr);
+            if (lv && cb + cq < ncol) rp[cb + cq] = stg[rr * 9 + cq];
+          }
+          __syncwarp();
+        }
+        continue;
+      }
       // the row's output segment is pulled towards L2 while the MMAs run
       if (live && (g.mode == 0 || g.mode == 2))
         for (int cb = 8 * part; cb < ncol; cb += 8 * nparts) asm volatile("prefetch.L2 [%0];" ::"l"(orow + cb));

@@ -452,11 +452,12 @@ def test_rayleigh_ritz_panels_and_blocked_dense(tiny_pair, engine, N):
 
 
 def test_tall_products_long_K_match_dfma(tiny_pair):
-    """The FP64 engine's tall product with K = N = 300 (three exact groups of
-    144, 144 and 12) and 256-row image panels gives the DFMA path's Ritz values
-    and vectors to FP64 rounding."""
+    """The FP64 engine's tall products with K = N = 400 (three exact groups of
+    144, 144 and 112; the triangular X R^-1 in column panels of 384 and 16) and
+    256-row image panels give the DFMA path's Ritz values to FP64 rounding, and
+    both match the oracle."""
     d, G = tiny_pair
-    N = 300
+    N = 400
     X = to_dev(W.random_block(d.system, N, seed=93))
     G.set_fp64_engine("dfma")
     Xa = X.clone()
