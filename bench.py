@@ -67,7 +67,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-scf", action="store_true")
-    p.add_argument("--no-converged", action="store_true", help="skip the time-to-converged-SCF comparison")
+    p.add_argument("--converged", default="co", choices=["co", "si16", "none"],
+                   help="system of the time-to-converged-SCF comparison (plain FP64 against mixed)")
     p.add_argument("--batch", action="store_true", help="also time the batched small systems (CUDA graph)")
     p.add_argument("--scf-steps", type=int, default=None, help="timed SCF iterations (default: 1 for si280, 3)")
     p.add_argument("--workload", default="si280", choices=sorted(WORKLOADS))
@@ -251,49 +252,63 @@ def batch_section(P, torch, stream, n_sys=8, m=20, steps=3):
 
 
 # ------------------------------------------------------------------------- converged SCF
-def converged_scf_section(P, torch, prec, tol_e=1e-7, tol_rho=2e-5, max_it=150):
+CONVERGED = {
+    # name: (generator, N, m, Anderson mixing, stages, atoms text)
+    "co": (W.carbon_monoxide, 12, 24, 0.5, 5, "C-O pair (Z = 6, 8; 14 electrons; 49,005 nodes, 10 enrichment functions)"),
+    "si16": (W.si_cluster, 135, 40, 0.2, 8, "si16: 16-atom Si-like cluster (224 electrons; 1.52M nodes, 80 enrichment "
+                                             "functions)"),
+}
+
+
+def converged_scf_section(P, torch, prec, which="co", tol_e_atom=1e-7, tol_rho=3e-5, max_it=150):
     """Time to a converged SCF (Sec. V), plain FP64 (DFMA) against the mixed mode
     (tensor-core filter, FP64 tail degrees, FP64-grade Rayleigh-Ritz on the
-    tensor cores), on the C-O pair (14 electrons, 49,005 nodes, Slater
-    enrichment): same start (atom-centred Gaussian clouds of charge Z), one
-    degree-24 filter pass per iteration, Anderson (5 stages, 0.5), T = 500 K;
-    converged when |dE| < tol_e and ||rho_out - rho_in|| < tol_rho (the mixed
-    mode's FP32-grade orbital values put its density noise near 1e-5)."""
-    s = W.carbon_monoxide()
+    tensor cores): same start (the density of the Rayleigh-Ritz-rotated start
+    block with Fermi occupations), one degree-m filter pass per iteration,
+    Anderson mixing, T = 500 K; converged when |dE| < tol_e_atom per atom and
+    ||rho_out - rho_in|| < tol_rho (the mixed mode's FP32-grade orbital values
+    put its density noise near 1e-5)."""
+    gen, N, m, beta, n_hist, text = CONVERGED[which]
+    s = gen()
     G = P.System(s)
     G.set_potential_analytic()
-    q = G.qpoints().cpu().numpy()
-    pts, w = q[:, :3], q[:, 3]
-    rho0 = np.zeros(len(w))
-    for R, z in zip(s["atoms"], s["Z"]):
-        g = np.exp(-np.sum((pts - R[None, :]) ** 2, axis=1) / 2.0)
-        rho0 += z * g / np.sum(w * g)
     ne = float(np.sum(s["Z"]))
+    tol_e = tol_e_atom * len(s["Z"])
+    X0 = torch.from_numpy(W.initial_block(s, N, seed=1)).cuda()
+    G.set_fp64_engine("dfma")
+    eps0, _ = G.rayleigh_ritz(X0, residuals=False)
+    occ0, _ = P._lib.fermi(eps0, ne, 500 * P._lib.KB_HA_PER_K)
+    rho0 = G.density(X0, occ0)
+    w = G.qpoints()[:, 3]
+    rho0 *= ne / float((w * rho0).sum())
     out = {}
     for label, p, eng in (("fp64", "fp64", "dfma"), ("mixed", prec, "tensor")):
         G.set_fp64_engine(eng)
-        X = torch.from_numpy(W.initial_block(s, 12, seed=1)).cuda()
-        rho_in = torch.from_numpy(rho0).cuda()
+        X = X0.clone()
+        rho_in = rho0.clone()
         rho_out = torch.empty_like(rho_in)
-        G.scf_init(ne)
+        G.scf_init(ne, beta=beta, n_hist=n_hist)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e_prev, r, it = None, None, 0
         for it in range(1, max_it + 1):
-            r = G.scf_step(X, rho_in, rho_out, 24, precision=p, fp64_tail=0 if p == "fp64" else 2)
+            r = G.scf_step(X, rho_in, rho_out, m, precision=p, fp64_tail=0 if p == "fp64" else 2)
             if e_prev is not None and abs(r["total"] - e_prev) < tol_e and r["drho"] < tol_rho:
                 break
             e_prev = r["total"]
         torch.cuda.synchronize()
-        out[label] = {"wall_s": time.perf_counter() - t0, "iterations": it, "total_energy_Ha": r["total"],
-                      "drho": r["drho"], "eig_occupied_Ha": [float(x) for x in r["eig"][:7]],
-                      "precision": p, "fp64_engine": eng}
+        nocc = int(np.sum(r["occ"] > 0.5))
+        out[label] = {"wall_s": time.perf_counter() - t0, "iterations": it, "converged": it < max_it,
+                      "total_energy_Ha": r["total"], "drho": r["drho"],
+                      "eig_head_Ha": [float(x) for x in r["eig"][:5]],
+                      "homo_Ha": float(r["eig"][max(nocc - 1, 0)]), "precision": p, "fp64_engine": eng}
     G.close()
-    return {"system": "C-O pair (Z = 6, 8; 14 electrons; 49,005 nodes, 10 enrichment functions), N = 12, m = 24",
-            "criterion": f"|dE| < {tol_e:g} Ha and ||rho_out - rho_in|| < {tol_rho:g}",
+    na = len(s["Z"])
+    return {"system": f"{text}, N = {N}, m = {m}, Anderson {n_hist} stages, mixing {beta}",
+            "criterion": f"|dE| < {tol_e_atom:g} Ha per atom and ||rho_out - rho_in|| < {tol_rho:g}",
             "fp64": out["fp64"], "mixed": out["mixed"],
             "speedup_mixed_vs_fp64": out["fp64"]["wall_s"] / out["mixed"]["wall_s"],
-            "abs_dE_per_atom_Ha": abs(out["mixed"]["total_energy_Ha"] - out["fp64"]["total_energy_Ha"]) / 2.0}
+            "abs_dE_per_atom_Ha": abs(out["mixed"]["total_energy_Ha"] - out["fp64"]["total_energy_Ha"]) / na}
 
 
 # ------------------------------------------------------------------------- reference arm
@@ -373,6 +388,8 @@ def main():
     X = initial_block(torch, system, G, N)
     v0 = torch.from_numpy(W.lanczos_start(system)).cuda()
     eps_start, _ = G.rayleigh_ritz(X, residuals=False)
+    # column tile of the tensor-core cell kernel for this system and N (autotuner)
+    tile, tile_ms = G.autotune(N, prec) if prec in ("tf32", "tf32x3") else (None, None)
     # the start of every leg, kept in pinned host memory (also the e2e input)
     X_host = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
     X_host.copy_(X)
@@ -474,7 +491,8 @@ def main():
                        "fp64_tail": args.fp64_tail if prec != "fp64" else 0, "fp64_engine": args.fp64_engine,
                        "l2": "vector blocks and cell matrices exceed the 129 MB L2 (no flush needed)",
                        "step": "Lanczos bound (10) + degree-m filter + CholQR + Rayleigh-Ritz (Ritz values)",
-                       "filter_flops_per_step": flops_step, "setup_s": t_setup},
+                       "filter_flops_per_step": flops_step, "setup_s": t_setup,
+                       "cell_tile": tile, "cell_tile_ms": None if tile_ms is None else [float(x) for x in tile_ms]},
             "s_per_step": ms * 1e-3, "gpu_launches": launches, "roofline": roof}
     if roof_other is not None:
         line["roofline_other_kernel"] = roof_other
@@ -561,8 +579,8 @@ def main():
                        "start": "density of the Rayleigh-Ritz-rotated start block, renormalised to N_e"}
         del rho_in, rho_out
     # time to a converged SCF, plain FP64 against the mixed mode (small multi-atom system)
-    if not args.no_converged and rank == 0:
-        line["converged_scf"] = converged_scf_section(P, torch, prec)
+    if args.converged != "none" and rank == 0:
+        line["converged_scf"] = converged_scf_section(P, torch, prec, args.converged)
     # many small systems (1-6 atoms, Z in {1, 6, 8, 14}, own graded meshes, N = ceil(0.6 N_e) + 8):
     # one ChFSI filter step of every system as one CUDA graph vs the same steps launched
     # one system after another; column tiles of the cell kernel picked by the autotuner

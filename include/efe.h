@@ -55,7 +55,8 @@ extern "C" {
 #define EFE_PREC_FP64 0    /* every product in FP64 */
 #define EFE_PREC_FP32 1    /* classical block in FP32, cell GEMMs FP32 (SIMT FFMA), FP32 accumulate */
 #define EFE_PREC_TF32 2    /* classical block in FP32, cell GEMMs on tcgen05 kind::tf32 (one pass), FP32 accumulate */
-#define EFE_PREC_BF16 3    /* reserved: classical block in BF16, tcgen05 kind::f16 (not available in this build) */
+#define EFE_PREC_BF16 3    /* classical block in FP32 storage, cell GEMMs on tcgen05 kind::f16 with BF16 operands
+                              (rounded to nearest in shared memory), FP32 accumulate */
 #define EFE_PREC_TF32X3 4  /* classical block in FP32, cell GEMMs on tcgen05 kind::tf32 with the 3-term operand
                               split (a1 b1 + a1 b2 + a2 b1): FP32-grade products, FP32 accumulate */
 
@@ -459,8 +460,8 @@ int efe_adam(void* p, const void* g, void* m, void* v, int64_t n, double lr, dou
  * Autotuner and batched systems
  * ------------------------------------------------------------------------ */
 /* Times the tensor-core cell kernel's column tiles (64, 96, 160) on one full
- * cell apply for N columns in the given mixed precision (EFE_PREC_TF32 or
- * EFE_PREC_TF32X3) and keeps the fastest for this handle and N; tile_out: the
+ * cell apply for N columns in the given mixed precision (EFE_PREC_TF32,
+ * EFE_PREC_TF32X3 or EFE_PREC_BF16) and keeps the fastest for this handle and N; tile_out: the
  * choice (host, may be NULL); ms_out: the three times in ms (host, may be NULL).
  * Needs a potential. */
 int efe_autotune(efe_handle* h, int32_t N, int32_t precision, int32_t* tile_out, double* ms_out);

@@ -50,7 +50,7 @@ struct efe_handle {
   double* Hcc = nullptr;
   float* Hcc32 = nullptr;
   float* Aimg32 = nullptr;  // FP32 images of H^cc_e in the tensor-core layout (chunk-major)
-  int tc_mode = 0;          // 1: TF32 tcgen05 cell products, 2: 3-term split TF32 (FP32-grade)
+  int tc_mode = 0;          // 1: TF32 tcgen05 cell products, 2: 3-term split TF32 (FP32-grade), 3: BF16
   int tc_tile = 0, tc_tile_N = 0;  // autotuned column tile of the tensor-core cell kernel for N
   int n_sm = 148;
   int grid_cap = 0;         // test/tuning cap on the persistent tensor-core grids (0: one CTA per SM)
@@ -469,7 +469,7 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
     } else {
       if (tc) {
         if (launch_cell_tc3(h->Aimg32, cl, nc, h->mesh, (const float*)Y, ldy, (float*)Wc, ldw, N,
-                            h->tc_mode == 2, tc_grid(h), h->info + 4, st, h->tc_tile_N == N ? h->tc_tile : 0,
+                            h->tc_mode - 1, tc_grid(h), h->info + 4, st, h->tc_tile_N == N ? h->tc_tile : 0,
                             h->opt_test_stall)) {
           h->err = "tensor-core cell kernel needs 16-byte aligned rows";
           return EFE_ERR_ARG;
@@ -1527,7 +1527,7 @@ static int chfsi_enqueue(efe_handle* h, double* X, int64_t ldx, int32_t N, int32
     return EFE_ERR_ARG;
   }
   if (precision != EFE_PREC_FP64 && precision != EFE_PREC_FP32 && precision != EFE_PREC_TF32 &&
-      precision != EFE_PREC_TF32X3) {
+      precision != EFE_PREC_TF32X3 && precision != EFE_PREC_BF16) {
     h->err = "precision mode not available in this build";
     return EFE_ERR_ARG;
   }
@@ -1543,7 +1543,7 @@ static int chfsi_enqueue(efe_handle* h, double* X, int64_t ldx, int32_t N, int32
   }
   TRY(stage_coefs(h, m, a, b, a0, st, in_graph));
   const int64_t nn = h->n_nodes;
-  h->tc_mode = (precision == EFE_PREC_TF32) ? 1 : (precision == EFE_PREC_TF32X3 ? 2 : 0);
+  h->tc_mode = (precision == EFE_PREC_TF32) ? 1 : (precision == EFE_PREC_TF32X3 ? 2 : (precision == EFE_PREC_BF16 ? 3 : 0));
   CK(cudaMemsetAsync(h->info + 4, 0, sizeof(int), st));
   // Two slots per precision: degree k writes Y_k over Y_{k-2} (the combine is
   // elementwise), degree 1 into the free slot.  FP64 slots: 0 = X (user, ldx),
@@ -2663,7 +2663,8 @@ int efe_adam(void* p, const void* g, void* m, void* v, int64_t n, double lr, dou
 extern "C" {
 
 int efe_autotune(efe_handle* h, int32_t N, int32_t precision, int32_t* tile_out, double* ms_out) {
-  if (!h || N < 1 || (precision != EFE_PREC_TF32 && precision != EFE_PREC_TF32X3)) return EFE_ERR_ARG;
+  if (!h || N < 1 || (precision != EFE_PREC_TF32 && precision != EFE_PREC_TF32X3 && precision != EFE_PREC_BF16))
+    return EFE_ERR_ARG;
   if (!h->potential_set) {
     h->err = "no potential set (call efe_set_potential first)";
     return EFE_ERR_STATE;
@@ -2691,7 +2692,8 @@ int efe_autotune(efe_handle* h, int32_t N, int32_t precision, int32_t* tile_out,
         const int64_t nc = h->colour_off[c + 1] - h->colour_off[c];
         if (nc == 0) continue;
         if (launch_cell_tc3(h->Aimg32, h->colour_cells + h->colour_off[c], nc, h->mesh, h->Yf[0], h->ld32, h->Wf,
-                            h->ld32, N, precision == EFE_PREC_TF32X3, tc_grid(h), h->info + 4, st, tiles[i])) {
+                            h->ld32, N, precision == EFE_PREC_TF32X3 ? 1 : (precision == EFE_PREC_BF16 ? 2 : 0),
+                            tc_grid(h), h->info + 4, st, tiles[i])) {
           h->err = "tensor-core cell kernel needs 16-byte aligned rows";
           return EFE_ERR_ARG;
         }
@@ -2904,7 +2906,7 @@ int efe_batch_chfsi_step(efe_batch* b, double* const* X, const int64_t* ldx, con
   // refresh the staged coefficients (read by the graph's copy nodes), then replay
   for (int i = 0; i < n; ++i) {
     fill_coefs(b->hs[i]->coefh, m, a[i], bnd[i], a0[i]);
-    b->hs[i]->tc_mode = (precision == EFE_PREC_TF32) ? 1 : (precision == EFE_PREC_TF32X3 ? 2 : 0);
+    b->hs[i]->tc_mode = (precision == EFE_PREC_TF32) ? 1 : (precision == EFE_PREC_TF32X3 ? 2 : (precision == EFE_PREC_BF16 ? 3 : 0));
   }
   if (cudaStreamSynchronize(caller) != cudaSuccess || cudaGraphLaunch(b->exec, b->s0) != cudaSuccess) {
     cudaGetLastError();

@@ -21,6 +21,7 @@
 //               scatter into W, arrive on `acc_empty`.
 // Two stages ring the chunks.  Every wait is bounded (about one second); on
 // timeout the CTA records an error, stops issuing, drains and frees its TMEM.
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "efe_kernels.h"
@@ -60,6 +61,24 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 
 __device__ __forceinline__ uint32_t idesc_tf32(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(T3_M >> 4) << 24);
+}
+
+// BF16 operands (kind::f16): FP32 accumulate, BF16 A and B
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(T3_M >> 4) << 24);
+}
+
+// K-major BF16 chunk of 32 K: core matrix 8 rows x 16 B (8 K); LBO = 128 B (next 8 K),
+// SBO = 512 B (next 8 rows)
+__device__ __forceinline__ uint64_t sdesc_bf16(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ uint32_t bmo(int row, int k) {
+  return (uint32_t)(row >> 3) * 512u + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+__device__ __forceinline__ uint16_t bf16r(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
 __device__ __forceinline__ float tf32r(float x) {
@@ -106,6 +125,13 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
       "l"(a), "l"(b), "r"(id), "r"(acc)
       : "memory");
 }
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
                : "memory");
@@ -123,7 +149,8 @@ __device__ __forceinline__ uint32_t cmo(int row, int k) {
   return (uint32_t)(row >> 3) * 1024u + (uint32_t)(k >> 2) * 128u + (uint32_t)(row & 7) * 16u;
 }
 
-template <bool SPLIT, int TW>
+// MODE 0: one TF32 pass; 1: 3-term TF32 split (a1 b1 + a1 b2 + a2 b1); 2: BF16 operands
+template <int MODE, int TW>
 __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restrict__ Ag,
                                                             const int32_t* __restrict__ cells, int64_t ncells,
                                                             MeshDev m, const float* __restrict__ Y, int64_t ldy,
@@ -229,14 +256,24 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
           unsigned char* S = sm + s * T3Layout<TW>::STAGE;
           const uint32_t a1 = su32(S), a2 = a1 + T3Layout<TW>::A, b1 = a1 + 2 * T3Layout<TW>::A, b2 = b1 + T3Layout<TW>::B;
           const uint32_t d = tmem + (uint32_t)(b * 256);
-          const uint32_t id = idesc_tf32(nmma);
+          if (MODE == 2) {
+            // BF16: the A chunk's BF16 copy in the A2 area, B in the B1 area; K = 16 per MMA
+            const uint32_t id = idesc_bf16(nmma);
 #pragma unroll
-          for (int ks = 0; ks < T3_KC / 8; ++ks) {
-            const uint32_t off = (uint32_t)ks * 256u;
-            mma_tf32(d, sdesc(a1 + off), sdesc(b1 + off), id, (kc > 0 || ks > 0) ? 1u : 0u);
-            if (SPLIT) {
-              mma_tf32(d, sdesc(a1 + off), sdesc(b2 + off), id, 1u);
-              mma_tf32(d, sdesc(a2 + off), sdesc(b1 + off), id, 1u);
+            for (int ks = 0; ks < T3_KC / 16; ++ks) {
+              const uint32_t off = (uint32_t)ks * 256u;
+              mma_bf16(d, sdesc_bf16(a2 + off), sdesc_bf16(b1 + off), id, (kc > 0 || ks > 0) ? 1u : 0u);
+            }
+          } else {
+            const uint32_t id = idesc_tf32(nmma);
+#pragma unroll
+            for (int ks = 0; ks < T3_KC / 8; ++ks) {
+              const uint32_t off = (uint32_t)ks * 256u;
+              mma_tf32(d, sdesc(a1 + off), sdesc(b1 + off), id, (kc > 0 || ks > 0) ? 1u : 0u);
+              if (MODE == 1) {
+                mma_tf32(d, sdesc(a1 + off), sdesc(b2 + off), id, 1u);
+                mma_tf32(d, sdesc(a2 + off), sdesc(b1 + off), id, 1u);
+              }
             }
           }
           mma_commit(empty + s);
@@ -269,6 +306,35 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
         unsigned char* B1 = S + 2 * T3Layout<TW>::A;
         unsigned char* B2 = B1 + T3Layout<TW>::B;
         const int nrows = min(T3_KC, NL - kc * T3_KC);
+        if (MODE == 2) {
+          // BF16 copies: the A chunk (FP32 image, 4-wide K core matrices) into the A2
+          // area and the raw rows into the B1 area, both in the 8-wide K layout
+          unsigned char* A2 = S + T3Layout<TW>::A;
+          const float4* a1 = reinterpret_cast<const float4*>(S);
+          for (int v = ct; v < (int)(T3Layout<TW>::A / 16); v += T3_CONV_WARPS * 32) {
+            // 16-byte unit v of the FP32 image: row r, K quad kq (cmo layout)
+            const int rg = v >> 6, kq = (v >> 3) & 7, ri = v & 7;
+            const int r = rg * 8 + ri, k = kq * 4;
+            const float4 x = a1[v];
+            ushort4 h;
+            h.x = bf16r(x.x); h.y = bf16r(x.y); h.z = bf16r(x.z); h.w = bf16r(x.w);
+            *reinterpret_cast<ushort4*>(A2 + bmo(r, k)) = h;
+          }
+          for (int v = ct; v < nmma * 8; v += T3_CONV_WARPS * 32) {
+            const int n = v % nmma, kq = v / nmma;
+            ushort4 h;
+            uint16_t* hp = reinterpret_cast<uint16_t*>(&h);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int kr = kq * 4 + q;
+              hp[q] = bf16r((kr < nrows && n < ncol) ? raw[kr * TW + n] : 0.f);
+            }
+            *reinterpret_cast<ushort4*>(B1 + bmo(n, kq * 4)) = h;
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bar_arrive(conv + s);
+          continue;
+        }
         {
           // the A chunk in place: A1 = TF32(A), A2 = TF32(A - A1) (elementwise, any layout)
           float4* a1 = reinterpret_cast<float4*>(S);
@@ -278,7 +344,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
             float4 h4;
             h4.x = tf32r(x.x); h4.y = tf32r(x.y); h4.z = tf32r(x.z); h4.w = tf32r(x.w);
             a1[v] = h4;
-            if (SPLIT) {
+            if (MODE == 1) {
               float4 l4;
               l4.x = tf32r(x.x - h4.x); l4.y = tf32r(x.y - h4.y); l4.z = tf32r(x.z - h4.z); l4.w = tf32r(x.w - h4.w);
               a2[v] = l4;
@@ -296,7 +362,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
           float4 h4, l4;
           h4.x = tf32r(y[0]); h4.y = tf32r(y[1]); h4.z = tf32r(y[2]); h4.w = tf32r(y[3]);
           *reinterpret_cast<float4*>(B1 + cmo(n, kq * 4)) = h4;
-          if (SPLIT) {
+          if (MODE == 1) {
             l4.x = tf32r(y[0] - h4.x); l4.y = tf32r(y[1] - h4.y); l4.z = tf32r(y[2] - h4.z); l4.w = tf32r(y[3] - h4.w);
             *reinterpret_cast<float4*>(B2 + cmo(n, kq * 4)) = l4;
           }
@@ -425,19 +491,21 @@ void launch_build_aimg(const double* Hcc, int64_t n_cell, float* A, cudaStream_t
 namespace {
 template <int TW>
 void tc3_launch(const float* A, const int32_t* cells, int64_t ncells, const MeshDev& m,
-                const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
+                const float* Y, int64_t ldy, float* W, int64_t ldw, int N, int mode, int n_sm, int* err,
                 cudaStream_t st, int stall) {
   const int ntiles = (N + TW - 1) / TW;
   const int64_t items = ncells * ntiles;
   const unsigned grid = (unsigned)(items < n_sm ? items : n_sm);
   const size_t smem = T3Layout<TW>::TOTAL;
-  if (split) {
-    cudaFuncSetAttribute(k_cell_tc3<true, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cell_tc3<true, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err, stall);
+  if (mode == 1) {
+    cudaFuncSetAttribute(k_cell_tc3<1, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cell_tc3<1, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err, stall);
+  } else if (mode == 2) {
+    cudaFuncSetAttribute(k_cell_tc3<2, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cell_tc3<2, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err, stall);
   } else {
-    cudaFuncSetAttribute(k_cell_tc3<false, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_cell_tc3<false, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err,
-                                                          stall);
+    cudaFuncSetAttribute(k_cell_tc3<0, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_cell_tc3<0, TW><<<grid, T3_THREADS, smem, st>>>(A, cells, ncells, m, Y, ldy, W, ldw, N, ntiles, err, stall);
   }
 }
 }  // namespace
@@ -449,16 +517,16 @@ const int* tc3_tiles(int* count) {
 }
 
 int launch_cell_tc3(const float* A, const int32_t* cells, int64_t ncells, const MeshDev& m,
-                    const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
+                    const float* Y, int64_t ldy, float* W, int64_t ldw, int N, int mode, int n_sm, int* err,
                     cudaStream_t st, int tile, int stall) {
   if (ncells <= 0 || N <= 0) return 0;
   if ((ldy & 3) || (ldw & 3)) return 1;
   if (tile == 64)
-    tc3_launch<64>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st, stall);
+    tc3_launch<64>(A, cells, ncells, m, Y, ldy, W, ldw, N, mode, n_sm, err, st, stall);
   else if (tile == 96)
-    tc3_launch<96>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st, stall);
+    tc3_launch<96>(A, cells, ncells, m, Y, ldy, W, ldw, N, mode, n_sm, err, st, stall);
   else if (tile == 160 || tile == 0)
-    tc3_launch<160>(A, cells, ncells, m, Y, ldy, W, ldw, N, split, n_sm, err, st, stall);
+    tc3_launch<160>(A, cells, ncells, m, Y, ldy, W, ldw, N, mode, n_sm, err, st, stall);
   else
     return 1;
   g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -124,8 +124,9 @@ void launch_build_aimg(const double* Hcc, int64_t n_cell, float* A, cudaStream_t
 // tile: column tile width (64, 96 or 160; 0 = default 160)
 // stall (tests only): the MMA warp first waits on a barrier nothing completes, so the
 // bounded wait runs out and the launch takes its abort path
+// mode 0: one TF32 pass; 1: 3-term TF32 split (FP32-grade); 2: BF16 operands (FP32 accumulate)
 int launch_cell_tc3(const float* A, const int32_t* cells, int64_t ncells, const MeshDev& m,
-                    const float* Y, int64_t ldy, float* W, int64_t ldw, int N, bool split, int n_sm, int* err,
+                    const float* Y, int64_t ldy, float* W, int64_t ldw, int N, int mode, int n_sm, int* err,
                     cudaStream_t st, int tile = 0, int stall = 0);
 const int* tc3_tiles(int* count);
 

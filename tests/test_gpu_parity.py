@@ -205,14 +205,16 @@ def test_hydrogen_config1_converged():
 
 
 @pytest.mark.parametrize("N", [17, 135, 300])
-@pytest.mark.parametrize("prec,tols", [("tf32", [(1, 3e-3), (7, 2e-2)]), ("tf32x3", [(1, 1e-5), (7, 5e-5)])])
+@pytest.mark.parametrize("prec,tols", [("tf32", [(1, 3e-3), (7, 2e-2)]), ("tf32x3", [(1, 1e-5), (7, 5e-5)]),
+                                       ("bf16", [(1, 3e-2)])])
 def test_chfsi_step_tf32_tensor_cores(tiny_pair, N, prec, tols):
     """tcgen05 cell products (FP32 accumulation, FP32 vector storage).  One TF32
     pass: one degree agrees with the FP64 oracle to TF32 accuracy (unit round-off
     2^-11, bound 3e-3 relative), a degree-7 filter to 2e-2.  The 3-term split
     (tf32x3) is FP32-grade: FP32 round-off 6e-8 times the cancellation factor
     ||H|| ||Y|| / ||H Y|| (about 30 here) gives ~2e-6 per degree; bounds 1e-5
-    (one degree) and 5e-5 (seven degrees).  N = 300 spans two
+    (one degree) and 5e-5 (seven degrees).  BF16 operands (kind::f16, unit
+    round-off 2^-8, eight times TF32's): one degree to 3e-2.  N = 300 spans two
     160-column tensor-core tiles with a ragged tail; N = 17 one partial tile."""
     from oracle.chfsi import chebyshev_filter_scaled
     d, G = tiny_pair
@@ -226,11 +228,12 @@ def test_chfsi_step_tf32_tensor_cores(tiny_pair, N, prec, tols):
         assert err < tol, (m, err)
 
 
-@pytest.mark.parametrize("prec,tol,atol", [("tf32", 1e-7, 1e-5), ("tf32x3", 1e-9, 1e-8)])
+@pytest.mark.parametrize("prec,tol,atol", [("tf32", 1e-7, 1e-5), ("tf32x3", 1e-9, 1e-8), ("bf16", 1e-6, 1e-4)])
 def test_chfsi_converges_mixed_tiny(tiny_pair, prec, tol, atol):
     """Mixed precision (tensor-core filter, FP64 tail degrees, FP64 CholQR and
     Rayleigh-Ritz) reaches the dense eigenvalues: within 1e-5 Ha with one TF32
-    pass, within 1e-8 Ha with the FP32-grade 3-term split."""
+    pass, within 1e-8 Ha with the FP32-grade 3-term split, within 1e-4 Ha with
+    BF16 operands."""
     from oracle.chfsi import dense_eigs
     d, G = tiny_pair
     N, m, nconv = 10, 12, 7
@@ -328,7 +331,8 @@ def _mid_bounds(d, X):
     return eps.max(), 1.05 * b, eps.min()
 
 
-@pytest.mark.parametrize("prec,tols", [("tf32", [(1, 6e-3), (7, 4e-2)]), ("tf32x3", [(1, 1e-5), (7, 5e-5)])])
+@pytest.mark.parametrize("prec,tols", [("tf32", [(1, 6e-3), (7, 4e-2)]), ("tf32x3", [(1, 1e-5), (7, 5e-5)]),
+                                       ("bf16", [(1, 6e-2)])])
 def test_tensor_core_cells_many_items_per_cta(mid_pair, prec, tols):
     """k_cell_tc3 capped at 2 CTAs: N = 300 is two 160-column tiles, so each CTA
     walks 8 (cell, tile) items per colour launch; the capped and uncapped
