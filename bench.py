@@ -67,6 +67,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-scf", action="store_true")
+    p.add_argument("--dof-degree", action="store_true",
+                   help="also run the enriched-vs-classical DoF x degree comparison (bare Z = 14 nucleus)")
+    p.add_argument("--heavy-z", action="store_true", help="also run the heavy-Z multi-pass filter case (Z = 79 dimer)")
     p.add_argument("--converged", default="co", choices=["co", "si16", "none"],
                    help="system of the time-to-converged-SCF comparison (plain FP64 against mixed)")
     p.add_argument("--batch", action="store_true", help="also time the batched small systems (CUDA graph)")
@@ -309,6 +312,76 @@ def converged_scf_section(P, torch, prec, which="co", tol_e_atom=1e-7, tol_rho=3
             "fp64": out["fp64"], "mixed": out["mixed"],
             "speedup_mixed_vs_fp64": out["fp64"]["wall_s"] / out["mixed"]["wall_s"],
             "abs_dE_per_atom_Ha": abs(out["mixed"]["total_energy_Ha"] - out["fp64"]["total_energy_Ha"]) / na}
+
+
+# ------------------------------------------------------------------------- DoF x degree, heavy Z
+def dof_degree_section(P, torch, Z=14.0, N=8, nconv=5, tol=1e-7, max_iter=150):
+    """The enriched-vs-classical comparison of Sec. VI.B.1 on a case with a closed
+    form: a bare nucleus of charge Z (the Si-like core; -Z^2/(2n^2): 1s at -98 Ha,
+    n = 2 at -24.5 Ha) in a 20-bohr box.  Enriched: 6^3 uniform cells with the
+    hydrogenic 1s/2s/2p functions, filter degree 20; classical (n_E = 0): graded
+    meshes refined to h_min at the nucleus, the degree scaled by sqrt(b / b_enriched)
+    (the Chebyshev damping depends on the spectral width over the wanted gap).
+    ChFSI in FP64 until the lowest five residuals are < tol; errors of the five
+    lowest eigenvalues against the closed form, DoF (unknowns), degree, filter
+    passes, wall time."""
+    exact = np.array([-Z * Z / 2.0] + [-Z * Z / 8.0] * 4)
+    rows, b_enr = [], None
+    for enriched, h in [(True, None), (False, 0.2), (False, 0.1), (False, 0.05)]:
+        s = W.bare_nucleus(Z=Z, enriched=enriched, h_min=h)
+        G = P.System(s)
+        G.set_potential_analytic()
+        G.set_fp64_engine("dfma")
+        X = torch.from_numpy(W.initial_block(s, N, seed=1)).cuda()
+        v0 = torch.from_numpy(W.lanczos_start(s)).cuda()
+        b = G.upper_bound(v0, 10)
+        if enriched:
+            b_enr = b
+        m = 20 if enriched else int(math.ceil(20 * math.sqrt(b / b_enr)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eps, res, it, _ = G.solve(X, m, tol=tol, max_iter=max_iter, v0=v0, n_conv=nconv)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        dof = int(np.sum(~W.boundary_mask(s))) + G.n_enrich
+        rows.append({"basis": "enriched (hydrogenic 1s/2s/2p)" if enriched else f"classical, h_min {h} bohr",
+                     "dof": dof, "cells": G.n_cells, "upper_bound_Ha": b, "degree": m, "filter_passes": it,
+                     "degree_x_passes": m * it, "wall_s": wall, "max_resid": float(np.max(res[:nconv])),
+                     "max_abs_err_Ha": float(np.max(np.abs(eps[:nconv] - exact)))})
+        G.close()
+        del X
+    return {"system": f"bare nucleus Z = {Z:g} in a 20-bohr box (closed form -Z^2/2n^2)", "N": N,
+            "states_compared": "1s, 2s, 2p x 3", "runs": rows}
+
+
+def heavy_z_section(P, torch, prec, passes_max=60, m=20, tol=1e-6):
+    """Heavy-Z stand-in (Sec. VI.B.2: the gold clusters' multi-pass filter, 30
+    passes of degree 20): two Z = 79 nuclei, Slater 1s/2s/2p enrichment, N = N_e/2
+    + 20 = 99, bare nuclear potential; passes of a degree-m filter, each followed
+    by Cholesky-QR and Rayleigh-Ritz, until the 79 lowest residuals are < tol."""
+    s = W.gold_dimer()
+    G = P.System(s)
+    G.set_potential_analytic()
+    out = {}
+    for label, p, eng in (("fp64", "fp64", "dfma"), ("mixed", prec, "tensor")):
+        G.set_fp64_engine(eng)
+        X = torch.from_numpy(W.initial_block(s, 99, seed=1)).cuda()
+        v0 = torch.from_numpy(W.lanczos_start(s)).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eps, res, it, b = G.solve(X, m, tol=tol, max_iter=passes_max, v0=v0, n_conv=79, precision=p,
+                                  fp64_tail=0 if p == "fp64" else 2)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out[label] = {"passes": it, "wall_s": wall, "s_per_pass": wall / max(it, 1), "upper_bound_Ha": b,
+                      "max_resid_79": float(np.max(res[:79])), "eig_head_Ha": [float(x) for x in eps[:3]],
+                      "precision": p, "fp64_engine": eng}
+    n_nodes, n_cells = G.n_nodes, G.n_cells
+    G.close()
+    return {"system": f"Au2-like dimer (Z = 79, 4.67 bohr), {n_nodes} nodes, {n_cells} cells, 10 enrichment functions",
+            "N": 99, "degree": m, "tol": tol, "fp64": out["fp64"], "mixed": out["mixed"],
+            "max_abs_eig_diff_Ha": float(np.max(np.abs(np.array(out["fp64"]["eig_head_Ha"]) -
+                                                        np.array(out["mixed"]["eig_head_Ha"]))))}
 
 
 # ------------------------------------------------------------------------- reference arm
@@ -581,6 +654,10 @@ def main():
     # time to a converged SCF, plain FP64 against the mixed mode (small multi-atom system)
     if args.converged != "none" and rank == 0:
         line["converged_scf"] = converged_scf_section(P, torch, prec, args.converged)
+    if args.dof_degree and rank == 0:
+        line["dof_degree"] = dof_degree_section(P, torch)
+    if args.heavy_z and rank == 0:
+        line["heavy_z"] = heavy_z_section(P, torch, prec)
     # many small systems (1-6 atoms, Z in {1, 6, 8, 14}, own graded meshes, N = ceil(0.6 N_e) + 8):
     # one ChFSI filter step of every system as one CUDA graph vs the same steps launched
     # one system after another; column tiles of the cell kernel picked by the autotuner

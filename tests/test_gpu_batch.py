@@ -77,3 +77,28 @@ def test_autotune_picks_a_tile_and_keeps_results(systems):
     G.chfsi_step(got, 7, a[0], b[0], a0[0], precision="tf32x3", fp64_tail=1)
     # another column tile regroups the columns; each column's products and sums are unchanged
     assert (got - ref).abs().max().item() <= 1e-6 * ref.abs().max().item()
+
+
+@pytest.mark.parametrize("prec,m,tol", [("fp64", 7, 1e-9), ("tf32x3", 7, 5e-5), ("bf16", 1, 5e-2)])
+def test_batch_each_system_matches_oracle(systems, prec, m, tol):
+    """Every system of a batched graph step (three meshes and block widths)
+    against the oracle's scaled filter of that system: FP64 to rounding, the
+    3-term TF32 split to FP32 grade, BF16 operands to BF16 grade (one degree)."""
+    from oracle.chfsi import chebyshev_filter_scaled
+    from oracle.operators import Discretisation
+    from paper_1610_02121_gb300 import Batch
+    from tests.gpu_util import rel_err
+    ss, Gs = systems
+    Ns = [12, 20, 8]
+    X0 = _blocks(ss, Ns)
+    a, b, a0 = _bounds(Gs, X0)
+    B = Batch(Gs)
+    try:
+        Xg = [x.clone() for x in X0]
+        B.chfsi_step(Xg, m, a, b, a0, precision=prec, fp64_tail=0, graph=True)
+    finally:
+        B.close()
+    for s, x0, xg, ai, bi, a0i in zip(ss, X0, Xg, a, b, a0):
+        d = Discretisation(s)
+        ref = chebyshev_filter_scaled(d.apply_Htilde, x0.cpu().numpy(), m, ai, bi, a0i)
+        assert rel_err(xg, ref) < tol, s["name"]

@@ -147,6 +147,56 @@ def hydrogen(cells=6, half=10.0, r_c=6.0, tau=1e-10, max_depth=10, n_gauss=6):
                    tau=tau, max_depth=max_depth, name=f"hydrogen_{cells}c_{2*half:g}bohr")
 
 
+def bare_nucleus(Z=14.0, enriched=True, cells=6, half=10.0, r_c=2.0, h_min=None, h_max=3.4, growth=1.3,
+                 tau=1e-10, max_depth=12, n_gauss=6):
+    """A bare nucleus of charge Z at the centre of a (2 half)^3 box, V = -Z/r: the
+    closed-form spectrum -Z^2/(2 n^2) (Z = 14: the Si-like core, 1s at -98 Ha).
+    enriched: uniform cells x cells x cells mesh with the hydrogenic 1s, 2s, 2p
+    functions of charge Z cut off at r_c (r0 = r_c/2, t = 1); classical
+    (n_E = 0): graded mesh refined towards the nucleus down to h_min."""
+    if enriched:
+        b = _uniform_breaks(-half, half, cells)
+        funcs = _hydrogenic_funcs(0, r_c / 2.0, 1.0)
+        breaks = [b, b, b]
+    else:
+        b = graded_breaks(-half, half, [0.0], h_min, h_max, growth=growth, fine_pad=2.0 * h_min)
+        funcs = []
+        breaks = [b, b, b]
+    pot = {"nuclear": True, "gauss_A": np.zeros(0), "gauss_s": np.zeros(0),
+           "gauss_c": np.zeros((0, 3)), "omega": 0.0}
+    tag = f"enr{cells}" if enriched else f"cls{h_min:g}"
+    return _system(breaks, 4, [[0.0, 0.0, 0.0]], [float(Z)], funcs, pot, n_gauss=n_gauss, tau=tau,
+                   max_depth=max_depth, name=f"Z{Z:g}_{tag}")
+
+
+def tiny_heavy(Z=79.0, seed=14, cells=2, half=2.0, r_c=1.6, tau=1e-8, max_depth=8):
+    """Heavy nucleus (Z = 79) at the centre vertex of a small uniform mesh with its
+    Slater 1s/2s/2p enrichment (Slater's-rules exponents, seeded +-5 %) and a
+    seeded Gaussian perturbation: parity case of the heavy-Z stand-in."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b = _uniform_breaks(-half, half, cells)
+    z1, z2 = slater_zetas(int(Z))
+    z1 *= 1.0 + 0.05 * rng.uniform(-1, 1)
+    z2 *= 1.0 + 0.05 * rng.uniform(-1, 1)
+    funcs = _slater_funcs(0, z1, z2, r_c / 2.0, 1.0)
+    pot = {"nuclear": True,
+           "gauss_A": rng.uniform(-0.5, 0.5, size=2),
+           "gauss_s": rng.uniform(0.5, 1.0, size=2),
+           "gauss_c": rng.uniform(-1.0, 1.0, size=(2, 3)),
+           "omega": 0.0}
+    return _system([b, b, b], 4, [[0.0, 0.0, 0.0]], [float(Z)], funcs, pot, tau=tau, max_depth=max_depth,
+                   name=f"heavy{Z:g}")
+
+
+def gold_dimer(h_min=0.9, h_max=3.0, pad=8.0, r_c=3.0, seed=13, tau=1e-8, max_depth=8):
+    """Heavy-Z stand-in (Sec. VI.B.2's gold clusters): two Z = 79 nuclei 4.67 bohr
+    apart, graded degree-4 mesh, Slater 1s/2s/2p enrichment per atom (exponents
+    from Slater's rules, seeded +-5 %), bare nuclear potential; 158 electrons."""
+    atoms = np.array([[0.0, 0.0, 0.0], [4.67, 0.0, 0.0]])
+    return _cluster_system(atoms, np.array([79.0, 79.0]), h_min, h_max, pad, r_c, seed, seed + 1, 0, tau, max_depth,
+                           name="au2")
+
+
 def harmonic(cells=8, half=8.0, omega=1.0, p=4):
     """3-D harmonic oscillator V = omega^2 r^2 / 2, classical basis only."""
     b = _uniform_breaks(-half, half, cells)
