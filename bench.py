@@ -347,7 +347,8 @@ def dof_degree_section(P, torch, Z=14.0, N=8, nconv=5, tol=1e-7, max_iter=150):
         rows.append({"basis": "enriched (hydrogenic 1s/2s/2p)" if enriched else f"classical, h_min {h} bohr",
                      "dof": dof, "cells": G.n_cells, "upper_bound_Ha": b, "degree": m, "filter_passes": it,
                      "degree_x_passes": m * it, "wall_s": wall, "max_resid": float(np.max(res[:nconv])),
-                     "max_abs_err_Ha": float(np.max(np.abs(eps[:nconv] - exact)))})
+                     "max_abs_err_Ha": float(np.max(np.abs(eps[:nconv] - exact))),
+                     "err_by_state_Ha": [float(x) for x in eps[:nconv] - exact]})
         G.close()
         del X
     return {"system": f"bare nucleus Z = {Z:g} in a 20-bohr box (closed form -Z^2/2n^2)", "N": N,

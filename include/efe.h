@@ -205,8 +205,9 @@ int efe_rr_shifted_passes(efe_handle* h, int64_t* count);
  * FP64 path); 1 = FP64-grade products on the BF16 tensor cores by error-free
  * operand slicing (Ozaki scheme: seven 7-bit digits per operand, exact FP32
  * accumulation of the leading digit products; error within a few units of
- * 2^-48 of sum |a||b|).  Applies to N > 8 cell products and to N <= 144 tall
- * products; other cases keep DFMA.  Host setting, no device work. */
+ * 2^-48 of sum |a||b|).  Applies to N > 8 cell products, to the tall and Gram
+ * products of Rayleigh-Ritz and to its dense N x N products for N > 512; other
+ * cases keep DFMA.  Host setting, no device work. */
 int efe_set_fp64_engine(efe_handle* h, int32_t engine);
 
 /* Test and tuning controls (no counterpart in the paper).  Host settings, no
@@ -232,6 +233,9 @@ int efe_set_fp64_engine(efe_handle* h, int32_t engine);
                                     kernel, FP64 engine) first wait on a barrier that nothing completes, so the
                                     bounded wait runs out; the launch drains its copies and MMAs, frees its TMEM and
                                     the call returns EFE_ERR_TIMEOUT.  0 (default): off */
+#define EFE_OPT_COUPLING_COLS 7   /* the columns product W_c += (H^ec)^T Y_e of the many-function coupling:
+                                    0 (default): dense tiles of 32-node blocks; 1: each node's own entries only.
+                                    Same products, FP32 sums in another order */
 int efe_set_option(efe_handle* h, int32_t option, int64_t value);
 
 /* Kernel timing: when enabled, the library brackets every launch of its

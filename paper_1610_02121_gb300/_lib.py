@@ -481,7 +481,7 @@ class System:
         return t.value, ms
 
     OPTIONS = {"grid_cap": 1, "image_rows": 2, "rr_panels": 3, "dense_blocked": 4, "coupling_sparse": 5,
-               "test_stall": 6}
+               "test_stall": 6, "coupling_cols": 7}
 
     def set_option(self, name, value):
         """Test/tuning control of the library (EFE_OPT_*): grid_cap (CTAs of the

@@ -118,9 +118,15 @@ struct efe_handle {
   int32_t *f_it0 = nullptr, *f_it1 = nullptr, *f_slot = nullptr;
   float *hec32 = nullptr, *mecD32 = nullptr;   // row-pattern FP32 values of H^ec and M^ec D^-1
   int64_t* ec_rowptr = nullptr;               // start of each function's row in the row pattern
+  int32_t* t_slot = nullptr;                  // slot of each transposed-pattern entry within its node block
+  // (hi, lo) float pairs of the coupling values for the FP64-grade coupling on the
+  // FP32 pipe (tensor-core FP64 engine): row pattern H^ec, M^ec, M^ec D^-1;
+  // transposed pattern H^ec, M^ec; xe2: an enrichment block as pairs (n_E x N)
+  float2 *hec2 = nullptr, *mec2 = nullptr, *mecD2 = nullptr, *hecT2 = nullptr, *mecT2 = nullptr, *xe2 = nullptr;
   double* gpart = nullptr;                    // n_gitems x grp_kmax() x N partial sums
   float* Xe32 = nullptr;                      // n_E x N FP32 copy of an enrichment block
   int opt_coup_sparse = 0;                    // 1: grouped sparse coupling whatever the size
+  int opt_coup_cols = 0;                      // columns product: 0 dense tiles, 1 per-node entries
   int opt_test_stall = 0;                     // tests: tensor-core launches take their abort path
   // dense FP32 tiles of the pattern over blocks of pattern nodes (mixed filter)
   int64_t cb_nblk = 0, cb_nslots = 0;
@@ -295,7 +301,10 @@ int reserve(efe_handle* h, int N) {
   if (h->whole_rr) TRY(dalloc(h, &h->B2, R * N));
   TRY(dalloc(h, &h->xe, std::max<int64_t>(1, h->nE) * N));
   TRY(dalloc(h, &h->rb, std::max<int64_t>(1, h->nE) * N));
-  TRY(dalloc(h, &h->part, std::max<int64_t>(1, h->nseg) * N));
+  TRY(dalloc(h, &h->part, std::max<int64_t>({1, h->nseg, (int64_t)h->n_gitems * grp_kmax()}) * N));
+  dfree(h, h->xe2);
+  h->xe2 = nullptr;
+  TRY(dalloc(h, &h->xe2, std::max<int64_t>(1, h->nE) * N));
   TRY(dalloc(h, &h->small, 24 * (int64_t)N * N + 8 * (int64_t)N));
   // split-K partials of the DFMA A^T B products and the segment partials of the
   // tensor-core ones (both fit their split counts to this size)
@@ -486,6 +495,11 @@ int cell_apply_all(efe_handle* h, const T* Hc, const T* Y, int64_t ldy, T* Wc, i
   return EFE_OK;
 }
 
+// The FP64 enrichment coupling runs in double-float arithmetic on the FP32 pipe
+// (FP64-grade like the tensor-core engine it comes with) for blocks of N > 8
+// vectors; the plain FP64 kernels otherwise.
+bool use_df(const efe_handle* h, int N) { return h->fp64_engine == 1 && h->nE > 0 && N > 8; }
+
 // --- H^E X: classical cell products + enrichment coupling (Eq. H2x2) ---
 //   Wc = H^cc Xc + (H^ec)^T Xe ;  We = H^ec Xc + H^ee Xe
 template <typename T>
@@ -499,6 +513,18 @@ int apply_H_generic(efe_handle* h, const T* Xc, int64_t ldx, const double* Xe, i
     CKL();
   }
   TRY(cell_apply_all<T>(h, Hc, Xc, ldx, Wc, ldw, N, st));
+  if constexpr (sizeof(T) == 8) {
+    if (use_df(h, N)) {
+      launch_df_rows(h->nE, N, Xe, ldxe, h->xe2, st);
+      launch_spmm_nodes_df(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->hecT2, 1.f, h->xe2, N, (double*)Wc, ldw, st);
+      launch_grp_rows_df(h->n_gitems, h->gitems, h->ec_rowptr, h->ec_col, h->hec2, (const double*)Xc, ldx, h->part,
+                         N, st);
+      launch_grp_reduce((int)h->nE, h->f_it0, h->f_it1, h->f_slot, h->part, N, 1.0, nullptr, 0, 0.0, We, ldwe, st);
+      launch_gemm_nn(h->nE, N, (int)h->nE, 1.0, h->Hee, h->nE, Xe, ldxe, 1.0, We, ldwe, st);
+      CKL();
+      return EFE_OK;
+    }
+  }
   if (h->nE > 0) {
     launch_spmm_nodes<T>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->hecT, 1.0, Xe, ldxe, Wc, ldw, N, st);
     launch_spmm_segments<T>(h->nseg, h->seg_start, h->seg_end, h->ec_col, h->hec, nullptr, Xc, ldx, h->part, N, st);
@@ -514,6 +540,18 @@ int apply_H_generic(efe_handle* h, const T* Xc, int64_t ldx, const double* Xe, i
 template <typename T>
 int minv_core(efe_handle* h, T* Wc, int64_t ldw, const double* We, int64_t ldwe, int N, cudaStream_t st) {
   if (h->nE == 0) return EFE_OK;
+  if constexpr (sizeof(T) == 8) {
+    if (use_df(h, N)) {
+      launch_grp_rows_df(h->n_gitems, h->gitems, h->ec_rowptr, h->ec_col, h->mecD2, (const double*)Wc, ldw, h->part,
+                         N, st);
+      launch_grp_reduce((int)h->nE, h->f_it0, h->f_it1, h->f_slot, h->part, N, -1.0, We, ldwe, 1.0, h->rb, N, st);
+      launch_gemm_nn(h->nE, N, (int)h->nE, 1.0, h->Sinv, h->nE, h->rb, N, 0.0, h->xe, N, st);
+      launch_df_rows(h->nE, N, h->xe, N, h->xe2, st);
+      launch_spmm_nodes_df(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->mecT2, -1.f, h->xe2, N, (double*)Wc, ldw, st);
+      CKL();
+      return EFE_OK;
+    }
+  }
   launch_spmm_segments<T>(h->nseg, h->seg_start, h->seg_end, h->ec_col, h->mec, h->Dinv, Wc, ldw, h->part, N, st);
   launch_seg_reduce((int)h->nE, h->row_seg_ptr, h->part, -1.0, We, ldwe, 1.0, h->rb, N, N, st);
   launch_gemm_nn(h->nE, N, (int)h->nE, 1.0, h->Sinv, h->nE, h->rb, N, 0.0, h->xe, N, st);
@@ -525,7 +563,15 @@ int minv_core(efe_handle* h, T* Wc, int64_t ldw, const double* We, int64_t ldwe,
 int apply_M_impl(efe_handle* h, const double* X, int64_t ldx, int N, double* Y, int64_t ldy, cudaStream_t st) {
   const int64_t nn = h->n_nodes;
   launch_row_scale<double>(nn, h->Dm, X, ldx, Y, ldy, N, st);
-  if (h->nE > 0) {
+  if (h->nE > 0 && use_df(h, N)) {
+    launch_df_rows(h->nE, N, X + nn * ldx, ldx, h->xe2, st);
+    launch_spmm_nodes_df(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->mecT2, 1.f, h->xe2, N, Y, ldy, st);
+    launch_row_scale<double>(nn, h->mask, Y, ldy, Y, ldy, N, st);
+    launch_grp_rows_df(h->n_gitems, h->gitems, h->ec_rowptr, h->ec_col, h->mec2, X, ldx, h->part, N, st);
+    launch_grp_reduce((int)h->nE, h->f_it0, h->f_it1, h->f_slot, h->part, N, 1.0, nullptr, 0, 0.0, Y + nn * ldy, ldy,
+                      st);
+    launch_gemm_nn(h->nE, N, (int)h->nE, 1.0, h->Mee, h->nE, X + nn * ldx, ldx, 1.0, Y + nn * ldy, ldy, st);
+  } else if (h->nE > 0) {
     launch_spmm_nodes<double>(h->n_tn, h->t_nodes, h->t_ptr, h->t_col, h->mecT, 1.0, X + nn * ldx, ldx, Y, ldy, N, st);
     launch_row_scale<double>(nn, h->mask, Y, ldy, Y, ldy, N, st);
     launch_spmm_segments<double>(h->nseg, h->seg_start, h->seg_end, h->ec_col, h->mec, nullptr, X, ldx, h->part, N,
@@ -616,8 +662,15 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
       // FP32 rows products with FP64 partial sums, FP64 n_E x n_E products
       const int64_t nE64 = h->nE;
       launch_f64_to_f32_rows(nE64, Yce, N, h->Xe32, N, N, st);
-      launch_coup_cols_chunk(h->n_tn, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileH, 1.f, h->Xe32, N, N, h->Wf, ld,
-                             st);
+      auto cols = [&](const float* tile, const float* valT, float sgn) {
+        if (h->opt_coup_cols)
+          launch_coup_cols_sparse(h->n_tn, h->t_nodes, h->t_ptr, h->t_slot, valT, h->cb_slot_off, h->cb_slots, sgn,
+                                  h->Xe32, N, N, h->Wf, ld, st);
+        else
+          launch_coup_cols_chunk(h->n_tn, h->t_nodes, h->cb_slot_off, h->cb_slots, tile, sgn, h->Xe32, N, N, h->Wf, ld,
+                                 st);
+      };
+      cols(h->tileH, h->hecT32, 1.f);
       TRY(gemm_ee(h, h->Hee, Yce, h->rb, N, st));                       // H^ee Y_e
       launch_grp_rows(h->n_gitems, h->gitems, h->ec_rowptr, h->ec_col, h->hec32, Yc, ld, h->gpart, N, st);
       launch_grp_reduce(nE, h->f_it0, h->f_it1, h->f_slot, h->gpart, N, 1.0, h->rb, N, 1.0, We, N, st);
@@ -626,8 +679,7 @@ int degree_f32(efe_handle* h, const float* Yc, const double* Yce, const float* Y
       launch_grp_reduce(nE, h->f_it0, h->f_it1, h->f_slot, h->gpart, N, -1.0, We, N, 1.0, h->rb, N, st);
       TRY(gemm_ee(h, h->Sinv, h->rb, h->xe, N, st));
       launch_f64_to_f32_rows(nE64, h->xe, N, h->Xe32, N, N, st);
-      launch_coup_cols_chunk(h->n_tn, h->t_nodes, h->cb_slot_off, h->cb_slots, h->tileM, -1.f, h->Xe32, N, N, h->Wf,
-                             ld, st);
+      cols(h->tileM, h->mecT32, -1.f);
       CKL();
     }
   }
@@ -1198,6 +1250,14 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
     TRY(dalloc(h, &h->hec32, h->nnz));
     launch_permute(h->nnz, h->mec, h->t_perm, h->mecT, 0);
     launch_to_f32(h->mecT, h->mecT32, h->nnz, 0);
+    TRY(dalloc(h, &h->mec2, h->nnz));
+    TRY(dalloc(h, &h->mecD2, h->nnz));
+    TRY(dalloc(h, &h->mecT2, h->nnz));
+    TRY(dalloc(h, &h->hec2, h->nnz));
+    TRY(dalloc(h, &h->hecT2, h->nnz));
+    launch_df_coef(h->nnz, h->mec, nullptr, nullptr, h->mec2, 0);
+    launch_df_coef(h->nnz, h->mec, h->Dinv, h->ec_col, h->mecD2, 0);
+    launch_df_coef(h->nnz, h->mecT, nullptr, nullptr, h->mecT2, 0);
     CKL();
     {
       // blocks of consecutive pattern nodes: their function slots and the tile
@@ -1205,7 +1265,7 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
       const int B = coup_block_nodes();
       const int64_t nblk = (h->n_tn + B - 1) / B;
       std::vector<int64_t> soff(nblk + 1, 0), pos(h->nnz);
-      std::vector<int32_t> slots;
+      std::vector<int32_t> slots, tslot(h->nnz);
       std::vector<int32_t> fs;
       for (int64_t b = 0; b < nblk; ++b) {
         const int64_t r0 = b * B, r1 = std::min<int64_t>(h->n_tn, r0 + B);
@@ -1216,6 +1276,7 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
           for (int64_t q = s.t_ptr[r]; q < s.t_ptr[r + 1]; ++q) {
             const int64_t k = std::lower_bound(fs.begin(), fs.end(), s.t_col[q]) - fs.begin();
             pos[q] = (soff[b] + k) * B + (r - r0);
+            tslot[q] = (int32_t)k;
           }
         slots.insert(slots.end(), fs.begin(), fs.end());
         soff[b + 1] = soff[b] + (int64_t)fs.size();
@@ -1226,6 +1287,7 @@ int efe_create(const efe_mesh_desc* mesh, const efe_atoms_desc* atoms, const efe
       h->cb_soff_host = soff;
       TRY(upload(h, &h->cb_slots, slots));
       TRY(upload(h, &h->cb_pos, pos));
+      TRY(upload(h, &h->t_slot, tslot));
       TRY(dalloc(h, &h->tileM, h->cb_nslots * B));
       TRY(dalloc(h, &h->tileH, h->cb_nslots * B));
       CK(cudaMemset(h->tileM, 0, sizeof(float) * h->cb_nslots * B));
@@ -1311,6 +1373,8 @@ int efe_set_potential(efe_handle* h, const double* Vq, void* stream) {
     launch_permute(h->nnz, h->hec, h->t_perm, h->hecT, st);
     launch_to_f32(h->hecT, h->hecT32, h->nnz, st);
     launch_to_f32(h->hec, h->hec32, h->nnz, st);
+    launch_df_coef(h->nnz, h->hec, nullptr, nullptr, h->hec2, st);
+    launch_df_coef(h->nnz, h->hecT, nullptr, nullptr, h->hecT2, st);
     launch_tile_scatter(h->nnz, h->cb_pos, h->hecT32, h->tileH, st);
     launch_gather_sum(h->nE * h->nE, h->Hee_kin, h->ee_cptr, h->ee_cidx, h->Qblk, h->Hee, st);
     launch_symmetrize(h->Hee, (int)h->nE, (int)h->nE, st);
@@ -1637,7 +1701,7 @@ int64_t image_panel_rows(const efe_handle* h, int64_t rows, int64_t bytes_per_ro
 
 // C = A B for a tall A (rows x K) and a small B (K x Nc, ld Nc): FP64-grade
 // tensor-core products when enabled (A sliced in row panels whose digit image
-// fits the budget; K in exact groups of 144 inside the kernel), FP64 DFMA
+// fits the budget; K in exact groups of 256 inside the kernel), FP64 DFMA
 // otherwise.
 int gemm_tall_ld(efe_handle* h, int64_t rows, int K, int Nc, const double* A, int64_t lda, const double* B,
                  int64_t ldb, double* C, int64_t ldc, cudaStream_t st);
@@ -1774,6 +1838,16 @@ int trinv_lower(efe_handle* h, const double* L, int n, double* Li, cudaStream_t 
   return EFE_OK;
 }
 
+// C = A B for N x N FP64 matrices (ld N) of the dense Rayleigh-Ritz steps: on the
+// tensor-core FP64 engine when it is selected and N takes the blocked dense path
+// (the DFMA pipe needs ~20 ms per product at N = 2200), else the DFMA kernel
+int dense_nn(efe_handle* h, int N, const double* A, const double* B, double* C, cudaStream_t st) {
+  if (h->fp64_engine == 1 && (N > DENSE_SMALL_MAX || h->opt_dense_blocked))
+    return gemm_tall_ld(h, N, N, N, A, N, B, N, C, N, st);
+  launch_gemm_nn(N, N, N, 1.0, A, N, B, N, 0.0, C, N, st);
+  return EFE_OK;
+}
+
 // Dense symmetric eigenproblem C = V diag(w) V^T of Rayleigh-Ritz (N x N, FP64).
 // FP64 rotations run at the FP64 rate of one SM, so C is first diagonalised in
 // FP32 (to a relative off-diagonal size ~1e-6); the FP32 vectors are made
@@ -1853,7 +1927,11 @@ int sym_eig_blocked(efe_handle* h, const double* C, int N, double* V, double* w,
   bool refine = true;
   if (r32 == 0) {
     launch_f32_to_f64_rows(N, V32, N, Q0, N, N, st);
-    launch_gemm_tn(N, N, N, Q0, N, Q0, N, G, N, h->tnwork, h->tnwork_elems, st, true);
+    if (h->fp64_engine == 1) {
+      TRY(gemm_gram(h, N, N, N, Q0, N, Q0, N, G, N, true, st));
+    } else {
+      launch_gemm_tn(N, N, N, Q0, N, Q0, N, G, N, h->tnwork, h->tnwork_elems, st, true);
+    }
     launch_symmetrize(G, N, N, st);
     TRY(chol_lower(h, G, N, st, nullptr, h->info + 2));
     int inf = 0;
@@ -1861,13 +1939,18 @@ int sym_eig_blocked(efe_handle* h, const double* C, int N, double* V, double* w,
     CK(cudaStreamSynchronize(st));
     refine = inf == 0;
   }
+  auto mm = [&](const double* A, const double* B, double* Cm) { return dense_nn(h, N, A, B, Cm, st); };
   const double* C64 = C;
   if (refine && r32 == 0) {
     TRY(trinv_lower(h, G, N, Li, st));
     launch_transpose(Li, N, N, LiT, N, st);
-    launch_gemm_nn(N, N, N, 1.0, Q0, N, LiT, N, 0.0, Q, N, st);
-    launch_gemm_tn(N, N, N, Q, N, C, N, T1, N, h->tnwork, h->tnwork_elems, st, false);
-    launch_gemm_nn(N, N, N, 1.0, T1, N, Q, N, 0.0, C2, N, st);
+    TRY(mm(Q0, LiT, Q));
+    if (h->fp64_engine == 1) {
+      TRY(gemm_gram(h, N, N, N, Q, N, C, N, T1, N, false, st));
+    } else {
+      launch_gemm_tn(N, N, N, Q, N, C, N, T1, N, h->tnwork, h->tnwork_elems, st, false);
+    }
+    TRY(mm(T1, Q, C2));
     launch_symmetrize(C2, N, N, st);
     C64 = C2;
   }
@@ -1884,7 +1967,7 @@ int sym_eig_blocked(efe_handle* h, const double* C, int N, double* V, double* w,
     h->err = "block Jacobi eigensolver did not converge";
     return EFE_ERR_NOCONV;
   }
-  if (C64 != C) launch_gemm_nn(N, N, N, 1.0, Q, N, V2, N, 0.0, V, N, st);
+  if (C64 != C) TRY(mm(Q, V2, V));
   CKL();
   return EFE_OK;
 }
@@ -2035,12 +2118,12 @@ int efe_rayleigh_ritz(efe_handle* h, double* X, int64_t ldx, int32_t N, double* 
   // C = Lm^-1 Hp Lm^-T, eig(C) = (eps, Z), Psi = Lm^-T Z
   TRY(trinv_lower(h, Lm, N, Lminv, st));
   launch_transpose(Lminv, N, N, LminvT, N, st);
-  launch_gemm_nn(N, N, N, 1.0, Lminv, N, Hp, N, 0.0, T1, N, st);
-  launch_gemm_nn(N, N, N, 1.0, T1, N, LminvT, N, 0.0, C, N, st);
+  TRY(dense_nn(h, N, Lminv, Hp, T1, st));
+  TRY(dense_nn(h, N, T1, LminvT, C, st));
   launch_symmetrize(C, N, N, st);
   TRY(sym_eig(h, C, N, Vj, wv, E0, st));
   launch_sort_eig(wv, Vj, N, N, eps, Z, N, st);
-  launch_gemm_nn(N, N, N, 1.0, LminvT, N, Z, N, 0.0, Psi, N, st);
+  TRY(dense_nn(h, N, LminvT, Z, Psi, st));
   // rotation and residuals
   TRY(gemm_tall(h, R, N, N, Q, N, Psi, X, ldx, st));
   if (resid_host) {
@@ -2121,6 +2204,10 @@ int efe_set_option(efe_handle* h, int32_t option, int64_t value) {
         h->opt_coup_sparse = (int)value;
         h->Nres32 = 0;   // the mixed workspace is remade at the next filter call
       }
+      return EFE_OK;
+    case EFE_OPT_COUPLING_COLS:
+      if (value > 1) return EFE_ERR_ARG;
+      h->opt_coup_cols = (int)value;
       return EFE_OK;
     default:
       h->err = "unknown option";

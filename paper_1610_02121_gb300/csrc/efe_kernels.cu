@@ -20,9 +20,8 @@ namespace efe {
 
 std::atomic<int64_t> g_launches{0};
 
-namespace {
 // SM count of the current device, looked up once per device ordinal
-std::atomic<int> g_sm_count[64];
+static std::atomic<int> g_sm_count[64];
 int current_sm_count() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
@@ -39,6 +38,8 @@ int current_sm_count() {
   }
   return n;
 }
+
+namespace {
 }  // namespace
 
 namespace {
@@ -626,9 +627,6 @@ __global__ void __launch_bounds__(256) k_coup_reduce(int nb, int nE, int N, cons
   }
 }
 
-// Columns product: W[g_u][c] += sgn * sum_slot tile[slot][u] * Xe[f(slot)][c]
-// (Xe staged in shared memory as FP32, rows padded to four floats), same block
-// tiles and CTA partition as the rows product.
 // Columns product for many enrichment functions, over the node blocks of the
 // dense tiles: a CTA takes one block of CPB consecutive pattern nodes and one
 // chunk of GRP_CT columns, stages the block's (slots x CPB) tile and the X_e
@@ -689,6 +687,240 @@ __global__ void __launch_bounds__(GRP_CT) k_coup_cols_chunk(int64_t n_tn, const 
   }
 }
 
+// The same columns product with each node's own entries only (the transposed
+// pattern: node rows, FP32 values and each entry's slot within its block)
+// instead of the block's dense tile, which is mostly zeros when many functions
+// meet a block (about 8 of 40 slots per node at 280 atoms).
+constexpr int CPE = 1024;   // entries of a block staged at a time
+__global__ void __launch_bounds__(GRP_CT) k_coup_cols_sparse(int64_t n_tn, const int32_t* __restrict__ t_nodes,
+                                                            const int64_t* __restrict__ t_ptr,
+                                                            const int32_t* __restrict__ t_slot,
+                                                            const float* __restrict__ val,
+                                                            const int64_t* __restrict__ slot_off,
+                                                            const int32_t* __restrict__ slots, float sgn,
+                                                            const float* __restrict__ Xe, int64_t ldxe, int N,
+                                                            float* __restrict__ W, int64_t ldw) {
+  __shared__ float Xs[CPF][GRP_CT];
+  __shared__ float2 ent[CPE];          // (value, slot as int bits)
+  __shared__ int64_t nd[CPB];
+  __shared__ int eoff[CPB + 1];
+  const int64_t b = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int c = blockIdx.y * GRP_CT + tid;
+  const int64_t r0 = b * CPB;
+  const int nb = (int)min((int64_t)CPB, n_tn - r0);
+  const int64_t q0 = t_ptr[r0];
+  if (tid <= nb) eoff[tid] = (int)(t_ptr[r0 + tid] - q0);
+  if (tid < nb) nd[tid] = t_nodes[r0 + tid];
+  const int64_t s0 = slot_off[b];
+  const int ns = (int)(slot_off[b + 1] - s0);
+  float acc[CPB];
+#pragma unroll
+  for (int i = 0; i < CPB; ++i) acc[i] = 0.f;
+  // slots in passes of CPF; entries whose slot falls in the pass are summed
+  for (int sp = 0; sp < ns; sp += CPF) {
+    const int nf = min(CPF, ns - sp);
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < nf; ++k) Xs[k][tid] = c < N ? Xe[(int64_t)slots[s0 + sp + k] * ldxe + c] : 0.f;
+    const int ne = eoff[nb];
+    for (int e0 = 0; e0 < ne; e0 += CPE) {
+      const int m = min(CPE, ne - e0);
+      __syncthreads();
+      for (int e = tid; e < m; e += GRP_CT) ent[e] = make_float2(val[q0 + e0 + e], __int_as_float(t_slot[q0 + e0 + e]));
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < CPB; ++i) {
+        if (i >= nb) break;
+        const int a0 = max(eoff[i] - e0, 0), a1 = min(eoff[i + 1] - e0, m);
+        float s = acc[i];
+        for (int e = a0; e < a1; ++e) {
+          const float2 v = ent[e];
+          const int k = __float_as_int(v.y) - sp;
+          if (k >= 0 && k < nf) s = fmaf(v.x, Xs[k][tid], s);
+        }
+        acc[i] = s;
+      }
+    }
+  }
+  if (c < N) {
+    // read-modify-write in two halves of 16 rows (loads batched per half)
+#pragma unroll
+    for (int h = 0; h < CPB; h += CPB / 2) {
+      float wv[CPB / 2];
+#pragma unroll
+      for (int i = 0; i < CPB / 2; ++i) wv[i] = h + i < nb ? W[nd[h + i] * ldw + c] : 0.f;
+#pragma unroll
+      for (int i = 0; i < CPB / 2; ++i)
+        if (h + i < nb) W[nd[h + i] * ldw + c] = fmaf(sgn, acc[h + i], wv[i]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64-grade enrichment coupling on the FP32 pipe (with the tensor-core FP64
+// engine selected; this part retires FP64 instructions at about 1/64 of the
+// FP32 rate, which bounds the plain FP64 coupling).  Every FP64 coefficient is
+// kept as an unevaluated sum of two floats (hi = nearest float, lo = the
+// rounded remainder) and every FP64 vector value is cut into two floats by its
+// bits; a product takes its high part exactly (the fma error term) plus the
+// two cross terms, and the sums run in double-float arithmetic (error-free
+// two-sum of the high words, low words added).  Error: a few units of 2^-48 of
+// sum |a||x| (the dropped lo*lo term and the 24-bit low words).  Values must
+// lie below 2^126 in magnitude (larger ones become infinite); parts below the
+// FP32 normal range are dropped (relative size below 2^-126).
+
+// FP32 value with the bits of the unbiased exponent ex and the 24-bit significand
+// m (leading bit set, given as an integer); 0 below the normal range.
+__device__ __forceinline__ float df_make(uint32_t sgn, int ex, uint32_t m24) {
+  const int be = ex + 127;
+  if (be <= 0) return 0.f;
+  if (be >= 255) return __uint_as_float(sgn | 0x7F800000u);
+  return __uint_as_float(sgn | ((uint32_t)be << 23) | (m24 & 0x7FFFFFu));
+}
+
+// x = hi + lo: hi = the leading 24 significant bits of x, lo = the next 29
+// bits truncated to 24 (integer operations only)
+__device__ __forceinline__ void df_split(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const uint32_t sgn = (uint32_t)(b >> 63) << 31;
+  if (e == 0) {
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  const int ex = e - 1023;
+  hi = df_make(sgn, ex, (uint32_t)(b >> 29) | 0x800000u);
+  const uint32_t r = (uint32_t)(b & 0x1FFFFFFFull);
+  if (r == 0) {
+    lo = 0.f;
+    return;
+  }
+  const int nb = 32 - __clz(r);   // significant bits of r (1..29)
+  const uint32_t m = nb > 24 ? (r >> (nb - 24)) : (r << (24 - nb));
+  lo = df_make(sgn, ex - 52 + nb - 1, m);
+}
+
+// exact FP64 value of a float (integer operations only; 0 for subnormal floats)
+__device__ __forceinline__ double df_f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t be = (u >> 23) & 0xFFu;
+  if (be == 0) return 0.0;
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                  ((unsigned long long)(be == 255 ? 2047u : be - 127u + 1023u) << 52) |
+                                  ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// (S, C) += (ah + al) (xh + xl)
+__device__ __forceinline__ void df_fma(float ah, float al, float xh, float xl, float& S, float& C) {
+  const float p = ah * xh;
+  const float c = fmaf(ah, xl, fmaf(al, xh, fmaf(ah, xh, -p)));
+  const float s = S + p;
+  const float bb = s - S;
+  const float err = (S - (s - bb)) + (p - bb);
+  S = s;
+  C += err + c;
+}
+
+// FP64 coefficients -> (hi, lo) float pairs, optionally times scale[col[q]]
+__global__ void k_df_coef(int64_t n, const double* __restrict__ v, const double* __restrict__ scale,
+                          const int32_t* __restrict__ col, float2* __restrict__ out) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const double a = scale ? v[q] * scale[col[q]] : v[q];
+  const float hi = (float)a;
+  out[q] = make_float2(hi, (float)(a - (double)hi));
+}
+
+// rows of an FP64 block -> (hi, lo) pairs by bits (rows x N, ld in, N out)
+__global__ void k_df_rows(int64_t rows, int N, const double* __restrict__ X, int64_t ldx, float2* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows * N) return;
+  float hi, lo;
+  df_split(X[(i / N) * ldx + i % N], hi, lo);
+  out[i] = make_float2(hi, lo);
+}
+
+// Columns product out[node] = out[node] + sgn sum_q val[q] Xe[col[q]] (one warp
+// per pattern node, lanes over the columns); Xe2: the enrichment rows as (hi, lo)
+// pairs (k_df_rows), the existing out value folded into the sum
+__global__ void k_spmm_nodes_df(int64_t nrows, const int32_t* __restrict__ rnode, const int64_t* __restrict__ ptr,
+                                const int32_t* __restrict__ col, const float2* __restrict__ val, float sgn,
+                                const float2* __restrict__ Xe2, int N, double* __restrict__ out, int64_t ldo) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  const int64_t g = rnode[w];
+  const int64_t q0 = ptr[w], q1 = ptr[w + 1];
+  for (int c = lane; c < N; c += 32) {
+    double* o = out + g * ldo + c;
+    float S, C;
+    df_split(*o, S, C);
+    for (int64_t q = q0; q < q1; ++q) {
+      const float2 a = val[q];
+      const float2 x = Xe2[(int64_t)col[q] * N + c];
+      df_fma(sgn * a.x, sgn * a.y, x.x, x.y, S, C);
+    }
+    *o = df_f2d(S) + df_f2d(C);
+  }
+}
+
+// Rows product over function groups (the items of k_grp_rows): part[item][k][c]
+// = sum over the item's nodes of coef[k][node] Xc[node][c], FP64 Xc, double-float
+// sums over the whole item
+__global__ void __launch_bounds__(GRP_CT) k_grp_rows_df(const int4* __restrict__ items, const int64_t* __restrict__ ec_ptr,
+                                                       const int32_t* __restrict__ ec_col, const float2* __restrict__ coef,
+                                                       const double* __restrict__ Xc, int64_t ldx, double* __restrict__ part,
+                                                       int N) {
+  __shared__ int64_t nd[GRP_CHUNK];
+  __shared__ float2 cf[GRP_KMAX][GRP_CHUNK];
+  __shared__ int64_t rowp[GRP_KMAX];
+  const int4 it = items[blockIdx.x];
+  const int f0 = it.x, kg = it.y, j0 = it.z, j1 = it.w;
+  const int c = blockIdx.y * GRP_CT + threadIdx.x;
+  if (threadIdx.x < kg) rowp[threadIdx.x] = ec_ptr[f0 + threadIdx.x];
+  float S[GRP_KMAX], C[GRP_KMAX];
+#pragma unroll
+  for (int k = 0; k < GRP_KMAX; ++k) {
+    S[k] = 0.f;
+    C[k] = 0.f;
+  }
+  for (int j = j0; j < j1; j += GRP_CHUNK) {
+    const int n = min(GRP_CHUNK, j1 - j);
+    __syncthreads();
+    const int64_t base = rowp[0];
+    if (threadIdx.x < n) nd[threadIdx.x] = ec_col[base + j + threadIdx.x];
+#pragma unroll
+    for (int u = 0; u < GRP_KMAX * GRP_CHUNK / GRP_CT; ++u) {
+      const int t = threadIdx.x + u * GRP_CT;
+      const int k = t / GRP_CHUNK, jj = t % GRP_CHUNK;
+      if (k < kg) cf[k][jj] = jj < n ? coef[rowp[k] + j + jj] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    if (c < N) {
+#pragma unroll 4
+      for (int jj = 0; jj < n; ++jj) {
+        float xh, xl;
+        df_split(Xc[nd[jj] * ldx + c], xh, xl);
+#pragma unroll
+        for (int k = 0; k < GRP_KMAX; ++k)
+          if (k < kg) df_fma(cf[k][jj].x, cf[k][jj].y, xh, xl, S[k], C[k]);
+      }
+    }
+  }
+  if (c < N) {
+    double* o = part + (int64_t)blockIdx.x * GRP_KMAX * N + c;
+#pragma unroll
+    for (int k = 0; k < GRP_KMAX; ++k)
+      if (k < kg) o[(int64_t)k * N] = df_f2d(S[k]) + df_f2d(C[k]);
+  }
+}
+
+// Columns product: W[g_u][c] += sgn * sum_slot tile[slot][u] * Xe[f(slot)][c]
+// (Xe staged in shared memory as FP32, rows padded to four floats), same block
+// tiles and CTA partition as the rows product.
 template <typename T>
 __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, const int64_t* __restrict__ cta_blk,
                                                    const int32_t* __restrict__ t_nodes,
@@ -772,7 +1004,8 @@ __global__ void __launch_bounds__(256) k_coup_cols(int64_t n_tn, const int64_t* 
 }
 
 // Chebyshev combine on 16-byte aligned FP32 rows (ld multiple of 4): four columns per thread.
-// as k_cheb_combine: Yn may be Yp
+// as k_cheb_combine: Yn may be Yp.  X (the cell-product output of this degree)
+// is zeroed after it is read, ready to accumulate the next degree's products.
 __global__ void k_cheb_combine_f4(int64_t nrows, int ld4, const double* __restrict__ rowscale,
                                   const float4* __restrict__ X, const float4* __restrict__ Yc,
                                   const float4* Yp, float4* Yn,
@@ -1638,6 +1871,17 @@ void launch_coup_cols_chunk(int64_t n_tn, const int32_t* t_nodes, const int64_t*
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
+void launch_coup_cols_sparse(int64_t n_tn, const int32_t* t_nodes, const int64_t* t_ptr, const int32_t* t_slot,
+                             const float* val, const int64_t* slot_off, const int32_t* slots, float sgn,
+                             const float* Xe, int64_t ldxe, int N, float* W, int64_t ldw, cudaStream_t st) {
+  const int64_t nblk = (n_tn + CPB - 1) / CPB;
+  if (nblk <= 0 || N <= 0) return;
+  dim3 g((unsigned)nblk, (unsigned)((N + GRP_CT - 1) / GRP_CT));
+  k_coup_cols_sparse<<<g, GRP_CT, 0, st>>>(n_tn, t_nodes, t_ptr, t_slot, val, slot_off, slots, sgn, Xe, ldxe, N, W,
+                                           ldw);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 void launch_spmm_nodes_f32(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
                            const float* val, float sgn, const float* Xe, int64_t ldxe, float* out, int64_t ldo, int N,
                            cudaStream_t st) {
@@ -1655,4 +1899,34 @@ void launch_cheb_combine_f4(int64_t nrows, int ld, const double* rowscale, const
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
+void launch_df_coef(int64_t n, const double* v, const double* scale, const int32_t* col, float2* out,
+                    cudaStream_t st) {
+  if (n <= 0) return;
+  k_df_coef<<<grid1(n, 256), 256, 0, st>>>(n, v, scale, col, out);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_df_rows(int64_t rows, int N, const double* X, int64_t ldx, float2* out, cudaStream_t st) {
+  if (rows <= 0 || N <= 0) return;
+  k_df_rows<<<grid1(rows * N, 256), 256, 0, st>>>(rows, N, X, ldx, out);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_spmm_nodes_df(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
+                          const float2* val, float sgn, const float2* Xe2, int N, double* out, int64_t ldo,
+                          cudaStream_t st) {
+  if (nrows <= 0 || N <= 0) return;
+  k_spmm_nodes_df<<<grid1(nrows * 32, 256), 256, 0, st>>>(nrows, rnode, ptr, col, val, sgn, Xe2, N, out, ldo);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void launch_grp_rows_df(int n_items, const int4* items, const int64_t* ec_ptr, const int32_t* ec_col,
+                        const float2* coef, const double* Xc, int64_t ldx, double* part, int N, cudaStream_t st) {
+  if (n_items <= 0 || N <= 0) return;
+  dim3 g((unsigned)n_items, (unsigned)((N + GRP_CT - 1) / GRP_CT));
+  k_grp_rows_df<<<g, GRP_CT, 0, st>>>(items, ec_ptr, ec_col, coef, Xc, ldx, part, N);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
 }  // namespace efe
+

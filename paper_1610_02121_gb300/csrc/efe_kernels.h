@@ -14,6 +14,9 @@ namespace efe {
 // number of kernels launched by this library since it was loaded
 extern std::atomic<int64_t> g_launches;
 
+// multiprocessor count of the current device (cached per device ordinal)
+int current_sm_count();
+
 // Reference element and mesh geometry passed by value to the set-up kernels.
 struct RefElem {
   double z[NP1], w[NP1];
@@ -77,10 +80,27 @@ void launch_grp_rows(int n_items, const int4* items, const int64_t* ec_ptr, cons
 void launch_grp_reduce(int nE, const int32_t* f_it0, const int32_t* f_it1, const int32_t* f_slot, const double* part,
                        int N, double sgn, const double* base, int64_t ldb, double alpha, double* out, int64_t ldo,
                        cudaStream_t st);
+// FP64-grade coupling on the FP32 pipe (double-float sums; coefficients and
+// vector values as (hi, lo) float pairs): coefficient pairs (optionally times
+// scale[col[q]]), vector rows to pairs, the node-major columns product (adds into
+// out) and the grouped rows product (partials per item, reduced by launch_grp_reduce)
+void launch_df_coef(int64_t n, const double* v, const double* scale, const int32_t* col, float2* out,
+                    cudaStream_t st);
+void launch_df_rows(int64_t rows, int N, const double* X, int64_t ldx, float2* out, cudaStream_t st);
+void launch_spmm_nodes_df(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
+                          const float2* val, float sgn, const float2* Xe2, int N, double* out, int64_t ldo,
+                          cudaStream_t st);
+void launch_grp_rows_df(int n_items, const int4* items, const int64_t* ec_ptr, const int32_t* ec_col,
+                        const float2* coef, const double* Xc, int64_t ldx, double* part, int N, cudaStream_t st);
 // columns product over the dense tiles' node blocks (X_e rows staged once per block), FP32
 void launch_coup_cols_chunk(int64_t n_tn, const int32_t* t_nodes, const int64_t* slot_off, const int32_t* slots,
                             const float* tile, float sgn, const float* Xe, int64_t ldxe, int N, float* W, int64_t ldw,
                             cudaStream_t st);
+// the same product with each node's own entries only (t_slot: slot of every
+// transposed-pattern entry within its 32-node block; val: FP32 values in that order)
+void launch_coup_cols_sparse(int64_t n_tn, const int32_t* t_nodes, const int64_t* t_ptr, const int32_t* t_slot,
+                             const float* val, const int64_t* slot_off, const int32_t* slots, float sgn,
+                             const float* Xe, int64_t ldxe, int N, float* W, int64_t ldw, cudaStream_t st);
 // columns product, node-major, FP32 (Xe: FP32 rows, ldxe)
 void launch_spmm_nodes_f32(int64_t nrows, const int32_t* rnode, const int64_t* ptr, const int32_t* col,
                            const float* val, float sgn, const float* Xe, int64_t ldxe, float* out, int64_t ldo, int N,

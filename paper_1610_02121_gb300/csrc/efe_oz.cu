@@ -7,7 +7,8 @@
 // is stored in BF16 as d_i 2^-7(i-1) (exact: 7 significant bits).  The product
 // sum_k a_i b_j of digit slices has weight 2^-7(i+j-2); for a fixed t = i + j
 // every partial sum is an integer multiple of 2^-7(t-2) below 2^24 of that
-// unit (K <= 144 per accumulation group, at most four pairs), so the FP32 tensor-core accumulators
+// unit (K <= 256 per accumulation group, at most four pairs, digits below 2^7 in
+// magnitude: 4 * 256 * 127^2 < 2^24), so the FP32 tensor-core accumulators
 // for t = 2, 3, 4, 5 are exact.  The pairs with t = 6..8 share a fifth
 // accumulator (their FP32 rounding is below 2^-52 of the result); pairs with
 // t > 8 fall below the 49-bit truncation and are dropped.  The epilogue adds
@@ -19,7 +20,7 @@
 //   CELL  W(cell nodes) += H^cc_e Y_e for the cells of one parity colour
 //         (Sec. V, last paragraph; cells of a colour share no node);
 //   ROWS  C = A B for a tall A (rows x K) and a small B (K x N); K is taken in
-//         groups of 144 (exact FP32 sums), each group's FP64 value added to C;
+//         groups of 256 (exact FP32 sums), each group's FP64 value added to C;
 //   GRAM  C = A^T B for tall A, B (K x Na, K x N, K large): items are (tile
 //         pair, K segment); each segment is formed in 256-row groups (exact
 //         FP32 sums for t <= 5) drained into FP64 partial tiles, which a
@@ -52,7 +53,7 @@ constexpr int OZ_M = 128;          // MMA rows
 constexpr int OZ_KC = 16;          // K per chunk (one BF16 MMA)
 constexpr int OZ_TW = 96;          // column tile
 constexpr int OZ_NACC = 5;         // accumulators: t = 2, 3, 4, 5 exact; t = 6..8 shared
-constexpr int OZ_ROWS_KG = 9;      // ROWS: 16-wide K chunks per exact accumulation group (K <= 144)
+constexpr int OZ_ROWS_KG = 16;     // ROWS: 16-wide K chunks per exact accumulation group (K <= 256)
 constexpr int OZ_STAGES = 4;
 constexpr int OZ_GROUPS = 2;        // slicer groups: group g fills the chunks ch = g (mod 2)
 constexpr int OZ_CONV_W0 = 1, OZ_CONV_WN = 7, OZ_EPI_W0 = 8;   // slicing: warps 1-7 slice, 8-15 epilogue
@@ -221,7 +222,7 @@ struct OzArgs {
   const double* B;          // K x N
   int64_t ldb;
   // common
-  int K;                    // reduction length (<= 144)
+  int K;                    // reduction length (CELL: 125; ROWS: any, in groups of 256)
   const double* Y;          // CELL: vector block (nodes x N)
   int64_t ldy;
   const int* fexp;          // per column of Y (CELL) or of B (ROWS)
@@ -280,6 +281,10 @@ __device__ __forceinline__ int64_t oz_cell_node(const MeshDev& m, int64_t e, int
   return (int64_t)(P * i + a) + (int64_t)m.nn[0] * ((int64_t)(P * j + b) + (int64_t)m.nn[1] * (int64_t)(P * kk + c));
 }
 
+// IMG: both operands arrive as pre-sliced images (ROWS / GRAM with images), so
+// no thread slices; a separate instantiation keeps the slicing code and its
+// registers out of that kernel (and the register epilogue out of the other)
+template <bool IMG>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -287,6 +292,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   if (tid == 0) s_skip = *(volatile int*)g.err;
   __syncthreads();
   if (s_skip) return;
+  if (IMG != (g.mode != 0 && g.Aimg != nullptr && g.Bimg != nullptr)) {
+    // the host picks the instantiation from the same test; a mismatch is an error
+    if (tid == 0) atomicExch(g.err, 1);
+    return;
+  }
   uint64_t* conv = reinterpret_cast<uint64_t*>(sm + OzL::BARS);  // [stages] slices written
   uint64_t* empty = conv + OZ_STAGES;                           // [stages] MMAs done with the stage
   uint64_t* accf = conv + 2 * OZ_STAGES;
@@ -295,11 +305,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   volatile int* abort_flag = reinterpret_cast<volatile int*>(accf + 3);
   uint64_t* afull = accf + 4;                                   // [stages] bulk-copied operand chunks landed
   uint64_t* never = afull + OZ_STAGES;                          // no thread ever arrives here (test stall)
-  const bool apre = g.Aimg != nullptr;
-  const bool bpre = g.mode != 0 && g.Bimg != nullptr;
+  const bool apre = IMG || g.Aimg != nullptr;
+  const bool bpre = IMG || (g.mode != 0 && g.Bimg != nullptr);
   // both operands pre-sliced: nothing to slice, so one thread issues the copies
   // and warps 4-15 share the epilogue (three warps per TMEM lane quarter)
-  const bool img_only = apre && bpre;
+  constexpr bool img_only = IMG;
   const int n_epi = img_only ? 12 : 8;
   const int epi_w0 = img_only ? 4 : OZ_EPI_W0;
   if (warp == 0) {
@@ -328,7 +338,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
   const int64_t nitems = (g.mode == 2) ? (int64_t)g.npairs * g.nseg : nA * g.ntiles;
   const int64_t my = nitems > blockIdx.x ? (nitems - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   // chunks of 16 K per item; the accumulators are drained every gsz chunks
-  // (GRAM: every 256 rows, ROWS: every 144 K -- where the FP32 sums of t <= 5
+  // (GRAM: every 256 rows, ROWS: every 256 K -- where the FP32 sums of t <= 5
   // are still exact -- and CELL once, K = 125); later groups add to the result
   const int nch = (g.mode == 2) ? (int)(g.seg_len / OZ_KC) : (g.K + OZ_KC - 1) / OZ_KC;
   const int gsz = (g.mode == 2) ? 16 : (g.mode == 1 ? min(nch, OZ_ROWS_KG) : nch);
@@ -896,16 +906,17 @@ __global__ void k_oz_rowexp(const double* __restrict__ A, int64_t lda, int64_t r
   if (lane == 0) eout[w] = E;
 }
 
-// per-column scale exponents (max over rows), combined with integer atomicMax
+// per-column scale exponents (max over rows), combined with integer atomicMax;
+// blockIdx.x: a range of rows, blockIdx.y: a range of blockDim.x columns
 __global__ void k_oz_colexp(const double* __restrict__ Y, int64_t ldy, int64_t rows, int N, int rows_per_block,
                             int* __restrict__ fout) {
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
   const int64_t r1 = min(rows, r0 + rows_per_block);
-  for (int c = threadIdx.x; c < N; c += blockDim.x) {
-    int E = -2000;
-    for (int64_t r = r0; r < r1; ++r) E = max(E, exp_of(Y[r * ldy + c]));
-    atomicMax(fout + c, E);
-  }
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  int E = -2000;
+  for (int64_t r = r0; r < r1; ++r) E = max(E, exp_of(Y[r * ldy + c]));
+  atomicMax(fout + c, E);
 }
 
 __global__ void k_oz_fill(int* p, int n, int v) {
@@ -932,8 +943,13 @@ int oz_launch(const OzArgs& a, int n_sm, cudaStream_t st) {
   const int64_t items = (a.mode == 2) ? (int64_t)a.npairs * a.nseg : nA * a.ntiles;
   if (items <= 0) return 0;
   const unsigned grid = (unsigned)(items < n_sm ? items : n_sm);
-  cudaFuncSetAttribute(k_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OzL::TOTAL);
-  k_oz<<<grid, OZ_THREADS, OzL::TOTAL, st>>>(a);
+  if (a.mode != 0 && a.Aimg != nullptr && a.Bimg != nullptr) {
+    cudaFuncSetAttribute(k_oz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OzL::TOTAL);
+    k_oz<true><<<grid, OZ_THREADS, OzL::TOTAL, st>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_oz<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OzL::TOTAL);
+    k_oz<false><<<grid, OZ_THREADS, OzL::TOTAL, st>>>(a);
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return 0;
 }
@@ -952,9 +968,13 @@ void launch_oz_hexp(const double* Hcc, int64_t n_cell, int* hexp, cudaStream_t s
 void launch_oz_colexp(const double* Y, int64_t ldy, int64_t rows, int N, int* fexp, cudaStream_t st) {
   if (N <= 0) return;
   k_oz_fill<<<(N + 255) / 256, 256, 0, st>>>(fexp, N, -2000);
-  const int rpb = 2048;
+  // about eight CTAs per SM, each thread on at most 2048 rows of one column
+  const int bt = N >= 128 ? 128 : 64;
+  const int64_t ncb = (N + bt - 1) / bt;
+  const int64_t want = 8LL * current_sm_count();
+  const int64_t rpb = std::max<int64_t>(32, std::min<int64_t>(2048, (rows * ncb + want - 1) / want));
   const int64_t nb = (rows + rpb - 1) / rpb;
-  if (nb > 0) k_oz_colexp<<<(unsigned)nb, N >= 128 ? 128 : 64, 0, st>>>(Y, ldy, rows, N, rpb, fexp);
+  if (nb > 0) k_oz_colexp<<<dim3((unsigned)nb, (unsigned)ncb), bt, 0, st>>>(Y, ldy, rows, N, (int)rpb, fexp);
   g_launches.fetch_add(2, std::memory_order_relaxed);
 }
 

@@ -245,10 +245,12 @@ def test_chfsi_converges_mixed_tiny(tiny_pair, prec, tol, atol):
 
 
 def test_fp64_tensor_engine_products(tiny_pair):
-    """FP64-grade products on the BF16 tensor cores (error-free 7-digit slicing):
-    the H apply (N > 8 uses the engine) and the filter agree with the FP64
-    oracle to FP64-level tolerances, and Rayleigh-Ritz (tall products through
-    the engine) reproduces the oracle's Ritz values."""
+    """FP64-grade products on the BF16 tensor cores (error-free 7-digit slicing)
+    and the FP64-grade enrichment coupling on the FP32 pipe (double-float sums)
+    that comes with them: the H, M and M^-1 applies (N > 8 use both) and the
+    filter agree with the FP64 oracle to FP64-level tolerances, and
+    Rayleigh-Ritz (tall products through the engine) reproduces the oracle's
+    Ritz values."""
     from oracle.chfsi import chebyshev_filter_scaled, cholqr, rayleigh_ritz
     d, G = tiny_pair
     G.set_fp64_engine("tensor")
@@ -256,6 +258,8 @@ def test_fp64_tensor_engine_products(tiny_pair):
         for N in (9, 33, 135, 200):
             X = W.random_block(d.system, N, seed=60 + N)
             assert rel_err(G.apply_H(to_dev(X)), d.apply_H_assembled(X)) < 1e-10
+            assert rel_err(G.apply_M(to_dev(X)), d.apply_M_assembled(X)) < 1e-12
+            assert rel_err(G.apply_Minv(to_dev(X)), d.apply_Minv_block(X)) < 1e-10
         N, m = 33, 7
         X = W.initial_block(d.system, N, seed=3)
         a, b, a0 = _bounds(d, N)
@@ -412,7 +416,7 @@ def test_in_place_products_rejected(tiny_pair):
 
 
 # --- the large-N code paths (280-atom cluster, N ~ 2200), driven on small inputs --------
-# Rayleigh-Ritz in column panels, the FP64 engine's tall products with K > 144
+# Rayleigh-Ritz in column panels, the FP64 engine's tall products with K > 256
 # (several exact accumulation groups) and with operand images in row panels,
 # the blocked multi-CTA Cholesky / triangular inverse / block Jacobi
 # eigensolver, and the FP32 recurrence slots living inside the FP64 workspace
@@ -430,7 +434,7 @@ def _rr_ref(d, X):
 def test_rayleigh_ritz_panels_and_blocked_dense(tiny_pair, engine, N):
     """Forced: two column panels, blocked dense kernels, and (tensor engine)
     image panels of 256 rows, so the Gram products accumulate over K panels and
-    the rotations run in row panels; N = 150 > 144 takes two K groups in the
+    the rotations run in row panels; N = 150 takes one K group (256) in the
     tall products.  Ritz values, residuals and M-orthonormality against the
     oracle's Cholesky-QR + Rayleigh-Ritz."""
     d, G = tiny_pair
@@ -456,8 +460,8 @@ def test_rayleigh_ritz_panels_and_blocked_dense(tiny_pair, engine, N):
 
 
 def test_tall_products_long_K_match_dfma(tiny_pair):
-    """The FP64 engine's tall products with K = N = 400 (three exact groups of
-    144, 144 and 112; the triangular X R^-1 in column panels of 384 and 16) and
+    """The FP64 engine's tall products with K = N = 400 (two exact groups of
+    256 and 144; the triangular X R^-1 in column panels of 384 and 16) and
     256-row image panels give the DFMA path's Ritz values to FP64 rounding, and
     both match the oracle."""
     d, G = tiny_pair
@@ -499,23 +503,27 @@ def test_mixed_filter_slots_inside_fp64_workspace(tiny_pair, prec, N, tol, tail)
     assert torch.equal(Xd, Xe)
 
 
+@pytest.mark.parametrize("cols", [0, 1])
 @pytest.mark.parametrize("prec,N,tol", [("tf32x3", 24, 5e-5), ("tf32x3", 300, 5e-5), ("fp32", 12, 2e-5)])
-def test_mixed_filter_grouped_coupling(tiny_pair, prec, N, tol):
-    """The many-function enrichment coupling of the mixed degrees (node-major
-    FP32 columns products; rows products over the functions that share a
-    support, FP32 over 64-node chunks, FP64 across chunks and items), forced on
-    the tiny mesh: a degree-7 filter against the oracle at the mixed-mode
-    tolerances of the dense-tile path."""
+def test_mixed_filter_grouped_coupling(tiny_pair, prec, N, tol, cols):
+    """The many-function enrichment coupling of the mixed degrees (columns
+    products over 32-node blocks -- dense tiles (cols 0) or each node's own
+    entries (cols 1); rows products over the functions that share a support,
+    FP32 over 64-node chunks, FP64 across chunks and items), forced on the tiny
+    mesh: a degree-7 filter against the oracle at the mixed-mode tolerances of
+    the dense-tile path."""
     from oracle.chfsi import chebyshev_filter_scaled
     d, G = tiny_pair
     X = W.random_block(d.system, N, seed=80 + N)
     a, b, a0 = _bounds(d, 10)
     ref = chebyshev_filter_scaled(d.apply_Htilde, X, 7, a, b, a0)
     G.set_option("coupling_sparse", 1)
+    G.set_option("coupling_cols", cols)
     try:
         Xd = to_dev(X)
         G.chfsi_step(Xd, 7, a, b, a0, precision=prec, fp64_tail=0)
     finally:
+        G.set_option("coupling_cols", 0)
         G.set_option("coupling_sparse", 0)
     assert rel_err(Xd, ref) < tol
 
