@@ -46,6 +46,8 @@ WORKLOADS = {
     "si16s": (lambda: W.si_cluster(h_min=1.6, h_max=4.0), 135, 40,
               "si16s: 16-atom Si-like cluster, coarser graded degree-4 mesh (h 1.6-4.0 bohr)"),
     "hydrogen": (W.hydrogen, 8, 20, "hydrogen Z=1, 6x6x6 cells"),
+    # the 280-atom block width on a small mesh (profiling case that fits a full ncu capture)
+    "co2200": (W.carbon_monoxide, 2200, 4, "C-O pair mesh (49,005 nodes) with an N = 2200 block"),
 }
 # the largest blocks are generated on the device (a seeded torch generator);
 # smaller ones by workloads.initial_block (NumPy PCG64)
@@ -588,7 +590,7 @@ def main():
         ms64, eps64 = leg[ref_eng]
         line["fp64"] = {"ms_per_step": ms64, "tflops": flops_step / (ms64 * 1e-3) / 1e12,
                         "engine": {"dfma": "dfma (plain FP64)",
-                                   "tensor": "FP64-grade products on the BF16 tensor cores (FP64 coupling DFMA)"}
+                                   "tensor": "FP64-grade products on the BF16 tensor cores (cell, Gram, rotation and dense products); FP64-grade double-float enrichment coupling on the FP32 pipe"}
                         [ref_eng],
                         "speedup_mixed_vs_fp64": ms64 / ms,
                         "max_abs_eig_diff_vs_fp64_Ha": float(np.abs(eps_chk - eps64).max()),

@@ -8,22 +8,19 @@
 // Roles of the 16 warps of a persistent CTA:
 //   warp 0      producer: per chunk one bulk copy of the cell's FP32 image
 //               (H^cc_e, 16 KB, already in the core-matrix layout) and one
-//               bulk copy per node row of Y into a raw stage, all completing
-//               on that stage's mbarrier `rfull`;
+//               bulk copy per node row of Y into a raw staging buffer, all
+//               completing on mbarrier `full`;
 //   warp 1      MMA issuer: 4 (one pass) or 12 (3-term split: A1 B1 + A1 B2 +
 //               A2 B1) tcgen05.mma per chunk into one of two TMEM
-//               accumulators, commits to `cempty` (operand stage reusable)
-//               and, after the last chunk, to `acc_full`;
-//   warps 2-7   converters: raw A -> A1 = TF32(A) (and A2 = the TF32
-//               remainder), raw rows -> K-major core-matrix B1 (and B2) in an
-//               operand stage; arrive on `cfull` and release the raw stage
-//               (`rempty`);
+//               accumulators, commits to `empty` (stage reusable) and, after
+//               the last chunk, to `acc_full`;
+//   warps 2-7   converters: the A chunk in place -> A1 = TF32(A) (and A2 =
+//               the TF32 remainder), raw rows -> K-major core-matrix B1 (and
+//               B2), arrive on `conv`;
 //   warps 8-15  epilogue: tcgen05.ld of the accumulator rows, read-modify-write
 //               scatter into W, arrive on `acc_empty`.
-// Two operand stages and two to four raw stages (by column tile) ring the
-// chunks: the copies run ahead of the conversions, which run ahead of the MMAs.
-// Every wait is bounded (about one second); on timeout the CTA records an
-// error, stops issuing, drains and frees its TMEM.
+// Two stages ring the chunks.  Every wait is bounded (about one second); on
+// timeout the CTA records an error, stops issuing, drains and frees its TMEM.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -34,7 +31,7 @@ namespace efe {
 namespace {
 
 constexpr int T3_M = 128, T3_K = 128, T3_KC = 32, T3_NCH = 4;
-constexpr int T3_CS = 2;   // converted (MMA operand) stages
+constexpr int T3_STAGES = 2;
 // column tile (template parameter TW of the kernel): 64, 96 or 160, picked per
 // system and N by the autotuner (efe_autotune); 160 by default
 constexpr int T3_THREADS = 512;
@@ -45,22 +42,14 @@ constexpr long long T3_WAIT = 2000000000LL;
 
 template <int TW>
 struct T3Layout {
-  // converted stages (MMA operands): A1 | A2 | B1 | B2; raw stages (bulk-copy
-  // targets): the cell's FP32 A chunk | the chunk's raw Y rows.  Raw stages are
-  // released as soon as they are converted, so the copies run up to RS chunks
-  // ahead of the conversions, which run up to T3_CS chunks ahead of the MMAs.
+  // stage: A1 | A2 | B1 | B2 | Braw      (bytes)
   static constexpr uint32_t A = T3_M * T3_KC * 4;           // 16 KB
   static constexpr uint32_t B = TW * T3_KC * 4;             // 20 KB at TW = 160
   static constexpr uint32_t RAW = T3_KC * TW * 4;           // 20 KB at TW = 160
-  static constexpr int RS = TW >= 160 ? 2 : 4;              // raw stages
-  static constexpr uint32_t CSTAGE = 2 * A + 2 * B;         // 72 KB at TW = 160
-  static constexpr uint32_t RSTAGE = A + RAW;               // 36 KB at TW = 160
-  static constexpr uint32_t RAW0 = T3_CS * CSTAGE;          // offset of the first raw stage
-  static constexpr uint32_t BARS = RAW0 + RS * RSTAGE;      // barrier area offset
+  static constexpr uint32_t STAGE = 2 * A + 2 * B + RAW;    // 92 KB at TW = 160
+  static constexpr uint32_t BARS = T3_STAGES * STAGE;       // barrier area offset
   static constexpr size_t TOTAL = (size_t)BARS + 256;
 };
-static_assert(T3Layout<160>::TOTAL <= 232448 && T3Layout<96>::TOTAL <= 232448 && T3Layout<64>::TOTAL <= 232448,
-              "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -174,17 +163,14 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
   if (tid == 0) s_skip = *(volatile int*)err;
   __syncthreads();
   if (s_skip) return;
-  using L = T3Layout<TW>;
-  constexpr int RS = L::RS;
-  uint64_t* rfull = reinterpret_cast<uint64_t*>(sm + L::BARS);  // [RS] raw chunk landed
-  uint64_t* rempty = rfull + 4;                                  // [RS] raw chunk converted
-  uint64_t* cfull = rfull + 8;                                   // [2] operands converted
-  uint64_t* cempty = rfull + 10;                                 // [2] MMAs done with the operands
-  uint64_t* accf = rfull + 12;                                   // [2]
-  uint64_t* acce = rfull + 14;                                   // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(rfull + 16);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(rfull + 17);
-  uint64_t* never = rfull + 18;   // no thread ever arrives here (the test stall waits on it)
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + T3Layout<TW>::BARS);  // [2]
+  uint64_t* conv = full + 2;                                          // [2]
+  uint64_t* empty = full + 4;                                         // [2]
+  uint64_t* accf = full + 6;                                          // [2]
+  uint64_t* acce = full + 8;                                          // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 10);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(full + 11);
+  uint64_t* never = full + 12;   // no thread ever arrives here (the test stall waits on it)
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
@@ -193,13 +179,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int s = 0; s < RS; ++s) {
-      bar_init(rfull + s, 1);
-      bar_init(rempty + s, T3_CONV_WARPS * 32);
-    }
-    for (int s = 0; s < T3_CS; ++s) {
-      bar_init(cfull + s, T3_CONV_WARPS * 32);
-      bar_init(cempty + s, 1);
+    for (int s = 0; s < T3_STAGES; ++s) {
+      bar_init(full + s, 1);
+      bar_init(conv + s, T3_CONV_WARPS * 32);
+      bar_init(empty + s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       bar_init(accf + b, 1);
@@ -229,19 +212,20 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
       const uint32_t row_bytes = (uint32_t)((ncol + 3) / 4) * 16u;
       for (int kc = 0; kc < T3_NCH; ++kc) {
         const int64_t ch = t * T3_NCH + kc;
-        const int s = (int)(ch % RS);
-        if (ch >= RS && !bar_wait(rempty + s, (uint32_t)((ch / RS - 1) & 1))) {
+        const int s = (int)(ch % T3_STAGES);
+        if (ch >= T3_STAGES && !bar_wait(empty + s, (uint32_t)((ch / T3_STAGES - 1) & 1))) {
           if (lane == 0) { *abort_flag = 1; atomicExch(err, 1); }
           break;
         }
-        unsigned char* R = sm + L::RAW0 + s * L::RSTAGE;
+        unsigned char* S = sm + s * T3Layout<TW>::STAGE;
         const int nrows = min(T3_KC, NL - kc * T3_KC);
-        if (lane == 0) bar_expect_tx(rfull + s, L::A + (uint32_t)nrows * row_bytes);
+        if (lane == 0) bar_expect_tx(full + s, T3Layout<TW>::A + (uint32_t)nrows * row_bytes);
         __syncwarp();
-        if (lane == 0) bulk_g2s(R, Ag + (e * T3_NCH + kc) * (T3_M * T3_KC), L::A, rfull + s);
+        if (lane == 0) bulk_g2s(S, Ag + (e * T3_NCH + kc) * (T3_M * T3_KC), T3Layout<TW>::A, full + s);
         if (lane < nrows) {
           const int64_t g = cell_node(m, e, kc * T3_KC + lane);
-          bulk_g2s(R + L::A + (uint32_t)lane * (TW * 4), Y + g * ldy + c0, row_bytes, rfull + s);
+          bulk_g2s(S + 2 * T3Layout<TW>::A + 2 * T3Layout<TW>::B + (uint32_t)lane * (TW * 4), Y + g * ldy + c0, row_bytes,
+                   full + s);
         }
         last_copy = ch;
         __syncwarp();
@@ -264,13 +248,13 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       for (int kc = 0; kc < T3_NCH && ok; ++kc) {
         const int64_t ch = t * T3_NCH + kc;
-        const int s = (int)(ch % T3_CS);
-        ok = bar_wait(cfull + s, (uint32_t)((ch / T3_CS) & 1));
+        const int s = (int)(ch % T3_STAGES);
+        ok = bar_wait(conv + s, (uint32_t)((ch / T3_STAGES) & 1));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) break;
         if (lane == 0) {
-          unsigned char* S = sm + s * L::CSTAGE;
-          const uint32_t a1 = su32(S), a2 = a1 + L::A, b1 = a1 + 2 * L::A, b2 = b1 + L::B;
+          unsigned char* S = sm + s * T3Layout<TW>::STAGE;
+          const uint32_t a1 = su32(S), a2 = a1 + T3Layout<TW>::A, b1 = a1 + 2 * T3Layout<TW>::A, b2 = b1 + T3Layout<TW>::B;
           const uint32_t d = tmem + (uint32_t)(b * 256);
           if (MODE == 2) {
             // BF16: the A chunk's BF16 copy in the A2 area, B in the B1 area; K = 16 per MMA
@@ -292,7 +276,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
               }
             }
           }
-          mma_commit(cempty + s);
+          mma_commit(empty + s);
           if (kc == T3_NCH - 1) mma_commit(accf + b);
         }
         last_mma = ch;
@@ -314,26 +298,24 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
       bool ok = true;
       for (int kc = 0; kc < T3_NCH; ++kc) {
         const int64_t ch = t * T3_NCH + kc;
-        const int rs = (int)(ch % RS), s = (int)(ch % T3_CS);
-        ok = bar_wait(rfull + rs, (uint32_t)((ch / RS) & 1));
-        if (ok && ch >= T3_CS) ok = bar_wait(cempty + s, (uint32_t)((ch / T3_CS - 1) & 1));
+        const int s = (int)(ch % T3_STAGES);
+        ok = bar_wait(full + s, (uint32_t)((ch / T3_STAGES) & 1));
         if (!ok) break;
-        unsigned char* R = sm + L::RAW0 + rs * L::RSTAGE;
-        unsigned char* S = sm + s * L::CSTAGE;
-        const float4* rawA = reinterpret_cast<const float4*>(R);
-        const float* raw = reinterpret_cast<const float*>(R + L::A);
-        unsigned char* B1 = S + 2 * L::A;
-        unsigned char* B2 = B1 + L::B;
+        unsigned char* S = sm + s * T3Layout<TW>::STAGE;
+        const float* raw = reinterpret_cast<const float*>(S + 2 * T3Layout<TW>::A + 2 * T3Layout<TW>::B);
+        unsigned char* B1 = S + 2 * T3Layout<TW>::A;
+        unsigned char* B2 = B1 + T3Layout<TW>::B;
         const int nrows = min(T3_KC, NL - kc * T3_KC);
         if (MODE == 2) {
           // BF16 copies: the A chunk (FP32 image, 4-wide K core matrices) into the A2
           // area and the raw rows into the B1 area, both in the 8-wide K layout
-          unsigned char* A2 = S + L::A;
-          for (int v = ct; v < (int)(L::A / 16); v += T3_CONV_WARPS * 32) {
+          unsigned char* A2 = S + T3Layout<TW>::A;
+          const float4* a1 = reinterpret_cast<const float4*>(S);
+          for (int v = ct; v < (int)(T3Layout<TW>::A / 16); v += T3_CONV_WARPS * 32) {
             // 16-byte unit v of the FP32 image: row r, K quad kq (cmo layout)
             const int rg = v >> 6, kq = (v >> 3) & 7, ri = v & 7;
             const int r = rg * 8 + ri, k = kq * 4;
-            const float4 x = rawA[v];
+            const float4 x = a1[v];
             ushort4 h;
             h.x = bf16r(x.x); h.y = bf16r(x.y); h.z = bf16r(x.z); h.w = bf16r(x.w);
             *reinterpret_cast<ushort4*>(A2 + bmo(r, k)) = h;
@@ -350,16 +332,15 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
             *reinterpret_cast<ushort4*>(B1 + bmo(n, kq * 4)) = h;
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          bar_arrive(cfull + s);
-          bar_arrive(rempty + rs);
+          bar_arrive(conv + s);
           continue;
         }
         {
-          // the A chunk: A1 = TF32(A), A2 = TF32(A - A1) (elementwise, same layout)
+          // the A chunk in place: A1 = TF32(A), A2 = TF32(A - A1) (elementwise, any layout)
           float4* a1 = reinterpret_cast<float4*>(S);
-          float4* a2 = reinterpret_cast<float4*>(S + L::A);
-          for (int v = ct; v < (int)(L::A / 16); v += T3_CONV_WARPS * 32) {
-            const float4 x = rawA[v];
+          float4* a2 = reinterpret_cast<float4*>(S + T3Layout<TW>::A);
+          for (int v = ct; v < (int)(T3Layout<TW>::A / 16); v += T3_CONV_WARPS * 32) {
+            const float4 x = a1[v];
             float4 h4;
             h4.x = tf32r(x.x); h4.y = tf32r(x.y); h4.z = tf32r(x.z); h4.w = tf32r(x.w);
             a1[v] = h4;
@@ -387,8 +368,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bar_arrive(cfull + s);
-        bar_arrive(rempty + rs);
+        bar_arrive(conv + s);
       }
       if (!ok) {
         *abort_flag = 1;
@@ -459,18 +439,18 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
     }
   }
   // all roles done.  After an abort, drain before the TMEM and the shared memory
-  // are released: every bulk copy issued into the raw ring lands (at most RS
-  // chunks are in flight: the producer waits for a raw stage to be converted
+  // are released: every bulk copy issued into the stage ring lands (at most
+  // T3_STAGES chunks are in flight: the producer waits for a stage to empty
   // before refilling it), and the last MMA commit (it covers every MMA this CTA
   // issued) arrives; each drain wait is bounded like the pipeline's own.
   __syncthreads();
   if (*abort_flag) {
     if (warp == 0 && lane == 0 && last_copy >= 0) {
-      for (int64_t ch = last_copy - RS + 1; ch <= last_copy; ++ch)
-        if (ch >= 0) bar_wait(rfull + (int)(ch % RS), (uint32_t)((ch / RS) & 1));
+      for (int64_t ch = last_copy - T3_STAGES + 1; ch <= last_copy; ++ch)
+        if (ch >= 0) bar_wait(full + (int)(ch % T3_STAGES), (uint32_t)((ch / T3_STAGES) & 1));
     }
     if (warp == 1 && lane == 0 && last_mma >= 0)
-      bar_wait(cempty + (int)(last_mma % T3_CS), (uint32_t)((last_mma / T3_CS) & 1));
+      bar_wait(empty + (int)(last_mma % T3_STAGES), (uint32_t)((last_mma / T3_STAGES) & 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

@@ -254,8 +254,10 @@ struct OzItem {
 __device__ __forceinline__ OzItem oz_item(const OzArgs& g, int64_t item) {
   OzItem it;
   if (g.mode == 2) {
-    const int64_t pr = item / g.nseg;
-    it.seg = (int)(item % g.nseg);
+    // segment-major: the CTAs running at one time share a segment's rows, so the
+    // operand images of that segment are read from L2 by every tile pair
+    const int64_t pr = item % g.npairs;
+    it.seg = (int)(item / g.npairs);
     const int2 tp = g.pairs[pr];
     it.ia = pr;
     it.e = 0;
