@@ -17,8 +17,9 @@
 //   warps 2-7   converters: the A chunk in place -> A1 = TF32(A) (and A2 =
 //               the TF32 remainder), raw rows -> K-major core-matrix B1 (and
 //               B2), arrive on `conv`;
-//   warps 8-15  epilogue: tcgen05.ld of the accumulator rows, read-modify-write
-//               scatter into W, arrive on `acc_empty`.
+//   warps 8-15  epilogue: tcgen05.ld of the accumulator rows, scatter-add into
+//               W as vector reductions performed in L2 (no read-back), arrive
+//               on `acc_empty`.
 // Two stages ring the chunks.  Every wait is bounded (about one second); on
 // timeout the CTA records an error, stops issuing, drains and frees its TMEM.
 #include <cuda_bf16.h>
@@ -390,9 +391,6 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
       const int b = (int)(t & 1);
       const int64_t g = (r < NL) ? cell_node(m, e, r) : 0;
       float* wr = W + g * ldw + c0;
-      // this thread's output segments are pulled towards L2 while the MMAs run
-      if (r < NL)
-        for (int cb = colgrp * 16; cb < ncol; cb += 32) asm volatile("prefetch.L2 [%0];" ::"l"(wr + cb));
       if (!bar_wait(accf + b, (uint32_t)((t / 2) & 1))) {
         *abort_flag = 1;
         atomicExch(err, 1);
@@ -400,14 +398,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       for (int cb = colgrp * 16; cb < ncol; cb += 32) {
-        // the values to add to are loaded before the accumulator columns
-        float4 o[4];
         const bool full16 = (r < NL) && cb + 16 <= ncol;
-        if (full16) {
-          const float4* w4 = reinterpret_cast<const float4*>(wr + cb);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) o[q] = w4[q];
-        }
         uint32_t v[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -416,21 +407,20 @@ __global__ void __launch_bounds__(T3_THREADS, 1) k_cell_tc3(const float* __restr
             : "r"(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + cb))
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // the products are added in L2 (vector reductions, no read-back): a W value
+        // receives one addition per launch (cells of a colour share no node)
         if (r < NL) {
           if (full16) {
-            float4* w4 = reinterpret_cast<float4*>(wr + cb);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              o[q].x += __uint_as_float(v[4 * q]);
-              o[q].y += __uint_as_float(v[4 * q + 1]);
-              o[q].z += __uint_as_float(v[4 * q + 2]);
-              o[q].w += __uint_as_float(v[4 * q + 3]);
-              w4[q] = o[q];
-            }
+            for (int q = 0; q < 4; ++q)
+              asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(wr + cb + 4 * q),
+                           "f"(__uint_as_float(v[4 * q])), "f"(__uint_as_float(v[4 * q + 1])),
+                           "f"(__uint_as_float(v[4 * q + 2])), "f"(__uint_as_float(v[4 * q + 3]))
+                           : "memory");
           } else {
 #pragma unroll
             for (int q = 0; q < 16; ++q)
-              if (cb + q < ncol) wr[cb + q] += __uint_as_float(v[q]);
+              if (cb + q < ncol) atomicAdd(wr + cb + q, __uint_as_float(v[q]));
           }
         }
       }

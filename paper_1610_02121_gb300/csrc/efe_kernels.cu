@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(GRP_CT) k_coup_cols_chunk(int64_t n_tn, const 
                                                            const float* __restrict__ Xe, int64_t ldxe, int N,
                                                            float* __restrict__ W, int64_t ldw) {
   __shared__ __align__(16) float T[CPF][CPB];
-  __shared__ float Xs[CPF][GRP_CT];
+  __shared__ __align__(16) float Xs[CPF][GRP_CT];
   __shared__ int64_t nd[CPB];
   const int64_t b = blockIdx.x;
   const int tid = threadIdx.x;
@@ -674,16 +674,25 @@ __global__ void __launch_bounds__(GRP_CT) k_coup_cols_chunk(int64_t n_tn, const 
       }
     }
   }
-  if (c < N) {
-    // all of the block's W values are loaded before any is stored (independent
-    // loads in flight together; the compiler cannot reorder loads past stores to
-    // rows it cannot prove distinct)
-    float wv[CPB];
+  // The block's results leave through shared memory: one bulk reduce-add per W
+  // row segment, performed in L2, so no W value travels back to the SM (W rows
+  // are padded to a multiple of 8 values; columns at or past N add zeros).
+  __syncthreads();                 // every thread is done with Xs
+  float* res = &Xs[0][0];          // CPB x GRP_CT results (CPB <= CPF)
 #pragma unroll
-    for (int i = 0; i < CPB; ++i) wv[i] = i < nb ? W[nd[i] * ldw + c] : 0.f;
-#pragma unroll
-    for (int i = 0; i < CPB; ++i)
-      if (i < nb) W[nd[i] * ldw + c] = fmaf(sgn, acc[i], wv[i]);
+  for (int i = 0; i < CPB; ++i) res[i * GRP_CT + tid] = sgn * acc[i];
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid < nb) {
+    const int c0 = blockIdx.y * GRP_CT;
+    const uint32_t bytes = (uint32_t)((min(GRP_CT, N - c0) + 3) / 4 * 16);
+    const uint32_t src = (uint32_t)__cvta_generic_to_shared(res + tid * GRP_CT);
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
+                     W + nd[tid] * ldw + c0),
+                 "r"(src), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
   }
 }
 
@@ -845,7 +854,8 @@ __global__ void k_df_rows(int64_t rows, int N, const double* __restrict__ X, int
 
 // Columns product out[node] = out[node] + sgn sum_q val[q] Xe[col[q]] (one warp
 // per pattern node, lanes over the columns); Xe2: the enrichment rows as (hi, lo)
-// pairs (k_df_rows), the existing out value folded into the sum
+// pairs (k_df_rows).  The FP64 sum is added to out by a reduction performed in L2
+// (each out value receives one addition per launch: the pattern nodes are distinct)
 __global__ void k_spmm_nodes_df(int64_t nrows, const int32_t* __restrict__ rnode, const int64_t* __restrict__ ptr,
                                 const int32_t* __restrict__ col, const float2* __restrict__ val, float sgn,
                                 const float2* __restrict__ Xe2, int N, double* __restrict__ out, int64_t ldo) {
@@ -855,15 +865,14 @@ __global__ void k_spmm_nodes_df(int64_t nrows, const int32_t* __restrict__ rnode
   const int64_t g = rnode[w];
   const int64_t q0 = ptr[w], q1 = ptr[w + 1];
   for (int c = lane; c < N; c += 32) {
-    double* o = out + g * ldo + c;
-    float S, C;
-    df_split(*o, S, C);
+    float S = 0.f, C = 0.f;
     for (int64_t q = q0; q < q1; ++q) {
       const float2 a = val[q];
       const float2 x = Xe2[(int64_t)col[q] * N + c];
       df_fma(sgn * a.x, sgn * a.y, x.x, x.y, S, C);
     }
-    *o = df_f2d(S) + df_f2d(C);
+    asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(out + g * ldo + c), "d"(df_f2d(S) + df_f2d(C))
+                 : "memory");
   }
 }
 

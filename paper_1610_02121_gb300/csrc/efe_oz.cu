@@ -676,8 +676,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
         }
         continue;
       }
-      // the row's output segment is pulled towards L2 while the MMAs run
-      if (live && (g.mode == 0 || g.mode == 2))
+      // GRAM (not from images): the row's output segment is pulled towards L2
+      // while the MMAs run
+      if (live && g.mode == 2)
         for (int cb = 8 * part; cb < ncol; cb += 8 * nparts) asm volatile("prefetch.L2 [%0];" ::"l"(orow + cb));
       bool stop = false;
       for (int grp = 0; grp < ngrp; ++grp) {
@@ -689,8 +690,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // CELL adds to what is there, GRAM and ROWS from their second group on
-        const bool add = (g.mode == 0) || grp > 0;
+        // CELL adds to what is there (in L2: FP64 reductions, no read-back; a W value
+        // receives one addition per launch since cells of a colour share no node),
+        // GRAM and ROWS from their second group on
+        const bool red = g.mode == 0;
+        const bool add = !red && grp > 0;
         // with twelve epilogue warps the results go out through a per-warp shared
         // tile (rows written 8 values at a time, 4 rows per instruction); with four,
         // each thread writes its own row and loads the values it adds to one
@@ -755,6 +759,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz(OzArgs g) {
               }
             }
             __syncwarp();
+          } else if (live && red) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if (cb + q < ncol) asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(orow + cb + q), "d"(val[q]) : "memory");
           } else if (live) {
 #pragma unroll
             for (int q = 0; q < 8; ++q)
