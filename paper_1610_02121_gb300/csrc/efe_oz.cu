@@ -137,27 +137,6 @@ __device__ __forceinline__ int exp_of(double x) {
   return ex == 0 ? -2000 : ex - 1022;
 }
 
-// seven BF16 digit slices of x with row/column exponent E, written to slice
-// buffers base + i * stride at byte offset off
-__device__ __forceinline__ void slice_store(double x, int E, unsigned char* base, uint32_t stride, uint32_t off) {
-  const long long bits = __double_as_longlong(x);
-  const int ex = (int)((bits >> 52) & 0x7FF);
-  const uint16_t sgn = (uint16_t)((bits >> 48) & 0x8000);
-  unsigned long long q = 0;
-  const int rs = 1026 + E - ex;
-  if (ex != 0 && rs >= 0 && rs < 64) q = ((unsigned long long)(bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> rs;
-#pragma unroll
-  for (int i = 0; i < OZ_S; ++i) {
-    const uint32_t d = (uint32_t)(q >> (42 - 7 * i)) & 127u;
-    uint16_t v = 0;
-    if (d) {
-      const int p = 31 - __clz(d);
-      v = (uint16_t)(sgn | (uint16_t)((p + 127 - 7 * i) << 7) | (uint16_t)((d << (7 - p)) & 0x7Fu));
-    }
-    *reinterpret_cast<uint16_t*>(base + i * stride + off) = v;
-  }
-}
-
 // digits of eight values with scale exponent E, packed slice by slice (two BF16
 // per word): pk[i] holds digit i of x[0..7] in K order
 __device__ __forceinline__ void oz_pack8(const double (&x)[8], int E, uint32_t (&pk)[OZ_S][4]) {
