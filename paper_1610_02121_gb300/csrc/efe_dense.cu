@@ -7,12 +7,12 @@
 //   * the inverse of a lower triangle by 2 x 2 block recursion (two half-size
 //     inverses and two GEMMs);
 //   * a two-sided block Jacobi eigensolver for symmetric matrices: the matrix
-//     is cut into blocks of 32 rows/columns, a round-robin tournament pairs the
-//     blocks, every pair's 64 x 64 subproblem is diagonalised in shared memory
-//     by one CTA (cyclic Jacobi), and the pair's rotation is applied to its 64
+//     is cut into blocks of B rows/columns, a round-robin tournament pairs the
+//     blocks, every pair's 2B x 2B subproblem is diagonalised in shared memory
+//     by one CTA (cyclic Jacobi), and the pair's rotation is applied to its 2B
 //     rows and columns of the whole matrix and to the eigenvector matrix by
-//     many CTAs (row-times-64 x 64 products).  Templated on float (the fast
-//     first stage) and double (the refinement).
+//     many CTAs (row-times-2B x 2B products).  Float with B = 32 (the fast
+//     first stage) and double with B = 16 (the refinement).
 // No atomics: every result has a fixed order of operations.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -30,9 +30,8 @@ extern std::atomic<int64_t> g_launches;
 namespace {
 
 constexpr int CB = 64;        // Cholesky panel width
-constexpr int BJ_B = 32;      // block Jacobi: block size
-constexpr int BJ_S = 2 * BJ_B;  // subproblem size
-constexpr int BJ_LD = BJ_S + 1;
+// block Jacobi: block size BJ_B (a template parameter: 32 for the FP32 stage,
+// 16 for the FP64 refinement), subproblems of BJ_S = 2 BJ_B, shared rows of BJ_S + 1
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -149,6 +148,7 @@ __device__ __forceinline__ void bj_pair(int k, int r, int nb, int& p, int& q) {
   q = max(a, b);
 }
 
+template <int BJ_B>
 __device__ __forceinline__ int bj_index(int i, int p, int q) { return i < BJ_B ? p * BJ_B + i : q * BJ_B + (i - BJ_B); }
 
 template <typename T>
@@ -160,13 +160,14 @@ __global__ void k_bj_pad(const double* __restrict__ C, int n, int ldc, T* __rest
   V[t] = i == j ? T(1) : T(0);
 }
 
-// One CTA per block pair of round r: diagonalise the 64 x 64 subproblem
+// One CTA per block pair of round r: diagonalise the BJ_S x BJ_S subproblem
 // [[A_pp, A_pq], [A_qp, A_qq]] in shared memory by cyclic Jacobi; write the
-// rotation J (64 x 64, row-major), the subproblem's eigenvalues, and whether
+// rotation J (BJ_S x BJ_S, row-major), the subproblem's eigenvalues, and whether
 // any rotation was applied.
-template <typename T>
+template <typename T, int BJ_B>
 __global__ void __launch_bounds__(256) k_bj_solve(const T* __restrict__ A, int np, int nb, int r, T* __restrict__ Jb,
                                                   T* __restrict__ lam, int* __restrict__ rotated, int max_sweeps) {
+  constexpr int BJ_S = 2 * BJ_B, BJ_LD = BJ_S + 1;
   extern __shared__ double smraw[];
   T* S = reinterpret_cast<T*>(smraw);
   T* J = S + BJ_S * BJ_LD;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(256) k_bj_solve(const T* __restrict__ A, int n
   bj_pair(k, r, nb, p, q);
   for (int t = tid; t < BJ_S * BJ_S; t += blockDim.x) {
     const int i = t / BJ_S, j = t % BJ_S;
-    S[i * BJ_LD + j] = A[(int64_t)bj_index(i, p, q) * np + bj_index(j, p, q)];
+    S[i * BJ_LD + j] = A[(int64_t)bj_index<BJ_B>(i, p, q) * np + bj_index<BJ_B>(j, p, q)];
     J[i * BJ_LD + j] = i == j ? T(1) : T(0);
   }
   if (tid == 0) any = 0;
@@ -251,9 +252,10 @@ __global__ void __launch_bounds__(256) k_bj_solve(const T* __restrict__ A, int n
 }
 
 // M[:, idx(p,q)] <- M[:, idx(p,q)] J_k for every pair k (rows in chunks of 32).
-template <typename T>
+template <typename T, int BJ_B>
 __global__ void __launch_bounds__(256) k_bj_cols(T* __restrict__ M, int np, int nb, int r, const T* __restrict__ Jb,
                                                  const int* __restrict__ rotated) {
+  constexpr int BJ_S = 2 * BJ_B;
   const int k = blockIdx.y;
   if (!rotated[k]) return;
   __shared__ T Js[BJ_S][BJ_S + 1];
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(256) k_bj_cols(T* __restrict__ M, int np, int 
   const int r0 = blockIdx.x * 32;
   for (int t = threadIdx.x; t < 32 * BJ_S; t += blockDim.x) {
     const int rr = t / BJ_S, c = t % BJ_S;
-    Xs[rr][c] = (r0 + rr < np) ? M[(int64_t)(r0 + rr) * np + bj_index(c, p, q)] : T(0);
+    Xs[rr][c] = (r0 + rr < np) ? M[(int64_t)(r0 + rr) * np + bj_index<BJ_B>(c, p, q)] : T(0);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < 32 * BJ_S; t += blockDim.x) {
@@ -274,19 +276,20 @@ __global__ void __launch_bounds__(256) k_bj_cols(T* __restrict__ M, int np, int 
     T acc = T(0);
 #pragma unroll 8
     for (int l = 0; l < BJ_S; ++l) acc = fma(Xs[rr][l], Js[l][c], acc);
-    M[(int64_t)(r0 + rr) * np + bj_index(c, p, q)] = acc;
+    M[(int64_t)(r0 + rr) * np + bj_index<BJ_B>(c, p, q)] = acc;
   }
 }
 
 // A[idx(p,q), :] <- J_k^T A[idx(p,q), :] for every pair k (columns in chunks
-// of 32 = one block); the pair's own 64 x 64 block becomes diag(lambda_k).
-template <typename T>
+// of one block); the pair's own BJ_S x BJ_S block becomes diag(lambda_k).
+template <typename T, int BJ_B>
 __global__ void __launch_bounds__(256) k_bj_rows(T* __restrict__ A, int np, int nb, int r, const T* __restrict__ Jb,
                                                  const T* __restrict__ lam, const int* __restrict__ rotated) {
+  constexpr int BJ_S = 2 * BJ_B;
   const int k = blockIdx.y;
   if (!rotated[k]) return;
   __shared__ T Js[BJ_S][BJ_S + 1];
-  __shared__ T Xs[BJ_S][33];
+  __shared__ T Xs[BJ_S][BJ_B + 1];
   int p, q;
   bj_pair(k, r, nb, p, q);
   const int cblk = blockIdx.x, c0 = cblk * BJ_B;
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(256) k_bj_rows(T* __restrict__ A, int np, int 
     const int off = cblk == p ? 0 : BJ_B;
     for (int t = threadIdx.x; t < BJ_S * BJ_B; t += blockDim.x) {
       const int i = t / BJ_B, c = t % BJ_B;
-      A[(int64_t)bj_index(i, p, q) * np + c0 + c] = (i == off + c) ? lam[(int64_t)k * BJ_S + i] : T(0);
+      A[(int64_t)bj_index<BJ_B>(i, p, q) * np + c0 + c] = (i == off + c) ? lam[(int64_t)k * BJ_S + i] : T(0);
     }
     return;
   }
@@ -303,7 +306,7 @@ __global__ void __launch_bounds__(256) k_bj_rows(T* __restrict__ A, int np, int 
   for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) Js[t / BJ_S][t % BJ_S] = Jk[t];
   for (int t = threadIdx.x; t < BJ_S * BJ_B; t += blockDim.x) {
     const int i = t / BJ_B, c = t % BJ_B;
-    Xs[i][c] = A[(int64_t)bj_index(i, p, q) * np + c0 + c];
+    Xs[i][c] = A[(int64_t)bj_index<BJ_B>(i, p, q) * np + c0 + c];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < BJ_S * BJ_B; t += blockDim.x) {
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(256) k_bj_rows(T* __restrict__ A, int np, int 
     T acc = T(0);
 #pragma unroll 8
     for (int l = 0; l < BJ_S; ++l) acc = fma(Js[l][i], Xs[l][c], acc);
-    A[(int64_t)bj_index(i, p, q) * np + c0 + c] = acc;
+    A[(int64_t)bj_index<BJ_B>(i, p, q) * np + c0 + c] = acc;
   }
 }
 
@@ -410,22 +413,30 @@ void launch_trinv_blocked(const double* L, int n, int lda, double* Li, int ldi, 
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
-int64_t block_jacobi_scratch_bytes(int n, int elem) {
-  const int nb0 = (n + BJ_B - 1) / BJ_B;
+static int64_t bj_scratch_bytes(int n, int elem, int B) {
+  const int S = 2 * B;
+  const int nb0 = (n + B - 1) / B;
   const int nb = std::max(2, nb0 + (nb0 & 1));
-  const int64_t np = (int64_t)nb * BJ_B;
+  const int64_t np = (int64_t)nb * B;
   const int64_t pairs = nb / 2;
-  return elem * (2 * np * np + pairs * BJ_S * BJ_S + pairs * BJ_S) + (int64_t)sizeof(int) * pairs +
+  return elem * (2 * np * np + pairs * S * S + pairs * S) + (int64_t)sizeof(int) * pairs +
          (int64_t)sizeof(double) * 2 * BJ_NORM_BLOCKS + 1024;
+}
+
+// scratch for either stage (block 32 in FP32, block 16 in FP64)
+int64_t block_jacobi_scratch_bytes(int n, int elem) {
+  return std::max(bj_scratch_bytes(n, elem, 32), bj_scratch_bytes(n, elem, 16));
 }
 
 // Symmetric C (n x n, FP64, ldc) = V diag(w) V^T by block Jacobi in precision T.
 // Sweeps until the off-diagonal square sum is <= tol2 times the total or
 // max_sweeps; returns 0 on convergence, 1 if the sweeps ran out, -1 on a CUDA
 // error.  The only host synchronisation is the norm check after each sweep.
-template <typename T>
-int block_jacobi(const double* C, int n, int ldc, T* V, int ldv, T* w, int max_sweeps, double tol2, void* scratch,
-                 cudaStream_t st, double* ratio_out) {
+namespace {
+template <typename T, int BJ_B>
+int block_jacobi_b(const double* C, int n, int ldc, T* V, int ldv, T* w, int max_sweeps, double tol2, void* scratch,
+                   cudaStream_t st, double* ratio_out) {
+  constexpr int BJ_S = 2 * BJ_B, BJ_LD = BJ_S + 1;
   const int nb0 = (n + BJ_B - 1) / BJ_B;
   const int nb = std::max(2, nb0 + (nb0 & 1));
   const int np = nb * BJ_B;
@@ -439,7 +450,7 @@ int block_jacobi(const double* C, int n, int ldc, T* V, int ldv, T* w, int max_s
   k_bj_pad<T><<<nblk((int64_t)np * np, 256), 256, 0, st>>>(C, n, ldc, A, Vp, np);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   const size_t smem = sizeof(T) * 2 * BJ_S * BJ_LD;
-  if (cudaFuncSetAttribute(k_bj_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_bj_solve<T, BJ_B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return -1;
   std::vector<double> hp(2 * BJ_NORM_BLOCKS);
   int rc = 1;
@@ -461,10 +472,10 @@ int block_jacobi(const double* C, int n, int ldc, T* V, int ldv, T* w, int max_s
     }
     if (sweep == max_sweeps) break;
     for (int r = 0; r < nb - 1; ++r) {
-      k_bj_solve<T><<<pairs, 256, smem, st>>>(A, np, nb, r, Jb, lam, rot, 30);
-      k_bj_cols<T><<<dim3(nblk(np, 32), pairs), 256, 0, st>>>(A, np, nb, r, Jb, rot);
-      k_bj_rows<T><<<dim3(nb, pairs), 256, 0, st>>>(A, np, nb, r, Jb, lam, rot);
-      k_bj_cols<T><<<dim3(nblk(np, 32), pairs), 256, 0, st>>>(Vp, np, nb, r, Jb, rot);
+      k_bj_solve<T, BJ_B><<<pairs, 256, smem, st>>>(A, np, nb, r, Jb, lam, rot, 30);
+      k_bj_cols<T, BJ_B><<<dim3(nblk(np, 32), pairs), 256, 0, st>>>(A, np, nb, r, Jb, rot);
+      k_bj_rows<T, BJ_B><<<dim3(nb, pairs), 256, 0, st>>>(A, np, nb, r, Jb, lam, rot);
+      k_bj_cols<T, BJ_B><<<dim3(nblk(np, 32), pairs), 256, 0, st>>>(Vp, np, nb, r, Jb, rot);
       g_launches.fetch_add(4, std::memory_order_relaxed);
     }
   }
@@ -472,6 +483,19 @@ int block_jacobi(const double* C, int n, int ldc, T* V, int ldv, T* w, int max_s
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (cudaGetLastError() != cudaSuccess) return -1;
   return rc;
+}
+}  // namespace
+
+// FP32 stage in 32-wide blocks; the FP64 refinement, whose subproblem solves run at
+// the FP64 rate of one SM each, in 16-wide blocks (an eighth of the solve work per
+// pair, twice the pairs per round; the update products are the same flops)
+template <typename T>
+int block_jacobi(const double* C, int n, int ldc, T* V, int ldv, T* w, int max_sweeps, double tol2, void* scratch,
+                 cudaStream_t st, double* ratio_out) {
+  if constexpr (sizeof(T) == 8)
+    return block_jacobi_b<T, 16>(C, n, ldc, V, ldv, w, max_sweeps, tol2, scratch, st, ratio_out);
+  else
+    return block_jacobi_b<T, 32>(C, n, ldc, V, ldv, w, max_sweeps, tol2, scratch, st, ratio_out);
 }
 
 template int block_jacobi<float>(const double*, int, int, float*, int, float*, int, double, void*, cudaStream_t,
