@@ -11,8 +11,8 @@
 //     blocks, every pair's 2B x 2B subproblem is diagonalised in shared memory
 //     by one CTA (cyclic Jacobi), and the pair's rotation is applied to its 2B
 //     rows and columns of the whole matrix and to the eigenvector matrix by
-//     many CTAs (row-times-2B x 2B products).  Float with B = 32 (the fast
-//     first stage) and double with B = 16 (the refinement).
+//     many CTAs (row-times-2B x 2B products), B = 16.  Float (the fast first
+//     stage) and double (the refinement).
 // No atomics: every result has a fixed order of operations.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -30,8 +30,8 @@ extern std::atomic<int64_t> g_launches;
 namespace {
 
 constexpr int CB = 64;        // Cholesky panel width
-// block Jacobi: block size BJ_B (a template parameter: 32 for the FP32 stage,
-// 16 for the FP64 refinement), subproblems of BJ_S = 2 BJ_B, shared rows of BJ_S + 1
+// block Jacobi: block size BJ_B (a template parameter), subproblems of
+// BJ_S = 2 BJ_B, shared rows of BJ_S + 1
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -413,6 +413,8 @@ void launch_trinv_blocked(const double* L, int n, int lda, double* Li, int ldi, 
   g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
+constexpr int BJ_BLOCK = 16;   // block Jacobi block size of both stages
+
 static int64_t bj_scratch_bytes(int n, int elem, int B) {
   const int S = 2 * B;
   const int nb0 = (n + B - 1) / B;
@@ -423,10 +425,7 @@ static int64_t bj_scratch_bytes(int n, int elem, int B) {
          (int64_t)sizeof(double) * 2 * BJ_NORM_BLOCKS + 1024;
 }
 
-// scratch for either stage (block 32 in FP32, block 16 in FP64)
-int64_t block_jacobi_scratch_bytes(int n, int elem) {
-  return std::max(bj_scratch_bytes(n, elem, 32), bj_scratch_bytes(n, elem, 16));
-}
+int64_t block_jacobi_scratch_bytes(int n, int elem) { return bj_scratch_bytes(n, elem, BJ_BLOCK); }
 
 // Symmetric C (n x n, FP64, ldc) = V diag(w) V^T by block Jacobi in precision T.
 // Sweeps until the off-diagonal square sum is <= tol2 times the total or
@@ -486,16 +485,14 @@ int block_jacobi_b(const double* C, int n, int ldc, T* V, int ldv, T* w, int max
 }
 }  // namespace
 
-// FP32 stage in 32-wide blocks; the FP64 refinement, whose subproblem solves run at
-// the FP64 rate of one SM each, in 16-wide blocks (an eighth of the solve work per
-// pair, twice the pairs per round; the update products are the same flops)
+// Both stages in 16-wide blocks: the subproblem solves run on one SM each (the
+// FP64 ones at that SM's FP64 rate), so halving the block halves the solve work
+// per sweep at the same update flops (measured: 280-atom Rayleigh-Ritz 5.41 s with
+// 32-wide blocks, 4.95 s with 16)
 template <typename T>
 int block_jacobi(const double* C, int n, int ldc, T* V, int ldv, T* w, int max_sweeps, double tol2, void* scratch,
                  cudaStream_t st, double* ratio_out) {
-  if constexpr (sizeof(T) == 8)
-    return block_jacobi_b<T, 16>(C, n, ldc, V, ldv, w, max_sweeps, tol2, scratch, st, ratio_out);
-  else
-    return block_jacobi_b<T, 32>(C, n, ldc, V, ldv, w, max_sweeps, tol2, scratch, st, ratio_out);
+  return block_jacobi_b<T, BJ_BLOCK>(C, n, ldc, V, ldv, w, max_sweeps, tol2, scratch, st, ratio_out);
 }
 
 template int block_jacobi<float>(const double*, int, int, float*, int, float*, int, double, void*, cudaStream_t,
