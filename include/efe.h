@@ -206,8 +206,13 @@ int efe_rr_shifted_passes(efe_handle* h, int64_t* count);
  * operand slicing (Ozaki scheme: seven 7-bit digits per operand, exact FP32
  * accumulation of the leading digit products; error within a few units of
  * 2^-48 of sum |a||b|).  Applies to N > 8 cell products, to the tall and Gram
- * products of Rayleigh-Ritz and to its dense N x N products for N > 512; other
- * cases keep DFMA.  Host setting, no device work. */
+ * products of Rayleigh-Ritz and to its dense N x N products for N > 512.  With
+ * engine 1 and N > 8 the enrichment coupling of the FP64 applies also leaves the
+ * FP64 pipe: double-float arithmetic on the FP32 pipe (coefficients and vector
+ * values as pairs of floats; error within a few units of 2^-48 of sum |a||x|;
+ * vector values must stay below 2^126 in magnitude, parts below FP32's normal
+ * range are dropped).  Other cases keep DFMA; efe_apply_M_noalloc always does.
+ * Host setting, no device work. */
 int efe_set_fp64_engine(efe_handle* h, int32_t engine);
 
 /* Test and tuning controls (no counterpart in the paper).  Host settings, no
